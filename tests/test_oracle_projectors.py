@@ -1,0 +1,110 @@
+"""Pins for the oracle's non-local (projector) term (no GPU).
+
+The oracle's projector part is pinned by brute force (dense assembly of the
+operator from unit vectors), by its spectrum computed through a different
+route (the small nproj x nproj problem), and by the rank-one eigen relation
+that the discrete normalisation implies.
+"""
+import numpy as np
+
+import oracle
+from workloads import rng, white_noise_states
+from tests._oracle_helpers import dense_h, wdot
+
+
+def _nonlocal_dense(m, centres, rcut, lmax, beta, hm):
+    V = np.zeros(m.P)
+    H0 = oracle.Hamiltonian(m, V)
+    H1 = oracle.Hamiltonian(m, V)
+    H1.set_projectors(centres, rcut, lmax, beta, hm)
+    return dense_h(H1, m.P) - dense_h(H0, m.P), H1
+
+
+def test_single_projector_eigenvector():
+    """One s-projector: H_nl p = h_00 <p|p> p = h_00 p (discrete normalisation)."""
+    m = oracle.Mesh(oracle.CUBE, 14, h=0.3)
+    H0 = oracle.Hamiltonian(m, np.zeros(m.P))
+    H1 = oracle.Hamiltonian(m, np.zeros(m.P))
+    H1.set_projectors([[0.13, -0.21, 0.07]], [1.4], [0], [0.35], [np.array([[0.6]])])
+    pts, vals = H1.atom(0)
+    p = np.zeros(m.P)
+    p[pts] = vals[0]
+    assert abs(m.h ** 3 * np.sum(p * p) - 1.0) < 1e-13
+    hnl = (H1.apply(p.reshape(-1, 1) + 0j) - H0.apply(p.reshape(-1, 1) + 0j)).ravel()
+    assert np.abs(hnl - 0.6 * p).max() < 1e-12 * np.abs(p).max()
+
+
+def test_sphere_membership():
+    """Projector sphere = mesh points within r_c of the centre (inclusive)."""
+    m = oracle.Mesh(oracle.SPHERE, radius=3.0, h=0.25)
+    H = oracle.Hamiltonian(m, np.zeros(m.P))
+    c = np.array([0.31, -0.42, 0.17])
+    H.set_projectors([c], [1.3], [1], [0.325], [np.eye(4)])
+    pts, _ = H.atom(0)
+    d = np.linalg.norm(m.xyz - c, axis=1)
+    assert set(pts.tolist()) == set(np.nonzero(d <= 1.3)[0].tolist())
+
+
+def test_angular_parts_are_solid_harmonics():
+    """p_i / p_s follows x, y, z, xy, yz, zx, x^2-y^2, 3z^2-r^2 up to a constant."""
+    m = oracle.Mesh(oracle.CUBE, 16, h=0.25)
+    H = oracle.Hamiltonian(m, np.zeros(m.P))
+    c = np.array([0.05, -0.11, 0.09])
+    H.set_projectors([c], [1.5], [2], [0.375], [np.eye(9)])
+    pts, vals = H.atom(0)
+    r = m.xyz[pts] - c
+    x, y, z = r[:, 0], r[:, 1], r[:, 2]
+    shapes = [np.ones_like(x), x, y, z, x * y, y * z, z * x, x * x - y * y,
+              3 * z * z - (x * x + y * y + z * z)]
+    for i, sh in enumerate(shapes):
+        ok = np.abs(sh) > 0.2 * np.abs(sh).max()
+        ratio = vals[i][ok] / (vals[0][ok] * sh[ok])
+        assert np.ptp(ratio) < 1e-10 * np.abs(ratio).mean(), i
+
+
+def test_dense_nonlocal_rank_and_spectrum():
+    """Brute-force assembly: Hermitian, rank = total projectors, and spectrum
+    equal to that of the small matrix h_a (h^3 P_a^T P_a) per atom pair block."""
+    g = rng(98)
+    m = oracle.Mesh(oracle.SPHERE, radius=2.2, h=0.4)
+    c = np.array([[0.3, 0.1, -0.2], [-0.5, 0.4, 0.6]])
+    A = g.uniform(-1, 1, (4, 4))
+    hm = [np.diag(g.uniform(-1, 1, 9)), A + A.T]
+    D, H1 = _nonlocal_dense(m, c, [1.6, 1.4], [2, 1], [0.4, 0.35], hm)
+    assert np.abs(D - D.conj().T).max() < 1e-12 * np.abs(D).max()
+    w = np.linalg.eigvalsh(D)
+    tol = 1e-9 * np.abs(w).max()
+    assert np.sum(np.abs(w) > tol) == 13
+    # small-problem route: nonzero spectrum of B h B^T h^3 = spectrum of
+    # h (h^3 B^T B), with B the P x 13 matrix of all projector columns.
+    cols, blocks = [], []
+    for a in range(2):
+        pts, vals = H1.atom(a)
+        for row in vals:
+            col = np.zeros(m.P)
+            col[pts] = row
+            cols.append(col)
+        blocks.append(hm[a])
+    B = np.stack(cols, axis=1)
+    Hb = np.zeros((13, 13))
+    Hb[:9, :9] = blocks[0]
+    Hb[9:, 9:] = blocks[1]
+    small = np.linalg.eigvals(Hb @ (m.h ** 3 * B.T @ B))
+    big = np.sort(w[np.abs(w) > tol])
+    assert np.allclose(np.sort(small.real), big, rtol=1e-9, atol=1e-12)
+
+
+def test_projectors_act_linearly_on_state_blocks():
+    """Applying to a block equals applying state by state (no cross-talk)."""
+    g = rng(97)
+    m = oracle.Mesh(oracle.CUBE, 10, h=0.4)
+    H = oracle.Hamiltonian(m, g.standard_normal(m.P))
+    H.set_projectors([[0.1, 0.2, -0.1]], [1.5], [1], [0.37], [np.diag([0.5, -0.3, 0.2, 0.9])])
+    psi = white_noise_states(g, m.P, 3)
+    blk = H.apply(psi)
+    for s in range(3):
+        one = H.apply(psi[:, s:s + 1].copy())
+        assert np.array_equal(one.ravel(), blk[:, s])
+    lin = H.apply(psi @ np.array([[1.0], [2.0 - 1j], [0.5j]]))
+    assert np.abs(lin.ravel() - blk @ np.array([1.0, 2.0 - 1j, 0.5j])).max() < 1e-11 * np.abs(blk).max()
+    _ = wdot  # keep the helper import used across the suite
