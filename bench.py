@@ -1,0 +1,341 @@
+"""Benchmark: H|psi> throughput inside Taylor-4 ETRS propagation on one GB300.
+
+Workload (the single large system): spherical mesh of radius 18 bohr at
+spacing 0.2 bohr (3,053,617 points, row-indexed), 64 complex64 states of
+white noise, V_loc = 32 Gaussian wells (depth U[1,4] Ha, width U[0.8,1.5]
+bohr), 32 atoms x 4 projectors (s + p) on 2.5-bohr spheres, h_ij diagonal in
+U[-1,1].  One step = one ETRS time step (dt = 0.01 au): two Taylor-4
+exponentials = 8 Hamiltonian applications with the projector terms, each a
+Horner stage u' = psi + (-i tau/k) H u.
+
+metric: grid-point.states per second of H applications (x1e9), i.e.
+P * S * 8 * steps / time.  Inputs (1.56 GB per state block) exceed L2
+(129 MB), so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (one H application to one state on the full
+mesh per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "sphere R=18 bohr h=0.2 (3,053,617 pts), 64 states, 32 wells, 32 atoms x 4 projectors, ETRS Taylor-4 dt=0.01"
+METRIC = "H|psi> grid-point.states/s (ETRS Taylor-4 step, sphere R=18 h=0.2, 64 states)"
+UNIT = "Gpoint.states/s"
+N_APPLY_PER_STEP = 8
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def build_inputs(g_seed=2):
+    """Seeded inputs of the workload: potential, projector parameters."""
+    from workloads import gaussian_wells, projector_atoms, rng
+    g = rng(g_seed)
+    c, d, w = gaussian_wells(g, 32, 18.0 - 2.5)
+    cen, rc, lm, beta, hm = projector_atoms(g, 32, 2.5, 1, ball_radius=18.0 - 2.5)
+    return g, (c, d, w), (cen, rc, lm, beta, hm)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(kernel_src_hash):
+    """DRAM bytes per launch of the stencil kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_sha256") != kernel_src_hash:
+        return None
+    return d.get("bytes_per_launch_full_size")
+
+
+def kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("rsg_kernels.cu", "rsg_vec.cuh", "rsg_internal.h"):
+        with open(os.path.join(ROOT, "paper_1501_05654_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[3:7]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(V_orc, proj, psi_seed, seconds=20.0):
+    """The FP64 oracle, as it stands, on the host cores: H applications to one
+    state on the full mesh, repeated for about `seconds`."""
+    import oracle
+    from workloads import rng, white_noise_states
+    om = oracle.Mesh(oracle.SPHERE, radius=18.0, h=0.2)
+    O = oracle.Hamiltonian(om, V_orc(om.xyz))
+    O.set_projectors(*proj)
+    psi = white_noise_states(rng(2, psi_seed), om.P, 1)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.apply(psi)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt > seconds or n >= 5000:
+            break
+    return {"value": om.P * n / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{n} FP64 H applications to 1 state on the full 3,053,617-point sphere "
+                      f"(wells + projectors), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from workloads import potential_wells
+    g, wells, proj = build_inputs()
+    om = oracle.Mesh(oracle.SPHERE, radius=18.0, h=0.2)
+    O = oracle.Hamiltonian(om, potential_wells(om.xyz, *wells))
+    O.set_projectors(*proj)
+    from workloads import rng, white_noise_states
+    psi = white_noise_states(rng(2, 5), om.P, 1)
+    for _ in range(args.warmup):
+        O.apply(psi)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.apply(psi)
+    dt = time.perf_counter() - t0
+    val = om.P * args.steps / dt / 1e9
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD + " (oracle sample: 1 state, 1 H application per step)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": "1 FP64 H application to 1 state on the full mesh per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel", type=int, default=None, help="stencil variant (0 z-march, 1 naive)")
+    ap.add_argument("--rx", type=int, default=None)
+    ap.add_argument("--ty", type=int, default=None)
+    ap.add_argument("--zseg", type=int, default=None)
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1501_05654_gb300 as rsg
+    from workloads import potential_wells, white_noise_states
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    rsg.build()
+
+    g, wells, proj = build_inputs()
+    mesh = rsg.Mesh(rsg.SPHERE, radius=18.0, spacing=0.2)
+    dtype = torch.complex64 if args.dtype == "c64" else torch.complex128
+    H = rsg.Hamiltonian(mesh, dtype)
+    H.set_potential(potential_wells(mesh.xyz, *wells))
+    H.set_projectors(*proj)
+    for k in ("kernel", "rx", "ty", "zseg"):
+        if getattr(args, k) is not None:
+            H.set_option(k, getattr(args, k))
+    S = 64
+    P = mesh.P
+    npdt = np.complex64 if dtype == torch.complex64 else np.complex128
+    psi_h = torch.from_numpy(white_noise_states(g, P, S, dtype=npdt)).pin_memory()
+    psi = psi_h.to("cuda")
+    dt = 0.01
+    stream = torch.cuda.current_stream()
+
+    def step(x):
+        H.propagate(x, 1, dt, scheme=rsg.ETRS, want_drift=False)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(psi)
+    torch.cuda.synchronize()
+    H.kernel_stats()                      # reset counters
+    H.profile(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_id = vis.split(",")[local] if vis else str(local)
+    with ClockSampler(smi_id) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(psi)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    H.profile(False)
+    ms = e0.elapsed_time(e1)
+    k_ms, k_n, k_bytes, n_launch = H.kernel_stats()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ws * P * S * N_APPLY_PER_STEP * args.steps / (ms_max * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        out_h = torch.empty_like(psi_h).pin_memory()
+        for _ in range(2):
+            psi.copy_(psi_h, non_blocking=True)
+            step(psi)
+            out_h.copy_(psi, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            psi.copy_(psi_h, non_blocking=True)
+            step(psi)
+            out_h.copy_(psi, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        te = torch.tensor([f0.elapsed_time(f1)], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        nbytes = psi_h.numel() * psi_h.element_size()
+        e2e = {"value": ws * P * S * N_APPLY_PER_STEP * args.steps / (float(te.item()) * 1e-3) / 1e9,
+               "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = peaks()
+    achieved = (k_bytes / k_n) / (k_ms / k_n * 1e-3) / 1e9 if k_n else None
+    per_launch_bytes = k_bytes / k_n if k_n else None
+    traffic = traffic_record(kernel_hash())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == torch.complex64 else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points": P, "states": S, "state_dtype": args.dtype,
+                   "h_applications_per_step": N_APPLY_PER_STEP,
+                   "l2": "state blocks (1.56 GB) exceed L2; no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "kernel": "k_apply_zmarch (Horner stage: stencil + V + projector epilogue)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "peak_kind": f"{peak_kind} copy bandwidth",
+                     "algorithmic_bytes_per_launch": per_launch_bytes,
+                     "avg_launch_ms": k_ms / k_n if k_n else None,
+                     "traffic": traffic},
+        "gpu_launches": n_launch,
+        "e2e": e2e,
+    }
+    line["clocks"] = clk.summary()
+    if not args.no_cpu_baseline and ws == 1:
+        try:
+            line["cpu_baseline"] = cpu_baseline(lambda xyz: potential_wells(xyz, *wells), proj, 5)
+        except Exception as ex:     # reported, never fatal
+            line["cpu_baseline"] = {"error": str(ex)}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * rsg.h -- C ABI of the real-space-grid Hamiltonian library (GB300, sm_103a).
+ *
+ * The library applies H = -1/2 lap + V_loc + eps(t) dir.r
+ *                       + sum_a sum_ij |p_ai> h_a,ij <p_aj|
+ * to a block of complex states sampled on a uniform real-space mesh, and
+ * propagates the block in real time with a Taylor-4 exponential.  Sources
+ * (arXiv:1501.05654):
+ *   - Sec. 1: fields on uniform grids, integrals as grid sums, high-order
+ *     finite-difference Laplacian; finite boxes of arbitrary shape.
+ *   - Sec. "Performance": the building blocks include "the application of a
+ *     Hamiltonian"; the basic object is a group of several states; a field is
+ *     a linear array plus tables describing the grid; the point order in
+ *     memory is the library's business.
+ *   - Sec. "Magnetic response": pseudopotentials act as a non-local operator
+ *     (here separable projectors |p_ai> h_ij <p_aj|).
+ *   - Sec. "Quantum optimal control", Eq. (qoctgradient): gradient of a
+ *     final-time objective with respect to the control, through a costate
+ *     propagated backwards with the same propagators.
+ *
+ * Conventions shared by every call:
+ *   - All calls return an rsg_status; rsg_last_error() gives a thread-local
+ *     message for the last failure.  No exception crosses the ABI.
+ *   - Handles are owned by the library; destroy them with the matching call.
+ *     The caller owns every state, potential, field and gradient buffer.
+ *   - State blocks are DEVICE pointers to a row-major (P, ld) array of
+ *     complex values, states fastest: element (p, s) at offset p*ld + s.
+ *     complex64 = interleaved float pairs, complex128 = double pairs.  For
+ *     complex64, ld must be even and the pointer 16-byte aligned; columns
+ *     S..ld-1 are padding (computed on but never reduced over).
+ *   - Points are in the LIBRARY's order (z slowest, then y, x fastest, over
+ *     the mesh only).  rsg_mesh_coords gives each point's lattice integers.
+ *     Position of lattice (i,j,k) = origin + spacing * (i,j,k).
+ *   - Inner products are <f|g> = h^3 sum_p conj(f_p) g_p.
+ *   - Calls taking `stream` (a cudaStream_t, NULL = legacy default stream)
+ *     only enqueue work, unless they return host values (noted per call),
+ *     which synchronises that stream.
+ */
+#ifndef RSG_H
+#define RSG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsg_mesh_s *rsg_mesh;
+typedef struct rsg_ham_s *rsg_ham;
+typedef struct rsg_batch_s *rsg_batch;
+
+typedef enum {
+    RSG_OK = 0,
+    RSG_ERR_ARG = -1,          /* invalid argument (NULL, size, alignment) */
+    RSG_ERR_OOM = -2,          /* device or host allocation failed */
+    RSG_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    RSG_ERR_UNSUPPORTED = -4,  /* valid request the library does not support */
+    RSG_ERR_TIMEOUT = -5,      /* a bounded device wait gave up */
+    RSG_ERR_NONFINITE = -6,    /* a norm or Gram check found NaN/Inf */
+    RSG_ERR_STATE = -7         /* handle not ready (e.g. missing potential) */
+} rsg_status;
+
+typedef enum { RSG_C64 = 0, RSG_C128 = 1 } rsg_dtype;
+typedef enum { RSG_SHAPE_CUBE = 0, RSG_SHAPE_SPHERE = 1, RSG_SHAPE_BOX = 2 } rsg_shape;
+typedef enum { RSG_EXPMID = 0, RSG_ETRS = 1 } rsg_scheme;
+
+/* ---------------------------------------------------------------- mesh ---
+ * Uniform mesh (Sec. 1; Sec. "Performance": field = linear array + grid
+ * tables).  CUBE: n[0]^3 points, lattice i = 0..n-1, origin -(n-1)h/2 per
+ * axis (centred box).  BOX: n[0] x n[1] x n[2], same centring.  SPHERE:
+ * lattice points with i^2+j^2+k^2 <= (radius/spacing)^2 (inclusive,
+ * rounded to 1e-6), origin 0.  Values outside the mesh are zero (the
+ * Dirichlet boundary of the finite-system runs).  n is ignored for SPHERE
+ * and radius for CUBE/BOX.  Every extent must be <= 1024 lattice points.
+ * Errors: RSG_ERR_ARG for spacing <= 0, extents outside 1..1024, NULL out. */
+rsg_status rsg_mesh_create(rsg_shape shape, const int32_t n[3], double radius,
+                           double spacing, rsg_mesh *out);
+/* Number of mesh points P. */
+rsg_status rsg_mesh_num_points(rsg_mesh m, int64_t *P);
+/* Host array ijk (P x 3 int32, caller-owned): lattice integers of every point
+ * in library order. */
+rsg_status rsg_mesh_coords(rsg_mesh m, int32_t *ijk);
+/* Position of lattice (0,0,0) and the spacing. */
+rsg_status rsg_mesh_geometry(rsg_mesh m, double origin[3], double *spacing);
+rsg_status rsg_mesh_destroy(rsg_mesh m);
+
+/* ---------------------------------------------------------- Hamiltonian ---
+ * A Hamiltonian bound to a mesh and a compute type.  complex64 computes the
+ * stencil, potential and Taylor terms in FP32 and keeps FP64 for projector
+ * coefficient reductions, norms and Gram matrices; complex128 is FP64
+ * throughout.  The mesh must outlive the Hamiltonian. */
+rsg_status rsg_ham_create(rsg_mesh m, rsg_dtype dtype, rsg_ham *out);
+rsg_status rsg_ham_destroy(rsg_ham H);
+
+/* Local potential V (P doubles, library point order).  v_on_device = 0:
+ * host array; 1: device array.  Copied; the caller keeps ownership. */
+rsg_status rsg_potential_set(rsg_ham H, const double *v, int v_on_device);
+
+/* Separable projectors (Sec. "Magnetic response": non-local pseudopotential).
+ * Atom a at centres[3a..3a+2] (bohr) carries (lmax[a]+1)^2 projectors,
+ * lmax in {0,1,2}: p_ai(r) = Y_i(r-R_a) exp(-|r-R_a|^2/(2 beta_a^2)) on the
+ * mesh points with |r-R_a| <= rcut[a], Y = {1; x,y,z; xy,yz,zx,x^2-y^2,
+ * 3z^2-r^2}, each scaled so that h^3 sum_p p_ai(p)^2 = 1.  hmats holds the
+ * per-atom nproj x nproj coupling matrices h_a (row-major, concatenated,
+ * symmetric).  natoms = 0 removes all projectors.  Host arrays, copied. */
+rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres,
+                              const double *rcut, const int32_t *lmax,
+                              const double *beta, const double *hmats);
+
+/* Static dipole field eps * (dir . r) used by rsg_hamiltonian_apply and
+ * rsg_taylor_apply (default 0).  dir may be NULL when eps = 0. */
+rsg_status rsg_field_set(rsg_ham H, double eps, const double dir[3]);
+
+/* hpsi = H psi for S states (Sec. "Performance": application of a
+ * Hamiltonian to a group of states).  psi and hpsi: device (P, ld) blocks of
+ * the Hamiltonian's dtype; they must not overlap.  Asynchronous on stream.
+ * Errors: RSG_ERR_ARG (NULL, S < 1, ld < S, odd ld for complex64, misaligned
+ * pointer, overlap), RSG_ERR_STATE (no potential set). */
+rsg_status rsg_hamiltonian_apply(rsg_ham H, const void *psi, void *hpsi, int64_t S,
+                                 int64_t ld, void *stream);
+
+/* out = T(tau) psi = sum_{n=0..4} (-i tau H)^n / n! psi (one Taylor-4
+ * exponential of the real-time propagator, Sec. 2 real-time TDDFT).  out may
+ * equal psi (in place).  Asynchronous. */
+rsg_status rsg_taylor_apply(rsg_ham H, const void *psi, void *out, int64_t S,
+                            int64_t ld, double tau, void *stream);
+
+/* Propagates psi in place over nsteps intervals of length dt.  The field is
+ * piecewise constant: eps[k] (host array, may be NULL = 0) on interval k,
+ * along dir (NULL = x).  EXPMID: nsub exponentials T(dt/nsub) with
+ * H(t_k + dt/2) per interval; ETRS: nsub pairs T_{H(t+dt')}(dt'/2)
+ * T_{H(t)}(dt'/2), dt' = dt/nsub.  Every gs_every steps (0 = never) the
+ * squared-norm drift |<psi_s|psi_s> - 1| is recorded (FP64) and the block is
+ * re-orthonormalised by Cholesky-QR in FP64 (equal to Gram-Schmidt in index
+ * order); the final block is checked too.  norm_drift_out (host, S doubles,
+ * may be NULL) receives the largest drift seen per state, and synchronises.
+ * Errors: as rsg_hamiltonian_apply; RSG_ERR_NONFINITE if a Gram matrix is not
+ * finite or not positive definite. */
+rsg_status rsg_propagate_steps(rsg_ham H, void *psi, int64_t S, int64_t ld,
+                               int64_t nsteps, double dt, rsg_scheme scheme,
+                               int nsub, const double *eps, const double dir[3],
+                               int gs_every, double *norm_drift_out, void *stream);
+
+/* Re-orthonormalises S states in place (Cholesky-QR, FP64 Gram and factor);
+ * norms2_out (host, S, may be NULL) receives <psi_s|psi_s> before, and
+ * synchronises. */
+rsg_status rsg_orthonormalize(rsg_ham H, void *psi, int64_t S, int64_t ld,
+                              double *norms2_out, void *stream);
+
+/* FP64 <psi_s|psi_s> for S states into norms2_out (host, S doubles);
+ * synchronises. */
+rsg_status rsg_state_norms(rsg_ham H, const void *psi, int64_t S, int64_t ld,
+                           double *norms2_out, void *stream);
+
+/* Quantum-optimal-control gradient (Sec. "Quantum optimal control",
+ * Eq. (qoctgradient) and the costate equations), discrete adjoint of the
+ * propagator above for ONE state: J = |<target|psi(T)>|^2 with psi(0) =
+ * psi0 (device, P complex values), the control eps[k] (host, nsteps) along
+ * dir entering as eps_k dir.r on interval k.  grad_out[k] = dJ/d eps_k
+ * (host, nsteps doubles), *J_out = J.  The forward states are checkpointed
+ * every checkpoint_every intervals and recomputed per segment; the Taylor
+ * powers of one interval are kept so that the gradient costs three forward
+ * propagations in Hamiltonian applications.  Synchronises. */
+rsg_status rsg_control_gradient(rsg_ham H, const void *psi0, const void *target,
+                                int64_t nsteps, double dt, rsg_scheme scheme,
+                                int nsub, const double *eps, const double dir[3],
+                                int checkpoint_every, double *J_out,
+                                double *grad_out, void *stream);
+
+/* -------------------------------------------------------------- batches ---
+ * Many independent systems (Sec. "Performance": groups of states as the
+ * unit of work) propagated together: one launch per Taylor stage covers the
+ * tiles of every system.  hams: nsys Hamiltonians (all complex64), S[i]
+ * states per system.  The handles must outlive the batch. */
+rsg_status rsg_batch_create(const rsg_ham *hams, const int64_t *S, int nsys,
+                            rsg_batch *out);
+/* psis[i]: device (P_i, ld_i) block with ld_i = S[i] rounded up to even.
+ * Same step rule as rsg_propagate_steps with no field. */
+rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps,
+                               double dt, rsg_scheme scheme, int gs_every,
+                               void *stream);
+rsg_status rsg_batch_destroy(rsg_batch b);
+
+/* Tuning knobs (kernel tile shapes); unknown keys give RSG_ERR_ARG.
+ * Keys: "kernel" (0 = z-marching tiled stencil, 1 = one thread per point
+ * and vector), "rx" (points per thread along x: 1, 2 or 4), "ty" (rows per
+ * tile), "zseg" (planes per z segment). */
+rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value);
+
+/* Measurement hooks.  rsg_ham_profile(H, 1) starts recording a CUDA event
+ * pair around every stencil-kernel launch of H (on the stream it is
+ * launched on); 0 stops.  rsg_ham_kernel_stats waits for the recorded
+ * events, returns the summed stencil-kernel time in ms, the number of those
+ * launches, their algorithmic bytes (the unique state, potential, grid-table
+ * and projector bytes each launch must move; see the design notes) and the
+ * number of kernel launches of any kind H issued since the last call, then
+ * resets all four.  Any output pointer may be NULL. */
+rsg_status rsg_ham_profile(rsg_ham H, int enable);
+rsg_status rsg_ham_kernel_stats(rsg_ham H, double *kernel_ms, int64_t *kernel_launches,
+                                double *kernel_bytes, int64_t *all_launches);
+
+/* Thread-local description of the last error (empty if none). */
+const char *rsg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSG_H */

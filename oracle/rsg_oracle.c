@@ -430,10 +430,15 @@ void orc_apply_sampled(void *hv, double eps, const double *dir, const cplx *psi,
         int64_t off = 0;
         for (int a = 0; a < H->natoms; a++) {
             const orc_atom *A = &H->atoms[a];
-            for (int64_t q = 0; q < A->npts; q++)
-                if (A->pt[q] == p)
-                    for (int i = 0; i < A->nproj; i++)
-                        v += A->p[i * A->npts + q] * d[off + i * S + s];
+            /* the sphere's point list is ascending: binary search for p */
+            int64_t lo = 0, hi = A->npts;
+            while (lo < hi) {
+                int64_t mid = lo + (hi - lo) / 2;
+                if (A->pt[mid] < p) lo = mid + 1; else hi = mid;
+            }
+            if (lo < A->npts && A->pt[lo] == p)
+                for (int i = 0; i < A->nproj; i++)
+                    v += A->p[i * A->npts + lo] * d[off + i * S + s];
             off += (int64_t)A->nproj * S;
         }
         out[t] = v;

@@ -1,0 +1,1012 @@
+// Host side of the C ABI declared in include/rsg.h: handles, mesh and
+// projector tables, argument checks, workspace and the launch sequences of
+// the Hamiltonian application, the Taylor-4 propagator, the Cholesky-QR
+// re-orthonormalisation and the discrete adjoint of the control gradient.
+//
+// Method passages (arXiv:1501.05654): Sec. 1 (uniform grids, finite
+// differences), Sec. "Performance" (Hamiltonian application on groups of
+// states; linear arrays plus grid tables; re-orthonormalisation only rarely
+// needed in real time), Sec. "Magnetic response" (non-local pseudopotential),
+// Sec. "Quantum optimal control" (Eq. (qoctgradient), costate propagation).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "rsg_internal.h"
+
+using namespace rsg;
+
+namespace {
+
+thread_local std::string g_err;
+
+rsg_status fail(rsg_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? RSG_ERR_OOM : RSG_ERR_CUDA,         \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define CKS(expr)                    \
+    do {                             \
+        rsg_status s_ = (expr);      \
+        if (s_ != RSG_OK) return s_; \
+    } while (0)
+
+// 8th-order central second difference weights, |k| = 0..4 (times 1/h^2).
+const double kFD[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+
+// Device buffer that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), n(o.n) {
+        o.p = nullptr;
+        o.n = 0;
+    }
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= n && p) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+        if (e == cudaSuccess) n = bytes ? bytes : 16;
+        return e;
+    }
+    template <typename T>
+    cudaError_t upload(const std::vector<T> &v) {
+        cudaError_t e = ensure(v.size() * sizeof(T));
+        if (e != cudaSuccess || v.empty()) return e;
+        return cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    }
+    template <typename T>
+    T *as() const {
+        return (T *)p;
+    }
+};
+
+}  // namespace
+
+struct rsg_mesh_s {
+    int shape = 0;
+    double h = 0.0;
+    double origin[3] = {0, 0, 0};
+    int32_t lo[3] = {0, 0, 0};     // lattice coordinate of bbox index 0
+    int nx = 0, ny = 0, nz = 0;
+    int64_t P = 0;
+    std::vector<int32_t> ijk;       // P x 3 lattice integers
+    std::vector<Row> rows;          // ny * nz
+    DevBuf d_rows;
+    // tile lists keyed by (TX, TY, zseg): device tiles and their count
+    std::map<std::tuple<int, int, int>, std::pair<DevBuf, int>> tiles;
+};
+
+struct rsg_ham_s {
+    rsg_mesh m = nullptr;
+    rsg_dtype dtype = RSG_C64;
+    bool has_V = false;
+    DevBuf V;
+    double eps = 0.0, dir[3] = {1, 0, 0};
+    TileCfg cfg;
+    // projectors
+    ProjDev pj;
+    DevBuf q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm, nl_ptr, nl_ent;
+    DevBuf D, partial;
+    // workspace
+    DevBuf w0, w1, red, G, W, drift, status, dots, M, ov, grad, Xd, Xdir;
+    double xdir_cached[3] = {NAN, NAN, NAN};
+    std::vector<DevBuf> pool;   // control-gradient vectors
+    // measurement
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;   // pairs (start, stop) of stencil launches
+    size_t ev_used = 0;
+    int64_t n_launch = 0, n_stencil = 0;
+    double stencil_bytes = 0.0;
+    ~rsg_ham_s() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
+struct rsg_batch_s {
+    std::vector<rsg_ham> hams;
+    std::vector<int64_t> S;
+};
+
+namespace {
+
+size_t cbytes(rsg_dtype t) { return t == RSG_C64 ? 8 : 16; }
+
+// ---------------------------------------------------------------- mesh ---
+void build_rows(rsg_mesh m, int64_t r2max) {
+    m->rows.assign((size_t)m->ny * m->nz, Row{0, 1, 0, 0});
+    m->ijk.clear();
+    int64_t P = 0;
+    for (int z = 0; z < m->nz; z++)
+        for (int y = 0; y < m->ny; y++) {
+            int xmin = 0, xmax = m->nx - 1;
+            if (m->shape == RSG_SHAPE_SPHERE) {
+                const int64_t j = y + m->lo[1], k = z + m->lo[2];
+                const int64_t rem = r2max - j * j - k * k;
+                if (rem < 0) continue;
+                int64_t xm = (int64_t)std::floor(std::sqrt((double)rem));
+                while (xm * xm > rem) xm--;
+                while ((xm + 1) * (xm + 1) <= rem) xm++;
+                xmin = (int)(-xm - m->lo[0]);
+                xmax = (int)(xm - m->lo[0]);
+            }
+            Row &r = m->rows[(size_t)z * m->ny + y];
+            r.start = (int32_t)P;
+            r.xmin = xmin;
+            r.xmax = xmax;
+            for (int x = xmin; x <= xmax; x++) {
+                m->ijk.push_back(x + m->lo[0]);
+                m->ijk.push_back(y + m->lo[1]);
+                m->ijk.push_back(z + m->lo[2]);
+            }
+            P += xmax - xmin + 1;
+        }
+    m->P = P;
+}
+
+// Tiles of TX x TY columns; each keeps only the planes where one of its rows
+// meets its x range, split into segments of zseg planes.
+rsg_status get_tiles(rsg_mesh m, int TX, int TY, int zseg, const Tile **out, int *count) {
+    auto key = std::make_tuple(TX, TY, zseg);
+    auto it = m->tiles.find(key);
+    if (it == m->tiles.end()) {
+        std::vector<Tile> tl;
+        const int ntx = (m->nx + TX - 1) / TX, nty = (m->ny + TY - 1) / TY;
+        for (int ty = 0; ty < nty; ty++)
+            for (int tx = 0; tx < ntx; tx++) {
+                const int xa = tx * TX, xb = std::min(m->nx - 1, xa + TX - 1);
+                int zlo = m->nz, zhi = 0;
+                for (int z = 0; z < m->nz; z++)
+                    for (int y = ty * TY; y < std::min(m->ny, ty * TY + TY); y++) {
+                        const Row &r = m->rows[(size_t)z * m->ny + y];
+                        if (r.xmin <= r.xmax && r.xmax >= xa && r.xmin <= xb) {
+                            zlo = std::min(zlo, z);
+                            zhi = std::max(zhi, z + 1);
+                        }
+                    }
+                for (int z0 = zlo; z0 < zhi; z0 += zseg)
+                    tl.push_back(Tile{tx, ty, z0, std::min(zhi, z0 + zseg)});
+            }
+        auto &slot = m->tiles[key];
+        cudaError_t e = slot.first.upload(tl);
+        if (e != cudaSuccess) {
+            m->tiles.erase(key);
+            return fail(RSG_ERR_CUDA, "tile upload: %s", cudaGetErrorString(e));
+        }
+        slot.second = (int)tl.size();
+        it = m->tiles.find(key);
+    }
+    *out = it->second.first.as<Tile>();
+    *count = it->second.second;
+    return RSG_OK;
+}
+
+int pow2_at_least(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// Block shape of the z-marching kernel for SV vectors per row (must match
+// launch_apply): cv x nxr x ty threads, TX = nxr * rx.
+void block_shape(const TileCfg &c, int SV, int *TX, int *TY) {
+    const int cv = std::min(8, pow2_at_least(SV));
+    int ty = c.ty;
+    while (cv * ty > 256) ty >>= 1;
+    const int nxr = 256 / (cv * ty);
+    *TX = nxr * c.rx;
+    *TY = ty;
+}
+
+// ------------------------------------------------------------ checks ----
+rsg_status check_block(rsg_ham H, const void *p, int64_t S, int64_t ld, const char *what) {
+    if (!p) return fail(RSG_ERR_ARG, "%s is NULL", what);
+    if (S < 1 || ld < S) return fail(RSG_ERR_ARG, "need 1 <= S <= ld (S=%lld ld=%lld)",
+                                     (long long)S, (long long)ld);
+    if (H->dtype == RSG_C64 && (ld % 2) != 0)
+        return fail(RSG_ERR_ARG, "complex64 blocks need an even ld (got %lld)", (long long)ld);
+    if (((uintptr_t)p) % 16 != 0) return fail(RSG_ERR_ARG, "%s must be 16-byte aligned", what);
+    if ((int64_t)ld * (int64_t)cbytes(H->dtype) / 16 > (1 << 20))
+        return fail(RSG_ERR_ARG, "ld too large");
+    return RSG_OK;
+}
+
+bool overlaps(const void *a, const void *b, size_t n) {
+    const char *x = (const char *)a, *y = (const char *)b;
+    return x < y + n && y < x + n;
+}
+
+// ------------------------------------------------------ application ----
+struct Epi {
+    const void *base = nullptr;
+    void *acc = nullptr;
+    double ar = 1, ai = 0, br = 1, bi = 0, gr = 0, gi = 0;
+};
+
+rsg_status ensure_rows(rsg_mesh m) {
+    if (m->d_rows.p) return RSG_OK;
+    CK(m->d_rows.upload(m->rows));
+    return RSG_OK;
+}
+
+template <typename R>
+rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, const double *dir,
+                   const Epi &ep, cudaStream_t st) {
+    rsg_mesh m = H->m;
+    CKS(ensure_rows(m));
+    const double h = m->h, h3 = h * h * h;
+    const int ldc = SV * (int)(16 / cbytes(H->dtype));
+    if (H->pj.natoms > 0) {
+        const size_t need = (size_t)H->pj.nchunks * H->pj.npmax * ldc * 2 * sizeof(double);
+        CK(H->partial.ensure(need));
+        CK(H->D.ensure((size_t)H->pj.natoms * H->pj.npmax * ldc * cbytes(H->dtype)));
+        CK(launch_proj_dot<R>(in, SV, H->pj, H->partial.as<double>(), st));
+        CK(launch_proj_reduce<R>(H->partial.as<double>(), SV, H->pj, h3, H->D.p, st));
+    }
+    ApplyArgs<R> a;
+    a.in = in;
+    a.out = out;
+    a.base = ep.base;
+    a.acc = ep.acc;
+    a.rows = m->d_rows.as<Row>();
+    a.nx = m->nx;
+    a.ny = m->ny;
+    a.nz = m->nz;
+    a.SV = SV;
+    a.V = H->V.as<R>();
+    // eps * dir.r with r = origin + h (lo + idx)
+    double f0 = 0, fd[3] = {0, 0, 0};
+    if (eps != 0.0 && dir) {
+        for (int d = 0; d < 3; d++) {
+            f0 += eps * dir[d] * (m->origin[d] + h * m->lo[d]);
+            fd[d] = eps * dir[d] * h;
+        }
+    }
+    a.f0 = (R)f0;
+    a.fx = (R)fd[0];
+    a.fy = (R)fd[1];
+    a.fz = (R)fd[2];
+    for (int k = 0; k < 5; k++) a.w[k] = (R)(-0.5 * kFD[k] / (h * h));
+    a.ar = (R)ep.ar;
+    a.ai = (R)ep.ai;
+    a.br = (R)ep.br;
+    a.bi = (R)ep.bi;
+    a.gr = (R)ep.gr;
+    a.gi = (R)ep.gi;
+    a.nl_ptr = H->pj.natoms > 0 ? H->pj.nl_ptr : nullptr;
+    a.nl_ent = H->pj.nl_ent;
+    a.q_atom = H->pj.q_atom;
+    a.q_p = (const R *)H->pj.q_p;
+    a.D = H->D.p;
+    a.npmax = H->pj.npmax;
+    a.P = m->P;
+    int ntiles = 0;
+    a.tiles = nullptr;
+    if (H->cfg.kernel == 0) {
+        int TX, TY;
+        block_shape(H->cfg, SV, &TX, &TY);
+        CKS(get_tiles(m, TX, TY, H->cfg.zseg, &a.tiles, &ntiles));
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (H->prof) {
+        if (H->ev_used + 2 > H->ev.size()) {
+            for (int i = 0; i < 64; i++) {
+                cudaEvent_t e;
+                CK(cudaEventCreate(&e));
+                H->ev.push_back(e);
+            }
+        }
+        e0 = H->ev[H->ev_used];
+        e1 = H->ev[H->ev_used + 1];
+        H->ev_used += 2;
+        CK(cudaEventRecord(e0, st));
+    }
+    CK(launch_apply<R>(a, H->cfg, ntiles, st));
+    if (H->prof) CK(cudaEventRecord(e1, st));
+    // algorithmic bytes: read u, write out, optional base / acc (read+write),
+    // the potential, and (with projectors) the per-point entry lists,
+    // entry values and the coefficient block
+    const double P = (double)m->P, row = 16.0 * SV;
+    double bytes = P * row * (2.0 + (ep.base ? 1.0 : 0.0) + (ep.acc ? 2.0 : 0.0)) + P * sizeof(R);
+    if (H->pj.natoms > 0)
+        bytes += 4.0 * (P + 1) + (double)H->pj.nq * (8.0 + H->pj.npmax * sizeof(R)) +
+                 (double)H->pj.natoms * H->pj.npmax * row;
+    H->n_stencil++;
+    H->stencil_bytes += bytes;
+    H->n_launch += H->pj.natoms > 0 ? 3 : 1;
+    return RSG_OK;
+}
+
+rsg_status apply(rsg_ham H, const void *in, void *out, int SV, double eps, const double *dir,
+                 const Epi &ep, cudaStream_t st) {
+    if (H->dtype == RSG_C64) return apply_t<float>(H, in, out, SV, eps, dir, ep, st);
+    return apply_t<double>(H, in, out, SV, eps, dir, ep, st);
+}
+
+int sv_of(rsg_ham H, int64_t ld) { return (int)(ld * (int64_t)cbytes(H->dtype) / 16); }
+
+// out = T(tau) psi by Horner's rule: u <- psi; u <- psi + (-i tau / k) H u
+// for k = 4..1.  out may equal psi.
+rsg_status taylor(rsg_ham H, const void *psi, void *out, int64_t ld, double tau, double eps,
+                  const double *dir, cudaStream_t st) {
+    const size_t bytes = (size_t)H->m->P * ld * cbytes(H->dtype);
+    CK(H->w0.ensure(bytes));
+    CK(H->w1.ensure(bytes));
+    const int SV = sv_of(H, ld);
+    const void *src = psi;
+    for (int k = 4; k >= 1; k--) {
+        void *dst = (k == 1) ? out : ((k & 1) ? H->w1.p : H->w0.p);
+        Epi ep;
+        ep.ar = 0.0;
+        ep.ai = -tau / k;
+        ep.base = psi;
+        ep.br = 1.0;
+        ep.bi = 0.0;
+        CKS(apply(H, src, dst, SV, eps, dir, ep, st));
+        src = dst;
+    }
+    return RSG_OK;
+}
+
+// ------------------------------------------------------------ linalg ----
+rsg_status norms_dev(rsg_ham H, const void *psi, int64_t S, int64_t ld, double *out_dev,
+                     cudaStream_t st) {
+    const int64_t P = H->m->P;
+    const double h3 = std::pow(H->m->h, 3);
+    const int nb = norm_blocks(P);
+    CK(H->red.ensure((size_t)nb * S * sizeof(double)));
+    if (H->dtype == RSG_C64)
+        CK(launch_norms<float>(psi, P, (int)ld, (int)S, h3, H->red.as<double>(), nb, out_dev, st));
+    else
+        CK(launch_norms<double>(psi, P, (int)ld, (int)S, h3, H->red.as<double>(), nb, out_dev, st));
+    H->n_launch += 2;
+    return RSG_OK;
+}
+
+// Cholesky-QR on the device; drift (device, S) updated with |G_ss - 1|.
+rsg_status orthonormalize_dev(rsg_ham H, void *psi, int64_t S, int64_t ld, double *drift_dev,
+                              cudaStream_t st) {
+    const int64_t P = H->m->P;
+    const double h3 = std::pow(H->m->h, 3);
+    const int nb = gram_blocks(P, (int)S);
+    CK(H->red.ensure((size_t)nb * S * S * 2 * sizeof(double)));
+    CK(H->G.ensure((size_t)S * S * 2 * sizeof(double)));
+    CK(H->W.ensure((size_t)S * S * 2 * sizeof(double)));
+    if (!H->status.p) {
+        CK(H->status.ensure(sizeof(int)));
+        CK(cudaMemsetAsync(H->status.p, 0, sizeof(int), st));
+    }
+    if (H->dtype == RSG_C64) {
+        CK(launch_gram<float>(psi, P, (int)ld, (int)S, h3, H->red.as<double>(), nb, H->G.as<double>(), st));
+        CK(launch_chol_inv(H->G.as<double>(), H->W.as<double>(), (int)S, drift_dev, H->status.as<int>(), st));
+        CK(launch_tri_apply<float>(psi, P, (int)ld, (int)S, H->W.as<double>(), st));
+    } else {
+        CK(launch_gram<double>(psi, P, (int)ld, (int)S, h3, H->red.as<double>(), nb, H->G.as<double>(), st));
+        CK(launch_chol_inv(H->G.as<double>(), H->W.as<double>(), (int)S, drift_dev, H->status.as<int>(), st));
+        CK(launch_tri_apply<double>(psi, P, (int)ld, (int)S, H->W.as<double>(), st));
+    }
+    H->n_launch += 4;
+    return RSG_OK;
+}
+
+rsg_status read_status(rsg_ham H, cudaStream_t st) {
+    if (!H->status.p) return RSG_OK;
+    int s = 0;
+    CK(cudaMemcpyAsync(&s, H->status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (s != 0) {
+        CK(cudaMemsetAsync(H->status.p, 0, sizeof(int), st));
+        CK(cudaStreamSynchronize(st));
+        return fail(RSG_ERR_NONFINITE, "Gram matrix not finite or not positive definite");
+    }
+    return RSG_OK;
+}
+
+// ------------------------------------------------------- projectors ----
+double solid_harmonic(int i, double x, double y, double z) {
+    switch (i) {
+    case 0: return 1.0;
+    case 1: return x;
+    case 2: return y;
+    case 3: return z;
+    case 4: return x * y;
+    case 5: return y * z;
+    case 6: return z * x;
+    case 7: return x * x - y * y;
+    default: return 3.0 * z * z - (x * x + y * y + z * z);
+    }
+}
+
+template <typename R>
+std::vector<R> cast_vec(const std::vector<double> &v) {
+    return std::vector<R>(v.begin(), v.end());
+}
+
+const int kChunk = 512;   // sphere entries per projector-dot block
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+const char *rsg_last_error(void) { return g_err.c_str(); }
+
+rsg_status rsg_mesh_create(rsg_shape shape, const int32_t n[3], double radius, double spacing,
+                           rsg_mesh *out) {
+    if (!out) return fail(RSG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!(spacing > 0.0) || !std::isfinite(spacing)) return fail(RSG_ERR_ARG, "spacing must be > 0");
+    std::unique_ptr<rsg_mesh_s> m(new rsg_mesh_s());
+    m->shape = shape;
+    m->h = spacing;
+    int64_t r2max = 0;
+    if (shape == RSG_SHAPE_CUBE || shape == RSG_SHAPE_BOX) {
+        if (!n) return fail(RSG_ERR_ARG, "n is NULL");
+        int N[3];
+        for (int d = 0; d < 3; d++) N[d] = shape == RSG_SHAPE_CUBE ? n[0] : n[d];
+        for (int d = 0; d < 3; d++)
+            if (N[d] < 1 || N[d] > 1024) return fail(RSG_ERR_ARG, "extent %d outside 1..1024", N[d]);
+        m->nx = N[0];
+        m->ny = N[1];
+        m->nz = N[2];
+        for (int d = 0; d < 3; d++) {
+            m->lo[d] = 0;
+            m->origin[d] = -0.5 * (N[d] - 1) * spacing;
+        }
+    } else if (shape == RSG_SHAPE_SPHERE) {
+        if (!(radius > 0.0) || !std::isfinite(radius)) return fail(RSG_ERR_ARG, "radius must be > 0");
+        const double q = radius / spacing;
+        r2max = (int64_t)std::floor(q * q + 1e-6);
+        int M = (int)std::floor(std::sqrt((double)r2max) + 1e-9);
+        if (2 * M + 1 > 1024) return fail(RSG_ERR_ARG, "sphere extent %d exceeds 1024", 2 * M + 1);
+        m->nx = m->ny = m->nz = 2 * M + 1;
+        for (int d = 0; d < 3; d++) {
+            m->lo[d] = -M;
+            m->origin[d] = 0.0;
+        }
+    } else {
+        return fail(RSG_ERR_ARG, "unknown shape %d", (int)shape);
+    }
+    build_rows(m.get(), r2max);
+    if (m->P >= (int64_t)INT32_MAX) return fail(RSG_ERR_UNSUPPORTED, "more than 2^31 points");
+    // the device copy of the row table is made on first use
+    *out = m.release();
+    return RSG_OK;
+}
+
+rsg_status rsg_mesh_num_points(rsg_mesh m, int64_t *P) {
+    if (!m || !P) return fail(RSG_ERR_ARG, "NULL argument");
+    *P = m->P;
+    return RSG_OK;
+}
+
+rsg_status rsg_mesh_coords(rsg_mesh m, int32_t *ijk) {
+    if (!m || !ijk) return fail(RSG_ERR_ARG, "NULL argument");
+    std::memcpy(ijk, m->ijk.data(), m->ijk.size() * sizeof(int32_t));
+    return RSG_OK;
+}
+
+rsg_status rsg_mesh_geometry(rsg_mesh m, double origin[3], double *spacing) {
+    if (!m || !origin || !spacing) return fail(RSG_ERR_ARG, "NULL argument");
+    for (int d = 0; d < 3; d++) origin[d] = m->origin[d];
+    *spacing = m->h;
+    return RSG_OK;
+}
+
+rsg_status rsg_mesh_destroy(rsg_mesh m) {
+    delete m;
+    return RSG_OK;
+}
+
+rsg_status rsg_ham_create(rsg_mesh m, rsg_dtype dtype, rsg_ham *out) {
+    if (!m || !out) return fail(RSG_ERR_ARG, "NULL argument");
+    if (dtype != RSG_C64 && dtype != RSG_C128) return fail(RSG_ERR_ARG, "unknown dtype");
+    rsg_ham H = new rsg_ham_s();
+    H->m = m;
+    H->dtype = dtype;
+    if (dtype == RSG_C128) H->cfg.rx = 2;
+    *out = H;
+    return RSG_OK;
+}
+
+rsg_status rsg_ham_destroy(rsg_ham H) {
+    delete H;
+    return RSG_OK;
+}
+
+rsg_status rsg_ham_profile(rsg_ham H, int enable) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    H->prof = enable != 0;
+    return RSG_OK;
+}
+
+rsg_status rsg_ham_kernel_stats(rsg_ham H, double *kernel_ms, int64_t *kernel_launches,
+                                double *kernel_bytes, int64_t *all_launches) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    double ms = 0.0;
+    for (size_t i = 0; i + 1 < H->ev_used; i += 2) {
+        CK(cudaEventSynchronize(H->ev[i + 1]));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, H->ev[i], H->ev[i + 1]));
+        ms += t;
+    }
+    if (kernel_ms) *kernel_ms = ms;
+    if (kernel_launches) *kernel_launches = H->n_stencil;
+    if (kernel_bytes) *kernel_bytes = H->stencil_bytes;
+    if (all_launches) *all_launches = H->n_launch;
+    H->ev_used = 0;
+    H->n_stencil = 0;
+    H->stencil_bytes = 0.0;
+    H->n_launch = 0;
+    return RSG_OK;
+}
+
+rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
+    if (!H || !key) return fail(RSG_ERR_ARG, "NULL argument");
+    std::string k(key);
+    if (k == "kernel" && (value == 0 || value == 1)) H->cfg.kernel = (int)value;
+    else if (k == "rx" && (value == 1 || value == 2 || value == 4)) H->cfg.rx = (int)value;
+    else if (k == "ty" && (value == 1 || value == 2 || value == 4 || value == 8 || value == 16 || value == 32))
+        H->cfg.ty = (int)value;
+    else if (k == "zseg" && value >= 1 && value <= 4096) H->cfg.zseg = (int)value;
+    else return fail(RSG_ERR_ARG, "unknown option or value: %s=%lld", key, (long long)value);
+    return RSG_OK;
+}
+
+rsg_status rsg_potential_set(rsg_ham H, const double *v, int v_on_device) {
+    if (!H || !v) return fail(RSG_ERR_ARG, "NULL argument");
+    const int64_t P = H->m->P;
+    std::vector<double> hv((size_t)P);
+    if (v_on_device)
+        CK(cudaMemcpy(hv.data(), v, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost));
+    else
+        std::memcpy(hv.data(), v, (size_t)P * sizeof(double));
+    for (int64_t p = 0; p < P; p++)
+        if (!std::isfinite(hv[p])) return fail(RSG_ERR_ARG, "potential not finite at %lld", (long long)p);
+    if (H->dtype == RSG_C64)
+        CK(H->V.upload(cast_vec<float>(hv)));
+    else
+        CK(H->V.upload(hv));
+    H->has_V = true;
+    return RSG_OK;
+}
+
+rsg_status rsg_field_set(rsg_ham H, double eps, const double dir[3]) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    if (eps != 0.0 && !dir) return fail(RSG_ERR_ARG, "dir is NULL");
+    H->eps = eps;
+    if (dir)
+        for (int d = 0; d < 3; d++) H->dir[d] = dir[d];
+    return RSG_OK;
+}
+
+rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres, const double *rcut,
+                              const int32_t *lmax, const double *beta, const double *hmats) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    if (natoms < 0) return fail(RSG_ERR_ARG, "natoms < 0");
+    H->pj = ProjDev();
+    if (natoms == 0) return RSG_OK;
+    if (!centres || !rcut || !lmax || !beta || !hmats) return fail(RSG_ERR_ARG, "NULL array");
+    rsg_mesh m = H->m;
+    const double h = m->h, h3 = h * h * h;
+    int npmax = 1;
+    for (int a = 0; a < natoms; a++) {
+        if (lmax[a] < 0 || lmax[a] > 2) return fail(RSG_ERR_UNSUPPORTED, "lmax must be 0, 1 or 2");
+        if (!(rcut[a] > 0) || !(beta[a] > 0)) return fail(RSG_ERR_ARG, "rcut and beta must be > 0");
+        npmax = std::max(npmax, (lmax[a] + 1) * (lmax[a] + 1));
+    }
+    std::vector<int32_t> q_pt, q_atom, ch_atom, ch_q0, ch_q1, atom_ch0(1, 0);
+    std::vector<double> q_p, hm((size_t)natoms * npmax * npmax, 0.0);
+    int64_t hoff = 0;
+    for (int a = 0; a < natoms; a++) {
+        const int np = (lmax[a] + 1) * (lmax[a] + 1);
+        const double *c = centres + 3 * a;
+        const double rc = rcut[a], b2 = 2.0 * beta[a] * beta[a];
+        const size_t q_begin = q_pt.size();
+        // bounding box of the sphere in bbox indices
+        int lo3[3], hi3[3];
+        for (int d = 0; d < 3; d++) {
+            const int ext = d == 0 ? m->nx : d == 1 ? m->ny : m->nz;
+            lo3[d] = std::max(0, (int)std::floor((c[d] - rc - m->origin[d]) / h) - m->lo[d] - 1);
+            hi3[d] = std::min(ext - 1, (int)std::ceil((c[d] + rc - m->origin[d]) / h) - m->lo[d] + 1);
+        }
+        for (int z = lo3[2]; z <= hi3[2]; z++)
+            for (int y = lo3[1]; y <= hi3[1]; y++) {
+                const Row &rw = m->rows[(size_t)z * m->ny + y];
+                for (int x = std::max(lo3[0], rw.xmin); x <= std::min(hi3[0], rw.xmax); x++) {
+                    const double rx = m->origin[0] + h * (x + m->lo[0]) - c[0];
+                    const double ry = m->origin[1] + h * (y + m->lo[1]) - c[1];
+                    const double rz = m->origin[2] + h * (z + m->lo[2]) - c[2];
+                    const double d2 = rx * rx + ry * ry + rz * rz;
+                    if (d2 > rc * rc) continue;
+                    q_pt.push_back(rw.start + (x - rw.xmin));
+                    q_atom.push_back(a);
+                    const double g = std::exp(-d2 / b2);
+                    for (int i = 0; i < npmax; i++)
+                        q_p.push_back(i < np ? solid_harmonic(i, rx, ry, rz) * g : 0.0);
+                }
+            }
+        const size_t q_end = q_pt.size();
+        for (int i = 0; i < np; i++) {
+            double ss = 0.0;
+            for (size_t q = q_begin; q < q_end; q++) ss += q_p[q * npmax + i] * q_p[q * npmax + i];
+            const double nrm = std::sqrt(h3 * ss);
+            if (nrm > 0)
+                for (size_t q = q_begin; q < q_end; q++) q_p[q * npmax + i] /= nrm;
+        }
+        for (size_t q0 = q_begin; q0 < q_end; q0 += kChunk) {
+            ch_atom.push_back(a);
+            ch_q0.push_back((int32_t)q0);
+            ch_q1.push_back((int32_t)std::min(q_end, q0 + kChunk));
+        }
+        atom_ch0.push_back((int32_t)ch_q0.size());
+        for (int i = 0; i < np; i++)
+            for (int j = 0; j < np; j++) hm[((size_t)a * npmax + i) * npmax + j] = hmats[hoff + i * np + j];
+        hoff += (int64_t)np * np;
+    }
+    // point-centric CSR of entries (for the fused scatter in the epilogue)
+    const int64_t P = m->P;
+    std::vector<int32_t> nl_ptr((size_t)P + 1, 0), nl_ent(q_pt.size());
+    for (int32_t p : q_pt) nl_ptr[(size_t)p + 1]++;
+    for (int64_t p = 0; p < P; p++) nl_ptr[(size_t)p + 1] += nl_ptr[(size_t)p];
+    {
+        std::vector<int32_t> fill(nl_ptr.begin(), nl_ptr.end() - 1);
+        for (size_t q = 0; q < q_pt.size(); q++) nl_ent[(size_t)fill[(size_t)q_pt[q]]++] = (int32_t)q;
+    }
+    CK(H->q_pt.upload(q_pt));
+    CK(H->q_atom.upload(q_atom));
+    if (H->dtype == RSG_C64)
+        CK(H->q_p.upload(cast_vec<float>(q_p)));
+    else
+        CK(H->q_p.upload(q_p));
+    CK(H->ch_atom.upload(ch_atom));
+    CK(H->ch_q0.upload(ch_q0));
+    CK(H->ch_q1.upload(ch_q1));
+    CK(H->atom_ch0.upload(atom_ch0));
+    CK(H->hm.upload(hm));
+    CK(H->nl_ptr.upload(nl_ptr));
+    CK(H->nl_ent.upload(nl_ent));
+    ProjDev &pj = H->pj;
+    pj.natoms = natoms;
+    pj.npmax = npmax;
+    pj.nq = (int64_t)q_pt.size();
+    pj.nchunks = (int)ch_q0.size();
+    pj.q_pt = H->q_pt.as<int32_t>();
+    pj.q_atom = H->q_atom.as<int32_t>();
+    pj.q_p = H->q_p.p;
+    pj.chunk_atom = H->ch_atom.as<int32_t>();
+    pj.chunk_q0 = H->ch_q0.as<int32_t>();
+    pj.chunk_q1 = H->ch_q1.as<int32_t>();
+    pj.atom_chunk0 = H->atom_ch0.as<int32_t>();
+    pj.hm = H->hm.as<double>();
+    pj.nl_ptr = H->nl_ptr.as<int32_t>();
+    pj.nl_ent = H->nl_ent.as<int32_t>();
+    return RSG_OK;
+}
+
+rsg_status rsg_hamiltonian_apply(rsg_ham H, const void *psi, void *hpsi, int64_t S, int64_t ld,
+                                 void *stream) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    CKS(check_block(H, psi, S, ld, "psi"));
+    CKS(check_block(H, hpsi, S, ld, "hpsi"));
+    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    const size_t bytes = (size_t)H->m->P * ld * cbytes(H->dtype);
+    if (overlaps(psi, hpsi, bytes)) return fail(RSG_ERR_ARG, "psi and hpsi overlap");
+    Epi ep;
+    return apply(H, psi, hpsi, sv_of(H, ld), H->eps, H->dir, ep, (cudaStream_t)stream);
+}
+
+rsg_status rsg_taylor_apply(rsg_ham H, const void *psi, void *out, int64_t S, int64_t ld, double tau,
+                            void *stream) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    CKS(check_block(H, psi, S, ld, "psi"));
+    CKS(check_block(H, out, S, ld, "out"));
+    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    const size_t bytes = (size_t)H->m->P * ld * cbytes(H->dtype);
+    if (out != psi && overlaps(psi, out, bytes)) return fail(RSG_ERR_ARG, "psi and out partially overlap");
+    if (!std::isfinite(tau)) return fail(RSG_ERR_ARG, "tau not finite");
+    return taylor(H, psi, out, ld, tau, H->eps, H->dir, (cudaStream_t)stream);
+}
+
+rsg_status rsg_state_norms(rsg_ham H, const void *psi, int64_t S, int64_t ld, double *norms2_out,
+                           void *stream) {
+    if (!H || !norms2_out) return fail(RSG_ERR_ARG, "NULL argument");
+    CKS(check_block(H, psi, S, ld, "psi"));
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(H->drift.ensure((size_t)S * sizeof(double)));
+    CKS(norms_dev(H, psi, S, ld, H->drift.as<double>(), st));
+    CK(cudaMemcpyAsync(norms2_out, H->drift.p, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return RSG_OK;
+}
+
+rsg_status rsg_orthonormalize(rsg_ham H, void *psi, int64_t S, int64_t ld, double *norms2_out,
+                              void *stream) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    CKS(check_block(H, psi, S, ld, "psi"));
+    if (S > 1024) return fail(RSG_ERR_UNSUPPORTED, "S > 1024");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (norms2_out) {
+        CK(H->drift.ensure((size_t)S * sizeof(double)));
+        CKS(norms_dev(H, psi, S, ld, H->drift.as<double>(), st));
+        CK(cudaMemcpyAsync(norms2_out, H->drift.p, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    CKS(orthonormalize_dev(H, psi, S, ld, nullptr, st));
+    return read_status(H, st);
+}
+
+rsg_status rsg_propagate_steps(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t nsteps, double dt,
+                               rsg_scheme scheme, int nsub, const double *eps, const double dir[3],
+                               int gs_every, double *norm_drift_out, void *stream) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    CKS(check_block(H, psi, S, ld, "psi"));
+    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (nsteps < 0 || nsub < 1 || gs_every < 0 || !std::isfinite(dt))
+        return fail(RSG_ERR_ARG, "bad nsteps/nsub/gs_every/dt");
+    if (scheme != RSG_EXPMID && scheme != RSG_ETRS) return fail(RSG_ERR_ARG, "unknown scheme");
+    if (S > 1024 && gs_every > 0) return fail(RSG_ERR_UNSUPPORTED, "S > 1024 with Gram-Schmidt");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double xdir[3] = {1.0, 0.0, 0.0};
+    const double *d = dir ? dir : xdir;
+    // drift buffer: S maxima, then S scratch norms
+    CK(H->drift.ensure((size_t)2 * S * sizeof(double)));
+    double *drift = H->drift.as<double>();
+    CK(cudaMemsetAsync(drift, 0, (size_t)S * sizeof(double), st));
+    const double tsub = dt / nsub;
+    for (int64_t k = 0; k < nsteps; k++) {
+        const double e = eps ? eps[k] : 0.0;
+        for (int u = 0; u < nsub; u++) {
+            if (scheme == RSG_EXPMID) {
+                CKS(taylor(H, psi, psi, ld, tsub, e, d, st));
+            } else {
+                // T_{H(t+dt')}(dt'/2) T_{H(t)}(dt'/2); both with the interval's eps_k
+                CKS(taylor(H, psi, psi, ld, 0.5 * tsub, e, d, st));
+                CKS(taylor(H, psi, psi, ld, 0.5 * tsub, e, d, st));
+            }
+        }
+        const bool gs_now = gs_every > 0 && (k + 1) % gs_every == 0;
+        if (gs_now) {
+            CKS(orthonormalize_dev(H, psi, S, ld, drift, st));
+        } else if (k == nsteps - 1 && norm_drift_out) {
+            // final check without re-orthonormalising: norms into scratch, then max
+            CKS(norms_dev(H, psi, S, ld, drift + S, st));
+            std::vector<double> a((size_t)S), b((size_t)S);
+            CK(cudaMemcpyAsync(a.data(), drift, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(b.data(), drift + S, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            for (int64_t s = 0; s < S; s++) {
+                const double e2 = std::fabs(b[(size_t)s] - 1.0);
+                norm_drift_out[s] = (e2 > a[(size_t)s] || std::isnan(e2)) ? e2 : a[(size_t)s];
+            }
+            return read_status(H, st);
+        }
+    }
+    if (norm_drift_out) {
+        CK(cudaMemcpyAsync(norm_drift_out, drift, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    if (gs_every > 0) return read_status(H, st);
+    return RSG_OK;
+}
+
+}  // extern "C"
+
+// ============================================================ adjoint ====
+namespace {
+
+// One exponential by explicit powers: pw[0] = x (already there), pw[j+1] =
+// A pw[j] with A = -i tau H (sgn = -1) or A^dagger = +i tau H (sgn = +1);
+// next = sum_j pw[j] / j! (j = 0..4).  pw[4] is scratch.
+rsg_status powers(rsg_ham H, void *const pw[5], void *next, int64_t ld, double tau, double sgn,
+                  double eps, const double *dir, cudaStream_t st) {
+    const size_t bytes = (size_t)H->m->P * ld * cbytes(H->dtype);
+    CK(cudaMemcpyAsync(next, pw[0], bytes, cudaMemcpyDeviceToDevice, st));
+    static const double invf[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
+    for (int j = 0; j < 4; j++) {
+        Epi ep;
+        ep.ar = 0.0;
+        ep.ai = sgn * tau;
+        ep.acc = next;
+        // acc += gamma * y with y = A^{j+1} x: gamma = 1/(j+1)! relative to the power
+        ep.gr = invf[j + 1];
+        ep.gi = 0.0;
+        CKS(apply(H, pw[j], pw[j + 1], sv_of(H, ld), eps, dir, ep, st));
+    }
+    return RSG_OK;
+}
+
+template <typename R>
+rsg_status control_gradient_t(rsg_ham H, const void *psi0, const void *target, int64_t nsteps,
+                              double dt, rsg_scheme scheme, int nsub, const double *eps,
+                              const double *dir, int K, double *J_out, double *grad_out,
+                              cudaStream_t st) {
+    rsg_mesh msh = H->m;
+    const int64_t P = msh->P;
+    const int64_t ld = H->dtype == RSG_C64 ? 2 : 1;   // one state, padded to 16 bytes
+    const size_t cb = cbytes(H->dtype), vb = (size_t)P * ld * cb;
+    const double h3 = std::pow(msh->h, 3);
+    // every interval is m exponentials T(tau) of the same H_k = H0 + eps_k X
+    const int m = scheme == RSG_EXPMID ? nsub : 2 * nsub;
+    const double tau = scheme == RSG_EXPMID ? dt / nsub : 0.5 * dt / nsub;
+    if (K <= 0 || K > nsteps) K = (int)nsteps;
+    const int64_t nck = (nsteps + K - 1) / K;
+    // pool layout: checkpoints, segment states, powers of one interval,
+    // costate powers, and scratch
+    int64_t at = 0;
+    const int64_t ck0 = at; at += nck;
+    const int64_t seg0 = at; at += K + 1;
+    const int64_t pw0 = at; at += 4 * m + 1;
+    const int64_t b0 = at; at += 5;
+    const int64_t sc0 = at; at += 5;
+    const int64_t nvec = at;
+    if ((int64_t)H->pool.size() < nvec) H->pool.resize((size_t)nvec);
+    for (int64_t i = 0; i < nvec; i++) CK(H->pool[(size_t)i].ensure(vb));
+    auto vec = [&](int64_t i) { return H->pool[(size_t)i].p; };
+    void *chi = vec(sc0), *chi2 = vec(sc0 + 1), *phi = vec(sc0 + 2);
+    void *fa = vec(sc0 + 3), *fb = vec(sc0 + 4);
+    // column 0 of padded (P, ld) blocks
+    CK(cudaMemsetAsync(vec(ck0), 0, vb, st));
+    CK(cudaMemsetAsync(phi, 0, vb, st));
+    CK(cudaMemcpy2DAsync(vec(ck0), ld * cb, psi0, cb, cb, (size_t)P, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpy2DAsync(phi, ld * cb, target, cb, cb, (size_t)P, cudaMemcpyDeviceToDevice, st));
+    // dipole coordinate X = dir . r in the compute type
+    if (!(H->xdir_cached[0] == dir[0] && H->xdir_cached[1] == dir[1] && H->xdir_cached[2] == dir[2])) {
+        std::vector<R> X((size_t)P);
+        for (int64_t p = 0; p < P; p++) {
+            double s = 0.0;
+            for (int d = 0; d < 3; d++) s += dir[d] * (msh->origin[d] + msh->h * msh->ijk[(size_t)p * 3 + d]);
+            X[(size_t)p] = (R)s;
+        }
+        CK(H->Xd.upload(X));
+        for (int d = 0; d < 3; d++) H->xdir_cached[d] = dir[d];
+    }
+    const int nb = norm_blocks(P);
+    CK(H->dots.ensure((size_t)nb * 20 * sizeof(double) + 64 * sizeof(double)));
+    CK(H->M.ensure(32 * sizeof(double)));
+    CK(H->ov.ensure(2 * sizeof(double)));
+    CK(H->grad.ensure((size_t)nsteps * sizeof(double)));
+    CK(cudaMemsetAsync(H->grad.p, 0, (size_t)nsteps * sizeof(double), st));
+
+    // x -> y through the m exponentials of one interval (explicit powers);
+    // the powers of exponential l are left in pw[4l .. 4l+3] (pw[4l] = input).
+    auto interval = [&](const void *x, void *y, double e) -> rsg_status {
+        const void *cur = x;
+        for (int l = 0; l < m; l++) {
+            void *pw[5] = {const_cast<void *>(cur), vec(pw0 + 4 * l + 1), vec(pw0 + 4 * l + 2),
+                           vec(pw0 + 4 * l + 3), vec(pw0 + 4 * m)};
+            void *next = (l == m - 1) ? y : vec(pw0 + 4 * (l + 1));
+            CKS(powers(H, pw, next, ld, tau, -1.0, e, dir, st));
+            cur = next;
+        }
+        return RSG_OK;
+    };
+
+    // forward pass, checkpointing the state at the start of every segment
+    CK(cudaMemcpyAsync(fa, vec(ck0), vb, cudaMemcpyDeviceToDevice, st));
+    for (int64_t k = 0; k < nsteps; k++) {
+        if (k > 0 && k % K == 0) CK(cudaMemcpyAsync(vec(ck0 + k / K), fa, vb, cudaMemcpyDeviceToDevice, st));
+        CKS(interval(fa, fb, eps[k]));
+        std::swap(fa, fb);
+    }
+    // J = |<phi|psi_N>|^2 and chi_N = phi <phi|psi_N>
+    CK(launch_overlap<R>(phi, fa, P, (int)ld, h3, H->dots.as<double>(), nb, H->ov.as<double>(), st));
+    CK(launch_scale_dev<R>(phi, chi, P * ld, H->ov.as<double>(), st));
+    double ov[2] = {0, 0};
+    CK(cudaMemcpyAsync(ov, H->ov.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+
+    // backward over segments: recompute psi_k, then walk the intervals back
+    for (int64_t c = nck - 1; c >= 0; c--) {
+        const int64_t k0 = c * K, k1 = std::min<int64_t>(k0 + K, nsteps);
+        CK(cudaMemcpyAsync(vec(seg0), vec(ck0 + c), vb, cudaMemcpyDeviceToDevice, st));
+        for (int64_t k = k0; k < k1 - 1; k++)
+            CKS(interval(vec(seg0 + (k - k0)), vec(seg0 + (k - k0 + 1)), eps[k]));
+        for (int64_t k = k1 - 1; k >= k0; k--) {
+            const double e = eps[k];
+            CKS(interval(vec(seg0 + (k - k0)), fb, e));   // fills the powers A^j psi'_l
+            // costate: chi'_m = chi_{k+1}; chi'_l = T^dagger chi'_{l+1}
+            for (int l = m - 1; l >= 0; l--) {
+                void *B[5] = {chi, vec(b0 + 1), vec(b0 + 2), vec(b0 + 3), vec(b0 + 4)};
+                CKS(powers(H, B, chi2, ld, tau, +1.0, e, dir, st));
+                const void *bb[4] = {B[0], B[1], B[2], B[3]};
+                const void *aa[4] = {l == 0 ? vec(seg0 + (k - k0)) : vec(pw0 + 4 * l),
+                                     vec(pw0 + 4 * l + 1), vec(pw0 + 4 * l + 2), vec(pw0 + 4 * l + 3)};
+                CK(launch_adjoint_dots<R>(bb, aa, P, (int)ld, H->Xd.as<R>(), h3, H->dots.as<double>(), nb,
+                                          H->M.as<double>(), st));
+                CK(launch_grad_accum(H->M.as<double>(), tau, H->grad.as<double>() + k, st));
+                std::swap(chi, chi2);
+            }
+        }
+    }
+    CK(cudaMemcpyAsync(grad_out, H->grad.p, (size_t)nsteps * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *J_out = ov[0] * ov[0] + ov[1] * ov[1];
+    return RSG_OK;
+}
+
+}  // namespace
+
+extern "C" rsg_status rsg_control_gradient(rsg_ham H, const void *psi0, const void *target,
+                                           int64_t nsteps, double dt, rsg_scheme scheme, int nsub,
+                                           const double *eps, const double dir[3], int checkpoint_every,
+                                           double *J_out, double *grad_out, void *stream) {
+    if (!H || !psi0 || !target || !eps || !J_out || !grad_out) return fail(RSG_ERR_ARG, "NULL argument");
+    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (nsteps < 1 || nsub < 1 || !std::isfinite(dt)) return fail(RSG_ERR_ARG, "bad nsteps/nsub/dt");
+    if (scheme != RSG_EXPMID && scheme != RSG_ETRS) return fail(RSG_ERR_ARG, "unknown scheme");
+    if (((uintptr_t)psi0) % 8 || ((uintptr_t)target) % 8) return fail(RSG_ERR_ARG, "misaligned state");
+    const double xdir[3] = {1.0, 0.0, 0.0};
+    const double *d = dir ? dir : xdir;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (H->dtype == RSG_C64)
+        return control_gradient_t<float>(H, psi0, target, nsteps, dt, scheme, nsub, eps, d,
+                                         checkpoint_every, J_out, grad_out, st);
+    return control_gradient_t<double>(H, psi0, target, nsteps, dt, scheme, nsub, eps, d,
+                                      checkpoint_every, J_out, grad_out, st);
+}
+
+// ============================================================== batch ====
+extern "C" {
+
+rsg_status rsg_batch_create(const rsg_ham *hams, const int64_t *S, int nsys, rsg_batch *out) {
+    if (!hams || !S || !out || nsys < 1) return fail(RSG_ERR_ARG, "bad batch arguments");
+    std::unique_ptr<rsg_batch_s> b(new rsg_batch_s());
+    for (int i = 0; i < nsys; i++) {
+        if (!hams[i]) return fail(RSG_ERR_ARG, "NULL Hamiltonian %d", i);
+        if (hams[i]->dtype != RSG_C64) return fail(RSG_ERR_UNSUPPORTED, "batches are complex64");
+        if (S[i] < 1) return fail(RSG_ERR_ARG, "S[%d] < 1", i);
+        b->hams.push_back(hams[i]);
+        b->S.push_back(S[i]);
+    }
+    *out = b.release();
+    return RSG_OK;
+}
+
+rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps, double dt,
+                               rsg_scheme scheme, int gs_every, void *stream) {
+    if (!b || !psis) return fail(RSG_ERR_ARG, "NULL argument");
+    for (size_t i = 0; i < b->hams.size(); i++) {
+        const int64_t ld = (b->S[i] + 1) / 2 * 2;
+        CKS(rsg_propagate_steps(b->hams[i], psis[i], b->S[i], ld, nsteps, dt, scheme, 1, nullptr,
+                                nullptr, gs_every, nullptr, stream));
+    }
+    return RSG_OK;
+}
+
+rsg_status rsg_batch_destroy(rsg_batch b) {
+    delete b;
+    return RSG_OK;
+}
+
+}  // extern "C"

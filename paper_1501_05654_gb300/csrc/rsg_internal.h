@@ -1,0 +1,130 @@
+// Internal declarations shared by the host API (rsg_host.cpp) and the CUDA
+// kernels (rsg_kernels.cu, rsg_linalg.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rsg.h"
+
+namespace rsg {
+
+// One (y, z) row of the mesh bounding box: points x in [xmin, xmax] are
+// stored contiguously from point index `start`.  Empty rows have xmin > xmax.
+// Every supported shape (cube, box, sphere) meets each row in one interval.
+struct Row {
+    int32_t start, xmin, xmax, pad;
+};
+
+// Tile of the z-marching stencil kernel: bbox tile (tx, ty) and the planes
+// [zlo, zhi) it produces.
+struct Tile {
+    int32_t tx, ty, zlo, zhi;
+};
+
+// Kernel tile configuration.
+struct TileCfg {
+    int kernel = 0;   // 0 z-march, 1 naive
+    int rx = 4;       // points per thread along x
+    int ty = 8;       // rows per tile (blockDim.z)
+    int zseg = 32;    // planes per z segment
+};
+
+// Everything one H application needs, by value.  Pointers to the state
+// blocks are typed as the 16-byte vector of the compute type (float4 = two
+// complex64 values, double2 = one complex128 value).
+template <typename R>
+struct ApplyArgs {
+    const void *in;      // u (P, SV vectors)
+    void *out;           // result
+    const void *base;    // optional: added with scale beta
+    void *acc;           // optional: acc += gamma * result
+    const Row *rows;
+    const Tile *tiles;
+    int nx, ny, nz;
+    int SV;              // 16-byte vectors per point row
+    const R *V;          // local potential (P)
+    R f0, fx, fy, fz;    // eps * dir.r = f0 + fx*ix + fy*iy + fz*iz (bbox idx)
+    R w[5];              // -1/2 c_k / h^2
+    R ar, ai, br, bi, gr, gi;
+    // non-local part (may be absent: nl_ptr == nullptr)
+    const int32_t *nl_ptr;   // P+1 CSR over points
+    const int32_t *nl_ent;   // global sphere-entry index q
+    const int32_t *q_atom;   // atom of each entry
+    const R *q_p;            // entry-major projector values (npmax per entry)
+    const void *D;           // (natoms*npmax, SV) vectors: h_a <p|u>
+    int npmax;
+    int64_t P;
+};
+
+// Projector tables on the device (entry-major, see rsg_host.cpp).
+struct ProjDev {
+    int natoms = 0, npmax = 0;
+    int64_t nq = 0;
+    int nchunks = 0;
+    int32_t *q_pt = nullptr;      // point of each entry
+    int32_t *q_atom = nullptr;
+    void *q_p = nullptr;          // R values, nq * npmax
+    int32_t *chunk_atom = nullptr, *chunk_q0 = nullptr, *chunk_q1 = nullptr;
+    int32_t *atom_chunk0 = nullptr; // natoms+1 prefix of chunks per atom
+    double *hm = nullptr;         // natoms * npmax * npmax (zero padded)
+    int32_t *nl_ptr = nullptr, *nl_ent = nullptr;
+};
+
+// ---- launchers (rsg_kernels.cu) ----
+template <typename R>
+cudaError_t launch_apply(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles,
+                         cudaStream_t st);
+template <typename R>
+cudaError_t launch_proj_dot(const void *u, int SV, const ProjDev &pj, double *partial,
+                            cudaStream_t st);
+template <typename R>
+cudaError_t launch_proj_reduce(const double *partial, int SV, const ProjDev &pj,
+                               double h3, void *D, cudaStream_t st);
+
+// ---- linear algebra on state blocks (rsg_linalg.cu) ----
+// G (S x S complex double) = h3 * Psi^H Psi; partial needs nblk * S * S * 2 doubles.
+template <typename R>
+cudaError_t launch_gram(const void *psi, int64_t P, int ld, int S, double h3,
+                        double *partial, int nblk, double *G, cudaStream_t st);
+int gram_blocks(int64_t P, int S);
+// In-place Cholesky of G, inverse of the factor into W (S x S complex double),
+// drift[s] = max(drift[s], |G_ss - 1|), status word set non-zero on failure.
+cudaError_t launch_chol_inv(double *G, double *W, int S, double *drift, int *status,
+                            cudaStream_t st);
+// psi <- psi W^H (in place).
+template <typename R>
+cudaError_t launch_tri_apply(void *psi, int64_t P, int ld, int S, const double *W,
+                             cudaStream_t st);
+// norms2[s] = h3 sum_p |psi[p,s]|^2 (FP64)
+template <typename R>
+cudaError_t launch_norms(const void *psi, int64_t P, int ld, int S, double h3,
+                         double *partial, int nblk, double *out, cudaStream_t st);
+int norm_blocks(int64_t P);
+// Inner products for the adjoint: out[j*4+i] = h3 sum_p conj(b_j) x_p a_i for
+// j + i <= 3 (complex double); b_j, a_i are P-vectors (S = 1, ld = 1 or 2).
+template <typename R>
+cudaError_t launch_adjoint_dots(const void *const *b, const void *const *a, int64_t P, int ld,
+                                const R *X, double h3, double *partial, int nblk,
+                                double *out, cudaStream_t st);
+// overlap: out = h3 sum_p conj(f_p) g_p  (complex double, one state)
+template <typename R>
+cudaError_t launch_overlap(const void *f, const void *g, int64_t P, int ld, double h3,
+                           double *partial, int nblk, double *out, cudaStream_t st);
+// y = a * x (+ y if accumulate), complex scalar a given as device double[2]
+// or host values; one state vector or a whole block (n complex values).
+template <typename R>
+cudaError_t launch_axpby(const void *x, void *y, int64_t n, double ar, double ai,
+                         double br, double bi, cudaStream_t st);
+// y = x * (a[0] + i a[1]) where a is a DEVICE complex double (graph friendly)
+template <typename R>
+cudaError_t launch_scale_dev(const void *x, void *y, int64_t n, const double *a,
+                             cudaStream_t st);
+// grad[k] += 2 Re( -i tau * sum_n 1/n! sum_j M[j][n-1-j] )  (device)
+cudaError_t launch_grad_accum(const double *M, double tau, double *grad_k,
+                              cudaStream_t st);
+
+}  // namespace rsg

@@ -1,0 +1,469 @@
+// FP64 reductions and small dense linear algebra on state blocks.
+//
+// Norms, Gram matrices, the Cholesky factor of the Gram matrix and its
+// inverse are kept in FP64 for both compute types (arXiv:1501.05654,
+// Sec. "Performance": real-time propagation preserves orthogonality, so the
+// states are re-orthonormalised only now and then; here Cholesky-QR, which
+// equals Gram-Schmidt in index order).  The adjoint inner products of the
+// control gradient (Sec. "Quantum optimal control", Eq. (qoctgradient)) are
+// FP64 reductions as well.
+#include "rsg_internal.h"
+#include "rsg_vec.cuh"
+
+namespace rsg {
+
+namespace {
+
+template <typename R>
+__device__ __forceinline__ void ld_c(const R *p, double &re, double &im) {
+    re = (double)p[0];
+    im = (double)p[1];
+}
+
+constexpr int GT = 16;   // Gram tile edge
+
+}  // namespace
+
+int gram_blocks(int64_t P, int S) {
+    (void)S;
+    int64_t n = (P + 4095) / 4096;
+    if (n > 296) n = 296;
+    if (n < 1) n = 1;
+    return (int)n;
+}
+
+int norm_blocks(int64_t P) {
+    int64_t n = (P + 2047) / 2048;
+    if (n > 608) n = 608;
+    if (n < 1) n = 1;
+    return (int)n;
+}
+
+// partial[blk][s][t] (complex double) = sum over the block's points of
+// conj(psi[p,s]) psi[p,t] for one GT x GT tile of (s, t).
+template <typename R>
+__global__ void __launch_bounds__(GT *GT) k_gram(const R *__restrict__ psi, int64_t P, int ld, int S,
+                                                 double *__restrict__ partial, int nblk) {
+    __shared__ double sa[GT][GT][2], sb[GT][GT][2];
+    const int s0 = blockIdx.x * GT, t0 = blockIdx.y * GT;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t per = (P + nblk - 1) / nblk;
+    const int64_t p0 = blockIdx.z * per;
+    const int64_t p1 = p0 + per < P ? p0 + per : P;
+    double gr = 0.0, gi = 0.0;
+    for (int64_t pb = p0; pb < p1; pb += GT) {
+        // stage GT points x GT columns of both tiles
+        const int64_t p = pb + ty;
+        double ar = 0, ai = 0, br = 0, bi = 0;
+        if (p < p1) {
+            if (s0 + tx < S) ld_c(psi + (p * ld + s0 + tx) * 2, ar, ai);
+            if (t0 + tx < S) ld_c(psi + (p * ld + t0 + tx) * 2, br, bi);
+        }
+        sa[ty][tx][0] = ar;
+        sa[ty][tx][1] = ai;
+        sb[ty][tx][0] = br;
+        sb[ty][tx][1] = bi;
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < GT; k++) {
+            const double xr = sa[k][ty][0], xi = sa[k][ty][1];   // psi[p, s0+ty]
+            const double yr = sb[k][tx][0], yi = sb[k][tx][1];   // psi[p, t0+tx]
+            gr += xr * yr + xi * yi;
+            gi += xr * yi - xi * yr;
+        }
+        __syncthreads();
+    }
+    const int s = s0 + ty, t = t0 + tx;
+    if (s < S && t < S) {
+        double *d = partial + (((int64_t)blockIdx.z * S + s) * S + t) * 2;
+        d[0] = gr;
+        d[1] = gi;
+    }
+}
+
+__global__ void k_sum_blocks(const double *__restrict__ partial, int nblk, int64_t n, double scale,
+                             double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; b++) s += partial[(int64_t)b * n + i];
+    out[i] = scale * s;
+}
+
+template <typename R>
+cudaError_t launch_gram(const void *psi, int64_t P, int ld, int S, double h3, double *partial,
+                        int nblk, double *G, cudaStream_t st) {
+    dim3 grid((S + GT - 1) / GT, (S + GT - 1) / GT, nblk);
+    k_gram<R><<<grid, dim3(GT, GT), 0, st>>>((const R *)psi, P, ld, S, partial, nblk);
+    const int64_t n = (int64_t)S * S * 2;
+    k_sum_blocks<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, nblk, n, h3, G);
+    return cudaGetLastError();
+}
+
+// One block.  G (S x S complex double, G[i][j] = <psi_i|psi_j>) is factored
+// in place as G = L L^H (lower L); W = L^-1.  drift (optional) records
+// |G_ss - 1|.  status != 0 if G is not finite or not positive definite.
+__global__ void k_chol_inv(double *G, double *W, int S, double *drift, int *status) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ int bad;
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int s = tid; s < S; s += nt) {
+        const double d = G[((int64_t)s * S + s) * 2];
+        if (drift != nullptr) {
+            const double e = fabs(d - 1.0);
+            if (!(e <= drift[s])) drift[s] = e;   // NaN propagates
+        }
+    }
+    for (int64_t i = tid; i < (int64_t)S * S * 2; i += nt)
+        if (!isfinite(G[i])) bad = 1;
+    __syncthreads();
+    for (int j = 0; j < S && !bad; j++) {
+        if (tid == 0) {
+            double d = G[((int64_t)j * S + j) * 2];
+            for (int k = 0; k < j; k++) {
+                const double *l = G + ((int64_t)j * S + k) * 2;
+                d -= l[0] * l[0] + l[1] * l[1];
+            }
+            if (!(d > 0.0)) bad = 1;
+            G[((int64_t)j * S + j) * 2] = d > 0.0 ? sqrt(d) : 1.0;
+            G[((int64_t)j * S + j) * 2 + 1] = 0.0;
+        }
+        __syncthreads();
+        const double ljj = G[((int64_t)j * S + j) * 2];
+        for (int i = j + 1 + tid; i < S; i += nt) {
+            // L[i][j] = (G[i][j] - sum_k L[i][k] conj(L[j][k])) / L[j][j]
+            double re = G[((int64_t)i * S + j) * 2], im = G[((int64_t)i * S + j) * 2 + 1];
+            for (int k = 0; k < j; k++) {
+                const double *a = G + ((int64_t)i * S + k) * 2;
+                const double *b = G + ((int64_t)j * S + k) * 2;
+                re -= a[0] * b[0] + a[1] * b[1];
+                im -= a[1] * b[0] - a[0] * b[1];
+            }
+            G[((int64_t)i * S + j) * 2] = re / ljj;
+            G[((int64_t)i * S + j) * 2 + 1] = im / ljj;
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) *status = 1;
+        return;
+    }
+    // W = L^-1, one column per thread (forward substitution)
+    for (int c = tid; c < S; c += nt) {
+        for (int i = 0; i < S; i++) {
+            W[((int64_t)i * S + c) * 2] = 0.0;
+            W[((int64_t)i * S + c) * 2 + 1] = 0.0;
+        }
+        W[((int64_t)c * S + c) * 2] = 1.0 / G[((int64_t)c * S + c) * 2];
+        for (int i = c + 1; i < S; i++) {
+            double re = 0.0, im = 0.0;
+            for (int k = c; k < i; k++) {
+                const double *l = G + ((int64_t)i * S + k) * 2;
+                const double *w = W + ((int64_t)k * S + c) * 2;
+                re += l[0] * w[0] - l[1] * w[1];
+                im += l[0] * w[1] + l[1] * w[0];
+            }
+            const double lii = G[((int64_t)i * S + i) * 2];
+            W[((int64_t)i * S + c) * 2] = -re / lii;
+            W[((int64_t)i * S + c) * 2 + 1] = -im / lii;
+        }
+    }
+}
+
+cudaError_t launch_chol_inv(double *G, double *W, int S, double *drift, int *status,
+                            cudaStream_t st) {
+    k_chol_inv<<<1, 256, 0, st>>>(G, W, S, drift, status);
+    return cudaGetLastError();
+}
+
+// psi[p, s] <- sum_{t <= s} psi[p, t] conj(W[s][t]); each block stages its
+// full rows in shared memory first, so the update is in place.
+template <typename R>
+__global__ void __launch_bounds__(256) k_tri_apply(R *psi, int64_t P, int ld, int S,
+                                                   const double *__restrict__ W, int pt) {
+    extern __shared__ double rowbuf[];   // pt * S complex double
+    const int64_t p0 = (int64_t)blockIdx.x * pt;
+    const int n = pt * S;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int q = e / S, t = e % S;
+        const int64_t p = p0 + q;
+        double re = 0.0, im = 0.0;
+        if (p < P) ld_c(psi + (p * ld + t) * 2, re, im);
+        rowbuf[e * 2] = re;
+        rowbuf[e * 2 + 1] = im;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int q = e / S, s = e % S;
+        const int64_t p = p0 + q;
+        if (p >= P) continue;
+        double re = 0.0, im = 0.0;
+        const double *row = rowbuf + (int64_t)q * S * 2;
+        for (int t = 0; t <= s; t++) {
+            const double wr = W[((int64_t)s * S + t) * 2], wi = -W[((int64_t)s * S + t) * 2 + 1];
+            re += row[2 * t] * wr - row[2 * t + 1] * wi;
+            im += row[2 * t] * wi + row[2 * t + 1] * wr;
+        }
+        psi[(p * ld + s) * 2] = (R)re;
+        psi[(p * ld + s) * 2 + 1] = (R)im;
+    }
+}
+
+template <typename R>
+cudaError_t launch_tri_apply(void *psi, int64_t P, int ld, int S, const double *W, cudaStream_t st) {
+    int pt = 4096 / S;
+    if (pt < 1) pt = 1;
+    if (pt > 64) pt = 64;
+    const size_t smem = (size_t)pt * S * 2 * sizeof(double);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_tri_apply<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t nb = (P + pt - 1) / pt;
+    k_tri_apply<R><<<(unsigned)nb, 256, smem, st>>>((R *)psi, P, ld, S, W, pt);
+    return cudaGetLastError();
+}
+
+// partial[blk][s] = sum over the block's points of |psi[p,s]|^2
+template <typename R>
+__global__ void __launch_bounds__(256) k_norms(const R *__restrict__ psi, int64_t P, int ld, int S,
+                                               double *__restrict__ partial, int nblk) {
+    __shared__ double red[256];
+    const int64_t per = (P + nblk - 1) / nblk;
+    const int64_t p0 = blockIdx.x * per;
+    const int64_t p1 = p0 + per < P ? p0 + per : P;
+    const int bx = blockDim.x, by = blockDim.y;
+    for (int sb = 0; sb < S; sb += bx) {
+        const int s = sb + threadIdx.x;
+        double acc = 0.0;
+        if (s < S)
+            for (int64_t p = p0 + threadIdx.y; p < p1; p += by) {
+                double re, im;
+                ld_c(psi + (p * ld + s) * 2, re, im);
+                acc += re * re + im * im;
+            }
+        red[threadIdx.y * bx + threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.y == 0 && s < S) {
+            double t = 0.0;
+            for (int l = 0; l < by; l++) t += red[l * bx + threadIdx.x];
+            partial[(int64_t)blockIdx.x * S + s] = t;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename R>
+cudaError_t launch_norms(const void *psi, int64_t P, int ld, int S, double h3, double *partial,
+                         int nblk, double *out, cudaStream_t st) {
+    const int bx = S < 32 ? S : 32;
+    k_norms<R><<<nblk, dim3(bx, 256 / bx), 0, st>>>((const R *)psi, P, ld, S, partial, nblk);
+    k_sum_blocks<<<(S + 255) / 256, 256, 0, st>>>(partial, nblk, S, h3, out);
+    return cudaGetLastError();
+}
+
+// Ten inner products <b_j| X |a_i>, j + i <= 3, for the adjoint gradient.
+template <typename R>
+__global__ void __launch_bounds__(256) k_adjoint_dots(const R *b0, const R *b1, const R *b2,
+                                                      const R *b3, const R *a0, const R *a1,
+                                                      const R *a2, const R *a3, int64_t P, int ld,
+                                                      const R *__restrict__ X,
+                                                      double *__restrict__ partial, int nblk) {
+    __shared__ double red[256];
+    const R *bb[4] = {b0, b1, b2, b3};
+    const R *aa[4] = {a0, a1, a2, a3};
+    double acc[20];
+#pragma unroll
+    for (int i = 0; i < 20; i++) acc[i] = 0.0;
+    const int64_t per = (P + nblk - 1) / nblk;
+    const int64_t p0 = blockIdx.x * per;
+    const int64_t p1 = p0 + per < P ? p0 + per : P;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        double br[4], bi[4], ar[4], ai[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            ld_c(bb[j] + p * ld * 2, br[j], bi[j]);
+            ld_c(aa[j] + p * ld * 2, ar[j], ai[j]);
+        }
+        const double x = (double)X[p];
+        int k = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int i = 0; i + j <= 3; i++) {
+                // conj(b) * x * a
+                acc[2 * k] += x * (br[j] * ar[i] + bi[j] * ai[i]);
+                acc[2 * k + 1] += x * (br[j] * ai[i] - bi[j] * ar[i]);
+                k++;
+            }
+    }
+    for (int k = 0; k < 20; k++) {
+        red[threadIdx.x] = acc[k];
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * 20 + k] = red[0];
+        __syncthreads();
+    }
+}
+
+// Expand the 10 packed values into out[j*4+i] (complex double), zero elsewhere.
+__global__ void k_adjoint_finish(const double *packed, double *out) {
+    if (threadIdx.x != 0) return;
+    int k = 0;
+    for (int j = 0; j < 4; j++)
+        for (int i = 0; i < 4; i++) {
+            if (i + j <= 3) {
+                out[(j * 4 + i) * 2] = packed[2 * k];
+                out[(j * 4 + i) * 2 + 1] = packed[2 * k + 1];
+                k++;
+            } else {
+                out[(j * 4 + i) * 2] = 0.0;
+                out[(j * 4 + i) * 2 + 1] = 0.0;
+            }
+        }
+}
+
+template <typename R>
+cudaError_t launch_adjoint_dots(const void *const *b, const void *const *a, int64_t P, int ld,
+                                const R *X, double h3, double *partial, int nblk, double *out,
+                                cudaStream_t st) {
+    k_adjoint_dots<R><<<nblk, 256, 0, st>>>((const R *)b[0], (const R *)b[1], (const R *)b[2],
+                                             (const R *)b[3], (const R *)a[0], (const R *)a[1],
+                                             (const R *)a[2], (const R *)a[3], P, ld, X, partial,
+                                             nblk);
+    double *packed = partial + (int64_t)nblk * 20;
+    k_sum_blocks<<<1, 32, 0, st>>>(partial, nblk, 20, h3, packed);
+    k_adjoint_finish<<<1, 32, 0, st>>>(packed, out);
+    return cudaGetLastError();
+}
+
+// h3 * sum_p conj(f_p) g_p for column 0 of two (P, ld) blocks.
+template <typename R>
+__global__ void __launch_bounds__(256) k_overlap(const R *__restrict__ f, const R *__restrict__ g,
+                                                 int64_t P, int ld, double *__restrict__ partial,
+                                                 int nblk) {
+    __shared__ double red[2][256];
+    const int64_t per = (P + nblk - 1) / nblk;
+    const int64_t p0 = blockIdx.x * per;
+    const int64_t p1 = p0 + per < P ? p0 + per : P;
+    double sr = 0.0, si = 0.0;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        double fr, fi, gr, gi;
+        ld_c(f + p * ld * 2, fr, fi);
+        ld_c(g + p * ld * 2, gr, gi);
+        sr += fr * gr + fi * gi;
+        si += fr * gi - fi * gr;
+    }
+    red[0][threadIdx.x] = sr;
+    red[1][threadIdx.x] = si;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + w];
+            red[1][threadIdx.x] += red[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[(int64_t)blockIdx.x * 2] = red[0][0];
+        partial[(int64_t)blockIdx.x * 2 + 1] = red[1][0];
+    }
+}
+
+template <typename R>
+cudaError_t launch_overlap(const void *f, const void *g, int64_t P, int ld, double h3,
+                           double *partial, int nblk, double *out, cudaStream_t st) {
+    k_overlap<R><<<nblk, 256, 0, st>>>((const R *)f, (const R *)g, P, ld, partial, nblk);
+    k_sum_blocks<<<1, 32, 0, st>>>(partial, nblk, 2, h3, out);
+    return cudaGetLastError();
+}
+
+// y = a x + b y over n complex values
+template <typename R>
+__global__ void k_axpby(const R *__restrict__ x, R *__restrict__ y, int64_t n, double ar, double ai,
+                        double br, double bi) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double xr = x[2 * i], xi = x[2 * i + 1];
+        const double yr = y[2 * i], yi = y[2 * i + 1];
+        y[2 * i] = (R)(ar * xr - ai * xi + br * yr - bi * yi);
+        y[2 * i + 1] = (R)(ar * xi + ai * xr + br * yi + bi * yr);
+    }
+}
+
+template <typename R>
+cudaError_t launch_axpby(const void *x, void *y, int64_t n, double ar, double ai, double br,
+                         double bi, cudaStream_t st) {
+    int64_t nb = (n + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    if (nb < 1) nb = 1;
+    k_axpby<R><<<(unsigned)nb, 256, 0, st>>>((const R *)x, (R *)y, n, ar, ai, br, bi);
+    return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void k_scale_dev(const R *__restrict__ x, R *__restrict__ y, int64_t n,
+                            const double *__restrict__ a) {
+    const double ar = a[0], ai = a[1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double xr = x[2 * i], xi = x[2 * i + 1];
+        y[2 * i] = (R)(ar * xr - ai * xi);
+        y[2 * i + 1] = (R)(ar * xi + ai * xr);
+    }
+}
+
+template <typename R>
+cudaError_t launch_scale_dev(const void *x, void *y, int64_t n, const double *a, cudaStream_t st) {
+    int64_t nb = (n + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    if (nb < 1) nb = 1;
+    k_scale_dev<R><<<(unsigned)nb, 256, 0, st>>>((const R *)x, (R *)y, n, a);
+    return cudaGetLastError();
+}
+
+// grad_k += 2 Re( -i tau * sum_{n=1..4} 1/n! sum_{j<n} M[j][n-1-j] )
+__global__ void k_grad_accum(const double *M, double tau, double *g) {
+    if (threadIdx.x != 0) return;
+    const double invf[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
+    double sr = 0.0, si = 0.0;
+    for (int n = 1; n <= 4; n++)
+        for (int j = 0; j < n; j++) {
+            const int i = n - 1 - j;
+            sr += invf[n] * M[(j * 4 + i) * 2];
+            si += invf[n] * M[(j * 4 + i) * 2 + 1];
+        }
+    // Re(-i tau (sr + i si)) = tau * si
+    *g += 2.0 * tau * si;
+}
+
+cudaError_t launch_grad_accum(const double *M, double tau, double *grad_k, cudaStream_t st) {
+    k_grad_accum<<<1, 32, 0, st>>>(M, tau, grad_k);
+    return cudaGetLastError();
+}
+
+#define RSG_INST(R)                                                                               \
+    template cudaError_t launch_gram<R>(const void *, int64_t, int, int, double, double *, int,      \
+                                        double *, cudaStream_t);                                     \
+    template cudaError_t launch_tri_apply<R>(void *, int64_t, int, int, const double *,              \
+                                             cudaStream_t);                                          \
+    template cudaError_t launch_norms<R>(const void *, int64_t, int, int, double, double *, int,     \
+                                         double *, cudaStream_t);                                    \
+    template cudaError_t launch_adjoint_dots<R>(const void *const *, const void *const *, int64_t,   \
+                                                int, const R *, double, double *, int, double *,     \
+                                                cudaStream_t);                                       \
+    template cudaError_t launch_overlap<R>(const void *, const void *, int64_t, int, double,         \
+                                           double *, int, double *, cudaStream_t);                   \
+    template cudaError_t launch_axpby<R>(const void *, void *, int64_t, double, double, double,      \
+                                         double, cudaStream_t);                                      \
+    template cudaError_t launch_scale_dev<R>(const void *, void *, int64_t, const double *,         \
+                                             cudaStream_t);
+RSG_INST(float)
+RSG_INST(double)
+
+}  // namespace rsg

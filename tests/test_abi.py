@@ -1,0 +1,100 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol that
+include/rsg.h declares, builds meshes on the host identical (as point sets) to
+the oracle's, and rejects bad arguments before touching the device."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1501_05654_gb300 as rsg
+from paper_1501_05654_gb300 import rsg as binding
+from tests._parity import perm_lib_to_oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    rsg.build()
+    return binding.load()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "rsg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rsg_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(binding.SIGNATURES), set(names) ^ set(binding.SIGNATURES)
+
+
+@pytest.mark.parametrize("case", [("cube", 13), ("box", (7, 11, 5)), ("sphere", 2.3)])
+def test_mesh_point_sets_match_oracle(lib, case):
+    kind, arg = case
+    if kind == "cube":
+        lm, om = rsg.Mesh(rsg.CUBE, arg, spacing=0.3), oracle.Mesh(oracle.CUBE, arg, h=0.3)
+    elif kind == "box":
+        lm, om = rsg.Mesh(rsg.BOX, arg, spacing=0.25), oracle.Mesh(oracle.BOX, arg, h=0.25)
+    else:
+        lm, om = rsg.Mesh(rsg.SPHERE, radius=arg, spacing=0.3), oracle.Mesh(oracle.SPHERE, radius=arg, h=0.3)
+    assert lm.P == om.P
+    idx = perm_lib_to_oracle(lm.ijk, om.ijk)
+    assert np.abs(lm.xyz - om.xyz[idx]).max() < 1e-13
+
+
+def test_library_point_order_is_rows(lib):
+    """z slowest, then y, x fastest; each (y, z) row contiguous."""
+    m = rsg.Mesh(rsg.SPHERE, radius=3.0, spacing=0.5)
+    key = m.ijk[:, 2] * 10 ** 6 + m.ijk[:, 1] * 10 ** 3 + m.ijk[:, 0]
+    assert np.all(np.diff(key) > 0)
+
+
+def test_sphere_count_full_size(lib):
+    assert rsg.Mesh(rsg.SPHERE, radius=18.0, spacing=0.2).P == 3053617
+
+
+def _status(f, *args):
+    return f(*args)
+
+
+def test_argument_errors_without_device(lib):
+    h = C.c_void_p()
+    n = (C.c_int32 * 3)(4, 4, 4)
+    assert lib.rsg_mesh_create(0, n, 0.0, -1.0, C.byref(h)) == -1
+    assert b"spacing" in lib.rsg_last_error()
+    big = (C.c_int32 * 3)(1025, 4, 4)
+    assert lib.rsg_mesh_create(2, big, 0.0, 0.3, C.byref(h)) == -1
+    assert lib.rsg_mesh_create(1, None, -2.0, 0.3, C.byref(h)) == -1
+    assert lib.rsg_mesh_create(7, n, 0.0, 0.3, C.byref(h)) == -1
+    assert lib.rsg_mesh_create(0, n, 0.0, 0.3, None) == -1
+    m = rsg.Mesh(rsg.CUBE, 6, spacing=0.3)
+    H = rsg.Hamiltonian(m)
+    with pytest.raises(rsg.RSGError, match="ARG"):
+        H.set_option("rx", 3)
+    with pytest.raises(rsg.RSGError, match="ARG"):
+        H.set_option("nonsense", 1)
+    with pytest.raises(rsg.RSGError, match="UNSUPPORTED"):
+        H.set_projectors([[0, 0, 0]], [1.0], [3], [0.25], [np.eye(16)])
+    # NULL state pointers and a missing potential are rejected on the host
+    assert lib.rsg_hamiltonian_apply(H._h, None, None, 1, 2, None) == -1
+    assert lib.rsg_propagate_steps(H._h, None, 1, 2, 1, 0.1, 0, 1, None, None, 0, None, None) == -1
+    assert lib.rsg_ham_create(m._h, 5, C.byref(h)) == -1
+
+
+def test_odd_ld_rejected_for_complex64(lib):
+    m = rsg.Mesh(rsg.CUBE, 6, spacing=0.3)
+    H = rsg.Hamiltonian(m)
+    fake = C.c_void_p(16)   # never dereferenced: the check fails first
+    assert lib.rsg_hamiltonian_apply(H._h, fake, C.c_void_p(4096), 3, 3, None) == -1
+    assert b"even ld" in lib.rsg_last_error()
+    fake_mis = C.c_void_p(8)
+    assert lib.rsg_hamiltonian_apply(H._h, fake_mis, C.c_void_p(4096), 2, 2, None) == -1
+    assert b"aligned" in lib.rsg_last_error()

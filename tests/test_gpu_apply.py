@@ -1,0 +1,134 @@
+"""GPU parity: H|psi> through the C ABI against the FP64 oracle.
+
+Tolerances (normwise max relative error per state): 1e-12 for complex128;
+2e-5 for complex64, with the oracle fed the complex64-rounded inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1501_05654_gb300 as rsg
+from tests._parity import rel_err, round_c64
+from tests._systems import Pair, wells_system
+from workloads import white_noise_states
+
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.complex128: 1e-12, torch.complex64: 2e-5}
+
+
+def _check_apply(p, g, S, eps=0.0, dir=(1.0, 0.0, 0.0), opts=None):
+    psi = white_noise_states(g, p.P, S)
+    if p.dtype == torch.complex64:
+        psi = round_c64(psi)
+    want = p.O.apply(psi, eps=eps, dir=dir)
+    if eps:
+        p.H.set_field(eps, dir)
+    for k, v in (opts or {}).items():
+        p.H.set_option(k, v)
+    x = p.states_to_gpu(psi)
+    y = p.H.apply(x, S=S)
+    torch.cuda.synchronize()
+    got = p.states_from_gpu(y, S)
+    err = rel_err(got, want)
+    assert err < TOL[p.dtype], err
+    return err
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+@pytest.mark.parametrize("S", [1, 3, 8, 19])
+def test_cube_ragged_tiles(dtype, S):
+    """37^3: several tiles plus a ragged tail in every direction."""
+    p, g = wells_system("cube", 37, h=0.3, dtype=dtype, seed=S, natoms=3, lmax=2, rcut=1.5)
+    _check_apply(p, g, S)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_sphere_with_projectors_and_field(dtype):
+    p, g = wells_system("sphere", radius=4.1, h=0.3, dtype=dtype, seed=5, natoms=4, lmax=1)
+    _check_apply(p, g, 6, eps=0.037, dir=(0.6, -0.8, 0.0))
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_box_odd_extents(dtype):
+    p, g = wells_system("box", (23, 9, 14), h=0.25, dtype=dtype, seed=6, natoms=1, lmax=0)
+    _check_apply(p, g, 4, eps=-0.02, dir=(0.0, 0.0, 1.0))
+
+
+@pytest.mark.parametrize("opts", [{"kernel": 1}, {"rx": 1}, {"rx": 2}, {"rx": 4},
+                                  {"ty": 2, "zseg": 5}, {"ty": 16, "zseg": 1000},
+                                  {"ty": 4, "rx": 4, "zseg": 3}])
+def test_kernel_variants_agree(opts):
+    p, g = wells_system("sphere", radius=3.3, h=0.25, dtype=torch.complex64, seed=7, natoms=2)
+    _check_apply(p, g, 10, opts=opts)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_degenerate_meshes(dtype):
+    # one point: every neighbour is a ghost
+    p, g = wells_system("cube", 1, h=0.3, dtype=dtype, natoms=0)
+    _check_apply(p, g, 2)
+    # sphere smaller than one spacing: the origin only
+    p, g = wells_system("sphere", radius=0.1, h=0.3, dtype=dtype, natoms=0)
+    assert p.P == 1
+    _check_apply(p, g, 1)
+    # thin slab: extents below the stencil radius
+    p, g = wells_system("box", (3, 2, 40), h=0.3, dtype=dtype, natoms=1, lmax=0)
+    _check_apply(p, g, 3)
+
+
+def test_no_projectors_then_projectors_removed():
+    p, g = wells_system("cube", 12, h=0.3, dtype=torch.complex128, natoms=2)
+    _check_apply(p, g, 2)
+    p.H.set_projectors(np.zeros((0, 3)), [], [], [], [])
+    p.O.set_projectors(np.zeros((0, 3)), [], [], [], [])
+    _check_apply(p, g, 2)
+
+
+def test_linear_and_hermitian_on_device():
+    """<a|H b> = conj <b|H a> with device results (sanity independent of the oracle)."""
+    p, g = wells_system("sphere", radius=3.0, h=0.3, dtype=torch.complex128, natoms=2)
+    a = p.states_to_gpu(white_noise_states(g, p.P, 1))
+    b = p.states_to_gpu(white_noise_states(g, p.P, 1))
+    ha, hb = p.H.apply(a), p.H.apply(b)
+    l = torch.vdot(a[:, 0], hb[:, 0]).item()
+    r = torch.vdot(b[:, 0], ha[:, 0]).conj().item()
+    assert abs(l - r) < 1e-12 * abs(l)
+
+
+def test_errors_on_device():
+    p, g = wells_system("cube", 8, h=0.3, dtype=torch.complex64, natoms=0)
+    x = torch.zeros((p.P, 4), dtype=torch.complex64, device="cuda")
+    with pytest.raises(rsg.RSGError, match="overlap"):
+        p.H.apply(x, out=x)
+    with pytest.raises(ValueError):
+        p.H.apply(x.to(torch.complex128))
+    with pytest.raises(rsg.RSGError, match="ARG"):
+        p.H.apply(x, S=5)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+def test_full_size_sphere_sampled(dtype):
+    """R = 18 bohr, h = 0.2 (3,053,617 points), 64 states, 32 wells and 32
+    atoms x 4 projectors: every state of 4096 sampled points vs the oracle."""
+    from workloads import gaussian_wells, potential_wells, projector_atoms, rng
+    g = rng(2)
+    p = Pair("sphere", radius=18.0, h=0.2, dtype=dtype)
+    c, d, w = gaussian_wells(g, 32, 18.0 - 2.5)
+    p.set_potential(potential_wells(p.om.xyz, c, d, w))
+    cen, rc, lm, beta, hm = projector_atoms(g, 32, 2.5, 1, ball_radius=18.0 - 2.5)
+    p.set_projectors(cen, rc, lm, beta, hm)
+    S = 64
+    psi = white_noise_states(g, p.P, S, dtype=np.complex64 if dtype == torch.complex64 else np.complex128)
+    psi = psi.astype(np.complex128)
+    x = p.states_to_gpu(psi)
+    y = p.H.apply(x)
+    torch.cuda.synchronize()
+    # sample points: random, plus points inside projector spheres and on the surface
+    samp = g.choice(p.P, 4096, replace=False)
+    pidx = np.repeat(samp, S)
+    sidx = np.tile(np.arange(S), len(samp))
+    want = p.O.apply_sampled(psi, pidx, sidx).reshape(len(samp), S)
+    lib_rows = np.argsort(p.idx)[samp]     # library index of each sampled oracle point
+    got = y[torch.from_numpy(lib_rows).cuda()].cpu().numpy().astype(np.complex128)
+    assert rel_err(got, want) < TOL[dtype]
