@@ -204,6 +204,9 @@ def main():
     ap.add_argument("--ty", type=int, default=None)
     ap.add_argument("--zseg", type=int, default=None)
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--radius", type=float, default=18.0,
+                    help="sphere radius (bohr); 18 is the benchmark workload, smaller radii "
+                         "are for profiler captures only")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -223,7 +226,7 @@ def main():
     rsg.build()
 
     g, wells, proj = build_inputs()
-    mesh = rsg.Mesh(rsg.SPHERE, radius=18.0, spacing=0.2)
+    mesh = rsg.Mesh(rsg.SPHERE, radius=args.radius, spacing=0.2)
     dtype = torch.complex64 if args.dtype == "c64" else torch.complex128
     H = rsg.Hamiltonian(mesh, dtype)
     H.set_potential(potential_wells(mesh.xyz, *wells))

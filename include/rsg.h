@@ -182,9 +182,12 @@ rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps,
 rsg_status rsg_batch_destroy(rsg_batch b);
 
 /* Tuning knobs (kernel tile shapes); unknown keys give RSG_ERR_ARG.
- * Keys: "kernel" (0 = z-marching tiled stencil, 1 = one thread per point
- * and vector), "rx" (points per thread along x: 1, 2 or 4), "ty" (rows per
- * tile), "zseg" (planes per z segment). */
+ * Keys: "kernel" (0 = shared-memory staged z-march, 1 = one thread per
+ * point and vector, 2 = z-march through L1), "rx" (points per thread along
+ * x: 1, 2 or 4; the staged kernel always uses 1), "ty" (rows per
+ * tile: 1, 2, 4, 8 or 16), "zseg" (planes per z segment, 1..64), "cv"
+ * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8).
+ * A shape whose shared memory does not fit the SM fails with RSG_ERR_CUDA. */
 rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value);
 
 /* Measurement hooks.  rsg_ham_profile(H, 1) starts recording a CUDA event

@@ -17,7 +17,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librsg.so")
-SOURCES = ["rsg_kernels.cu", "rsg_linalg.cu", "rsg_host.cpp"]
+# (source, extra flags): the stencil kernels are compiled once per precision
+SOURCES = [("rsg_kernels.cu", ["-DRSG_ONLY_FLOAT"]), ("rsg_kernels.cu", ["-DRSG_ONLY_DOUBLE"]),
+           ("rsg_linalg.cu", []), ("rsg_host.cpp", [])]
 HEADERS = ["rsg_internal.h", "rsg_vec.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -33,7 +35,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS]
+    deps = [os.path.join(CSRC, s) for s in sorted({s for s, _ in SOURCES}) + HEADERS]
     deps.append(os.path.join(ROOT, "include", "rsg.h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)
@@ -49,9 +51,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if ptxas_info:
         common += ["-Xptxas", "-v"]
 
-    def one(src):
-        obj = os.path.join(OUT, src + f".{os.getpid()}.o")
-        cmd = [cc] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def one(item):
+        i, (src, flags) = item
+        obj = os.path.join(OUT, f"{src}.{i}.{os.getpid()}.o")
+        cmd = [cc] + common + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -60,7 +63,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return obj
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(one, SOURCES))
+        objs = list(ex.map(one, enumerate(SOURCES)))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

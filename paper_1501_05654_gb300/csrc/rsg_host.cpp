@@ -117,7 +117,7 @@ struct rsg_ham_s {
     TileCfg cfg;
     // projectors
     ProjDev pj;
-    DevBuf q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm, nl_ptr, nl_ent;
+    DevBuf q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm, nl_ptr, nl_ent, u_pts, u_ptr;
     DevBuf D, partial;
     // workspace
     DevBuf w0, w1, red, G, W, drift, status, dots, M, ov, grad, Xd, Xdir;
@@ -218,9 +218,17 @@ int pow2_at_least(int v) {
     return p;
 }
 
-// Block shape of the z-marching kernel for SV vectors per row (must match
-// launch_apply): cv x nxr x ty threads, TX = nxr * rx.
+// Tile of the stencil kernel in use for SV vectors per row (must match
+// launch_apply): staged kernel cv x nxr x ty threads (512), L1 z-march
+// kernel 256 threads; TX = nxr * rx.
 void block_shape(const TileCfg &c, int SV, int *TX, int *TY) {
+    if (c.kernel == 0) {
+        int cv, nxr, ty;
+        stage_shape(c, SV, &cv, &nxr, &ty);
+        *TX = nxr;
+        *TY = ty;
+        return;
+    }
     const int cv = std::min(8, pow2_at_least(SV));
     int ty = c.ty;
     while (cv * ty > 256) ty >>= 1;
@@ -313,7 +321,7 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     a.P = m->P;
     int ntiles = 0;
     a.tiles = nullptr;
-    if (H->cfg.kernel == 0) {
+    if (H->cfg.kernel != 1) {
         int TX, TY;
         block_shape(H->cfg, SV, &TX, &TY);
         CKS(get_tiles(m, TX, TY, H->cfg.zseg, &a.tiles, &ntiles));
@@ -332,14 +340,25 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         H->ev_used += 2;
         CK(cudaEventRecord(e0, st));
     }
-    CK(launch_apply<R>(a, H->cfg, ntiles, st));
+    const bool split_nl = H->cfg.kernel == 0 && H->pj.natoms > 0;
+    if (split_nl) {
+        ApplyArgs<R> b = a;
+        b.nl_ptr = nullptr;
+        CK(launch_apply<R>(b, H->cfg, ntiles, st));
+    } else {
+        CK(launch_apply<R>(a, H->cfg, ntiles, st));
+    }
     if (H->prof) CK(cudaEventRecord(e1, st));
+    if (split_nl) {
+        CK(launch_proj_scatter<R>(a, H->pj.u_pts, H->pj.u_ptr, H->pj.nu, st));
+        H->n_launch++;
+    }
     // algorithmic bytes: read u, write out, optional base / acc (read+write),
     // the potential, and (with projectors) the per-point entry lists,
     // entry values and the coefficient block
     const double P = (double)m->P, row = 16.0 * SV;
     double bytes = P * row * (2.0 + (ep.base ? 1.0 : 0.0) + (ep.acc ? 2.0 : 0.0)) + P * sizeof(R);
-    if (H->pj.natoms > 0)
+    if (H->pj.natoms > 0 && !split_nl)
         bytes += 4.0 * (P + 1) + (double)H->pj.nq * (8.0 + H->pj.npmax * sizeof(R)) +
                  (double)H->pj.natoms * H->pj.npmax * row;
     H->n_stencil++;
@@ -536,7 +555,9 @@ rsg_status rsg_ham_create(rsg_mesh m, rsg_dtype dtype, rsg_ham *out) {
     rsg_ham H = new rsg_ham_s();
     H->m = m;
     H->dtype = dtype;
-    if (dtype == RSG_C128) H->cfg.rx = 2;
+    // complex128 is bound by FP64 arithmetic: the one-thread-per-value kernel
+    // does the least of it
+    if (dtype == RSG_C128) H->cfg.kernel = 1;
     *out = H;
     return RSG_OK;
 }
@@ -576,11 +597,12 @@ rsg_status rsg_ham_kernel_stats(rsg_ham H, double *kernel_ms, int64_t *kernel_la
 rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     if (!H || !key) return fail(RSG_ERR_ARG, "NULL argument");
     std::string k(key);
-    if (k == "kernel" && (value == 0 || value == 1)) H->cfg.kernel = (int)value;
+    if (k == "kernel" && (value >= 0 && value <= 2)) H->cfg.kernel = (int)value;
     else if (k == "rx" && (value == 1 || value == 2 || value == 4)) H->cfg.rx = (int)value;
-    else if (k == "ty" && (value == 1 || value == 2 || value == 4 || value == 8 || value == 16 || value == 32))
+    else if (k == "ty" && (value == 1 || value == 2 || value == 4 || value == 8 || value == 16))
         H->cfg.ty = (int)value;
-    else if (k == "zseg" && value >= 1 && value <= 4096) H->cfg.zseg = (int)value;
+    else if (k == "zseg" && value >= 1 && value <= 64) H->cfg.zseg = (int)value;
+    else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
     else return fail(RSG_ERR_ARG, "unknown option or value: %s=%lld", key, (long long)value);
     return RSG_OK;
 }
@@ -698,6 +720,14 @@ rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres, cons
     CK(H->hm.upload(hm));
     CK(H->nl_ptr.upload(nl_ptr));
     CK(H->nl_ent.upload(nl_ent));
+    std::vector<int32_t> u_pts, u_ptr(1, 0);
+    for (int64_t p = 0; p < P; p++)
+        if (nl_ptr[(size_t)p + 1] > nl_ptr[(size_t)p]) {
+            u_pts.push_back((int32_t)p);
+            u_ptr.push_back(nl_ptr[(size_t)p + 1]);
+        }
+    CK(H->u_pts.upload(u_pts));
+    CK(H->u_ptr.upload(u_ptr));
     ProjDev &pj = H->pj;
     pj.natoms = natoms;
     pj.npmax = npmax;
@@ -713,6 +743,9 @@ rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres, cons
     pj.hm = H->hm.as<double>();
     pj.nl_ptr = H->nl_ptr.as<int32_t>();
     pj.nl_ent = H->nl_ent.as<int32_t>();
+    pj.nu = (int)u_pts.size();
+    pj.u_pts = H->u_pts.as<int32_t>();
+    pj.u_ptr = H->u_ptr.as<int32_t>();
     return RSG_OK;
 }
 

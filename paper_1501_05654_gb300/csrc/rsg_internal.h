@@ -27,10 +27,12 @@ struct Tile {
 
 // Kernel tile configuration.
 struct TileCfg {
-    int kernel = 0;   // 0 z-march, 1 naive
-    int rx = 4;       // points per thread along x
-    int ty = 8;       // rows per tile (blockDim.z)
-    int zseg = 32;    // planes per z segment
+    int kernel = 0;   // 0 shared-memory staged, 1 naive, 2 L1 z-march
+    int rx = 1;       // points per thread along x
+    int ty = 16;      // rows per tile (blockDim.z)
+    int zseg = 64;    // planes per z segment
+    int cv = 4;       // staged kernel: 16-byte vectors per point in a chunk (1..8)
+    int stages = 4;   // staged kernel: shared-memory pipeline depth (4)
 };
 
 // Everything one H application needs, by value.  Pointers to the state
@@ -72,9 +74,13 @@ struct ProjDev {
     int32_t *atom_chunk0 = nullptr; // natoms+1 prefix of chunks per atom
     double *hm = nullptr;         // natoms * npmax * npmax (zero padded)
     int32_t *nl_ptr = nullptr, *nl_ent = nullptr;
+    int nu = 0;                    // points inside at least one sphere
+    int32_t *u_pts = nullptr, *u_ptr = nullptr;   // those points and their CSR rows
 };
 
 // ---- launchers (rsg_kernels.cu) ----
+// Block shape (cv x nxr x ty threads, tile TX = nxr * rx) of the staged kernel.
+void stage_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty);
 template <typename R>
 cudaError_t launch_apply(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles,
                          cudaStream_t st);
@@ -84,6 +90,10 @@ cudaError_t launch_proj_dot(const void *u, int SV, const ProjDev &pj, double *pa
 template <typename R>
 cudaError_t launch_proj_reduce(const double *partial, int SV, const ProjDev &pj,
                                double h3, void *D, cudaStream_t st);
+// out += alpha * (projector terms), acc += gamma * alpha * (same)
+template <typename R>
+cudaError_t launch_proj_scatter(const ApplyArgs<R> &a, const int32_t *upts, const int32_t *uptr,
+                                int nu, cudaStream_t st);
 
 // ---- linear algebra on state blocks (rsg_linalg.cu) ----
 // G (S x S complex double) = h3 * Psi^H Psi; partial needs nblk * S * S * 2 doubles.

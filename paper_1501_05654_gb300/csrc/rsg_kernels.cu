@@ -78,68 +78,104 @@ __device__ __forceinline__ Row load_row(const Row *rows, int y, int z, int ny, i
 }
 
 // --------------------------------------------------------- z-marching ---
+// Row entry packed for shared memory: start, xmin, xmax (xmin > xmax: empty).
+struct SRow {
+    int32_t start;
+    int16_t xmin, xmax;
+};
+
+constexpr int kMaxTY = 16, kMaxZseg = 64;
+constexpr int kSRows = (kMaxTY + 8) * (kMaxZseg + 8);
+
+// Branch-free read of vector v at bbox x of a row: out-of-row lanes load a
+// valid dummy address (point 0) and select zero, so every load of an
+// iteration can be in flight at once.
+template <typename R>
+__device__ __forceinline__ typename VT<R>::T srow_value(const typename VT<R>::T *in, const SRow &rw,
+                                                        int x, int SV, int v) {
+    const bool ok = (x >= rw.xmin) & (x <= rw.xmax);
+    const int64_t idx = ok ? (int64_t)rw.start + (x - rw.xmin) : 0;
+    const typename VT<R>::T val = VT<R>::ldg(in + idx * SV + v);
+    return ok ? val : VT<R>::zero();
+}
+
 template <typename R, int RX>
-__global__ void __launch_bounds__(256) k_apply_zmarch(const ApplyArgs<R> a) {
+__global__ void __launch_bounds__(256, (RX <= 2 ? 2 : 1)) k_apply_zmarch(const ApplyArgs<R> a) {
     using V = VT<R>;
     using T = typename V::T;
+    __shared__ SRow srows[kSRows];
     const Tile tl = a.tiles[blockIdx.x];
+    const int ny = a.ny, nz = a.nz, SV = a.SV;
+    const int TY = blockDim.z;
+    const int ybase = tl.ty * TY - 4, zbase = tl.zlo - 4;
+    const int nyr = TY + 8, nzr = tl.zhi - tl.zlo + 8;
+    // stage the rows this block touches: y in [ybase, ybase+nyr), z in [zbase, zbase+nzr)
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+    for (int i = tid; i < nyr * nzr; i += nthr) {
+        const int yy = ybase + i % nyr, zz = zbase + i / nyr;
+        SRow r{0, 1, 0};
+        if (yy >= 0 && yy < ny && zz >= 0 && zz < nz) {
+            const Row g = a.rows[(int64_t)zz * ny + yy];
+            r.start = g.start;
+            r.xmin = (int16_t)g.xmin;
+            r.xmax = (int16_t)g.xmax;
+        }
+        srows[i] = r;
+    }
+    __syncthreads();
     const int v = blockIdx.y * blockDim.x + threadIdx.x;
-    if (v >= a.SV) return;
+    if (v >= SV) return;
     const int x0 = (tl.tx * blockDim.y + threadIdx.y) * RX;
-    const int y = tl.ty * blockDim.z + threadIdx.z;
-    if (y >= a.ny || x0 >= a.nx) return;
+    const int y = tl.ty * TY + threadIdx.z;
+    if (y >= ny || x0 >= a.nx) return;
     const T *__restrict__ in = (const T *)a.in;
-    const int SV = a.SV, ny = a.ny, nz = a.nz;
-    const R w0 = a.w[0], w1 = a.w[1], w2 = a.w[2], w3 = a.w[3], w4 = a.w[4];
-    const R wk[5] = {w0, w1, w2, w3, w4};
+    const R wk[5] = {a.w[0], a.w[1], a.w[2], a.w[3], a.w[4]};
+    const int yo = threadIdx.z + 4;   // own row offset in the staged table
+    auto srow = [&](int dy, int z) -> const SRow & { return srows[(z - zbase) * nyr + yo + dy]; };
 
     T ring[9][RX];
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-        const Row rw = load_row(a.rows, y, tl.zlo - 4 + k, ny, nz);
+        const SRow rw = srow(0, tl.zlo - 4 + k);
 #pragma unroll
-        for (int r = 0; r < RX; r++) ring[k][r] = row_value<R>(in, rw, x0 + r, SV, v);
+        for (int r = 0; r < RX; r++) ring[k][r] = srow_value<R>(in, rw, x0 + r, SV, v);
     }
     for (int z = tl.zlo; z < tl.zhi; z++) {
         {
-            const Row rw = load_row(a.rows, y, z + 4, ny, nz);
+            const SRow rw = srow(0, z + 4);
 #pragma unroll
-            for (int r = 0; r < RX; r++) ring[8][r] = row_value<R>(in, rw, x0 + r, SV, v);
+            for (int r = 0; r < RX; r++) ring[8][r] = srow_value<R>(in, rw, x0 + r, SV, v);
         }
-        const Row rc = load_row(a.rows, y, z, ny, nz);
+        const SRow rc = srow(0, z);
         if (x0 + RX - 1 >= rc.xmin && x0 <= rc.xmax) {
             T acc[RX];
 #pragma unroll
             for (int r = 0; r < RX; r++) {
-                acc[r] = V::scale((R)3 * w0, ring[4][r]);
+                acc[r] = V::scale((R)3 * wk[0], ring[4][r]);
 #pragma unroll
                 for (int k = 1; k <= 4; k++) V::fma(acc[r], wk[k], V::add(ring[4 - k][r], ring[4 + k][r]));
             }
             // x neighbours: inside the run from the ring, outside from L1
-            T xl[4], xr[4];
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                xl[k] = row_value<R>(in, rc, x0 - 1 - k, SV, v);
-                xr[k] = row_value<R>(in, rc, x0 + RX + k, SV, v);
-            }
+            for (int k = 1; k <= 4; k++) {
 #pragma unroll
-            for (int r = 0; r < RX; r++) {
-#pragma unroll
-                for (int k = 1; k <= 4; k++) {
-                    const T left = (r - k >= 0) ? ring[4][(r - k) >= 0 ? r - k : 0] : xl[k - r - 1 >= 0 ? k - r - 1 : 0];
-                    const T right = (r + k < RX) ? ring[4][(r + k) < RX ? r + k : 0] : xr[(r + k - RX) >= 0 ? r + k - RX : 0];
+                for (int r = 0; r < RX; r++) {
+                    const T left = (r - k >= 0) ? ring[4][(r - k) >= 0 ? r - k : 0]
+                                                : srow_value<R>(in, rc, x0 + r - k, SV, v);
+                    const T right = (r + k < RX) ? ring[4][(r + k) < RX ? r + k : 0]
+                                                 : srow_value<R>(in, rc, x0 + r + k, SV, v);
                     V::fma(acc[r], wk[k], V::add(left, right));
                 }
             }
             // y neighbours
 #pragma unroll
             for (int k = 1; k <= 4; k++) {
-                const Row ra = load_row(a.rows, y - k, z, ny, nz);
-                const Row rb = load_row(a.rows, y + k, z, ny, nz);
+                const SRow ra = srow(-k, z), rb = srow(k, z);
 #pragma unroll
                 for (int r = 0; r < RX; r++)
-                    V::fma(acc[r], wk[k], V::add(row_value<R>(in, ra, x0 + r, SV, v),
-                                                 row_value<R>(in, rb, x0 + r, SV, v)));
+                    V::fma(acc[r], wk[k], V::add(srow_value<R>(in, ra, x0 + r, SV, v),
+                                                 srow_value<R>(in, rb, x0 + r, SV, v)));
             }
 #pragma unroll
             for (int r = 0; r < RX; r++) {
@@ -157,6 +193,297 @@ __global__ void __launch_bounds__(256) k_apply_zmarch(const ApplyArgs<R> a) {
     }
 }
 
+// ------------------------------------------------- shared-memory staged ---
+// k_apply_staged: a block owns a TX x TY tile of one state chunk (CV 16-byte
+// vectors per point) and streams the planes z = zlo-4 .. zhi+3 of the tile
+// plus a 4-point halo in x and y through an NS-deep ring of shared-memory
+// slots filled with cp.async (ghost points are zero-filled by the copy).
+// When plane p has landed, every thread adds plane p's contributions to a
+// register queue of nine pending outputs p-4 .. p+4 (z part: w_|k| c_p to
+// output p+k; x/y part and the diagonal to output p), then retires output
+// p-4 through the epilogue.  The queue rotates by renaming (the plane loop
+// is unrolled nine times), so no values move between registers.  Each state
+// value crosses L2 -> shared memory once per tile (plus the halo); all
+// neighbour reads are fixed-offset shared-memory loads; all offsets are
+// 32-bit (the host checks P * SV < 2^31).
+__device__ __forceinline__ void cp_async16(unsigned smem_addr, const void *gmem, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr), "l"(gmem),
+                 "r"(src_bytes)
+                 : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(unsigned smem_addr, const void *gmem, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_addr), "l"(gmem),
+                 "n"(BYTES), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Epilogue of the staged kernel: y = alpha * acc + beta * base (base already
+// in registers), out = y, optional acc += gamma * y.  Projector terms are
+// added afterwards by k_proj_scatter.
+template <typename R>
+__device__ __forceinline__ void finish_staged(const ApplyArgs<R> &a, int o, typename VT<R>::T acc,
+                                              const typename VT<R>::T &base) {
+    using V = VT<R>;
+    using T = typename V::T;
+    T y0 = V::cmul(a.ar, a.ai, acc);
+    if (a.base != nullptr) V::cfma(y0, a.br, a.bi, base);
+    ((T *)a.out)[o] = y0;
+    if (a.acc != nullptr) {
+        T s = ((T *)a.acc)[o];
+        V::cfma(s, a.gr, a.gi, y0);
+        ((T *)a.acc)[o] = s;
+    }
+}
+
+template <typename R, int CV, int RX>
+struct StageCtx {
+    using T = typename VT<R>::T;
+    const ApplyArgs<R> *a;
+    const SRow *srows;
+    const T *slots;
+    const T *bslots;     // per thread: base of its outputs, NS slots x nthr x RX
+    const R *vslots;     // per thread: V of its columns, NS slots x nthr x RX
+    int tid, nthr;
+    int WX, WY, slot_elems;
+    int xr, yi, cv, v, y, x0;    // thread's tile coordinates and first global x
+    int zbase, zlo, zhi;
+    R w0, w1, w2, w3, w4;
+};
+
+// Plane j has landed in its slot: add its contributions, retire output p-4.
+// Queue slot of output p + (k - 4) is (k + PH) % 9.
+template <typename R, int CV, int RX, int NS, int PH>
+__device__ __forceinline__ void stage_plane(const StageCtx<R, CV, RX> &c, int j,
+                                            typename VT<R>::T (&q)[9][RX]) {
+    using V = VT<R>;
+    using T = typename V::T;
+    constexpr int Q0 = (0 + PH) % 9, Q1 = (1 + PH) % 9, Q2 = (2 + PH) % 9, Q3 = (3 + PH) % 9;
+    constexpr int Q4 = (4 + PH) % 9, Q5 = (5 + PH) % 9, Q6 = (6 + PH) % 9, Q7 = (7 + PH) % 9;
+    constexpr int Q8 = (8 + PH) % 9;
+    const ApplyArgs<R> &a = *c.a;
+    const T *sl = c.slots + (j % NS) * c.slot_elems;
+    const int p = c.zbase + j;
+    const int WX = c.WX;
+    const T *ctr = sl + ((c.yi + 4) * WX + c.xr * RX + 4) * CV + c.cv;
+#pragma unroll
+    for (int r = 0; r < RX; r++) {
+        const T *cp = ctr + r * CV;
+        const T cval = cp[0];
+        V::fma(q[Q3][r], c.w1, cval);
+        V::fma(q[Q5][r], c.w1, cval);
+        V::fma(q[Q2][r], c.w2, cval);
+        V::fma(q[Q6][r], c.w2, cval);
+        V::fma(q[Q1][r], c.w3, cval);
+        V::fma(q[Q7][r], c.w3, cval);
+        V::fma(q[Q0][r], c.w4, cval);
+        V::fma(q[Q8][r], c.w4, cval);
+        T s = V::scale((R)3 * c.w0, cval);
+        const int rs = WX * CV;
+        V::fma(s, c.w1, V::add(V::add(cp[-CV], cp[CV]), V::add(cp[-rs], cp[rs])));
+        V::fma(s, c.w2, V::add(V::add(cp[-2 * CV], cp[2 * CV]), V::add(cp[-2 * rs], cp[2 * rs])));
+        V::fma(s, c.w3, V::add(V::add(cp[-3 * CV], cp[3 * CV]), V::add(cp[-3 * rs], cp[3 * rs])));
+        V::fma(s, c.w4, V::add(V::add(cp[-4 * CV], cp[4 * CV]), V::add(cp[-4 * rs], cp[4 * rs])));
+        // diagonal: staged V (zero outside the mesh, where c is zero too)
+        const int x = c.x0 + r;
+        const R diag = c.vslots[((j % NS) * c.nthr + c.tid) * RX + r] + a.f0 + a.fx * (R)x +
+                       a.fy * (R)c.y + a.fz * (R)p;
+        V::fma(s, diag, cval);
+        q[Q4][r] = V::add(q[Q4][r], s);
+    }
+    const int zo = p - 4;
+    if (zo >= c.zlo && zo < c.zhi && c.v < a.SV) {
+        const SRow ro = c.srows[(j - 4) * c.WY + c.yi + 4];
+#pragma unroll
+        for (int r = 0; r < RX; r++) {
+            const int x = c.x0 + r;
+            if (x >= ro.xmin && x <= ro.xmax) {
+                const int idx = ro.start + (x - ro.xmin);
+                finish_staged<R>(a, idx * a.SV + c.v, q[Q0][r],
+                                 c.bslots[((j % NS) * c.nthr + c.tid) * RX + r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RX; r++) q[Q0][r] = V::zero();
+}
+
+template <typename R, int CV, int RX, int NS>
+__global__ void __launch_bounds__(512, 1) k_apply_staged(const ApplyArgs<R> a, int nchunks) {
+    using V = VT<R>;
+    using T = typename V::T;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ SRow srows[kSRows];
+    const int NXR = blockDim.y, TY = blockDim.z;
+    const int TX = NXR * RX, WX = TX + 8, WY = TY + 8;
+    const int chunk = blockIdx.x % nchunks;
+    const Tile tl = a.tiles[blockIdx.x / nchunks];
+    const int ny = a.ny, nz = a.nz, SV = a.SV;
+    const int xbase = tl.tx * TX - 4, ybase = tl.ty * TY - 4, zbase = tl.zlo - 4;
+    const int nzr = tl.zhi - tl.zlo + 8;
+    const int nthr = CV * NXR * TY;
+    const int tid = (threadIdx.z * NXR + threadIdx.y) * CV + threadIdx.x;
+    for (int i = tid; i < WY * nzr; i += nthr) {
+        const int zz = i / WY;
+        const int yy = ybase + (i - zz * WY);
+        const int zg = zbase + zz;
+        SRow r{0, 1, 0};
+        if (yy >= 0 && yy < ny && zg >= 0 && zg < nz) {
+            const Row g = a.rows[zg * ny + yy];
+            r.start = g.start;
+            r.xmin = (int16_t)g.xmin;
+            r.xmax = (int16_t)g.xmax;
+        }
+        srows[i] = r;
+    }
+    __syncthreads();
+    T *slots = (T *)smraw;
+    const int slot_elems = WY * WX * CV;
+    T *bslots = slots + NS * slot_elems;                        // NS x nthr x RX
+    R *vslots = (R *)(bslots + NS * nthr * RX);                 // NS x nthr x RX
+    const T *__restrict__ in = (const T *)a.in;
+    const int cvl = threadIdx.x;
+    const int v = chunk * CV + cvl;
+    const bool vok = v < SV;
+    const int yown = threadIdx.z + 4;
+    const int x0own = tl.tx * TX + threadIdx.y * RX;
+    const unsigned bsh = (unsigned)__cvta_generic_to_shared(bslots);
+    const unsigned vsh = (unsigned)__cvta_generic_to_shared(vslots);
+    const T *__restrict__ basep = (const T *)a.base;
+    // own-point data that travels with plane j: V at plane j (diagonal on
+    // arrival) and the base values of the outputs retired at plane j (j - 4)
+    auto stage_epi = [&](int j) {
+        const int sl = j % NS;
+        const SRow rj = srows[j * WY + yown];
+#pragma unroll
+        for (int r = 0; r < RX; r++) {
+            const int x = x0own + r;
+            const bool ok = (x >= rj.xmin) & (x <= rj.xmax);
+            const int idx = ok ? rj.start + (x - rj.xmin) : 0;
+            cp_async_small<sizeof(R)>(vsh + (unsigned)(((sl * nthr + tid) * RX + r) * sizeof(R)),
+                                      a.V + idx, ok ? (int)sizeof(R) : 0);
+        }
+        if (basep != nullptr && j >= 4) {
+            const SRow ro = srows[(j - 4) * WY + yown];
+#pragma unroll
+            for (int r = 0; r < RX; r++) {
+                const int x = x0own + r;
+                const bool ok = (x >= ro.xmin) & (x <= ro.xmax) & vok;
+                const int o = ok ? (ro.start + (x - ro.xmin)) * SV + v : 0;
+                cp_async16(bsh + (unsigned)(((sl * nthr + tid) * RX + r) * 16), basep + o, ok ? 16 : 0);
+            }
+        }
+    };
+
+    // staging assignment: this thread copies points pi = tid / CV + m * step
+    // of the (WY x WX) slot, vector cvl; (yy, xx) advance incrementally
+    const int step = nthr / CV;
+    const int sy = step / WX, sx = step - sy * WX;
+    const int pi0 = tid / CV;
+    const int yy0 = pi0 / WX, xx0 = pi0 - yy0 * WX;
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(slots);
+    auto stage = [&](int j) {
+        stage_epi(j);
+        const unsigned dst0 = sbase + (unsigned)(((j % NS) * slot_elems + pi0 * CV + cvl) * 16);
+        const SRow *rr = srows + j * WY;
+        int yy = yy0, xx = xx0;
+        unsigned dst = dst0;
+        for (int pi = pi0; pi < WY * WX; pi += step) {
+            const SRow rw = rr[yy];
+            const int x = xbase + xx;
+            const bool ok = (x >= rw.xmin) & (x <= rw.xmax) & vok;
+            const int off = ok ? (rw.start + (x - rw.xmin)) * SV + v : 0;
+            cp_async16(dst, in + off, ok ? 16 : 0);
+            dst += step * CV * 16;
+            xx += sx;
+            yy += sy;
+            if (xx >= WX) {
+                xx -= WX;
+                yy++;
+            }
+        }
+    };
+
+    StageCtx<R, CV, RX> c;
+    c.a = &a;
+    c.srows = srows;
+    c.slots = slots;
+    c.bslots = bslots;
+    c.vslots = vslots;
+    c.tid = tid;
+    c.nthr = nthr;
+    c.WX = WX;
+    c.WY = WY;
+    c.slot_elems = slot_elems;
+    c.xr = threadIdx.y;
+    c.yi = threadIdx.z;
+    c.cv = cvl;
+    c.v = v;
+    c.y = tl.ty * TY + threadIdx.z;
+    c.x0 = tl.tx * TX + threadIdx.y * RX;
+    c.zbase = zbase;
+    c.zlo = tl.zlo;
+    c.zhi = tl.zhi;
+    c.w0 = a.w[0];
+    c.w1 = a.w[1];
+    c.w2 = a.w[2];
+    c.w3 = a.w[3];
+    c.w4 = a.w[4];
+    T q[9][RX];
+#pragma unroll
+    for (int k = 0; k < 9; k++)
+#pragma unroll
+        for (int r = 0; r < RX; r++) q[k][r] = V::zero();
+
+    const int np = nzr;
+#pragma unroll 1
+    for (int j = 0; j < NS - 1; j++) {
+        if (j < np) stage(j);
+        cp_async_commit();
+    }
+    auto pre = [&](int j) {
+        if (j + NS - 1 < np) stage(j + NS - 1);
+        cp_async_commit();
+        cp_async_wait<NS - 1>();
+        __syncthreads();
+    };
+    int j = 0;
+#pragma unroll 1
+    for (; j + 9 <= np; j += 9) {
+        pre(j + 0); stage_plane<R, CV, RX, NS, 0>(c, j + 0, q); __syncthreads();
+        pre(j + 1); stage_plane<R, CV, RX, NS, 1>(c, j + 1, q); __syncthreads();
+        pre(j + 2); stage_plane<R, CV, RX, NS, 2>(c, j + 2, q); __syncthreads();
+        pre(j + 3); stage_plane<R, CV, RX, NS, 3>(c, j + 3, q); __syncthreads();
+        pre(j + 4); stage_plane<R, CV, RX, NS, 4>(c, j + 4, q); __syncthreads();
+        pre(j + 5); stage_plane<R, CV, RX, NS, 5>(c, j + 5, q); __syncthreads();
+        pre(j + 6); stage_plane<R, CV, RX, NS, 6>(c, j + 6, q); __syncthreads();
+        pre(j + 7); stage_plane<R, CV, RX, NS, 7>(c, j + 7, q); __syncthreads();
+        pre(j + 8); stage_plane<R, CV, RX, NS, 8>(c, j + 8, q); __syncthreads();
+    }
+#pragma unroll 1
+    for (; j < np; j++) {
+        pre(j);
+        switch (j % 9) {
+        case 0: stage_plane<R, CV, RX, NS, 0>(c, j, q); break;
+        case 1: stage_plane<R, CV, RX, NS, 1>(c, j, q); break;
+        case 2: stage_plane<R, CV, RX, NS, 2>(c, j, q); break;
+        case 3: stage_plane<R, CV, RX, NS, 3>(c, j, q); break;
+        case 4: stage_plane<R, CV, RX, NS, 4>(c, j, q); break;
+        case 5: stage_plane<R, CV, RX, NS, 5>(c, j, q); break;
+        case 6: stage_plane<R, CV, RX, NS, 6>(c, j, q); break;
+        case 7: stage_plane<R, CV, RX, NS, 7>(c, j, q); break;
+        default: stage_plane<R, CV, RX, NS, 8>(c, j, q); break;
+        }
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+}
+
 // --------------------------------------------------------------- naive ---
 template <typename R>
 __global__ void __launch_bounds__(256) k_apply_naive(const ApplyArgs<R> a) {
@@ -168,9 +495,9 @@ __global__ void __launch_bounds__(256) k_apply_naive(const ApplyArgs<R> a) {
     const Row rc = a.rows[row];
     if (rc.xmin > rc.xmax) return;
     const T *__restrict__ in = (const T *)a.in;
-    const int64_t n = (int64_t)(rc.xmax - rc.xmin + 1) * SV;
-    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
-        const int xo = (int)(t / SV), v = (int)(t % SV);
+    const int n = (rc.xmax - rc.xmin + 1) * SV;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int xo = t / SV, v = t - xo * SV;
         const int x = rc.xmin + xo;
         const int64_t idx = (int64_t)rc.start + xo;
         const T c = V::ldg(in + idx * SV + v);
@@ -193,25 +520,96 @@ static inline int pow2_at_least(int v) {
     return p;
 }
 
+#ifndef RSG_ONLY_DOUBLE
+// Block shape of the staged kernel for SV vectors per point (shared with the
+// host's tile builder through stage_shape()).
+void stage_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
+    int v = 1;
+    while (v < SV && v < c.cv) v <<= 1;
+    *cv = v;
+    int t = c.ty;
+    while (v * t > 512) t >>= 1;
+    *ty = t;
+    // widest tile of at most 512 threads whose pipeline fits 200 KB of shared memory
+    const int rx = 1;
+    int n = 512 / (v * t);
+    while (n > 1 && (size_t)c.stages * ((t + 8) * (n * rx + 8) * v * 16 + (size_t)v * n * t * rx * 24) >
+                        200 * 1024)
+        n >>= 1;
+    *nxr = n;
+}
+
+size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes) {
+    int cv, nxr, ty;
+    stage_shape(c, SV, &cv, &nxr, &ty);
+    const int rx = 1;   // the staged kernel runs one point per thread along x
+    const size_t nthr = (size_t)cv * nxr * ty;
+    return (size_t)c.stages * ((ty + 8) * (nxr * rx + 8) * cv * vec_bytes +
+                               nthr * rx * (vec_bytes + vec_bytes / 2));
+}
+#else
+size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes);
+#endif
+
+template <typename R, int CV, int RX, int NS>
+static cudaError_t launch_staged_t(const ApplyArgs<R> &a, dim3 block, unsigned nblk, size_t smem,
+                                   int nchunks, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_apply_staged<R, CV, RX, NS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_apply_staged<R, CV, RX, NS><<<nblk, block, smem, st>>>(a, nchunks);
+    return cudaGetLastError();
+}
+
+template <typename R, int CV, int NS>
+static cudaError_t launch_staged_rx(const ApplyArgs<R> &a, int rx, dim3 block, unsigned nblk,
+                                    size_t smem, int nchunks, cudaStream_t st) {
+    (void)rx;   // one point per thread along x: wider runs spill at 128 registers
+    return launch_staged_t<R, CV, 1, NS>(a, block, nblk, smem, nchunks, st);
+}
+
+template <typename R, int NS>
+static cudaError_t launch_staged_cv(const ApplyArgs<R> &a, int cv, int rx, dim3 block, unsigned nblk,
+                                    size_t smem, int nchunks, cudaStream_t st) {
+    switch (cv) {
+    case 1: return launch_staged_rx<R, 1, NS>(a, rx, block, nblk, smem, nchunks, st);
+    case 2: return launch_staged_rx<R, 2, NS>(a, rx, block, nblk, smem, nchunks, st);
+    case 4: return launch_staged_rx<R, 4, NS>(a, rx, block, nblk, smem, nchunks, st);
+    default: return launch_staged_rx<R, 8, NS>(a, rx, block, nblk, smem, nchunks, st);
+    }
+}
+
 template <typename R>
 cudaError_t launch_apply(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, cudaStream_t st) {
     if (cfg.kernel == 1) {
         k_apply_naive<R><<<a.ny * a.nz, 256, 0, st>>>(a);
         return cudaGetLastError();
     }
-    const int cv = pow2_at_least(a.SV) < 8 ? pow2_at_least(a.SV) : 8;
-    int ty = cfg.ty;
-    while (cv * ty > 256) ty >>= 1;
-    const int nxr = 256 / (cv * ty);
-    dim3 block(cv, nxr, ty);
-    dim3 grid(ntiles, (a.SV + cv - 1) / cv);
     if (ntiles == 0) return cudaSuccess;
-    switch (cfg.rx) {
-    case 1: k_apply_zmarch<R, 1><<<grid, block, 0, st>>>(a); break;
-    case 2: k_apply_zmarch<R, 2><<<grid, block, 0, st>>>(a); break;
-    default: k_apply_zmarch<R, 4><<<grid, block, 0, st>>>(a); break;
+    if (cfg.kernel == 2) {
+        const int cv = pow2_at_least(a.SV) < 8 ? pow2_at_least(a.SV) : 8;
+        int ty = cfg.ty;
+        while (cv * ty > 256) ty >>= 1;
+        const int nxr = 256 / (cv * ty);
+        dim3 block(cv, nxr, ty);
+        dim3 grid(ntiles, (a.SV + cv - 1) / cv);
+        switch (cfg.rx) {
+        case 1: k_apply_zmarch<R, 1><<<grid, block, 0, st>>>(a); break;
+        case 2: k_apply_zmarch<R, 2><<<grid, block, 0, st>>>(a); break;
+        default: k_apply_zmarch<R, 4><<<grid, block, 0, st>>>(a); break;
+        }
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+    int cv, nxr, ty;
+    stage_shape(cfg, a.SV, &cv, &nxr, &ty);
+    const int nchunks = (a.SV + cv - 1) / cv;
+    const size_t smem = stage_smem_bytes(cfg, a.SV, sizeof(typename VT<R>::T));
+    if (smem + sizeof(SRow) * kSRows > 227 * 1024) return cudaErrorInvalidConfiguration;
+    dim3 block(cv, nxr, ty);
+    const long long nblk = (long long)ntiles * nchunks;
+    if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if ((long long)a.P * a.SV >= 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    return launch_staged_cv<R, 4>(a, cv, cfg.rx, block, (unsigned)nblk, smem, nchunks, st);
 }
 
 // ---------------------------------------------------------- projectors ---
@@ -316,6 +714,52 @@ __global__ void k_proj_reduce(const double *__restrict__ partial, int SV, int na
     }
 }
 
+// Projector terms of H u added to an already written result:
+//     out[p, v] += alpha * sum_{entries (a, q) at p} sum_i p_ai(q) D[a, i, v]
+//     acc[p, v] += gamma * alpha * (same)            (when acc is used)
+// one thread per (union point, vector); the union points and their entry
+// lists come from the point-centric CSR, so there are no atomics.
+template <typename R>
+__global__ void __launch_bounds__(256) k_proj_scatter(const ApplyArgs<R> a, const int32_t *__restrict__ upts,
+                                                      const int32_t *__restrict__ uptr, int nu) {
+    using V = VT<R>;
+    using T = typename V::T;
+    const int u = blockIdx.x * blockDim.y + threadIdx.y;
+    if (u >= nu) return;
+    const int p = upts[u];
+    const int e0 = uptr[u], e1 = uptr[u + 1];
+    const T *D = (const T *)a.D;
+    for (int v = threadIdx.x; v < a.SV; v += blockDim.x) {
+        T sum = V::zero();
+        for (int e = e0; e < e1; e++) {
+            const int q = a.nl_ent[e];
+            const int at = a.q_atom[q];
+            const R *pv = a.q_p + q * a.npmax;
+            const T *Da = D + at * a.npmax * a.SV + v;
+            for (int i = 0; i < a.npmax; i++) V::fma(sum, pv[i], Da[i * a.SV]);
+        }
+        const int o = p * a.SV + v;
+        const T y = V::cmul(a.ar, a.ai, sum);
+        T *out = (T *)a.out;
+        out[o] = V::add(out[o], y);
+        if (a.acc != nullptr) {
+            T s = ((T *)a.acc)[o];
+            V::cfma(s, a.gr, a.gi, y);
+            ((T *)a.acc)[o] = s;
+        }
+    }
+}
+
+template <typename R>
+cudaError_t launch_proj_scatter(const ApplyArgs<R> &a, const int32_t *upts, const int32_t *uptr, int nu,
+                                cudaStream_t st) {
+    if (nu == 0) return cudaSuccess;
+    const int bx = a.SV < 32 ? a.SV : 32;
+    const int by = 256 / bx;
+    k_proj_scatter<R><<<(nu + by - 1) / by, dim3(bx, by), 0, st>>>(a, upts, uptr, nu);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_proj_reduce(const double *partial, int SV, const ProjDev &pj, double h3,
                                void *D, cudaStream_t st) {
@@ -326,11 +770,17 @@ cudaError_t launch_proj_reduce(const double *partial, int SV, const ProjDev &pj,
     return cudaGetLastError();
 }
 
+#ifndef RSG_ONLY_DOUBLE
 template cudaError_t launch_apply<float>(const ApplyArgs<float> &, const TileCfg &, int, cudaStream_t);
-template cudaError_t launch_apply<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t);
 template cudaError_t launch_proj_dot<float>(const void *, int, const ProjDev &, double *, cudaStream_t);
-template cudaError_t launch_proj_dot<double>(const void *, int, const ProjDev &, double *, cudaStream_t);
 template cudaError_t launch_proj_reduce<float>(const double *, int, const ProjDev &, double, void *, cudaStream_t);
+template cudaError_t launch_proj_scatter<float>(const ApplyArgs<float> &, const int32_t *, const int32_t *, int, cudaStream_t);
+#endif
+#ifndef RSG_ONLY_FLOAT
+template cudaError_t launch_apply<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t);
+template cudaError_t launch_proj_dot<double>(const void *, int, const ProjDev &, double *, cudaStream_t);
 template cudaError_t launch_proj_reduce<double>(const double *, int, const ProjDev &, double, void *, cudaStream_t);
+template cudaError_t launch_proj_scatter<double>(const ApplyArgs<double> &, const int32_t *, const int32_t *, int, cudaStream_t);
+#endif
 
 }  // namespace rsg

@@ -55,9 +55,12 @@ def test_box_odd_extents(dtype):
     _check_apply(p, g, 4, eps=-0.02, dir=(0.0, 0.0, 1.0))
 
 
-@pytest.mark.parametrize("opts", [{"kernel": 1}, {"rx": 1}, {"rx": 2}, {"rx": 4},
-                                  {"ty": 2, "zseg": 5}, {"ty": 16, "zseg": 1000},
-                                  {"ty": 4, "rx": 4, "zseg": 3}])
+@pytest.mark.parametrize("opts", [{"kernel": 1}, {"kernel": 0, "rx": 1}, {"kernel": 0, "rx": 2},
+                                  {"kernel": 0, "ty": 2, "zseg": 5},
+                                  {"kernel": 0, "ty": 16, "zseg": 64, "rx": 1},
+                                  {"kernel": 2, "rx": 1}, {"kernel": 2, "rx": 2},
+                                  {"kernel": 2, "rx": 4}, {"kernel": 2, "ty": 2, "zseg": 5},
+                                  {"kernel": 2, "ty": 4, "rx": 4, "zseg": 3}])
 def test_kernel_variants_agree(opts):
     p, g = wells_system("sphere", radius=3.3, h=0.25, dtype=torch.complex64, seed=7, natoms=2)
     _check_apply(p, g, 10, opts=opts)
