@@ -184,7 +184,7 @@ rsg_status rsg_batch_destroy(rsg_batch b);
 /* Tuning knobs (kernel tile shapes); unknown keys give RSG_ERR_ARG.
  * Keys: "kernel" (0 = shared-memory staged z-march, 1 = one thread per
  * point and vector, 2 = z-march through L1), "rx" (points per thread along
- * x: 1, 2 or 4; the staged kernel always uses 1), "ty" (rows per
+ * x: 1, 2 or 4; the staged kernel uses 1 or 2), "ty" (rows per
  * tile: 1, 2, 4, 8 or 16), "zseg" (planes per z segment, 1..64), "cv"
  * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8).
  * A shape whose shared memory does not fit the SM fails with RSG_ERR_CUDA. */

@@ -313,8 +313,15 @@ __device__ __forceinline__ void stage_plane(const StageCtx<R, CV, RX> &c, int j,
     for (int r = 0; r < RX; r++) q[Q0][r] = V::zero();
 }
 
+// Threads per block: 512 for one point per thread along x, 384 for two (the
+// nine-deep queue of two points needs up to 170 registers).
+template <int RX>
+struct StagedThreads {
+    static constexpr int value = RX == 1 ? 512 : 384;
+};
+
 template <typename R, int CV, int RX, int NS>
-__global__ void __launch_bounds__(512, 1) k_apply_staged(const ApplyArgs<R> a, int nchunks) {
+__global__ void __launch_bounds__(StagedThreads<RX>::value, 1) k_apply_staged(const ApplyArgs<R> a, int nchunks) {
     using V = VT<R>;
     using T = typename V::T;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -527,12 +534,13 @@ void stage_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
     int v = 1;
     while (v < SV && v < c.cv) v <<= 1;
     *cv = v;
+    const int rx = c.rx >= 2 ? 2 : 1;
+    const int nthr = rx == 1 ? 512 : 384;
     int t = c.ty;
-    while (v * t > 512) t >>= 1;
+    while (v * t > nthr / 2 && t > 1) t >>= 1;
     *ty = t;
-    // widest tile of at most 512 threads whose pipeline fits 200 KB of shared memory
-    const int rx = 1;
-    int n = 512 / (v * t);
+    // widest tile of nthr threads whose pipeline fits 200 KB of shared memory
+    int n = nthr / (v * t);
     while (n > 1 && (size_t)c.stages * ((t + 8) * (n * rx + 8) * v * 16 + (size_t)v * n * t * rx * 24) >
                         200 * 1024)
         n >>= 1;
@@ -542,7 +550,7 @@ void stage_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
 size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes) {
     int cv, nxr, ty;
     stage_shape(c, SV, &cv, &nxr, &ty);
-    const int rx = 1;   // the staged kernel runs one point per thread along x
+    const int rx = c.rx >= 2 ? 2 : 1;
     const size_t nthr = (size_t)cv * nxr * ty;
     return (size_t)c.stages * ((ty + 8) * (nxr * rx + 8) * cv * vec_bytes +
                                nthr * rx * (vec_bytes + vec_bytes / 2));
@@ -564,8 +572,8 @@ static cudaError_t launch_staged_t(const ApplyArgs<R> &a, dim3 block, unsigned n
 template <typename R, int CV, int NS>
 static cudaError_t launch_staged_rx(const ApplyArgs<R> &a, int rx, dim3 block, unsigned nblk,
                                     size_t smem, int nchunks, cudaStream_t st) {
-    (void)rx;   // one point per thread along x: wider runs spill at 128 registers
-    return launch_staged_t<R, CV, 1, NS>(a, block, nblk, smem, nchunks, st);
+    return rx >= 2 ? launch_staged_t<R, CV, 2, NS>(a, block, nblk, smem, nchunks, st)
+                   : launch_staged_t<R, CV, 1, NS>(a, block, nblk, smem, nchunks, st);
 }
 
 template <typename R, int NS>

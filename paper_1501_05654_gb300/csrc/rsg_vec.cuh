@@ -13,23 +13,54 @@ namespace rsg {
 template <typename R>
 struct VT;
 
+// Packed FP32x2 arithmetic (Blackwell): one instruction on two floats, with
+// the same round-to-nearest result as two scalar operations.
+union F2U {
+    float2 f;
+    unsigned long long u;
+};
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    F2U x, y, z, d;
+    x.f = a;
+    y.f = b;
+    z.f = c;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.u) : "l"(x.u), "l"(y.u), "l"(z.u));
+    return d.f;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+    F2U x, y, d;
+    x.f = a;
+    y.f = b;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.u) : "l"(x.u), "l"(y.u));
+    return d.f;
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    F2U x, y, d;
+    x.f = a;
+    y.f = b;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.u) : "l"(x.u), "l"(y.u));
+    return d.f;
+}
+
 template <>
 struct VT<float> {
     using T = float4;
     static constexpr int NC = 2;   // complex values per vector
+    __device__ __forceinline__ static float2 lo(const T &a) { return make_float2(a.x, a.y); }
+    __device__ __forceinline__ static float2 hi(const T &a) { return make_float2(a.z, a.w); }
+    __device__ __forceinline__ static T join(float2 l, float2 h) { return make_float4(l.x, l.y, h.x, h.y); }
     __device__ __forceinline__ static T zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
     __device__ __forceinline__ static T ldg(const T *p) { return __ldg(p); }
     __device__ __forceinline__ static void fma(T &acc, float w, const T &x) {
-        acc.x = fmaf(w, x.x, acc.x);
-        acc.y = fmaf(w, x.y, acc.y);
-        acc.z = fmaf(w, x.z, acc.z);
-        acc.w = fmaf(w, x.w, acc.w);
+        const float2 ww = make_float2(w, w);
+        acc = join(f2_fma(ww, lo(x), lo(acc)), f2_fma(ww, hi(x), hi(acc)));
     }
     __device__ __forceinline__ static T add(const T &a, const T &b) {
-        return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+        return join(f2_add(lo(a), lo(b)), f2_add(hi(a), hi(b)));
     }
     __device__ __forceinline__ static T scale(float w, const T &a) {
-        return make_float4(w * a.x, w * a.y, w * a.z, w * a.w);
+        const float2 ww = make_float2(w, w);
+        return join(f2_mul(ww, lo(a)), f2_mul(ww, hi(a)));
     }
     // (ar + i ai) * a, per complex component
     __device__ __forceinline__ static T cmul(float ar, float ai, const T &a) {
