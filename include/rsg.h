@@ -152,6 +152,24 @@ rsg_status rsg_orthonormalize(rsg_ham H, void *psi, int64_t S, int64_t ld,
 rsg_status rsg_state_norms(rsg_ham H, const void *psi, int64_t S, int64_t ld,
                            double *norms2_out, void *stream);
 
+/* Allocation-free variant of rsg_state_norms.  The paper has no counterpart:
+ * this is an interface for callers that cannot let the library allocate
+ * device memory -- code whose memory belongs to another allocator (a
+ * framework's caching allocator or a fixed pool that accounts for every
+ * byte) and latency-critical loops where cudaMalloc/cudaFree would
+ * synchronise the whole device.  Writes <psi_s|psi_s> (FP64) for S states to
+ * norms2_dev (DEVICE array of S doubles, caller-owned, 8-byte aligned);
+ * asynchronous on stream.  The partial sums live in one fixed 128 KiB device
+ * array inside the library, which every GPU that loads the library holds
+ * until the process exits; hence S <= 128 (larger S: RSG_ERR_UNSUPPORTED).
+ * No cudaMalloc, cudaFree or allocating library routine is called.  All
+ * calls share that array: calls that can overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.  The first
+ * call on each device looks up the array's device address with that device
+ * current; make that first call before any stream capture. */
+rsg_status rsg_state_norms_noalloc(rsg_ham H, const void *psi, int64_t S, int64_t ld,
+                                   double *norms2_dev, void *stream);
+
 /* Quantum-optimal-control gradient (Sec. "Quantum optimal control",
  * Eq. (qoctgradient) and the costate equations), discrete adjoint of the
  * propagator above for ONE state: J = |<target|psi(T)>|^2 with psi(0) =

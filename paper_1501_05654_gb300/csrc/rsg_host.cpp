@@ -476,6 +476,15 @@ const int kChunk = 512;   // sphere entries per projector-dot block
 
 }  // namespace
 
+namespace rsg {
+void ham_info(rsg_ham H, rsg_dtype *dtype, int64_t *P, double *spacing) {
+    *dtype = H->dtype;
+    *P = H->m->P;
+    *spacing = H->m->h;
+}
+rsg_status set_error(rsg_status s, const char *msg) { return fail(s, "%s", msg); }
+}  // namespace rsg
+
 // ===================================================================== ABI
 
 extern "C" {

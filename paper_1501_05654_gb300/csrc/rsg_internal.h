@@ -137,4 +137,9 @@ cudaError_t launch_scale_dev(const void *x, void *y, int64_t n, const double *a,
 cudaError_t launch_grad_accum(const double *M, double tau, double *grad_k,
                               cudaStream_t st);
 
+// Host-side accessors for code outside rsg_host.cpp: the Hamiltonian's
+// compute type, point count and spacing, and the thread-local error message.
+void ham_info(rsg_ham H, rsg_dtype *dtype, int64_t *P, double *spacing);
+rsg_status set_error(rsg_status s, const char *msg);
+
 }  // namespace rsg

@@ -44,6 +44,7 @@ SIGNATURES = {
     "rsg_propagate_steps": [_vp, _vp, _i64, _i64, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp],
     "rsg_orthonormalize": [_vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_state_norms": [_vp, _vp, _i64, _i64, _vp, _vp],
+    "rsg_state_norms_noalloc": [_vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_control_gradient": [_vp, _vp, _vp, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp, _vp],
     "rsg_batch_create": [_vp, _vp, _int, _vp],
     "rsg_batch_propagate": [_vp, _vp, _i64, _dbl, _int, _int, _vp],
