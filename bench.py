@@ -160,6 +160,75 @@ def cpu_baseline(V_orc, proj, psi_seed, seconds=20.0):
                       f"(wells + projectors), {dt:.1f} s"}
 
 
+def time_steps(H, psi, steps, fn):
+    import torch
+    for _ in range(2):
+        fn(psi)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn(psi)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def extras(mesh, wells, proj, g):
+    """Side measurements on the same GPU: the FP64 (complex128) path with the
+    default and the plain one-thread-per-value stencil, the FP32 plain
+    stencil, and the optimal-control adjoint gradient against a forward
+    propagation of the control workload (64^3 double well, dipole field,
+    2000 intervals of dt = 0.05 au, 4 ETRS substeps, checkpoints every 50)."""
+    import torch
+    import paper_1501_05654_gb300 as rsg
+    from workloads import (control_field, potential_double_well, potential_wells, rng,
+                           white_noise_states)
+    out = {}
+    P, S = mesh.P, 64
+    for name, dtype, kernel in (("c64_plain_kernel", torch.complex64, 1),
+                                ("c128_default", torch.complex128, None),
+                                ("c128_staged_kernel", torch.complex128, 0)):
+        H = rsg.Hamiltonian(mesh, dtype)
+        H.set_potential(potential_wells(mesh.xyz, *wells))
+        H.set_projectors(*proj)
+        if kernel is not None:
+            H.set_option("kernel", kernel)
+        npdt = np.complex64 if dtype == torch.complex64 else np.complex128
+        psi = torch.from_numpy(white_noise_states(g, P, S, dtype=npdt)).cuda()
+        ms = time_steps(H, psi, 2, lambda x: H.propagate(x, 1, 0.01, scheme=rsg.ETRS, want_drift=False))
+        out[name] = {"ms_per_step": ms, "value": P * S * N_APPLY_PER_STEP / (ms * 1e-3) / 1e9,
+                     "unit": UNIT}
+        del psi, H
+        torch.cuda.empty_cache()
+    # control gradient vs forward (the optimal-control workload)
+    cm = rsg.Mesh(rsg.CUBE, 64, spacing=0.3)
+    gg = rng(4)
+    eps = control_field(gg, 2000, 0.05)
+    for dtype in (torch.complex128, torch.complex64):
+        H = rsg.Hamiltonian(cm, dtype)
+        H.set_potential(potential_double_well(cm.xyz, 0.02, 2.0, 0.5))
+        x = torch.from_numpy(white_noise_states(gg, cm.P, 1)[:, 0]).to(dtype).cuda()
+        x /= torch.linalg.vector_norm(x) * cm.h ** 1.5
+        tgt = torch.roll(x, 1).contiguous()
+        ld = rsg.padded_ld(1, dtype)
+        blk = torch.zeros((cm.P, ld), dtype=dtype, device="cuda")
+        blk[:, 0] = x
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H.propagate(blk, 2000, 0.05, scheme=rsg.ETRS, nsub=4, eps=eps, want_drift=False, S=1)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        J, grad = H.control_gradient(x, tgt, eps, 0.05, scheme=rsg.ETRS, nsub=4, checkpoint_every=50)
+        tg = time.perf_counter() - t0
+        out[f"control_gradient_{'c128' if dtype == torch.complex128 else 'c64'}"] = {
+            "forward_s": tf, "gradient_s": tg, "ratio": tg / tf,
+            "workload": "64^3 h=0.3 double well, 2000 intervals dt=0.05, ETRS nsub=4, K=50"}
+        del H, blk
+    return out
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
@@ -204,6 +273,8 @@ def main():
     ap.add_argument("--ty", type=int, default=None)
     ap.add_argument("--zseg", type=int, default=None)
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the complex128 / plain-kernel / control-gradient side measurements")
     ap.add_argument("--radius", type=float, default=18.0,
                     help="sphere radius (bohr); 18 is the benchmark workload, smaller radii "
                          "are for profiler captures only")
@@ -319,7 +390,7 @@ def main():
                    "h_applications_per_step": N_APPLY_PER_STEP,
                    "l2": "state blocks (1.56 GB) exceed L2; no flush",
                    "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "hbm", "kernel": "k_apply_zmarch (Horner stage: stencil + V + projector epilogue)",
+        "roofline": {"bound": "hbm", "kernel": "k_apply_staged (Horner stage: stencil + V, base and result streams)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "peak_kind": f"{peak_kind} copy bandwidth",
@@ -330,6 +401,8 @@ def main():
         "e2e": e2e,
     }
     line["clocks"] = clk.summary()
+    if not args.no_extras and ws == 1:
+        line["extras"] = extras(mesh, wells, proj, g)
     if not args.no_cpu_baseline and ws == 1:
         try:
             line["cpu_baseline"] = cpu_baseline(lambda xyz: potential_wells(xyz, *wells), proj, 5)

@@ -193,7 +193,13 @@ rsg_status rsg_control_gradient(rsg_ham H, const void *psi0, const void *target,
 rsg_status rsg_batch_create(const rsg_ham *hams, const int64_t *S, int nsys,
                             rsg_batch *out);
 /* psis[i]: device (P_i, ld_i) block with ld_i = S[i] rounded up to even.
- * Same step rule as rsg_propagate_steps with no field. */
+ * Same step rule as rsg_propagate_steps with no field and nsub = 1.  When
+ * every system has S <= 16 and all projector sets have the same size, each
+ * Horner stage of every system is one launch of each kernel (projector
+ * coefficients, their reduction, stencil, projector scatter) and one time
+ * step is a captured CUDA graph replayed nsteps times on an internal stream
+ * ordered after `stream`; otherwise the systems are propagated one by one.
+ * gs_every > 0 re-orthonormalises every system every gs_every steps. */
 rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps,
                                double dt, rsg_scheme scheme, int gs_every,
                                void *stream);

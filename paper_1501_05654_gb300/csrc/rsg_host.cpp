@@ -115,6 +115,7 @@ struct rsg_ham_s {
     DevBuf V;
     double eps = 0.0, dir[3] = {1, 0, 0};
     TileCfg cfg;
+    bool force_kernel = false;   // set when the caller chose the kernel explicitly
     // projectors
     ProjDev pj;
     DevBuf q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm, nl_ptr, nl_ent, u_pts, u_ptr;
@@ -136,7 +137,26 @@ struct rsg_ham_s {
 
 struct rsg_batch_s {
     std::vector<rsg_ham> hams;
-    std::vector<int64_t> S;
+    std::vector<int64_t> S, ld;
+    std::vector<SysArgs> args;               // host copy of the device table
+    DevBuf d_args, d_work, d_dot, d_red, d_sca;
+    std::vector<DevBuf> w0, w1, D, partial;  // per-system work blocks and projector buffers
+    int nwork = 0, ndot = 0, nred = 0, nsca = 0, npmax = 0;
+    bool batched = false;                    // false: fall back to per-system propagation
+    // one captured time step
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t step = nullptr;
+    double step_dt = NAN;
+    int step_scheme = -1;
+    std::vector<void *> step_psis;
+    int64_t n_launch_step = 0;
+    ~rsg_batch_s() {
+        if (step) cudaGraphExecDestroy(step);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (cs) cudaStreamDestroy(cs);
+    }
 };
 
 namespace {
@@ -259,6 +279,7 @@ bool overlaps(const void *a, const void *b, size_t n) {
 struct Epi {
     const void *base = nullptr;
     void *acc = nullptr;
+    const void *acc_base = nullptr;
     double ar = 1, ai = 0, br = 1, bi = 0, gr = 0, gi = 0;
 };
 
@@ -287,6 +308,7 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     a.out = out;
     a.base = ep.base;
     a.acc = ep.acc;
+    a.acc_base = ep.acc_base;
     a.rows = m->d_rows.as<Row>();
     a.nx = m->nx;
     a.ny = m->ny;
@@ -321,10 +343,19 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     a.P = m->P;
     int ntiles = 0;
     a.tiles = nullptr;
-    if (H->cfg.kernel != 1) {
+    TileCfg cfg = H->cfg;
+    if (cfg.kernel != 1) {
         int TX, TY;
-        block_shape(H->cfg, SV, &TX, &TY);
-        CKS(get_tiles(m, TX, TY, H->cfg.zseg, &a.tiles, &ntiles));
+        block_shape(cfg, SV, &TX, &TY);
+        CKS(get_tiles(m, TX, TY, cfg.zseg, &a.tiles, &ntiles));
+        if (cfg.kernel == 0 && !H->force_kernel) {
+            // the staged kernel runs one block per SM: small problems that
+            // give fewer than two blocks per SM go to the one-thread-per-value
+            // kernel instead
+            int cv, nxr, ty;
+            stage_shape(cfg, SV, &cv, &nxr, &ty);
+            if ((int64_t)ntiles * ((SV + cv - 1) / cv) < 2 * 152) cfg.kernel = 1;
+        }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (H->prof) {
@@ -340,13 +371,13 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         H->ev_used += 2;
         CK(cudaEventRecord(e0, st));
     }
-    const bool split_nl = H->cfg.kernel == 0 && H->pj.natoms > 0;
+    const bool split_nl = cfg.kernel == 0 && H->pj.natoms > 0;
     if (split_nl) {
         ApplyArgs<R> b = a;
         b.nl_ptr = nullptr;
-        CK(launch_apply<R>(b, H->cfg, ntiles, st));
+        CK(launch_apply<R>(b, cfg, ntiles, st));
     } else {
-        CK(launch_apply<R>(a, H->cfg, ntiles, st));
+        CK(launch_apply<R>(a, cfg, ntiles, st));
     }
     if (H->prof) CK(cudaEventRecord(e1, st));
     if (split_nl) {
@@ -606,7 +637,10 @@ rsg_status rsg_ham_kernel_stats(rsg_ham H, double *kernel_ms, int64_t *kernel_la
 rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     if (!H || !key) return fail(RSG_ERR_ARG, "NULL argument");
     std::string k(key);
-    if (k == "kernel" && (value >= 0 && value <= 2)) H->cfg.kernel = (int)value;
+    if (k == "kernel" && (value >= 0 && value <= 2)) {
+        H->cfg.kernel = (int)value;
+        H->force_kernel = true;
+    }
     else if (k == "rx" && (value == 1 || value == 2 || value == 4)) H->cfg.rx = (int)value;
     else if (k == "ty" && (value == 1 || value == 2 || value == 4 || value == 8 || value == 16))
         H->cfg.ty = (int)value;
@@ -873,14 +907,13 @@ namespace {
 // next = sum_j pw[j] / j! (j = 0..4).  pw[4] is scratch.
 rsg_status powers(rsg_ham H, void *const pw[5], void *next, int64_t ld, double tau, double sgn,
                   double eps, const double *dir, cudaStream_t st) {
-    const size_t bytes = (size_t)H->m->P * ld * cbytes(H->dtype);
-    CK(cudaMemcpyAsync(next, pw[0], bytes, cudaMemcpyDeviceToDevice, st));
     static const double invf[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
     for (int j = 0; j < 4; j++) {
         Epi ep;
         ep.ar = 0.0;
         ep.ai = sgn * tau;
         ep.acc = next;
+        if (j == 0) ep.acc_base = pw[0];   // next = pw[0] + A pw[0] + ...
         // acc += gamma * y with y = A^{j+1} x: gamma = 1/(j+1)! relative to the power
         ep.gr = invf[j + 1];
         ep.gi = 0.0;
@@ -956,11 +989,13 @@ rsg_status control_gradient_t(rsg_ham H, const void *psi0, const void *target, i
     };
 
     // forward pass, checkpointing the state at the start of every segment
+    // (Horner stages, the same arithmetic as rsg_propagate_steps; the
+    // backward sweep recomputes each segment with explicit powers)
     CK(cudaMemcpyAsync(fa, vec(ck0), vb, cudaMemcpyDeviceToDevice, st));
+    (void)fb;
     for (int64_t k = 0; k < nsteps; k++) {
         if (k > 0 && k % K == 0) CK(cudaMemcpyAsync(vec(ck0 + k / K), fa, vb, cudaMemcpyDeviceToDevice, st));
-        CKS(interval(fa, fb, eps[k]));
-        std::swap(fa, fb);
+        for (int l = 0; l < m; l++) CKS(taylor(H, fa, fa, ld, tau, eps[k], dir, st));
     }
     // J = |<phi|psi_N>|^2 and chi_N = phi <phi|psi_N>
     CK(launch_overlap<R>(phi, fa, P, (int)ld, h3, H->dots.as<double>(), nb, H->ov.as<double>(), st));
@@ -1019,6 +1054,118 @@ extern "C" rsg_status rsg_control_gradient(rsg_ham H, const void *psi0, const vo
 }
 
 // ============================================================== batch ====
+namespace {
+
+// Batched launch sequence of one exponential T(tau) on every system: four
+// Horner stages, each = projector coefficients + reduction, staged stencil,
+// projector scatter.  Codes: 0 = psi, 1 = w0, 2 = w1 (as in taylor()).
+rsg_status batch_exponential(rsg_batch b, double tau, cudaStream_t st) {
+    int src = 0;
+    for (int k = 4; k >= 1; k--) {
+        const int dst = (k == 1) ? 0 : ((k & 1) ? 2 : 1);
+        const float ai = (float)(-tau / k);
+        if (b->ndot > 0)
+            CK(launch_batch_proj(b->d_args.as<SysArgs>(), b->d_dot.as<BWork>(), b->ndot, b->d_red.as<BWork>(),
+                                 b->nred, src, b->npmax, st));
+        CK(launch_batch_stencil(b->d_args.as<SysArgs>(), b->d_work.as<BWork>(), b->nwork, src, dst, 0.f, ai, st));
+        if (b->nsca > 0)
+            CK(launch_batch_scatter(b->d_args.as<SysArgs>(), b->d_sca.as<BWork>(), b->nsca, dst, 0.f, ai, st));
+        src = dst;
+    }
+    return RSG_OK;
+}
+
+rsg_status batch_build(rsg_batch b) {
+    const int n = (int)b->hams.size();
+    b->args.assign((size_t)n, SysArgs{});
+    b->w0.resize((size_t)n);
+    b->w1.resize((size_t)n);
+    b->D.resize((size_t)n);
+    b->partial.resize((size_t)n);
+    std::vector<BWork> work, dot, red, sca;
+    int npmax = 0;
+    bool uniform = true;
+    for (int i = 0; i < n; i++) {
+        rsg_ham H = b->hams[(size_t)i];
+        rsg_mesh m = H->m;
+        if (!H->has_V) return fail(RSG_ERR_STATE, "system %d has no potential", i);
+        if (H->pj.natoms > 0) {
+            if (npmax == 0) npmax = H->pj.npmax;
+            else if (npmax != H->pj.npmax) uniform = false;
+        }
+        if ((int64_t)m->P * b->ld[(size_t)i] >= 0x7fffffffLL) uniform = false;
+        if (b->ld[(size_t)i] > 16) uniform = false;   // batched kernels cover 8 vectors per point
+    }
+    b->batched = uniform;
+    b->npmax = npmax;
+    if (!uniform) return RSG_OK;
+    for (int i = 0; i < n; i++) {
+        rsg_ham H = b->hams[(size_t)i];
+        rsg_mesh m = H->m;
+        CKS(ensure_rows(m));
+        const int64_t ld = b->ld[(size_t)i];
+        const int SV = (int)(ld / 2);
+        const size_t bytes = (size_t)m->P * ld * 8;
+        CK(b->w0[(size_t)i].ensure(bytes));
+        CK(b->w1[(size_t)i].ensure(bytes));
+        const Tile *tiles = nullptr;
+        int ntiles = 0;
+        CKS(get_tiles(m, kBatchNXR, kBatchTY, kBatchZseg, &tiles, &ntiles));
+        SysArgs &A = b->args[(size_t)i];
+        A.vec[0] = nullptr;
+        A.vec[1] = b->w0[(size_t)i].p;
+        A.vec[2] = b->w1[(size_t)i].p;
+        A.rows = m->d_rows.as<Row>();
+        A.tiles = tiles;
+        A.nx = m->nx;
+        A.ny = m->ny;
+        A.nz = m->nz;
+        A.SV = SV;
+        A.P = (int)m->P;
+        A.V = H->V.as<float>();
+        for (int k = 0; k < 5; k++) A.w[k] = (float)(-0.5 * kFD[k] / (m->h * m->h));
+        A.h3 = m->h * m->h * m->h;
+        const int nch = (SV + kBatchCV - 1) / kBatchCV;
+        for (int t = 0; t < ntiles; t++)
+            for (int c = 0; c < nch; c++) work.push_back(BWork{i, t, c, 0});
+        const ProjDev &pj = H->pj;
+        A.natoms = pj.natoms;
+        A.npmax = pj.npmax;
+        A.nu = pj.nu;
+        if (pj.natoms > 0) {
+            A.q_pt = pj.q_pt;
+            A.q_atom = pj.q_atom;
+            A.nl_ent = pj.nl_ent;
+            A.chunk_q0 = pj.chunk_q0;
+            A.chunk_q1 = pj.chunk_q1;
+            A.atom_chunk0 = pj.atom_chunk0;
+            A.u_pts = pj.u_pts;
+            A.u_ptr = pj.u_ptr;
+            A.q_p = (const float *)pj.q_p;
+            A.hm = pj.hm;
+            CK(b->D[(size_t)i].ensure((size_t)pj.natoms * pj.npmax * ld * 8));
+            CK(b->partial[(size_t)i].ensure((size_t)pj.nchunks * pj.npmax * ld * 2 * sizeof(double)));
+            A.D = b->D[(size_t)i].as<float>();
+            A.partial = b->partial[(size_t)i].as<double>();
+            for (int c = 0; c < pj.nchunks; c++) dot.push_back(BWork{i, c, 0, 0});
+            for (int at = 0; at < pj.natoms; at++) red.push_back(BWork{i, at, 0, 0});
+            for (int u = 0; u < pj.nu; u += 32) sca.push_back(BWork{i, u, std::min(32, pj.nu - u), 0});
+        }
+    }
+    CK(b->d_work.upload(work));
+    CK(b->d_dot.upload(dot));
+    CK(b->d_red.upload(red));
+    CK(b->d_sca.upload(sca));
+    b->nwork = (int)work.size();
+    b->ndot = (int)dot.size();
+    b->nred = (int)red.size();
+    b->nsca = (int)sca.size();
+    b->n_launch_step = (b->ndot > 0 ? 2 : 0) + 1 + (b->nsca > 0 ? 1 : 0);
+    return RSG_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 rsg_status rsg_batch_create(const rsg_ham *hams, const int64_t *S, int nsys, rsg_batch *out) {
@@ -1030,7 +1177,9 @@ rsg_status rsg_batch_create(const rsg_ham *hams, const int64_t *S, int nsys, rsg
         if (S[i] < 1) return fail(RSG_ERR_ARG, "S[%d] < 1", i);
         b->hams.push_back(hams[i]);
         b->S.push_back(S[i]);
+        b->ld.push_back((S[i] + 1) / 2 * 2);
     }
+    CKS(batch_build(b.get()));
     *out = b.release();
     return RSG_OK;
 }
@@ -1038,11 +1187,67 @@ rsg_status rsg_batch_create(const rsg_ham *hams, const int64_t *S, int nsys, rsg
 rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps, double dt,
                                rsg_scheme scheme, int gs_every, void *stream) {
     if (!b || !psis) return fail(RSG_ERR_ARG, "NULL argument");
-    for (size_t i = 0; i < b->hams.size(); i++) {
-        const int64_t ld = (b->S[i] + 1) / 2 * 2;
-        CKS(rsg_propagate_steps(b->hams[i], psis[i], b->S[i], ld, nsteps, dt, scheme, 1, nullptr,
-                                nullptr, gs_every, nullptr, stream));
+    if (nsteps < 0 || gs_every < 0 || !std::isfinite(dt)) return fail(RSG_ERR_ARG, "bad nsteps/dt/gs_every");
+    if (scheme != RSG_EXPMID && scheme != RSG_ETRS) return fail(RSG_ERR_ARG, "unknown scheme");
+    const size_t n = b->hams.size();
+    for (size_t i = 0; i < n; i++)
+        if (!psis[i] || ((uintptr_t)psis[i]) % 16) return fail(RSG_ERR_ARG, "psis[%zu] NULL or misaligned", i);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!b->batched) {
+        for (size_t i = 0; i < n; i++)
+            CKS(rsg_propagate_steps(b->hams[i], psis[i], b->S[i], b->ld[i], nsteps, dt, scheme, 1, nullptr,
+                                    nullptr, gs_every, nullptr, stream));
+        return RSG_OK;
     }
+    // (re)capture one time step when the step or the state blocks change
+    bool same = b->step && b->step_dt == dt && b->step_scheme == (int)scheme && b->step_psis.size() == n;
+    for (size_t i = 0; same && i < n; i++) same = b->step_psis[i] == psis[i];
+    if (!same) {
+        for (size_t i = 0; i < n; i++) b->args[i].vec[0] = psis[i];
+        CK(b->d_args.upload(b->args));
+        if (!b->cs) {
+            CK(cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
+        }
+        if (b->step) {
+            CK(cudaGraphExecDestroy(b->step));
+            b->step = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
+        rsg_status s = RSG_OK;
+        if (scheme == RSG_EXPMID) {
+            s = batch_exponential(b, dt, b->cs);
+        } else {
+            s = batch_exponential(b, 0.5 * dt, b->cs);
+            if (s == RSG_OK) s = batch_exponential(b, 0.5 * dt, b->cs);
+        }
+        cudaError_t ee = cudaStreamEndCapture(b->cs, &g);
+        if (s != RSG_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        CK(ee);
+        cudaError_t ie = cudaGraphInstantiate(&b->step, g, 0);
+        cudaGraphDestroy(g);
+        CK(ie);
+        b->step_dt = dt;
+        b->step_scheme = (int)scheme;
+        b->step_psis.assign(psis, psis + n);
+    }
+    CK(cudaEventRecord(b->ev_in, st));
+    CK(cudaStreamWaitEvent(b->cs, b->ev_in, 0));
+    for (int64_t k = 0; k < nsteps; k++) {
+        CK(cudaGraphLaunch(b->step, b->cs));
+        if (gs_every > 0 && (k + 1) % gs_every == 0) {
+            for (size_t i = 0; i < n; i++) CKS(orthonormalize_dev(b->hams[i], psis[i], b->S[i], b->ld[i], nullptr, b->cs));
+        }
+    }
+    CK(cudaEventRecord(b->ev_out, b->cs));
+    CK(cudaStreamWaitEvent(st, b->ev_out, 0));
+    if (gs_every > 0)
+        for (size_t i = 0; i < n; i++) CKS(read_status(b->hams[i], st));
     return RSG_OK;
 }
 

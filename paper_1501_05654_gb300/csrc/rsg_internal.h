@@ -43,7 +43,8 @@ struct ApplyArgs {
     const void *in;      // u (P, SV vectors)
     void *out;           // result
     const void *base;    // optional: added with scale beta
-    void *acc;           // optional: acc += gamma * result
+    void *acc;           // optional: acc = (acc_base or acc) + gamma * result
+    const void *acc_base;    // optional: initial value of acc (acc is then write-only)
     const Row *rows;
     const Tile *tiles;
     int nx, ny, nz;
@@ -136,6 +137,39 @@ cudaError_t launch_scale_dev(const void *x, void *y, int64_t n, const double *a,
 // grad[k] += 2 Re( -i tau * sum_n 1/n! sum_j M[j][n-1-j] )  (device)
 cudaError_t launch_grad_accum(const double *M, double tau, double *grad_k,
                               cudaStream_t st);
+
+// ---- batches of independent complex64 systems (rsg_kernels.cu) ----
+// Per-system arguments, resident on the device.  vec[] = {psi, w0, w1}: the
+// caller's state block and two work blocks; kernels pick input, output and
+// base by index so one captured step serves every system.
+struct SysArgs {
+    void *vec[3];
+    const Row *rows;
+    const Tile *tiles;
+    int nx, ny, nz, SV, P;
+    const float *V;
+    float w[5];
+    int natoms, npmax, nu;
+    const int32_t *q_pt, *q_atom, *nl_ent, *chunk_q0, *chunk_q1, *atom_chunk0, *u_pts, *u_ptr;
+    const float *q_p;
+    const double *hm;
+    float *D;
+    double *partial;
+    double h3;
+};
+// Work item: stencil (sys, tile, chunk); projector dot (sys, chunk);
+// projector reduce (sys, atom); scatter (sys, first union point).
+struct BWork {
+    int32_t sys, a, b, pad;
+};
+// Staged stencil over every system's tiles (block 2 x 16 x 16, cv = 2).
+cudaError_t launch_batch_stencil(const SysArgs *sys, const BWork *work, int nwork, int in_c, int out_c,
+                                 float ar, float ai, cudaStream_t st);
+constexpr int kBatchCV = 2, kBatchTY = 16, kBatchNXR = 16, kBatchZseg = 64;
+cudaError_t launch_batch_proj(const SysArgs *sys, const BWork *dot_work, int ndot, const BWork *red_work,
+                              int nred, int in_c, int npmax, cudaStream_t st);
+cudaError_t launch_batch_scatter(const SysArgs *sys, const BWork *work, int nwork, int out_c, float ar,
+                                 float ai, cudaStream_t st);
 
 // Host-side accessors for code outside rsg_host.cpp: the Hamiltonian's
 // compute type, point count and spacing, and the thread-local error message.

@@ -57,7 +57,7 @@ __device__ __forceinline__ void finish_point(const ApplyArgs<R> &a, int64_t idx,
     if (a.base != nullptr) V::cfma(y0, a.br, a.bi, ((const T *)a.base)[o]);
     ((T *)a.out)[o] = y0;
     if (a.acc != nullptr) {
-        T s = ((T *)a.acc)[o];
+        T s = a.acc_base != nullptr ? ((const T *)a.acc_base)[o] : ((T *)a.acc)[o];
         V::cfma(s, a.gr, a.gi, y0);
         ((T *)a.acc)[o] = s;
     }
@@ -235,7 +235,7 @@ __device__ __forceinline__ void finish_staged(const ApplyArgs<R> &a, int o, type
     if (a.base != nullptr) V::cfma(y0, a.br, a.bi, base);
     ((T *)a.out)[o] = y0;
     if (a.acc != nullptr) {
-        T s = ((T *)a.acc)[o];
+        T s = a.acc_base != nullptr ? ((const T *)a.acc_base)[o] : ((T *)a.acc)[o];
         V::cfma(s, a.gr, a.gi, y0);
         ((T *)a.acc)[o] = s;
     }
@@ -320,16 +320,15 @@ struct StagedThreads {
     static constexpr int value = RX == 1 ? 512 : 384;
 };
 
+// One block of the staged kernel: tile tl, state chunk `chunk` of the
+// system described by a.  Shared by the single-system and batched kernels.
 template <typename R, int CV, int RX, int NS>
-__global__ void __launch_bounds__(StagedThreads<RX>::value, 1) k_apply_staged(const ApplyArgs<R> a, int nchunks) {
+__device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile tl, const int chunk,
+                                             unsigned char *smraw, SRow *srows) {
     using V = VT<R>;
     using T = typename V::T;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ SRow srows[kSRows];
     const int NXR = blockDim.y, TY = blockDim.z;
     const int TX = NXR * RX, WX = TX + 8, WY = TY + 8;
-    const int chunk = blockIdx.x % nchunks;
-    const Tile tl = a.tiles[blockIdx.x / nchunks];
     const int ny = a.ny, nz = a.nz, SV = a.SV;
     const int xbase = tl.tx * TX - 4, ybase = tl.ty * TY - 4, zbase = tl.zlo - 4;
     const int nzr = tl.zhi - tl.zlo + 8;
@@ -489,6 +488,13 @@ __global__ void __launch_bounds__(StagedThreads<RX>::value, 1) k_apply_staged(co
         __syncthreads();
     }
     cp_async_wait<0>();
+}
+
+template <typename R, int CV, int RX, int NS>
+__global__ void __launch_bounds__(StagedThreads<RX>::value, 1) k_apply_staged(const ApplyArgs<R> a, int nchunks) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ SRow srows[kSRows];
+    staged_block<R, CV, RX, NS>(a, a.tiles[blockIdx.x / nchunks], blockIdx.x % nchunks, smraw, srows);
 }
 
 // --------------------------------------------------------------- naive ---
@@ -777,6 +783,194 @@ cudaError_t launch_proj_reduce(const double *partial, int SV, const ProjDev &pj,
                                                        pj.atom_chunk0, pj.hm, h3, (R *)D);
     return cudaGetLastError();
 }
+
+// ------------------------------------------------------------- batches ---
+// One launch per Horner stage for many independent complex64 systems: every
+// block takes a (system, tile, chunk) work item and runs the staged stencil
+// block for that system.  Projector coefficients, their reduction and the
+// projector scatter are batched the same way.
+#ifndef RSG_ONLY_DOUBLE
+__device__ __forceinline__ ApplyArgs<float> batch_args(const SysArgs &S, int in_c, int out_c, float ar,
+                                                       float ai) {
+    ApplyArgs<float> a;
+    a.in = S.vec[in_c];
+    a.out = S.vec[out_c];
+    a.base = S.vec[0];
+    a.acc = nullptr;
+    a.acc_base = nullptr;
+    a.rows = S.rows;
+    a.tiles = S.tiles;
+    a.nx = S.nx;
+    a.ny = S.ny;
+    a.nz = S.nz;
+    a.SV = S.SV;
+    a.V = S.V;
+    a.f0 = a.fx = a.fy = a.fz = 0.f;
+    for (int k = 0; k < 5; k++) a.w[k] = S.w[k];
+    a.ar = ar;
+    a.ai = ai;
+    a.br = 1.f;
+    a.bi = 0.f;
+    a.gr = a.gi = 0.f;
+    a.nl_ptr = nullptr;
+    a.nl_ent = nullptr;
+    a.q_atom = nullptr;
+    a.q_p = nullptr;
+    a.D = nullptr;
+    a.npmax = 0;
+    a.P = S.P;
+    return a;
+}
+
+__global__ void __launch_bounds__(512, 1) k_batch_stencil(const SysArgs *__restrict__ sys,
+                                                          const BWork *__restrict__ work, int in_c,
+                                                          int out_c, float ar, float ai) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ SRow srows[kSRows];
+    const BWork w = work[blockIdx.x];
+    const SysArgs &S = sys[w.sys];
+    const ApplyArgs<float> a = batch_args(S, in_c, out_c, ar, ai);
+    staged_block<float, kBatchCV, 1, 4>(a, S.tiles[w.a], w.b, smraw, srows);
+}
+
+cudaError_t launch_batch_stencil(const SysArgs *sys, const BWork *work, int nwork, int in_c, int out_c,
+                                 float ar, float ai, cudaStream_t st) {
+    if (nwork == 0) return cudaSuccess;
+    TileCfg c;
+    c.cv = kBatchCV;
+    c.ty = kBatchTY;
+    c.rx = 1;
+    const size_t smem = stage_smem_bytes(c, kBatchCV, sizeof(float4));
+    cudaError_t e = cudaFuncSetAttribute(k_batch_stencil, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_batch_stencil<<<nwork, dim3(kBatchCV, kBatchNXR, kBatchTY), smem, st>>>(sys, work, in_c, out_c, ar, ai);
+    return cudaGetLastError();
+}
+
+// <p_ai|u> partial sums over one sphere chunk of one system (block 8 x 32).
+template <int NP>
+__global__ void __launch_bounds__(256) k_batch_proj_dot(const SysArgs *__restrict__ sys,
+                                                        const BWork *__restrict__ work, int in_c) {
+    using V = VT<float>;
+    using T = float4;
+    __shared__ double red[256 * 4];
+    const BWork w = work[blockIdx.x];
+    const SysArgs &S = sys[w.sys];
+    const int c = w.a, v = threadIdx.x, SV = S.SV;
+    const T *u = (const T *)S.vec[in_c];
+    const int q0 = S.chunk_q0[c], q1 = S.chunk_q1[c];
+    T acc[NP];
+#pragma unroll
+    for (int i = 0; i < NP; i++) acc[i] = V::zero();
+    if (v < SV)
+        for (int q = q0 + threadIdx.y; q < q1; q += blockDim.y) {
+            const T val = V::ldg(u + S.q_pt[q] * SV + v);
+#pragma unroll
+            for (int i = 0; i < NP; i++) V::fma(acc[i], S.q_p[q * NP + i], val);
+        }
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int i = 0; i < NP; i++) {
+        red[tid * 4 + 0] = acc[i].x;
+        red[tid * 4 + 1] = acc[i].y;
+        red[tid * 4 + 2] = acc[i].z;
+        red[tid * 4 + 3] = acc[i].w;
+        __syncthreads();
+        if (threadIdx.y == 0 && v < SV) {
+            double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+            for (int l = 0; l < (int)blockDim.y; l++) {
+                const double *r = red + (l * blockDim.x + threadIdx.x) * 4;
+                s0 += r[0];
+                s1 += r[1];
+                s2 += r[2];
+                s3 += r[3];
+            }
+            double *dst = S.partial + (((int64_t)c * NP + i) * SV + v) * 4;
+            dst[0] = s0;
+            dst[1] = s1;
+            dst[2] = s2;
+            dst[3] = s3;
+        }
+        __syncthreads();
+    }
+}
+
+// D[a, i, s] = sum_j h_a[i][j] h^3 sum_chunks partial  (one block per (sys, atom))
+__global__ void k_batch_proj_reduce(const SysArgs *__restrict__ sys, const BWork *__restrict__ work) {
+    const BWork w = work[blockIdx.x];
+    const SysArgs &S = sys[w.sys];
+    const int a = w.a, s = threadIdx.x, ldc = 2 * S.SV, npmax = S.npmax;
+    if (s >= ldc) return;
+    double cr[9], ci[9];
+    for (int i = 0; i < npmax; i++) {
+        double sr = 0.0, si = 0.0;
+        for (int c = S.atom_chunk0[a]; c < S.atom_chunk0[a + 1]; c++) {
+            const double *p = S.partial + (((int64_t)c * npmax + i) * ldc + s) * 2;
+            sr += p[0];
+            si += p[1];
+        }
+        cr[i] = S.h3 * sr;
+        ci[i] = S.h3 * si;
+    }
+    for (int i = 0; i < npmax; i++) {
+        double dr = 0.0, di = 0.0;
+        for (int j = 0; j < npmax; j++) {
+            const double hij = S.hm[((int64_t)a * npmax + i) * npmax + j];
+            dr += hij * cr[j];
+            di += hij * ci[j];
+        }
+        float *dst = S.D + (((int64_t)a * npmax + i) * ldc + s) * 2;
+        dst[0] = (float)dr;
+        dst[1] = (float)di;
+    }
+}
+
+cudaError_t launch_batch_proj(const SysArgs *sys, const BWork *dot_work, int ndot, const BWork *red_work,
+                              int nred, int in_c, int npmax, cudaStream_t st) {
+    if (ndot == 0) return cudaSuccess;
+    switch (npmax) {
+    case 1: k_batch_proj_dot<1><<<ndot, dim3(8, 32), 0, st>>>(sys, dot_work, in_c); break;
+    case 4: k_batch_proj_dot<4><<<ndot, dim3(8, 32), 0, st>>>(sys, dot_work, in_c); break;
+    case 9: k_batch_proj_dot<9><<<ndot, dim3(8, 32), 0, st>>>(sys, dot_work, in_c); break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_batch_proj_reduce<<<nred, 32, 0, st>>>(sys, red_work);
+    return cudaGetLastError();
+}
+
+// out += alpha * projector terms at up to 32 union points of one system.
+__global__ void __launch_bounds__(256) k_batch_scatter(const SysArgs *__restrict__ sys,
+                                                       const BWork *__restrict__ work, int out_c, float ar,
+                                                       float ai) {
+    using V = VT<float>;
+    using T = float4;
+    const BWork w = work[blockIdx.x];
+    const SysArgs &S = sys[w.sys];
+    const int u = w.a + threadIdx.y, v = threadIdx.x, SV = S.SV;
+    if (u >= S.nu || u >= w.a + w.b || v >= SV) return;
+    const int p = S.u_pts[u];
+    const T *D = (const T *)S.D;
+    T sum = V::zero();
+    for (int e = S.u_ptr[u]; e < S.u_ptr[u + 1]; e++) {
+        const int q = S.nl_ent[e];
+        const int at = S.q_atom[q];
+        const float *pv = S.q_p + q * S.npmax;
+        const T *Da = D + at * S.npmax * SV + v;
+        for (int i = 0; i < S.npmax; i++) V::fma(sum, pv[i], Da[i * SV]);
+    }
+    T *out = (T *)S.vec[out_c];
+    const int o = p * SV + v;
+    out[o] = V::add(out[o], V::cmul(ar, ai, sum));
+}
+
+cudaError_t launch_batch_scatter(const SysArgs *sys, const BWork *work, int nwork, int out_c, float ar,
+                                 float ai, cudaStream_t st) {
+    if (nwork == 0) return cudaSuccess;
+    k_batch_scatter<<<nwork, dim3(8, 32), 0, st>>>(sys, work, out_c, ar, ai);
+    return cudaGetLastError();
+}
+#endif
 
 #ifndef RSG_ONLY_DOUBLE
 template cudaError_t launch_apply<float>(const ApplyArgs<float> &, const TileCfg &, int, cudaStream_t);

@@ -1,0 +1,85 @@
+"""GPU parity: a batch of uneven complex64 systems (one launch per Horner stage
+for all systems, one captured graph per time step) against single-system
+propagation and against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1501_05654_gb300 as rsg
+from tests._parity import rel_err, round_c64
+from tests._systems import Pair
+from workloads import (gaussian_wells, potential_wells, projector_atoms, rng,
+                       wavepacket_params, wavepacket_states)
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [(9, 1, 1), (14, 3, 2), (20, 4, 0), (24, 6, 3), (11, 2, 1), (17, 5, 2)]   # (n, S, atoms)
+
+
+def _systems(lmax_of=lambda i: 1, seed=0):
+    g = rng(3, seed)
+    out = []
+    for i, (n, S, na) in enumerate(SPECS):
+        p = Pair("cube", n, h=0.25, dtype=torch.complex64)
+        half = 0.5 * (n - 1) * 0.25
+        c, d, w = gaussian_wells(g, 2, 0.0, cube_half=0.6 * half)
+        p.set_potential(potential_wells(p.om.xyz, c, d, w))
+        if na:
+            cen, rc, lm, beta, hm = projector_atoms(g, na, 1.0, lmax_of(i), cube_half=0.5 * half)
+            p.set_projectors(cen, rc, lm, beta, hm)
+        psi = p.om.mgs(wavepacket_states(p.om.xyz, wavepacket_params(g, S, 0.5 * half)))
+        out.append((p, round_c64(psi), S))
+    return out
+
+
+def _run_batch(systems, nsteps, dt, scheme, gs_every=0):
+    batch = rsg.Batch([p.H for p, _, _ in systems], [S for _, _, S in systems])
+    xs = [p.states_to_gpu(psi) for p, psi, _ in systems]
+    batch.propagate(xs, nsteps, dt, scheme=scheme, gs_every=gs_every)
+    torch.cuda.synchronize()
+    return batch, xs
+
+
+def test_batch_matches_single_system_and_oracle():
+    systems = _systems()
+    _, xs = _run_batch(systems, 4, 0.02, rsg.ETRS)
+    for (p, psi, S), x in zip(systems, xs):
+        y = p.states_to_gpu(psi)
+        p.H.propagate(y, 4, 0.02, scheme=rsg.ETRS)
+        torch.cuda.synchronize()
+        got, ref = p.states_from_gpu(x, S), p.states_from_gpu(y, S)
+        assert rel_err(got, ref) < 2e-5
+    p, psi, S = systems[3]
+    want, _ = p.O.propagate(psi, 4, 0.02, scheme=oracle.ETRS)
+    assert rel_err(p.states_from_gpu(xs[3], S), want) < 2e-5
+
+
+def test_batch_expmid_and_recapture_on_new_buffers():
+    systems = _systems(seed=1)
+    batch, xs = _run_batch(systems, 2, 0.01, rsg.EXPMID)
+    # a second call with fresh buffers must not reuse the old graph's pointers
+    ys = [p.states_to_gpu(psi) for p, psi, _ in systems]
+    batch.propagate(ys, 2, 0.01, scheme=rsg.EXPMID)
+    torch.cuda.synchronize()
+    for (p, psi, S), x, y in zip(systems, xs, ys):
+        assert rel_err(p.states_from_gpu(y, S), p.states_from_gpu(x, S)) < 1e-6
+        want, _ = p.O.propagate(psi, 2, 0.01, scheme=oracle.EXPMID)
+        assert rel_err(p.states_from_gpu(y, S), want) < 2e-5
+
+
+def test_batch_with_gram_schmidt():
+    systems = _systems(seed=2)
+    _, xs = _run_batch(systems, 4, 0.02, rsg.ETRS, gs_every=2)
+    for (p, psi, S), x in zip(systems, xs):
+        got = p.states_from_gpu(x, S)
+        G = p.h ** 3 * got.conj().T @ got
+        assert np.abs(G - np.eye(S)).max() < 1e-5
+
+
+def test_batch_mixed_projector_counts_falls_back():
+    systems = _systems(lmax_of=lambda i: i % 2, seed=3)     # npmax 1 and 4 mixed
+    _, xs = _run_batch(systems, 2, 0.02, rsg.ETRS)
+    for (p, psi, S), x in zip(systems, xs):
+        want, _ = p.O.propagate(psi, 2, 0.02, scheme=oracle.ETRS)
+        assert rel_err(p.states_from_gpu(x, S), want) < 2e-5
