@@ -55,7 +55,8 @@ typedef enum {
     RSG_ERR_OOM = -2,          /* device or host allocation failed */
     RSG_ERR_CUDA = -3,         /* a CUDA runtime call failed */
     RSG_ERR_UNSUPPORTED = -4,  /* valid request the library does not support */
-    RSG_ERR_TIMEOUT = -5,      /* a bounded device wait gave up */
+    RSG_ERR_TIMEOUT = -5,      /* a bounded device wait gave up (reported by the
+                                  next call that synchronises the stream) */
     RSG_ERR_NONFINITE = -6,    /* a norm or Gram check found NaN/Inf */
     RSG_ERR_STATE = -7         /* handle not ready (e.g. missing potential) */
 } rsg_status;
@@ -206,13 +207,19 @@ rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps,
 rsg_status rsg_batch_destroy(rsg_batch b);
 
 /* Tuning knobs (kernel tile shapes); unknown keys give RSG_ERR_ARG.
- * Keys: "kernel" (0 = shared-memory staged z-march, 1 = one thread per
- * point and vector, 2 = z-march through L1), "rx" (points per thread along
+ * Keys: "kernel" (0 = shared-memory staged z-march with cp.async, 1 = one
+ * thread per point and vector, 2 = z-march through L1, 3 = z-march with
+ * plane tiles gathered by the TMA), "rx" (points per thread along
  * x: 1, 2 or 4; the staged kernel uses 1 or 2), "ty" (rows per
- * tile: 1, 2, 4, 8 or 16), "zseg" (planes per z segment, 1..64), "cv"
+ * tile: 1, 2, 4, 8 or 16), "zseg" (planes per z segment, 1..120), "cv"
  * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8).
  * A shape whose shared memory does not fit the SM fails with RSG_ERR_CUDA. */
 rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value);
+
+/* Reads an option set above, or "last_kernel": the stencil kernel (0..3)
+ * that the last Hamiltonian application actually ran (-1 before any), after
+ * automatic fallbacks (small problems, TMA unavailable). */
+rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value);
 
 /* Measurement hooks.  rsg_ham_profile(H, 1) starts recording a CUDA event
  * pair around every stencil-kernel launch of H (on the stream it is

@@ -116,6 +116,7 @@ struct rsg_ham_s {
     double eps = 0.0, dir[3] = {1, 0, 0};
     TileCfg cfg;
     bool force_kernel = false;   // set when the caller chose the kernel explicitly
+    int last_kernel = -1;        // stencil kernel of the last application
     // projectors
     ProjDev pj;
     DevBuf q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm, nl_ptr, nl_ent, u_pts, u_ptr;
@@ -242,6 +243,13 @@ int pow2_at_least(int v) {
 // launch_apply): staged kernel cv x nxr x ty threads (512), L1 z-march
 // kernel 256 threads; TX = nxr * rx.
 void block_shape(const TileCfg &c, int SV, int *TX, int *TY) {
+    if (c.kernel == 3) {
+        int cv, nxr, ty;
+        tma_shape(c, SV, &cv, &nxr, &ty);
+        *TX = nxr;
+        *TY = ty;
+        return;
+    }
     if (c.kernel == 0) {
         int cv, nxr, ty;
         stage_shape(c, SV, &cv, &nxr, &ty);
@@ -255,6 +263,14 @@ void block_shape(const TileCfg &c, int SV, int *TX, int *TY) {
     const int nxr = 256 / (cv * ty);
     *TX = nxr * c.rx;
     *TY = ty;
+}
+
+// Tile list of kernel configuration c (0 tiles on failure).
+int tiles_for(rsg_ham H, const TileCfg &c, int SV, const Tile **tiles) {
+    int TX, TY, n = 0;
+    block_shape(c, SV, &TX, &TY);
+    if (get_tiles(H->m, TX, TY, c.zseg, tiles, &n) != RSG_OK) return 0;
+    return n;
 }
 
 // ------------------------------------------------------------ checks ----
@@ -341,6 +357,11 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     a.D = H->D.p;
     a.npmax = H->pj.npmax;
     a.P = m->P;
+    if (!H->status.p) {
+        CK(H->status.ensure(sizeof(int)));
+        CK(cudaMemsetAsync(H->status.p, 0, sizeof(int), st));
+    }
+    a.err = H->status.as<int>();
     int ntiles = 0;
     a.tiles = nullptr;
     TileCfg cfg = H->cfg;
@@ -348,7 +369,7 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         int TX, TY;
         block_shape(cfg, SV, &TX, &TY);
         CKS(get_tiles(m, TX, TY, cfg.zseg, &a.tiles, &ntiles));
-        if (cfg.kernel == 0 && !H->force_kernel) {
+        if ((cfg.kernel == 0 || cfg.kernel == 3) && !H->force_kernel) {
             // the staged kernel runs one block per SM: small problems that
             // give fewer than two blocks per SM go to the one-thread-per-value
             // kernel instead
@@ -371,13 +392,24 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         H->ev_used += 2;
         CK(cudaEventRecord(e0, st));
     }
-    const bool split_nl = cfg.kernel == 0 && H->pj.natoms > 0;
-    if (split_nl) {
+    const bool split_nl = (cfg.kernel == 0 || cfg.kernel == 3) && H->pj.natoms > 0;
+    {
         ApplyArgs<R> b = a;
-        b.nl_ptr = nullptr;
-        CK(launch_apply<R>(b, cfg, ntiles, st));
-    } else {
-        CK(launch_apply<R>(a, cfg, ntiles, st));
+        if (split_nl) b.nl_ptr = nullptr;
+        bool done = false;
+        if (cfg.kernel == 3) CK(launch_apply_tma<R>(b, cfg, ntiles, st, &done));
+        if (done) {
+            H->last_kernel = 3;
+        } else {
+            TileCfg c0 = cfg;
+            int n = ntiles;
+            if (c0.kernel == 3) {
+                c0.kernel = 0;
+                n = tiles_for(H, c0, SV, &b.tiles);
+            }
+            CK(launch_apply<R>(b, c0, n, st));
+            H->last_kernel = c0.kernel;
+        }
     }
     if (H->prof) CK(cudaEventRecord(e1, st));
     if (split_nl) {
@@ -478,6 +510,8 @@ rsg_status read_status(rsg_ham H, cudaStream_t st) {
     if (s != 0) {
         CK(cudaMemsetAsync(H->status.p, 0, sizeof(int), st));
         CK(cudaStreamSynchronize(st));
+        if (s == 2) return fail(RSG_ERR_TIMEOUT, "a bounded wait in the stencil kernel gave up");
+        if (s == 3) return fail(RSG_ERR_CUDA, "TMA destination not 128-byte aligned (copy skipped)");
         return fail(RSG_ERR_NONFINITE, "Gram matrix not finite or not positive definite");
     }
     return RSG_OK;
@@ -634,17 +668,30 @@ rsg_status rsg_ham_kernel_stats(rsg_ham H, double *kernel_ms, int64_t *kernel_la
     return RSG_OK;
 }
 
+rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value) {
+    if (!H || !key || !value) return fail(RSG_ERR_ARG, "NULL argument");
+    std::string k(key);
+    if (k == "kernel") *value = H->cfg.kernel;
+    else if (k == "last_kernel") *value = H->last_kernel;
+    else if (k == "rx") *value = H->cfg.rx;
+    else if (k == "ty") *value = H->cfg.ty;
+    else if (k == "zseg") *value = H->cfg.zseg;
+    else if (k == "cv") *value = H->cfg.cv;
+    else return fail(RSG_ERR_ARG, "unknown option: %s", key);
+    return RSG_OK;
+}
+
 rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     if (!H || !key) return fail(RSG_ERR_ARG, "NULL argument");
     std::string k(key);
-    if (k == "kernel" && (value >= 0 && value <= 2)) {
+    if (k == "kernel" && (value >= 0 && value <= 3)) {
         H->cfg.kernel = (int)value;
         H->force_kernel = true;
     }
     else if (k == "rx" && (value == 1 || value == 2 || value == 4)) H->cfg.rx = (int)value;
     else if (k == "ty" && (value == 1 || value == 2 || value == 4 || value == 8 || value == 16))
         H->cfg.ty = (int)value;
-    else if (k == "zseg" && value >= 1 && value <= 64) H->cfg.zseg = (int)value;
+    else if (k == "zseg" && value >= 1 && value <= 120) H->cfg.zseg = (int)value;
     else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
     else return fail(RSG_ERR_ARG, "unknown option or value: %s=%lld", key, (long long)value);
     return RSG_OK;
@@ -825,7 +872,7 @@ rsg_status rsg_state_norms(rsg_ham H, const void *psi, int64_t S, int64_t ld, do
     CKS(norms_dev(H, psi, S, ld, H->drift.as<double>(), st));
     CK(cudaMemcpyAsync(norms2_out, H->drift.p, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    return RSG_OK;
+    return read_status(H, st);
 }
 
 rsg_status rsg_orthonormalize(rsg_ham H, void *psi, int64_t S, int64_t ld, double *norms2_out,
@@ -893,7 +940,7 @@ rsg_status rsg_propagate_steps(rsg_ham H, void *psi, int64_t S, int64_t ld, int6
         CK(cudaMemcpyAsync(norm_drift_out, drift, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
-    if (gs_every > 0) return read_status(H, st);
+    if (gs_every > 0 || norm_drift_out) return read_status(H, st);
     return RSG_OK;
 }
 
@@ -1029,7 +1076,7 @@ rsg_status control_gradient_t(rsg_ham H, const void *psi0, const void *target, i
     CK(cudaMemcpyAsync(grad_out, H->grad.p, (size_t)nsteps * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     *J_out = ov[0] * ov[0] + ov[1] * ov[1];
-    return RSG_OK;
+    return read_status(H, st);
 }
 
 }  // namespace

@@ -27,10 +27,10 @@ struct Tile {
 
 // Kernel tile configuration.
 struct TileCfg {
-    int kernel = 0;   // 0 shared-memory staged, 1 naive, 2 L1 z-march
+    int kernel = 0;   // 0 shared-memory staged, 1 naive, 2 L1 z-march, 3 TMA gather
     int rx = 1;       // points per thread along x
     int ty = 16;      // rows per tile (blockDim.z)
-    int zseg = 64;    // planes per z segment
+    int zseg = 120;   // planes per z segment
     int cv = 4;       // staged kernel: 16-byte vectors per point in a chunk (1..8)
     int stages = 4;   // staged kernel: shared-memory pipeline depth (4)
 };
@@ -61,6 +61,7 @@ struct ApplyArgs {
     const void *D;           // (natoms*npmax, SV) vectors: h_a <p|u>
     int npmax;
     int64_t P;
+    int *err;                // device status word (bounded waits record timeouts)
 };
 
 // Projector tables on the device (entry-major, see rsg_host.cpp).
@@ -82,6 +83,12 @@ struct ProjDev {
 // ---- launchers (rsg_kernels.cu) ----
 // Block shape (cv x nxr x ty threads, tile TX = nxr * rx) of the staged kernel.
 void stage_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty);
+// Block shape of the TMA-gather kernel (tile TX = nxr).
+void tma_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty);
+// TMA-gather stencil (kernel 3); *launched = false when it does not apply.
+template <typename R>
+cudaError_t launch_apply_tma(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
+                             bool *launched);
 template <typename R>
 cudaError_t launch_apply(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles,
                          cudaStream_t st);

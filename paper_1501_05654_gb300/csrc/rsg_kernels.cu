@@ -25,6 +25,8 @@
 //   k_proj_dot      partial sums of <p_ai|u_s> over sphere chunks (FP32
 //                   products and partial sums for complex64, FP64 across
 //                   chunks), k_proj_reduce: h^3 sum over chunks, times h_a.
+#include <cuda.h>
+
 #include "rsg_internal.h"
 #include "rsg_vec.cuh"
 
@@ -84,7 +86,7 @@ struct SRow {
     int16_t xmin, xmax;
 };
 
-constexpr int kMaxTY = 16, kMaxZseg = 64;
+constexpr int kMaxTY = 16, kMaxZseg = 120;
 constexpr int kSRows = (kMaxTY + 8) * (kMaxZseg + 8);
 
 // Branch-free read of vector v at bbox x of a row: out-of-row lanes load a
@@ -253,6 +255,7 @@ struct StageCtx {
     int WX, WY, slot_elems;
     int xr, yi, cv, v, y, x0;    // thread's tile coordinates and first global x
     int zbase, zlo, zhi;
+    int zc0, zc1;                // planes where the thread's columns have points
     R w0, w1, w2, w3, w4;
 };
 
@@ -271,8 +274,12 @@ __device__ __forceinline__ void stage_plane(const StageCtx<R, CV, RX> &c, int j,
     const int p = c.zbase + j;
     const int WX = c.WX;
     const T *ctr = sl + ((c.yi + 4) * WX + c.xr * RX + 4) * CV + c.cv;
+    // a column off the mesh at plane p contributes nothing (its values and
+    // outputs there are zero / absent): skip the arithmetic
+    const bool live = p >= c.zc0 && p <= c.zc1;
 #pragma unroll
     for (int r = 0; r < RX; r++) {
+        if (!live) break;
         const T *cp = ctr + r * CV;
         const T cval = cp[0];
         V::fma(q[Q3][r], c.w1, cval);
@@ -447,29 +454,44 @@ __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile t
         for (int r = 0; r < RX; r++) q[k][r] = V::zero();
 
     const int np = nzr;
+    // column z-range of this thread (the mesh meets each column in one run)
+    c.zc0 = 1 << 30;
+    c.zc1 = -(1 << 30);
+    for (int jj = 0; jj < np; jj++) {
+        const SRow rw = srows[jj * WY + yown];
+#pragma unroll
+        for (int r = 0; r < RX; r++)
+            if (x0own + r >= rw.xmin && x0own + r <= rw.xmax) {
+                c.zc0 = min(c.zc0, zbase + jj);
+                c.zc1 = max(c.zc1, zbase + jj);
+            }
+    }
 #pragma unroll 1
     for (int j = 0; j < NS - 1; j++) {
         if (j < np) stage(j);
         cp_async_commit();
     }
+    // plane j has landed for every thread after the barrier; the slot then
+    // refilled (plane j + NS - 1) was last read at plane j - 1, which every
+    // thread finished before reaching the barrier: one barrier per plane
     auto pre = [&](int j) {
+        cp_async_wait<NS - 2>();
+        __syncthreads();
         if (j + NS - 1 < np) stage(j + NS - 1);
         cp_async_commit();
-        cp_async_wait<NS - 1>();
-        __syncthreads();
     };
     int j = 0;
 #pragma unroll 1
     for (; j + 9 <= np; j += 9) {
-        pre(j + 0); stage_plane<R, CV, RX, NS, 0>(c, j + 0, q); __syncthreads();
-        pre(j + 1); stage_plane<R, CV, RX, NS, 1>(c, j + 1, q); __syncthreads();
-        pre(j + 2); stage_plane<R, CV, RX, NS, 2>(c, j + 2, q); __syncthreads();
-        pre(j + 3); stage_plane<R, CV, RX, NS, 3>(c, j + 3, q); __syncthreads();
-        pre(j + 4); stage_plane<R, CV, RX, NS, 4>(c, j + 4, q); __syncthreads();
-        pre(j + 5); stage_plane<R, CV, RX, NS, 5>(c, j + 5, q); __syncthreads();
-        pre(j + 6); stage_plane<R, CV, RX, NS, 6>(c, j + 6, q); __syncthreads();
-        pre(j + 7); stage_plane<R, CV, RX, NS, 7>(c, j + 7, q); __syncthreads();
-        pre(j + 8); stage_plane<R, CV, RX, NS, 8>(c, j + 8, q); __syncthreads();
+        pre(j + 0); stage_plane<R, CV, RX, NS, 0>(c, j + 0, q);
+        pre(j + 1); stage_plane<R, CV, RX, NS, 1>(c, j + 1, q);
+        pre(j + 2); stage_plane<R, CV, RX, NS, 2>(c, j + 2, q);
+        pre(j + 3); stage_plane<R, CV, RX, NS, 3>(c, j + 3, q);
+        pre(j + 4); stage_plane<R, CV, RX, NS, 4>(c, j + 4, q);
+        pre(j + 5); stage_plane<R, CV, RX, NS, 5>(c, j + 5, q);
+        pre(j + 6); stage_plane<R, CV, RX, NS, 6>(c, j + 6, q);
+        pre(j + 7); stage_plane<R, CV, RX, NS, 7>(c, j + 7, q);
+        pre(j + 8); stage_plane<R, CV, RX, NS, 8>(c, j + 8, q);
     }
 #pragma unroll 1
     for (; j < np; j++) {
@@ -485,7 +507,6 @@ __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile t
         case 7: stage_plane<R, CV, RX, NS, 7>(c, j, q); break;
         default: stage_plane<R, CV, RX, NS, 8>(c, j, q); break;
         }
-        __syncthreads();
     }
     cp_async_wait<0>();
 }
@@ -560,6 +581,19 @@ size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes) {
     const size_t nthr = (size_t)cv * nxr * ty;
     return (size_t)c.stages * ((ty + 8) * (nxr * rx + 8) * cv * vec_bytes +
                                nthr * rx * (vec_bytes + vec_bytes / 2));
+}
+// Block shape of the TMA kernel: 512 threads, one point per thread along x,
+// pipeline (4 slots of the halo tile plus the base tile) within 200 KB.
+void tma_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
+    int v = 1;
+    while (v < SV && v < c.cv) v <<= 1;
+    *cv = v;
+    int t = c.ty;
+    while (v * t > 256 && t > 1) t >>= 1;
+    *ty = t;
+    int n = 512 / (v * t);
+    while (n > 4 && (size_t)4 * ((size_t)(t + 8) * (n + 8) * v + (size_t)t * n * v) * 16 > 200 * 1024) n >>= 1;
+    *nxr = n;
 }
 #else
 size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes);
@@ -784,6 +818,309 @@ cudaError_t launch_proj_reduce(const double *partial, int SV, const ProjDev &pj,
     return cudaGetLastError();
 }
 
+// ----------------------------------------------------------- TMA gather ---
+// k_apply_tma: the staged z-march with the plane tiles brought in by the
+// tensor memory accelerator.  Warp 0 gathers each plane's (TY+8) x (TX+8)
+// points, four arbitrary point indices per cp.async.bulk.tensor...gather4
+// (points outside the mesh get the out-of-range index P, which the TMA
+// zero-fills), plus the base values of the outputs retired at that plane;
+// completion is tracked by one mbarrier per slot.  The other warps only
+// compute.  Every mbarrier wait is bounded: on timeout the block records an
+// error (a.err = 2) and leaves at the next block barrier.
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_arrive(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_gather4(unsigned dst, const CUtensorMap *tm, int col, int r0, int r1,
+                                            int r2, int r3, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(tm), "r"(col), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(bar)
+        : "memory");
+}
+
+constexpr long kWaitLimit = 1L << 22;   // try_wait polls before a slot is declared lost
+
+template <typename R, int CV, int NS>
+__global__ void __launch_bounds__(512, 1) k_apply_tma(const ApplyArgs<R> a, const __grid_constant__ CUtensorMap tm_in,
+                                                      const __grid_constant__ CUtensorMap tm_base, int nchunks,
+                                                      int *err) {
+    using V = VT<R>;
+    using T = typename V::T;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ SRow srows[kSRows];
+    __shared__ __align__(8) unsigned long long mbar[NS];
+    __shared__ int s_abort;
+    const int NXR = blockDim.y, TY = blockDim.z;
+    const int TX = NXR, WX = TX + 8, WY = TY + 8;
+    const int chunk = blockIdx.x % nchunks;
+    const Tile tl = a.tiles[blockIdx.x / nchunks];
+    const int ny = a.ny, nz = a.nz, SV = a.SV, P = (int)a.P;
+    const int xbase = tl.tx * TX - 4, ybase = tl.ty * TY - 4, zbase = tl.zlo - 4;
+    const int nzr = tl.zhi - tl.zlo + 8;
+    const int nthr = CV * NXR * TY;
+    const int tid = (threadIdx.z * NXR + threadIdx.y) * CV + threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < WY * nzr; i += nthr) {
+        const int zz = i / WY;
+        const int yy = ybase + (i - zz * WY);
+        const int zg = zbase + zz;
+        SRow r{0, 1, 0};
+        if (yy >= 0 && yy < ny && zg >= 0 && zg < nz) {
+            const Row g = a.rows[zg * ny + yy];
+            r.start = g.start;
+            r.xmin = (int16_t)g.xmin;
+            r.xmax = (int16_t)g.xmax;
+        }
+        srows[i] = r;
+    }
+    const unsigned mbar0 = (unsigned)__cvta_generic_to_shared(mbar);
+    if (tid == 0) {
+        for (int k = 0; k < NS; k++) mbar_init(mbar0 + 8 * k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    __syncthreads();
+    const int slot_elems = WY * WX * CV, bslot_elems = TY * TX * CV;
+    // tensor copies need 128-byte aligned destinations: round the dynamic
+    // region up (the launch reserves 128 bytes of slack); with TX % 4 == 0
+    // and CV >= 2 every slot and every four-point group is then aligned
+    const unsigned raw = (unsigned)__cvta_generic_to_shared(smraw);
+    T *slots = (T *)(smraw + ((128u - (raw & 127u)) & 127u));
+    T *bslots = slots + NS * slot_elems;
+    const unsigned sh_slots = (unsigned)__cvta_generic_to_shared(slots);
+    const unsigned sh_bslots = (unsigned)__cvta_generic_to_shared(bslots);
+    const int col = chunk * CV * (int)(16 / sizeof(R));     // element column of this chunk
+    const bool has_base = a.base != nullptr;
+    const unsigned tx_bytes = (unsigned)(slot_elems + (has_base ? bslot_elems : 0)) * 16u;
+    const unsigned tx_bytes_nobase = (unsigned)slot_elems * 16u;
+
+    // warp 0: gather plane j and the base of outputs retired at plane j
+    auto issue = [&](int j) {
+        const int sl = j % NS;
+        const unsigned bar = mbar0 + 8 * sl;
+        const SRow *rr = srows + j * WY;
+        for (int g = lane; g < WY * WX / 4; g += 32) {
+            int idx[4];
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                const int pi = 4 * g + t;
+                const int yy = pi / WX, xx = pi - yy * WX;
+                const SRow rw = rr[yy];
+                const int x = xbase + xx;
+                idx[t] = (x >= rw.xmin && x <= rw.xmax) ? rw.start + (x - rw.xmin) : P;
+            }
+            const unsigned dst = sh_slots + (unsigned)((sl * slot_elems + 4 * g * CV) * 16);
+            if (dst & 127u) {   // never expected: record it and leave the slot incomplete
+                atomicExch(err, 3);
+                continue;
+            }
+            tma_gather4(dst, &tm_in, col, idx[0], idx[1], idx[2], idx[3], bar);
+        }
+        const bool base_now = has_base && j >= 4;
+        if (base_now) {
+            const SRow *ro = srows + (j - 4) * WY + 4;
+            for (int g = lane; g < TY * TX / 4; g += 32) {
+                int idx[4];
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    const int pi = 4 * g + t;
+                    const int yi = pi / TX, xi = pi - yi * TX;
+                    const SRow rw = ro[yi];
+                    const int x = tl.tx * TX + xi;
+                    idx[t] = (x >= rw.xmin && x <= rw.xmax) ? rw.start + (x - rw.xmin) : P;
+                }
+                const unsigned dst = sh_bslots + (unsigned)((sl * bslot_elems + 4 * g * CV) * 16);
+                if (dst & 127u) {
+                    atomicExch(err, 3);
+                    continue;
+                }
+                tma_gather4(dst, &tm_base, col, idx[0], idx[1], idx[2], idx[3], bar);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_expect_arrive(bar, base_now ? tx_bytes : tx_bytes_nobase);
+    };
+
+    const int cv = threadIdx.x, xr = threadIdx.y, yi = threadIdx.z;
+    const int v = chunk * CV + cv;
+    const int y = tl.ty * TY + yi;
+    const int x = tl.tx * TX + xr;
+    const R w1 = a.w[1], w2 = a.w[2], w3 = a.w[3], w4 = a.w[4], w03 = (R)3 * a.w[0];
+    // own potential, two planes ahead in registers
+    auto vload = [&](int j) -> R {
+        if (j >= nzr) return (R)0;
+        const SRow rw = srows[j * WY + yi + 4];
+        return (x >= rw.xmin && x <= rw.xmax) ? a.V[rw.start + (x - rw.xmin)] : (R)0;
+    };
+    R vq0 = vload(0), vq1 = vload(1);
+    T q[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) q[k] = V::zero();
+    if (warp == 0)
+        for (int j = 0; j < NS - 1 && j < nzr; j++) issue(j);
+    const int rs = WX * CV;
+    for (int j = 0; j < nzr; j++) {
+        if (warp == 0 && j + NS - 1 < nzr) issue(j + NS - 1);
+        const R vq2 = vload(j + 2);
+        const unsigned bar = mbar0 + 8 * (j % NS);
+        bool ok = false;
+        for (long it = 0; it < kWaitLimit; ++it)
+            if (mbar_try(bar, (unsigned)((j / NS) & 1))) {
+                ok = true;
+                break;
+            }
+        if (!ok) s_abort = 1;
+        if (ok) {
+            const T *sl = slots + (j % NS) * slot_elems;
+            const T *cp = sl + ((yi + 4) * WX + xr + 4) * CV + cv;
+            const T cval = cp[0];
+            const int p = zbase + j;
+            // queue rotates by renaming inside the nine-way unrolled body below
+            T s = V::scale(w03, cval);
+            V::fma(s, w1, V::add(V::add(cp[-CV], cp[CV]), V::add(cp[-rs], cp[rs])));
+            V::fma(s, w2, V::add(V::add(cp[-2 * CV], cp[2 * CV]), V::add(cp[-2 * rs], cp[2 * rs])));
+            V::fma(s, w3, V::add(V::add(cp[-3 * CV], cp[3 * CV]), V::add(cp[-3 * rs], cp[3 * rs])));
+            V::fma(s, w4, V::add(V::add(cp[-4 * CV], cp[4 * CV]), V::add(cp[-4 * rs], cp[4 * rs])));
+            const R diag = vq0 + a.f0 + a.fx * (R)x + a.fy * (R)y + a.fz * (R)p;
+            V::fma(s, diag, cval);
+            // shift-free queue: output p+k-4 lives in q[(k + j) % 9]
+            const int jm = j % 9;
+            switch (jm) {
+#define RSG_PHASE(PH)                                                                          \
+    case PH: {                                                                                 \
+        constexpr int Q0 = (0 + PH) % 9, Q1 = (1 + PH) % 9, Q2 = (2 + PH) % 9, Q3 = (3 + PH) % 9; \
+        constexpr int Q4 = (4 + PH) % 9, Q5 = (5 + PH) % 9, Q6 = (6 + PH) % 9, Q7 = (7 + PH) % 9; \
+        constexpr int Q8 = (8 + PH) % 9;                                                       \
+        V::fma(q[Q3], w1, cval);                                                               \
+        V::fma(q[Q5], w1, cval);                                                               \
+        V::fma(q[Q2], w2, cval);                                                               \
+        V::fma(q[Q6], w2, cval);                                                               \
+        V::fma(q[Q1], w3, cval);                                                               \
+        V::fma(q[Q7], w3, cval);                                                               \
+        V::fma(q[Q0], w4, cval);                                                               \
+        V::fma(q[Q8], w4, cval);                                                               \
+        q[Q4] = V::add(q[Q4], s);                                                              \
+        if (p - 4 >= tl.zlo && p - 4 < tl.zhi && v < SV) {                                     \
+            const SRow ro = srows[(j - 4) * WY + yi + 4];                                      \
+            if (x >= ro.xmin && x <= ro.xmax) {                                                \
+                const int o = (ro.start + (x - ro.xmin)) * SV + v;                             \
+                const T bv = bslots[((j % NS) * TY + yi) * TX * CV + xr * CV + cv];            \
+                finish_staged<R>(a, o, q[Q0], bv);                                             \
+            }                                                                                  \
+        }                                                                                      \
+        q[Q0] = V::zero();                                                                     \
+    } break;
+                RSG_PHASE(0)
+                RSG_PHASE(1)
+                RSG_PHASE(2)
+                RSG_PHASE(3)
+                RSG_PHASE(4)
+                RSG_PHASE(5)
+                RSG_PHASE(6)
+                RSG_PHASE(7)
+                RSG_PHASE(8)
+#undef RSG_PHASE
+            }
+        }
+        vq0 = vq1;
+        vq1 = vq2;
+        __syncthreads();
+        if (s_abort) {
+            if (tid == 0) atomicExch(err, 2);
+            // give copies still in flight a bounded chance to land before leaving
+            for (int k = 0; k < NS; k++)
+                for (long it = 0; it < 4096; ++it)
+                    if (mbar_try(mbar0 + 8 * k, 0) || mbar_try(mbar0 + 8 * k, 1)) break;
+            return;
+        }
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// 2-D view of a (P, SV) block of 16-byte vectors as R elements: rows are
+// points, a box is one point's CV vectors.
+template <typename R>
+static bool encode_rows(CUtensorMap *tm, const void *base, int64_t P, int SV, int CV) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || !base) return false;
+    const int epv = 16 / (int)sizeof(R);
+    cuuint64_t dims[2] = {(cuuint64_t)SV * epv, (cuuint64_t)P};
+    cuuint64_t strides[1] = {(cuuint64_t)SV * 16};
+    cuuint32_t box[2] = {(cuuint32_t)(CV * epv), 1};
+    cuuint32_t es[2] = {1, 1};
+    const CUtensorMapDataType dt = sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    return fn(tm, dt, 2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename R, int CV>
+static cudaError_t launch_tma_cv(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, int nxr, int ty,
+                                 cudaStream_t st, bool *launched) {
+    constexpr int NS = 4;
+    CUtensorMap tm_in, tm_base;
+    if (!encode_rows<R>(&tm_in, a.in, a.P, a.SV, CV)) return cudaSuccess;
+    if (!encode_rows<R>(&tm_base, a.base ? a.base : a.in, a.P, a.SV, CV)) return cudaSuccess;
+    const int WX = nxr + 8, WY = ty + 8;
+    const size_t smem = (size_t)NS * ((size_t)WY * WX * CV + (size_t)ty * nxr * CV) * 16 + 128;
+    cudaError_t e = cudaFuncSetAttribute(k_apply_tma<R, CV, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nchunks = (a.SV + CV - 1) / CV;
+    k_apply_tma<R, CV, NS><<<(unsigned)((long long)ntiles * nchunks), dim3(CV, nxr, ty), smem, st>>>(
+        a, tm_in, tm_base, nchunks, a.err);
+    *launched = true;
+    (void)cfg;
+    return cudaGetLastError();
+}
+
+// Returns with *launched = false when the TMA path does not apply (no
+// encoder, tile width not a multiple of 4, too much shared memory).
+template <typename R>
+cudaError_t launch_apply_tma(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
+                             bool *launched) {
+    *launched = false;
+    if (ntiles == 0 || a.err == nullptr || (long long)a.P >= 0x7fffffffLL) return cudaSuccess;
+    int cv, nxr, ty;
+    tma_shape(cfg, a.SV, &cv, &nxr, &ty);
+    // four-point groups of at least 128 bytes keep every destination aligned
+    if (nxr % 4 != 0 || cv < 2) return cudaSuccess;
+    switch (cv) {
+    case 2: return launch_tma_cv<R, 2>(a, cfg, ntiles, nxr, ty, st, launched);
+    case 4: return launch_tma_cv<R, 4>(a, cfg, ntiles, nxr, ty, st, launched);
+    default: return launch_tma_cv<R, 8>(a, cfg, ntiles, nxr, ty, st, launched);
+    }
+}
+
 // ------------------------------------------------------------- batches ---
 // One launch per Horner stage for many independent complex64 systems: every
 // block takes a (system, tile, chunk) work item and runs the staged stencil
@@ -973,12 +1310,14 @@ cudaError_t launch_batch_scatter(const SysArgs *sys, const BWork *work, int nwor
 #endif
 
 #ifndef RSG_ONLY_DOUBLE
+template cudaError_t launch_apply_tma<float>(const ApplyArgs<float> &, const TileCfg &, int, cudaStream_t, bool *);
 template cudaError_t launch_apply<float>(const ApplyArgs<float> &, const TileCfg &, int, cudaStream_t);
 template cudaError_t launch_proj_dot<float>(const void *, int, const ProjDev &, double *, cudaStream_t);
 template cudaError_t launch_proj_reduce<float>(const double *, int, const ProjDev &, double, void *, cudaStream_t);
 template cudaError_t launch_proj_scatter<float>(const ApplyArgs<float> &, const int32_t *, const int32_t *, int, cudaStream_t);
 #endif
 #ifndef RSG_ONLY_FLOAT
+template cudaError_t launch_apply_tma<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t, bool *);
 template cudaError_t launch_apply<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t);
 template cudaError_t launch_proj_dot<double>(const void *, int, const ProjDev &, double *, cudaStream_t);
 template cudaError_t launch_proj_reduce<double>(const double *, int, const ProjDev &, double, void *, cudaStream_t);

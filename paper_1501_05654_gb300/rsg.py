@@ -50,6 +50,7 @@ SIGNATURES = {
     "rsg_batch_propagate": [_vp, _vp, _i64, _dbl, _int, _int, _vp],
     "rsg_batch_destroy": [_vp],
     "rsg_ham_set_option": [_vp, C.c_char_p, _i64],
+    "rsg_ham_get_option": [_vp, C.c_char_p, _vp],
     "rsg_ham_profile": [_vp, _int],
     "rsg_ham_kernel_stats": [_vp, _vp, _vp, _vp, _vp],
     "rsg_last_error": [],
@@ -182,6 +183,11 @@ class Hamiltonian:
 
     def set_option(self, key: str, value: int):
         _ck(load().rsg_ham_set_option(self._h, key.encode(), int(value)))
+
+    def get_option(self, key: str) -> int:
+        v = C.c_int64()
+        _ck(load().rsg_ham_get_option(self._h, key.encode(), C.byref(v)))
+        return int(v.value)
 
     def profile(self, enable: bool):
         _ck(load().rsg_ham_profile(self._h, 1 if enable else 0))

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 TOL = {torch.complex128: 1e-12, torch.complex64: 2e-5}
 
 
-def _check_apply(p, g, S, eps=0.0, dir=(1.0, 0.0, 0.0), opts=None):
+def _check_apply(p, g, S, eps=0.0, dir=(1.0, 0.0, 0.0), opts=None, expect_kernel=None):
     psi = white_noise_states(g, p.P, S)
     if p.dtype == torch.complex64:
         psi = round_c64(psi)
@@ -29,6 +29,8 @@ def _check_apply(p, g, S, eps=0.0, dir=(1.0, 0.0, 0.0), opts=None):
     x = p.states_to_gpu(psi)
     y = p.H.apply(x, S=S)
     torch.cuda.synchronize()
+    if expect_kernel is not None:
+        assert p.H.get_option("last_kernel") == expect_kernel
     got = p.states_from_gpu(y, S)
     err = rel_err(got, want)
     assert err < TOL[p.dtype], err
@@ -63,7 +65,25 @@ def test_box_odd_extents(dtype):
                                   {"kernel": 2, "ty": 4, "rx": 4, "zseg": 3}])
 def test_kernel_variants_agree(opts):
     p, g = wells_system("sphere", radius=3.3, h=0.25, dtype=torch.complex64, seed=7, natoms=2)
-    _check_apply(p, g, 10, opts=opts)
+    _check_apply(p, g, 10, opts=opts, expect_kernel=opts["kernel"])
+
+
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+@pytest.mark.parametrize("opts", [{"kernel": 3}, {"kernel": 3, "cv": 2}, {"kernel": 3, "cv": 8, "ty": 8},
+                                  {"kernel": 3, "cv": 2, "ty": 4, "zseg": 7}])
+def test_tma_gather_kernel(dtype, opts):
+    """The TMA-gather stencil on a ragged sphere with projectors and a field."""
+    p, g = wells_system("sphere", radius=4.6, h=0.25, dtype=dtype, seed=8, natoms=3, lmax=2)
+    _check_apply(p, g, 13, eps=0.02, dir=(0.0, 0.6, 0.8), opts=opts, expect_kernel=3)
+    # Horner stage through the same kernel (base stream gathered by the TMA)
+    psi = white_noise_states(g, p.P, 5)
+    if dtype == torch.complex64:
+        psi = round_c64(psi)
+    want = p.O.taylor4(psi, 0.01, eps=0.02, dir=(0.0, 0.6, 0.8))
+    y = p.H.taylor(p.states_to_gpu(psi), 0.01, S=5)
+    torch.cuda.synchronize()
+    assert p.H.get_option("last_kernel") == 3
+    assert rel_err(p.states_from_gpu(y, 5), want) < TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
