@@ -212,7 +212,10 @@ rsg_status rsg_batch_destroy(rsg_batch b);
  * plane tiles gathered by the TMA), "rx" (points per thread along
  * x: 1, 2 or 4; the staged kernel uses 1 or 2), "ty" (rows per
  * tile: 1, 2, 4, 8 or 16), "zseg" (planes per z segment, 1..120), "cv"
- * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8).
+ * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8),
+ * "adjoint_keep_powers" (rsg_control_gradient: 1 keeps the Taylor powers of
+ * a whole checkpoint segment, 0 recomputes them per interval, -1 = choose by
+ * free device memory, the default).
  * A shape whose shared memory does not fit the SM fails with RSG_ERR_CUDA. */
 rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value);
 

@@ -117,6 +117,7 @@ struct rsg_ham_s {
     TileCfg cfg;
     bool force_kernel = false;   // set when the caller chose the kernel explicitly
     int last_kernel = -1;        // stencil kernel of the last application
+    int adj_keep = -1;           // adjoint: keep segment powers (1), recompute (0), by memory (-1)
     // projectors
     ProjDev pj;
     DevBuf q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm, nl_ptr, nl_ent, u_pts, u_ptr;
@@ -693,6 +694,7 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
         H->cfg.ty = (int)value;
     else if (k == "zseg" && value >= 1 && value <= 120) H->cfg.zseg = (int)value;
     else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
+    else if (k == "adjoint_keep_powers" && value >= -1 && value <= 1) H->adj_keep = (int)value;
     else return fail(RSG_ERR_ARG, "unknown option or value: %s=%lld", key, (long long)value);
     return RSG_OK;
 }
@@ -984,20 +986,26 @@ rsg_status control_gradient_t(rsg_ham H, const void *psi0, const void *target, i
     const double tau = scheme == RSG_EXPMID ? dt / nsub : 0.5 * dt / nsub;
     if (K <= 0 || K > nsteps) K = (int)nsteps;
     const int64_t nck = (nsteps + K - 1) / K;
-    // pool layout: checkpoints, segment states, powers of one interval,
-    // costate powers, and scratch
+    // Taylor powers A^j psi' (j = 0..3) of every exponential of one segment
+    // are kept when they fit, so the backward sweep applies H only to the
+    // costate (3 forward propagations in total); otherwise each interval's
+    // powers are recomputed from the segment's stored states.
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const int64_t have = (int64_t)H->pool.size();
+    const int64_t seg_vecs = (int64_t)K * m * 4 + 1;
+    const bool keep_powers = H->adj_keep >= 0 ? H->adj_keep == 1
+                                              : (double)std::max<int64_t>(seg_vecs - have, 0) * vb < 0.6 * (double)free_b;
     int64_t at = 0;
     const int64_t ck0 = at; at += nck;
-    const int64_t seg0 = at; at += K + 1;
-    const int64_t pw0 = at; at += 4 * m + 1;
+    const int64_t pw0 = at; at += keep_powers ? (int64_t)K * m * 4 + 1 : (int64_t)(K + 1) + 4 * m + 1;
     const int64_t b0 = at; at += 5;
-    const int64_t sc0 = at; at += 5;
+    const int64_t sc0 = at; at += 4;
     const int64_t nvec = at;
     if ((int64_t)H->pool.size() < nvec) H->pool.resize((size_t)nvec);
     for (int64_t i = 0; i < nvec; i++) CK(H->pool[(size_t)i].ensure(vb));
     auto vec = [&](int64_t i) { return H->pool[(size_t)i].p; };
-    void *chi = vec(sc0), *chi2 = vec(sc0 + 1), *phi = vec(sc0 + 2);
-    void *fa = vec(sc0 + 3), *fb = vec(sc0 + 4);
+    void *chi = vec(sc0), *chi2 = vec(sc0 + 1), *phi = vec(sc0 + 2), *fa = vec(sc0 + 3);
     // column 0 of padded (P, ld) blocks
     CK(cudaMemsetAsync(vec(ck0), 0, vb, st));
     CK(cudaMemsetAsync(phi, 0, vb, st));
@@ -1018,28 +1026,13 @@ rsg_status control_gradient_t(rsg_ham H, const void *psi0, const void *target, i
     CK(H->dots.ensure((size_t)nb * 20 * sizeof(double) + 64 * sizeof(double)));
     CK(H->M.ensure(32 * sizeof(double)));
     CK(H->ov.ensure(2 * sizeof(double)));
-    CK(H->grad.ensure((size_t)nsteps * sizeof(double)));
-    CK(cudaMemsetAsync(H->grad.p, 0, (size_t)nsteps * sizeof(double), st));
+    CK(H->grad.ensure((size_t)nsteps * sizeof(double) + 64));
+    CK(cudaMemsetAsync(H->grad.p, 0, (size_t)nsteps * sizeof(double) + 64, st));
+    unsigned *counter = (unsigned *)((char *)H->grad.p + (size_t)nsteps * sizeof(double));
 
-    // x -> y through the m exponentials of one interval (explicit powers);
-    // the powers of exponential l are left in pw[4l .. 4l+3] (pw[4l] = input).
-    auto interval = [&](const void *x, void *y, double e) -> rsg_status {
-        const void *cur = x;
-        for (int l = 0; l < m; l++) {
-            void *pw[5] = {const_cast<void *>(cur), vec(pw0 + 4 * l + 1), vec(pw0 + 4 * l + 2),
-                           vec(pw0 + 4 * l + 3), vec(pw0 + 4 * m)};
-            void *next = (l == m - 1) ? y : vec(pw0 + 4 * (l + 1));
-            CKS(powers(H, pw, next, ld, tau, -1.0, e, dir, st));
-            cur = next;
-        }
-        return RSG_OK;
-    };
-
-    // forward pass, checkpointing the state at the start of every segment
-    // (Horner stages, the same arithmetic as rsg_propagate_steps; the
-    // backward sweep recomputes each segment with explicit powers)
+    // forward pass by Horner stages (the same arithmetic as
+    // rsg_propagate_steps), saving the state at the start of every segment
     CK(cudaMemcpyAsync(fa, vec(ck0), vb, cudaMemcpyDeviceToDevice, st));
-    (void)fb;
     for (int64_t k = 0; k < nsteps; k++) {
         if (k > 0 && k % K == 0) CK(cudaMemcpyAsync(vec(ck0 + k / K), fa, vb, cudaMemcpyDeviceToDevice, st));
         for (int l = 0; l < m; l++) CKS(taylor(H, fa, fa, ld, tau, eps[k], dir, st));
@@ -1050,25 +1043,58 @@ rsg_status control_gradient_t(rsg_ham H, const void *psi0, const void *target, i
     double ov[2] = {0, 0};
     CK(cudaMemcpyAsync(ov, H->ov.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
 
-    // backward over segments: recompute psi_k, then walk the intervals back
+    // powers of exponential (k, l) of the current segment: slots j = 0..3
+    auto pslot = [&](int64_t kk, int l, int j) -> void * {
+        if (keep_powers) return vec(pw0 + (kk * m + l) * 4 + j);
+        return j == 0 ? nullptr : vec(pw0 + (K + 1) + 4 * l + j);
+    };
+    const int64_t scratch = keep_powers ? pw0 + (int64_t)K * m * 4 : pw0 + (K + 1) + 4 * m;
+    // x -> y through the m exponentials of interval kk (explicit powers),
+    // leaving the powers of exponential l in pslot(kk, l, .)
+    auto interval = [&](int64_t kk, const void *x, void *y, double e) -> rsg_status {
+        const void *cur = x;
+        for (int l = 0; l < m; l++) {
+            void *p0 = keep_powers ? pslot(kk, l, 0) : const_cast<void *>(cur);
+            if (keep_powers && p0 != cur) CK(cudaMemcpyAsync(p0, cur, vb, cudaMemcpyDeviceToDevice, st));
+            void *pw[5] = {p0, pslot(kk, l, 1), pslot(kk, l, 2), pslot(kk, l, 3), vec(scratch)};
+            void *next = (l == m - 1) ? y : (keep_powers ? pslot(kk, l + 1, 0) : pslot(kk, l + 1, 0));
+            if (!keep_powers && l < m - 1) next = vec(pw0 + (K + 1) + 4 * (l + 1));   // holds the next input
+            CKS(powers(H, pw, next, ld, tau, -1.0, e, dir, st));
+            cur = next;
+        }
+        return RSG_OK;
+    };
+
     for (int64_t c = nck - 1; c >= 0; c--) {
         const int64_t k0 = c * K, k1 = std::min<int64_t>(k0 + K, nsteps);
-        CK(cudaMemcpyAsync(vec(seg0), vec(ck0 + c), vb, cudaMemcpyDeviceToDevice, st));
-        for (int64_t k = k0; k < k1 - 1; k++)
-            CKS(interval(vec(seg0 + (k - k0)), vec(seg0 + (k - k0 + 1)), eps[k]));
+        if (keep_powers) {
+            // one recompute sweep over the segment keeps every power
+            CK(cudaMemcpyAsync(pslot(0, 0, 0), vec(ck0 + c), vb, cudaMemcpyDeviceToDevice, st));
+            for (int64_t k = k0; k < k1; k++) {
+                void *y = (k + 1 < k1) ? pslot(k + 1 - k0, 0, 0) : fa;   // fa: free after the forward pass
+                CKS(interval(k - k0, pslot(k - k0, 0, 0), y, eps[k]));
+            }
+        } else {
+            CK(cudaMemcpyAsync(vec(pw0), vec(ck0 + c), vb, cudaMemcpyDeviceToDevice, st));
+            for (int64_t k = k0; k < k1 - 1; k++)
+                CKS(interval(0, vec(pw0 + (k - k0)), vec(pw0 + (k - k0 + 1)), eps[k]));
+        }
         for (int64_t k = k1 - 1; k >= k0; k--) {
             const double e = eps[k];
-            CKS(interval(vec(seg0 + (k - k0)), fb, e));   // fills the powers A^j psi'_l
+            const void *first = keep_powers ? pslot(k - k0, 0, 0) : vec(pw0 + (k - k0));
+            if (!keep_powers) CKS(interval(0, first, fa, e));   // powers of this interval (output unused)
             // costate: chi'_m = chi_{k+1}; chi'_l = T^dagger chi'_{l+1}
             for (int l = m - 1; l >= 0; l--) {
                 void *B[5] = {chi, vec(b0 + 1), vec(b0 + 2), vec(b0 + 3), vec(b0 + 4)};
                 CKS(powers(H, B, chi2, ld, tau, +1.0, e, dir, st));
                 const void *bb[4] = {B[0], B[1], B[2], B[3]};
-                const void *aa[4] = {l == 0 ? vec(seg0 + (k - k0)) : vec(pw0 + 4 * l),
-                                     vec(pw0 + 4 * l + 1), vec(pw0 + 4 * l + 2), vec(pw0 + 4 * l + 3)};
-                CK(launch_adjoint_dots<R>(bb, aa, P, (int)ld, H->Xd.as<R>(), h3, H->dots.as<double>(), nb,
-                                          H->M.as<double>(), st));
-                CK(launch_grad_accum(H->M.as<double>(), tau, H->grad.as<double>() + k, st));
+                const void *a0 = keep_powers ? pslot(k - k0, l, 0)
+                                             : (l == 0 ? first : vec(pw0 + (K + 1) + 4 * l));
+                const void *aa[4] = {a0, keep_powers ? pslot(k - k0, l, 1) : pslot(0, l, 1),
+                                     keep_powers ? pslot(k - k0, l, 2) : pslot(0, l, 2),
+                                     keep_powers ? pslot(k - k0, l, 3) : pslot(0, l, 3)};
+                CK(launch_adjoint_grad<R>(bb, aa, P, (int)ld, H->Xd.as<R>(), h3, tau, H->dots.as<double>(), nb,
+                                          counter, H->grad.as<double>() + k, st));
                 std::swap(chi, chi2);
             }
         }

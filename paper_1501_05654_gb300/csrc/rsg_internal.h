@@ -128,6 +128,12 @@ template <typename R>
 cudaError_t launch_adjoint_dots(const void *const *b, const void *const *a, int64_t P, int ld,
                                 const R *X, double h3, double *partial, int nblk,
                                 double *out, cudaStream_t st);
+// Fused adjoint inner products + reduction + grad_k update (one launch);
+// counter (device, zero on entry) is reset by the kernel.
+template <typename R>
+cudaError_t launch_adjoint_grad(const void *const *b, const void *const *a, int64_t P, int ld,
+                                const R *X, double h3, double tau, double *partial, int nblk,
+                                unsigned *counter, double *grad_k, cudaStream_t st);
 // overlap: out = h3 sum_p conj(f_p) g_p  (complex double, one state)
 template <typename R>
 cudaError_t launch_overlap(const void *f, const void *g, int64_t P, int ld, double h3,

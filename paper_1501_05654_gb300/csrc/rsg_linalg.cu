@@ -311,6 +311,94 @@ __global__ void __launch_bounds__(256) k_adjoint_dots(const R *b0, const R *b1, 
     }
 }
 
+// Fused form for the control gradient: the same per-block partial sums, then
+// the last block to finish (ticket counter) sums the partials in block order
+// and adds 2 Re(-i tau sum_n 1/n! sum_j M[j][n-1-j]) = 2 tau Im(...) to grad_k.
+// The counter is left at zero for the next call.
+template <typename R>
+__global__ void __launch_bounds__(256) k_adjoint_grad(const R *b0, const R *b1, const R *b2, const R *b3,
+                                                      const R *a0, const R *a1, const R *a2, const R *a3,
+                                                      int64_t P, int ld, const R *__restrict__ X, double h3,
+                                                      double tau, double *__restrict__ partial, int nblk,
+                                                      unsigned *counter, double *grad_k) {
+    __shared__ double red[256];
+    __shared__ bool last;
+    const R *bb[4] = {b0, b1, b2, b3};
+    const R *aa[4] = {a0, a1, a2, a3};
+    double acc[20];
+#pragma unroll
+    for (int i = 0; i < 20; i++) acc[i] = 0.0;
+    const int64_t per = (P + nblk - 1) / nblk;
+    const int64_t p0 = blockIdx.x * per;
+    const int64_t p1 = p0 + per < P ? p0 + per : P;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        double br[4], bi[4], ar[4], ai[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            ld_c(bb[j] + p * ld * 2, br[j], bi[j]);
+            ld_c(aa[j] + p * ld * 2, ar[j], ai[j]);
+        }
+        const double x = (double)X[p];
+        int k = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int i = 0; i + j <= 3; i++) {
+                acc[2 * k] += x * (br[j] * ar[i] + bi[j] * ai[i]);
+                acc[2 * k + 1] += x * (br[j] * ai[i] - bi[j] * ar[i]);
+                k++;
+            }
+    }
+    for (int k = 0; k < 20; k++) {
+        red[threadIdx.x] = acc[k];
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * 20 + k] = red[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1u) == (unsigned)(nblk - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // the last block: ten threads each sum the imaginary part of one packed
+    // inner product over the blocks (fixed order), then thread 0 combines
+    __shared__ double Mi[10];
+    if (threadIdx.x < 10) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; b++) s += partial[(int64_t)b * 20 + 2 * threadIdx.x + 1];
+        Mi[threadIdx.x] = h3 * s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    // packed order: j = 0..3, i = 0..3-j; the term has order n = i + j + 1
+    const double invf[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
+    double si = 0.0;
+    int k = 0;
+    for (int j = 0; j < 4; j++)
+        for (int i = 0; i + j <= 3; i++) {
+            si += invf[i + j + 1] * Mi[k];
+            k++;
+        }
+    *grad_k += 2.0 * tau * si;
+    *counter = 0u;
+}
+
+template <typename R>
+cudaError_t launch_adjoint_grad(const void *const *b, const void *const *a, int64_t P, int ld, const R *X,
+                                double h3, double tau, double *partial, int nblk, unsigned *counter,
+                                double *grad_k, cudaStream_t st) {
+    k_adjoint_grad<R><<<nblk, 256, 0, st>>>((const R *)b[0], (const R *)b[1], (const R *)b[2], (const R *)b[3],
+                                            (const R *)a[0], (const R *)a[1], (const R *)a[2], (const R *)a[3], P,
+                                            ld, X, h3, tau, partial, nblk, counter, grad_k);
+    return cudaGetLastError();
+}
+
 // Expand the 10 packed values into out[j*4+i] (complex double), zero elsewhere.
 __global__ void k_adjoint_finish(const double *packed, double *out) {
     if (threadIdx.x != 0) return;
@@ -457,6 +545,9 @@ cudaError_t launch_grad_accum(const double *M, double tau, double *grad_k, cudaS
     template cudaError_t launch_adjoint_dots<R>(const void *const *, const void *const *, int64_t,   \
                                                 int, const R *, double, double *, int, double *,     \
                                                 cudaStream_t);                                       \
+    template cudaError_t launch_adjoint_grad<R>(const void *const *, const void *const *, int64_t, int, \
+                                                const R *, double, double, double *, int, unsigned *,  \
+                                                double *, cudaStream_t);                               \
     template cudaError_t launch_overlap<R>(const void *, const void *, int64_t, int, double,         \
                                            double *, int, double *, cudaStream_t);                   \
     template cudaError_t launch_axpby<R>(const void *, void *, int64_t, double, double, double,      \

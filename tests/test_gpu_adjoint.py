@@ -30,9 +30,11 @@ def _setup(dtype, n=14, h=0.5, nsteps=12, seed=0):
     return p, a[:, 0], b[:, 0], psi0, phi, eps
 
 
+@pytest.mark.parametrize("keep", [-1, 0, 1])
 @pytest.mark.parametrize("scheme,nsub,K", [(1, 1, 5), (0, 2, 3), (1, 2, 12)])
-def test_adjoint_matches_oracle_c128(scheme, nsub, K):
+def test_adjoint_matches_oracle_c128(scheme, nsub, K, keep):
     p, a, b, psi0, phi, eps = _setup(torch.complex128)
+    p.H.set_option("adjoint_keep_powers", keep)
     Jw, gw = p.O.control_gradient(a, b, eps, 0.05, scheme=scheme, nsub=nsub, checkpoint_every=4)
     J, gr = p.H.control_gradient(psi0, phi, eps, 0.05, scheme=scheme, nsub=nsub,
                                  checkpoint_every=K)
