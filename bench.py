@@ -77,7 +77,7 @@ def traffic_record(kernel_src_hash):
 def kernel_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("rsg_kernels.cu", "rsg_vec.cuh", "rsg_internal.h"):
+    for f in ("rsg_kernels.cu", "rsg_vec.cuh"):
         with open(os.path.join(ROOT, "paper_1501_05654_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
