@@ -254,7 +254,7 @@ void block_shape(const TileCfg &c, int SV, int *TX, int *TY) {
     if (c.kernel == 0) {
         int cv, nxr, ty;
         stage_shape(c, SV, &cv, &nxr, &ty);
-        *TX = nxr * (c.rx >= 2 ? 2 : 1);
+        *TX = nxr;
         *TY = ty;
         return;
     }

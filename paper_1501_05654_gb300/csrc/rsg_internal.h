@@ -178,7 +178,7 @@ struct BWork {
 // Staged stencil over every system's tiles (block 2 x 16 x 16, cv = 2).
 cudaError_t launch_batch_stencil(const SysArgs *sys, const BWork *work, int nwork, int in_c, int out_c,
                                  float ar, float ai, cudaStream_t st);
-constexpr int kBatchCV = 2, kBatchTY = 16, kBatchNXR = 16, kBatchZseg = 64;
+constexpr int kBatchCV = 2, kBatchTY = 16, kBatchNXR = 16, kBatchZseg = 120;
 cudaError_t launch_batch_proj(const SysArgs *sys, const BWork *dot_work, int ndot, const BWork *red_work,
                               int nred, int in_c, int npmax, cudaStream_t st);
 cudaError_t launch_batch_scatter(const SysArgs *sys, const BWork *work, int nwork, int out_c, float ar,

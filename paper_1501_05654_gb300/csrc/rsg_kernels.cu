@@ -243,105 +243,96 @@ __device__ __forceinline__ void finish_staged(const ApplyArgs<R> &a, int o, type
     }
 }
 
-template <typename R, int CV, int RX>
+// Fixed geometry of the staged kernel: 512 threads = CV vectors x TX
+// columns x 16 rows, one point per thread along x; every shared-memory offset
+// is then a compile-time constant.
+template <int CV>
+struct StagedGeom {
+    static constexpr int TY = 16, TX = 32 / CV, WX = TX + 8, WY = TY + 8, NTHR = 512;
+    // the star stencil reads a cross: the TY middle rows at full width and
+    // four rows above and below at the interior width; corners are not staged
+    static constexpr int NMID = TY * WX, NCROSS = NMID + 8 * TX, SLOT = WY * WX * CV;
+};
+
+template <typename R, int CV>
 struct StageCtx {
     using T = typename VT<R>::T;
     const ApplyArgs<R> *a;
     const SRow *srows;
     const T *slots;
-    const T *bslots;     // per thread: base of its outputs, NS slots x nthr x RX
-    const R *vslots;     // per thread: V of its columns, NS slots x nthr x RX
-    int tid, nthr;
-    int WX, WY, slot_elems;
-    int xr, yi, cv, v, y, x0;    // thread's tile coordinates and first global x
+    const T *bslots;     // per thread: base of its output, NS slots x 512
+    const R *vslots;     // per thread: V of its column, NS slots x 512
+    int tid;
+    int xr, yi, cv, v, y, x0;    // thread's tile coordinates and global x
     int zbase, zlo, zhi;
-    int zc0, zc1;                // planes where the thread's columns have points
+    int zc0, zc1;                // planes where the thread's column has points
     R w0, w1, w2, w3, w4;
 };
 
 // Plane j has landed in its slot: add its contributions, retire output p-4.
 // Queue slot of output p + (k - 4) is (k + PH) % 9.
-template <typename R, int CV, int RX, int NS, int PH>
-__device__ __forceinline__ void stage_plane(const StageCtx<R, CV, RX> &c, int j,
-                                            typename VT<R>::T (&q)[9][RX]) {
+template <typename R, int CV, int NS, int PH>
+__device__ __forceinline__ void stage_plane(const StageCtx<R, CV> &c, int j, typename VT<R>::T (&q)[9]) {
     using V = VT<R>;
     using T = typename V::T;
+    using G = StagedGeom<CV>;
     constexpr int Q0 = (0 + PH) % 9, Q1 = (1 + PH) % 9, Q2 = (2 + PH) % 9, Q3 = (3 + PH) % 9;
     constexpr int Q4 = (4 + PH) % 9, Q5 = (5 + PH) % 9, Q6 = (6 + PH) % 9, Q7 = (7 + PH) % 9;
     constexpr int Q8 = (8 + PH) % 9;
+    constexpr int RS = G::WX * CV;     // one slot row
     const ApplyArgs<R> &a = *c.a;
-    const T *sl = c.slots + (j % NS) * c.slot_elems;
+    const T *sl = c.slots + (j % NS) * G::SLOT;
     const int p = c.zbase + j;
-    const int WX = c.WX;
-    const T *ctr = sl + ((c.yi + 4) * WX + c.xr * RX + 4) * CV + c.cv;
+    const T *cp = sl + ((c.yi + 4) * G::WX + c.xr + 4) * CV + c.cv;
     // a column off the mesh at plane p contributes nothing (its values and
     // outputs there are zero / absent): skip the arithmetic
-    const bool live = p >= c.zc0 && p <= c.zc1;
-#pragma unroll
-    for (int r = 0; r < RX; r++) {
-        if (!live) break;
-        const T *cp = ctr + r * CV;
+    if (p >= c.zc0 && p <= c.zc1) {
         const T cval = cp[0];
-        V::fma(q[Q3][r], c.w1, cval);
-        V::fma(q[Q5][r], c.w1, cval);
-        V::fma(q[Q2][r], c.w2, cval);
-        V::fma(q[Q6][r], c.w2, cval);
-        V::fma(q[Q1][r], c.w3, cval);
-        V::fma(q[Q7][r], c.w3, cval);
-        V::fma(q[Q0][r], c.w4, cval);
-        V::fma(q[Q8][r], c.w4, cval);
+        V::fma(q[Q3], c.w1, cval);
+        V::fma(q[Q5], c.w1, cval);
+        V::fma(q[Q2], c.w2, cval);
+        V::fma(q[Q6], c.w2, cval);
+        V::fma(q[Q1], c.w3, cval);
+        V::fma(q[Q7], c.w3, cval);
+        V::fma(q[Q0], c.w4, cval);
+        V::fma(q[Q8], c.w4, cval);
         T s = V::scale((R)3 * c.w0, cval);
-        const int rs = WX * CV;
-        V::fma(s, c.w1, V::add(V::add(cp[-CV], cp[CV]), V::add(cp[-rs], cp[rs])));
-        V::fma(s, c.w2, V::add(V::add(cp[-2 * CV], cp[2 * CV]), V::add(cp[-2 * rs], cp[2 * rs])));
-        V::fma(s, c.w3, V::add(V::add(cp[-3 * CV], cp[3 * CV]), V::add(cp[-3 * rs], cp[3 * rs])));
-        V::fma(s, c.w4, V::add(V::add(cp[-4 * CV], cp[4 * CV]), V::add(cp[-4 * rs], cp[4 * rs])));
+        V::fma(s, c.w1, V::add(V::add(cp[-CV], cp[CV]), V::add(cp[-RS], cp[RS])));
+        V::fma(s, c.w2, V::add(V::add(cp[-2 * CV], cp[2 * CV]), V::add(cp[-2 * RS], cp[2 * RS])));
+        V::fma(s, c.w3, V::add(V::add(cp[-3 * CV], cp[3 * CV]), V::add(cp[-3 * RS], cp[3 * RS])));
+        V::fma(s, c.w4, V::add(V::add(cp[-4 * CV], cp[4 * CV]), V::add(cp[-4 * RS], cp[4 * RS])));
         // diagonal: staged V (zero outside the mesh, where c is zero too)
-        const int x = c.x0 + r;
-        const R diag = c.vslots[((j % NS) * c.nthr + c.tid) * RX + r] + a.f0 + a.fx * (R)x +
-                       a.fy * (R)c.y + a.fz * (R)p;
+        const R diag = c.vslots[(j % NS) * G::NTHR + c.tid] + a.f0 + a.fx * (R)c.x0 + a.fy * (R)c.y +
+                       a.fz * (R)p;
         V::fma(s, diag, cval);
-        q[Q4][r] = V::add(q[Q4][r], s);
+        q[Q4] = V::add(q[Q4], s);
     }
     const int zo = p - 4;
     if (zo >= c.zlo && zo < c.zhi && c.v < a.SV) {
-        const SRow ro = c.srows[(j - 4) * c.WY + c.yi + 4];
-#pragma unroll
-        for (int r = 0; r < RX; r++) {
-            const int x = c.x0 + r;
-            if (x >= ro.xmin && x <= ro.xmax) {
-                const int idx = ro.start + (x - ro.xmin);
-                finish_staged<R>(a, idx * a.SV + c.v, q[Q0][r],
-                                 c.bslots[((j % NS) * c.nthr + c.tid) * RX + r]);
-            }
+        const SRow ro = c.srows[(j - 4) * G::WY + c.yi + 4];
+        const int x = c.x0;
+        if (x >= ro.xmin && x <= ro.xmax) {
+            const int idx = ro.start + (x - ro.xmin);
+            finish_staged<R>(a, idx * a.SV + c.v, q[Q0], c.bslots[(j % NS) * G::NTHR + c.tid]);
         }
     }
-#pragma unroll
-    for (int r = 0; r < RX; r++) q[Q0][r] = V::zero();
+    q[Q0] = V::zero();
 }
-
-// Threads per block: 512 for one point per thread along x, 384 for two (the
-// nine-deep queue of two points needs up to 170 registers).
-template <int RX>
-struct StagedThreads {
-    static constexpr int value = RX == 1 ? 512 : 384;
-};
 
 // One block of the staged kernel: tile tl, state chunk `chunk` of the
 // system described by a.  Shared by the single-system and batched kernels.
-template <typename R, int CV, int RX, int NS>
+template <typename R, int CV, int NS>
 __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile tl, const int chunk,
                                              unsigned char *smraw, SRow *srows) {
     using V = VT<R>;
     using T = typename V::T;
-    const int NXR = blockDim.y, TY = blockDim.z;
-    const int TX = NXR * RX, WX = TX + 8, WY = TY + 8;
+    using G = StagedGeom<CV>;
+    constexpr int TX = G::TX, TY = G::TY, WX = G::WX, WY = G::WY;
     const int ny = a.ny, nz = a.nz, SV = a.SV;
     const int xbase = tl.tx * TX - 4, ybase = tl.ty * TY - 4, zbase = tl.zlo - 4;
     const int nzr = tl.zhi - tl.zlo + 8;
-    const int nthr = CV * NXR * TY;
-    const int tid = (threadIdx.z * NXR + threadIdx.y) * CV + threadIdx.x;
-    for (int i = tid; i < WY * nzr; i += nthr) {
+    const int tid = (threadIdx.z * TX + threadIdx.y) * CV + threadIdx.x;
+    for (int i = tid; i < WY * nzr; i += G::NTHR) {
         const int zz = i / WY;
         const int yy = ybase + (i - zz * WY);
         const int zg = zbase + zz;
@@ -356,89 +347,76 @@ __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile t
     }
     __syncthreads();
     T *slots = (T *)smraw;
-    const int slot_elems = WY * WX * CV;
-    T *bslots = slots + NS * slot_elems;                        // NS x nthr x RX
-    R *vslots = (R *)(bslots + NS * nthr * RX);                 // NS x nthr x RX
+    T *bslots = slots + NS * G::SLOT;                          // NS x 512
+    R *vslots = (R *)(bslots + NS * G::NTHR);                  // NS x 512
     const T *__restrict__ in = (const T *)a.in;
     const int cvl = threadIdx.x;
     const int v = chunk * CV + cvl;
     const bool vok = v < SV;
     const int yown = threadIdx.z + 4;
-    const int x0own = tl.tx * TX + threadIdx.y * RX;
+    const int xown = tl.tx * TX + threadIdx.y;
     const unsigned bsh = (unsigned)__cvta_generic_to_shared(bslots);
     const unsigned vsh = (unsigned)__cvta_generic_to_shared(vslots);
     const T *__restrict__ basep = (const T *)a.base;
     // own-point data that travels with plane j: V at plane j (diagonal on
-    // arrival) and the base values of the outputs retired at plane j (j - 4)
+    // arrival) and the base value of the output retired at plane j (j - 4)
     auto stage_epi = [&](int j) {
         const int sl = j % NS;
         const SRow rj = srows[j * WY + yown];
-#pragma unroll
-        for (int r = 0; r < RX; r++) {
-            const int x = x0own + r;
-            const bool ok = (x >= rj.xmin) & (x <= rj.xmax);
-            const int idx = ok ? rj.start + (x - rj.xmin) : 0;
-            cp_async_small<sizeof(R)>(vsh + (unsigned)(((sl * nthr + tid) * RX + r) * sizeof(R)),
-                                      a.V + idx, ok ? (int)sizeof(R) : 0);
-        }
+        const bool okj = (xown >= rj.xmin) & (xown <= rj.xmax);
+        cp_async_small<sizeof(R)>(vsh + (unsigned)((sl * G::NTHR + tid) * sizeof(R)),
+                                  a.V + (okj ? rj.start + (xown - rj.xmin) : 0), okj ? (int)sizeof(R) : 0);
         if (basep != nullptr && j >= 4) {
             const SRow ro = srows[(j - 4) * WY + yown];
-#pragma unroll
-            for (int r = 0; r < RX; r++) {
-                const int x = x0own + r;
-                const bool ok = (x >= ro.xmin) & (x <= ro.xmax) & vok;
-                const int o = ok ? (ro.start + (x - ro.xmin)) * SV + v : 0;
-                cp_async16(bsh + (unsigned)(((sl * nthr + tid) * RX + r) * 16), basep + o, ok ? 16 : 0);
-            }
+            const bool ok = (xown >= ro.xmin) & (xown <= ro.xmax) & vok;
+            const int o = ok ? (ro.start + (xown - ro.xmin)) * SV + v : 0;
+            cp_async16(bsh + (unsigned)((sl * G::NTHR + tid) * 16), basep + o, ok ? 16 : 0);
         }
     };
 
-    // staging assignment: this thread copies points pi = tid / CV + m * step
-    // of the (WY x WX) slot, vector cvl; (yy, xx) advance incrementally
-    const int step = nthr / CV;
-    const int sy = step / WX, sx = step - sy * WX;
+    // staging assignment: this thread copies cross points pi = tid / CV + m * STEP
+    constexpr int STEP = G::NTHR / CV;
     const int pi0 = tid / CV;
-    const int yy0 = pi0 / WX, xx0 = pi0 - yy0 * WX;
     const unsigned sbase = (unsigned)__cvta_generic_to_shared(slots);
     auto stage = [&](int j) {
         stage_epi(j);
-        const unsigned dst0 = sbase + (unsigned)(((j % NS) * slot_elems + pi0 * CV + cvl) * 16);
+        const unsigned dst0 = sbase + (unsigned)(((j % NS) * G::SLOT + cvl) * 16);
         const SRow *rr = srows + j * WY;
-        int yy = yy0, xx = xx0;
-        unsigned dst = dst0;
-        for (int pi = pi0; pi < WY * WX; pi += step) {
-            const SRow rw = rr[yy];
-            const int x = xbase + xx;
-            const bool ok = (x >= rw.xmin) & (x <= rw.xmax) & vok;
-            const int off = ok ? (rw.start + (x - rw.xmin)) * SV + v : 0;
-            cp_async16(dst, in + off, ok ? 16 : 0);
-            dst += step * CV * 16;
-            xx += sx;
-            yy += sy;
-            if (xx >= WX) {
-                xx -= WX;
-                yy++;
+#pragma unroll
+        for (int m = 0; m < (G::NCROSS + STEP - 1) / STEP; m++) {
+            const int pi = pi0 + m * STEP;
+            if (pi < G::NCROSS) {
+                int yy, xx;
+                if (pi < G::NMID) {
+                    yy = 4 + pi / WX;
+                    xx = pi - (yy - 4) * WX;
+                } else {
+                    const int e = pi - G::NMID, r = e / TX;
+                    yy = r < 4 ? r : TY + r;
+                    xx = 4 + (e - r * TX);
+                }
+                const SRow rw = rr[yy];
+                const int x = xbase + xx;
+                const bool ok = (x >= rw.xmin) & (x <= rw.xmax) & vok;
+                const int off = ok ? (rw.start + (x - rw.xmin)) * SV + v : 0;
+                cp_async16(dst0 + (unsigned)((yy * WX + xx) * CV * 16), in + off, ok ? 16 : 0);
             }
         }
     };
 
-    StageCtx<R, CV, RX> c;
+    StageCtx<R, CV> c;
     c.a = &a;
     c.srows = srows;
     c.slots = slots;
     c.bslots = bslots;
     c.vslots = vslots;
     c.tid = tid;
-    c.nthr = nthr;
-    c.WX = WX;
-    c.WY = WY;
-    c.slot_elems = slot_elems;
     c.xr = threadIdx.y;
     c.yi = threadIdx.z;
     c.cv = cvl;
     c.v = v;
     c.y = tl.ty * TY + threadIdx.z;
-    c.x0 = tl.tx * TX + threadIdx.y * RX;
+    c.x0 = xown;
     c.zbase = zbase;
     c.zlo = tl.zlo;
     c.zhi = tl.zhi;
@@ -447,11 +425,9 @@ __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile t
     c.w2 = a.w[2];
     c.w3 = a.w[3];
     c.w4 = a.w[4];
-    T q[9][RX];
+    T q[9];
 #pragma unroll
-    for (int k = 0; k < 9; k++)
-#pragma unroll
-        for (int r = 0; r < RX; r++) q[k][r] = V::zero();
+    for (int k = 0; k < 9; k++) q[k] = V::zero();
 
     const int np = nzr;
     // column z-range of this thread (the mesh meets each column in one run)
@@ -459,12 +435,10 @@ __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile t
     c.zc1 = -(1 << 30);
     for (int jj = 0; jj < np; jj++) {
         const SRow rw = srows[jj * WY + yown];
-#pragma unroll
-        for (int r = 0; r < RX; r++)
-            if (x0own + r >= rw.xmin && x0own + r <= rw.xmax) {
-                c.zc0 = min(c.zc0, zbase + jj);
-                c.zc1 = max(c.zc1, zbase + jj);
-            }
+        if (xown >= rw.xmin && xown <= rw.xmax) {
+            c.zc0 = min(c.zc0, zbase + jj);
+            c.zc1 = max(c.zc1, zbase + jj);
+        }
     }
 #pragma unroll 1
     for (int j = 0; j < NS - 1; j++) {
@@ -483,40 +457,41 @@ __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile t
     int j = 0;
 #pragma unroll 1
     for (; j + 9 <= np; j += 9) {
-        pre(j + 0); stage_plane<R, CV, RX, NS, 0>(c, j + 0, q);
-        pre(j + 1); stage_plane<R, CV, RX, NS, 1>(c, j + 1, q);
-        pre(j + 2); stage_plane<R, CV, RX, NS, 2>(c, j + 2, q);
-        pre(j + 3); stage_plane<R, CV, RX, NS, 3>(c, j + 3, q);
-        pre(j + 4); stage_plane<R, CV, RX, NS, 4>(c, j + 4, q);
-        pre(j + 5); stage_plane<R, CV, RX, NS, 5>(c, j + 5, q);
-        pre(j + 6); stage_plane<R, CV, RX, NS, 6>(c, j + 6, q);
-        pre(j + 7); stage_plane<R, CV, RX, NS, 7>(c, j + 7, q);
-        pre(j + 8); stage_plane<R, CV, RX, NS, 8>(c, j + 8, q);
+        pre(j + 0); stage_plane<R, CV, NS, 0>(c, j + 0, q);
+        pre(j + 1); stage_plane<R, CV, NS, 1>(c, j + 1, q);
+        pre(j + 2); stage_plane<R, CV, NS, 2>(c, j + 2, q);
+        pre(j + 3); stage_plane<R, CV, NS, 3>(c, j + 3, q);
+        pre(j + 4); stage_plane<R, CV, NS, 4>(c, j + 4, q);
+        pre(j + 5); stage_plane<R, CV, NS, 5>(c, j + 5, q);
+        pre(j + 6); stage_plane<R, CV, NS, 6>(c, j + 6, q);
+        pre(j + 7); stage_plane<R, CV, NS, 7>(c, j + 7, q);
+        pre(j + 8); stage_plane<R, CV, NS, 8>(c, j + 8, q);
     }
 #pragma unroll 1
     for (; j < np; j++) {
         pre(j);
         switch (j % 9) {
-        case 0: stage_plane<R, CV, RX, NS, 0>(c, j, q); break;
-        case 1: stage_plane<R, CV, RX, NS, 1>(c, j, q); break;
-        case 2: stage_plane<R, CV, RX, NS, 2>(c, j, q); break;
-        case 3: stage_plane<R, CV, RX, NS, 3>(c, j, q); break;
-        case 4: stage_plane<R, CV, RX, NS, 4>(c, j, q); break;
-        case 5: stage_plane<R, CV, RX, NS, 5>(c, j, q); break;
-        case 6: stage_plane<R, CV, RX, NS, 6>(c, j, q); break;
-        case 7: stage_plane<R, CV, RX, NS, 7>(c, j, q); break;
-        default: stage_plane<R, CV, RX, NS, 8>(c, j, q); break;
+        case 0: stage_plane<R, CV, NS, 0>(c, j, q); break;
+        case 1: stage_plane<R, CV, NS, 1>(c, j, q); break;
+        case 2: stage_plane<R, CV, NS, 2>(c, j, q); break;
+        case 3: stage_plane<R, CV, NS, 3>(c, j, q); break;
+        case 4: stage_plane<R, CV, NS, 4>(c, j, q); break;
+        case 5: stage_plane<R, CV, NS, 5>(c, j, q); break;
+        case 6: stage_plane<R, CV, NS, 6>(c, j, q); break;
+        case 7: stage_plane<R, CV, NS, 7>(c, j, q); break;
+        default: stage_plane<R, CV, NS, 8>(c, j, q); break;
         }
     }
     cp_async_wait<0>();
 }
 
-template <typename R, int CV, int RX, int NS>
-__global__ void __launch_bounds__(StagedThreads<RX>::value, 1) k_apply_staged(const ApplyArgs<R> a, int nchunks) {
+template <typename R, int CV, int NS>
+__global__ void __launch_bounds__(512, 1) k_apply_staged(const ApplyArgs<R> a, int nchunks) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ SRow srows[kSRows];
-    staged_block<R, CV, RX, NS>(a, a.tiles[blockIdx.x / nchunks], blockIdx.x % nchunks, smraw, srows);
+    staged_block<R, CV, NS>(a, a.tiles[blockIdx.x / nchunks], blockIdx.x % nchunks, smraw, srows);
 }
+
 
 // --------------------------------------------------------------- naive ---
 template <typename R>
@@ -561,27 +536,17 @@ void stage_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
     int v = 1;
     while (v < SV && v < c.cv) v <<= 1;
     *cv = v;
-    const int rx = c.rx >= 2 ? 2 : 1;
-    const int nthr = rx == 1 ? 512 : 384;
-    int t = c.ty;
-    while (v * t > nthr / 2 && t > 1) t >>= 1;
-    *ty = t;
-    // widest tile of nthr threads whose pipeline fits 200 KB of shared memory
-    int n = nthr / (v * t);
-    while (n > 1 && (size_t)c.stages * ((t + 8) * (n * rx + 8) * v * 16 + (size_t)v * n * t * rx * 24) >
-                        200 * 1024)
-        n >>= 1;
-    *nxr = n;
+    *ty = 16;          // fixed geometry: 512 threads = cv x (32 / cv) x 16
+    *nxr = 32 / v;
 }
 
 size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes) {
     int cv, nxr, ty;
     stage_shape(c, SV, &cv, &nxr, &ty);
-    const int rx = c.rx >= 2 ? 2 : 1;
-    const size_t nthr = (size_t)cv * nxr * ty;
-    return (size_t)c.stages * ((ty + 8) * (nxr * rx + 8) * cv * vec_bytes +
-                               nthr * rx * (vec_bytes + vec_bytes / 2));
+    // NS slots of the (ty + 8) x (nxr + 8) halo tile, plus per-thread base and V
+    return (size_t)c.stages * ((size_t)(ty + 8) * (nxr + 8) * cv * vec_bytes + 512 * (vec_bytes + vec_bytes / 2));
 }
+
 // Block shape of the TMA kernel: 512 threads, one point per thread along x,
 // pipeline (4 slots of the halo tile plus the base tile) within 200 KB.
 void tma_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
@@ -599,31 +564,25 @@ void tma_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
 size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes);
 #endif
 
-template <typename R, int CV, int RX, int NS>
-static cudaError_t launch_staged_t(const ApplyArgs<R> &a, dim3 block, unsigned nblk, size_t smem,
-                                   int nchunks, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply_staged<R, CV, RX, NS>,
+template <typename R, int CV, int NS>
+static cudaError_t launch_staged_t(const ApplyArgs<R> &a, unsigned nblk, size_t smem, int nchunks,
+                                   cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_apply_staged<R, CV, NS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_apply_staged<R, CV, RX, NS><<<nblk, block, smem, st>>>(a, nchunks);
+    using G = StagedGeom<CV>;
+    k_apply_staged<R, CV, NS><<<nblk, dim3(CV, G::TX, G::TY), smem, st>>>(a, nchunks);
     return cudaGetLastError();
 }
 
-template <typename R, int CV, int NS>
-static cudaError_t launch_staged_rx(const ApplyArgs<R> &a, int rx, dim3 block, unsigned nblk,
-                                    size_t smem, int nchunks, cudaStream_t st) {
-    return rx >= 2 ? launch_staged_t<R, CV, 2, NS>(a, block, nblk, smem, nchunks, st)
-                   : launch_staged_t<R, CV, 1, NS>(a, block, nblk, smem, nchunks, st);
-}
-
 template <typename R, int NS>
-static cudaError_t launch_staged_cv(const ApplyArgs<R> &a, int cv, int rx, dim3 block, unsigned nblk,
-                                    size_t smem, int nchunks, cudaStream_t st) {
+static cudaError_t launch_staged_cv(const ApplyArgs<R> &a, int cv, unsigned nblk, size_t smem, int nchunks,
+                                    cudaStream_t st) {
     switch (cv) {
-    case 1: return launch_staged_rx<R, 1, NS>(a, rx, block, nblk, smem, nchunks, st);
-    case 2: return launch_staged_rx<R, 2, NS>(a, rx, block, nblk, smem, nchunks, st);
-    case 4: return launch_staged_rx<R, 4, NS>(a, rx, block, nblk, smem, nchunks, st);
-    default: return launch_staged_rx<R, 8, NS>(a, rx, block, nblk, smem, nchunks, st);
+    case 1: return launch_staged_t<R, 1, NS>(a, nblk, smem, nchunks, st);
+    case 2: return launch_staged_t<R, 2, NS>(a, nblk, smem, nchunks, st);
+    case 4: return launch_staged_t<R, 4, NS>(a, nblk, smem, nchunks, st);
+    default: return launch_staged_t<R, 8, NS>(a, nblk, smem, nchunks, st);
     }
 }
 
@@ -653,11 +612,10 @@ cudaError_t launch_apply(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, 
     const int nchunks = (a.SV + cv - 1) / cv;
     const size_t smem = stage_smem_bytes(cfg, a.SV, sizeof(typename VT<R>::T));
     if (smem + sizeof(SRow) * kSRows > 227 * 1024) return cudaErrorInvalidConfiguration;
-    dim3 block(cv, nxr, ty);
     const long long nblk = (long long)ntiles * nchunks;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if ((long long)a.P * a.SV >= 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    return launch_staged_cv<R, 4>(a, cv, cfg.rx, block, (unsigned)nblk, smem, nchunks, st);
+    return launch_staged_cv<R, 4>(a, cv, (unsigned)nblk, smem, nchunks, st);
 }
 
 // ---------------------------------------------------------- projectors ---
@@ -1167,7 +1125,7 @@ __global__ void __launch_bounds__(512, 1) k_batch_stencil(const SysArgs *__restr
     const BWork w = work[blockIdx.x];
     const SysArgs &S = sys[w.sys];
     const ApplyArgs<float> a = batch_args(S, in_c, out_c, ar, ai);
-    staged_block<float, kBatchCV, 1, 4>(a, S.tiles[w.a], w.b, smraw, srows);
+    staged_block<float, kBatchCV, 4>(a, S.tiles[w.a], w.b, smraw, srows);
 }
 
 cudaError_t launch_batch_stencil(const SysArgs *sys, const BWork *work, int nwork, int in_c, int out_c,
@@ -1180,7 +1138,8 @@ cudaError_t launch_batch_stencil(const SysArgs *sys, const BWork *work, int nwor
     const size_t smem = stage_smem_bytes(c, kBatchCV, sizeof(float4));
     cudaError_t e = cudaFuncSetAttribute(k_batch_stencil, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_batch_stencil<<<nwork, dim3(kBatchCV, kBatchNXR, kBatchTY), smem, st>>>(sys, work, in_c, out_c, ar, ai);
+    k_batch_stencil<<<nwork, dim3(kBatchCV, StagedGeom<kBatchCV>::TX, StagedGeom<kBatchCV>::TY), smem, st>>>(
+        sys, work, in_c, out_c, ar, ai);
     return cudaGetLastError();
 }
 
