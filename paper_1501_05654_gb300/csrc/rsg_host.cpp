@@ -678,6 +678,7 @@ rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value) {
     else if (k == "ty") *value = H->cfg.ty;
     else if (k == "zseg") *value = H->cfg.zseg;
     else if (k == "cv") *value = H->cfg.cv;
+    else if (k == "threads") *value = H->cfg.threads;
     else return fail(RSG_ERR_ARG, "unknown option: %s", key);
     return RSG_OK;
 }
@@ -695,6 +696,7 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     else if (k == "zseg" && value >= 1 && value <= 120) H->cfg.zseg = (int)value;
     else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
     else if (k == "adjoint_keep_powers" && value >= -1 && value <= 1) H->adj_keep = (int)value;
+    else if (k == "threads" && (value == 256 || value == 512)) H->cfg.threads = (int)value;
     else return fail(RSG_ERR_ARG, "unknown option or value: %s=%lld", key, (long long)value);
     return RSG_OK;
 }

@@ -31,8 +31,9 @@ struct TileCfg {
     int rx = 1;       // points per thread along x
     int ty = 16;      // rows per tile (blockDim.z)
     int zseg = 120;   // planes per z segment
-    int cv = 4;       // staged kernel: 16-byte vectors per point in a chunk (1..8)
+    int cv = 2;       // staged kernel: 16-byte vectors per point in a chunk (1..8)
     int stages = 4;   // staged kernel: shared-memory pipeline depth (4)
+    int threads = 256;   // staged kernel: threads per block (256 with two blocks per SM, or 512)
 };
 
 // Everything one H application needs, by value.  Pointers to the state

@@ -243,18 +243,18 @@ __device__ __forceinline__ void finish_staged(const ApplyArgs<R> &a, int o, type
     }
 }
 
-// Fixed geometry of the staged kernel: 512 threads = CV vectors x TX
+// Fixed geometry of the staged kernel: NT threads = CV vectors x TX
 // columns x 16 rows, one point per thread along x; every shared-memory offset
 // is then a compile-time constant.
-template <int CV>
+template <int CV, int NT = 512>
 struct StagedGeom {
-    static constexpr int TY = 16, TX = 32 / CV, WX = TX + 8, WY = TY + 8, NTHR = 512;
+    static constexpr int TY = 16, TX = NT / 16 / CV, WX = TX + 8, WY = TY + 8, NTHR = NT;
     // the star stencil reads a cross: the TY middle rows at full width and
     // four rows above and below at the interior width; corners are not staged
     static constexpr int NMID = TY * WX, NCROSS = NMID + 8 * TX, SLOT = WY * WX * CV;
 };
 
-template <typename R, int CV>
+template <typename R, int CV, int NT>
 struct StageCtx {
     using T = typename VT<R>::T;
     const ApplyArgs<R> *a;
@@ -271,11 +271,11 @@ struct StageCtx {
 
 // Plane j has landed in its slot: add its contributions, retire output p-4.
 // Queue slot of output p + (k - 4) is (k + PH) % 9.
-template <typename R, int CV, int NS, int PH>
-__device__ __forceinline__ void stage_plane(const StageCtx<R, CV> &c, int j, typename VT<R>::T (&q)[9]) {
+template <typename R, int CV, int NT, int NS, int PH>
+__device__ __forceinline__ void stage_plane(const StageCtx<R, CV, NT> &c, int j, typename VT<R>::T (&q)[9]) {
     using V = VT<R>;
     using T = typename V::T;
-    using G = StagedGeom<CV>;
+    using G = StagedGeom<CV, NT>;
     constexpr int Q0 = (0 + PH) % 9, Q1 = (1 + PH) % 9, Q2 = (2 + PH) % 9, Q3 = (3 + PH) % 9;
     constexpr int Q4 = (4 + PH) % 9, Q5 = (5 + PH) % 9, Q6 = (6 + PH) % 9, Q7 = (7 + PH) % 9;
     constexpr int Q8 = (8 + PH) % 9;
@@ -321,12 +321,12 @@ __device__ __forceinline__ void stage_plane(const StageCtx<R, CV> &c, int j, typ
 
 // One block of the staged kernel: tile tl, state chunk `chunk` of the
 // system described by a.  Shared by the single-system and batched kernels.
-template <typename R, int CV, int NS>
+template <typename R, int CV, int NS, int NT = 512>
 __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile tl, const int chunk,
                                              unsigned char *smraw, SRow *srows) {
     using V = VT<R>;
     using T = typename V::T;
-    using G = StagedGeom<CV>;
+    using G = StagedGeom<CV, NT>;
     constexpr int TX = G::TX, TY = G::TY, WX = G::WX, WY = G::WY;
     const int ny = a.ny, nz = a.nz, SV = a.SV;
     const int xbase = tl.tx * TX - 4, ybase = tl.ty * TY - 4, zbase = tl.zlo - 4;
@@ -404,7 +404,7 @@ __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile t
         }
     };
 
-    StageCtx<R, CV> c;
+    StageCtx<R, CV, NT> c;
     c.a = &a;
     c.srows = srows;
     c.slots = slots;
@@ -457,39 +457,39 @@ __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile t
     int j = 0;
 #pragma unroll 1
     for (; j + 9 <= np; j += 9) {
-        pre(j + 0); stage_plane<R, CV, NS, 0>(c, j + 0, q);
-        pre(j + 1); stage_plane<R, CV, NS, 1>(c, j + 1, q);
-        pre(j + 2); stage_plane<R, CV, NS, 2>(c, j + 2, q);
-        pre(j + 3); stage_plane<R, CV, NS, 3>(c, j + 3, q);
-        pre(j + 4); stage_plane<R, CV, NS, 4>(c, j + 4, q);
-        pre(j + 5); stage_plane<R, CV, NS, 5>(c, j + 5, q);
-        pre(j + 6); stage_plane<R, CV, NS, 6>(c, j + 6, q);
-        pre(j + 7); stage_plane<R, CV, NS, 7>(c, j + 7, q);
-        pre(j + 8); stage_plane<R, CV, NS, 8>(c, j + 8, q);
+        pre(j + 0); stage_plane<R, CV, NT, NS, 0>(c, j + 0, q);
+        pre(j + 1); stage_plane<R, CV, NT, NS, 1>(c, j + 1, q);
+        pre(j + 2); stage_plane<R, CV, NT, NS, 2>(c, j + 2, q);
+        pre(j + 3); stage_plane<R, CV, NT, NS, 3>(c, j + 3, q);
+        pre(j + 4); stage_plane<R, CV, NT, NS, 4>(c, j + 4, q);
+        pre(j + 5); stage_plane<R, CV, NT, NS, 5>(c, j + 5, q);
+        pre(j + 6); stage_plane<R, CV, NT, NS, 6>(c, j + 6, q);
+        pre(j + 7); stage_plane<R, CV, NT, NS, 7>(c, j + 7, q);
+        pre(j + 8); stage_plane<R, CV, NT, NS, 8>(c, j + 8, q);
     }
 #pragma unroll 1
     for (; j < np; j++) {
         pre(j);
         switch (j % 9) {
-        case 0: stage_plane<R, CV, NS, 0>(c, j, q); break;
-        case 1: stage_plane<R, CV, NS, 1>(c, j, q); break;
-        case 2: stage_plane<R, CV, NS, 2>(c, j, q); break;
-        case 3: stage_plane<R, CV, NS, 3>(c, j, q); break;
-        case 4: stage_plane<R, CV, NS, 4>(c, j, q); break;
-        case 5: stage_plane<R, CV, NS, 5>(c, j, q); break;
-        case 6: stage_plane<R, CV, NS, 6>(c, j, q); break;
-        case 7: stage_plane<R, CV, NS, 7>(c, j, q); break;
-        default: stage_plane<R, CV, NS, 8>(c, j, q); break;
+        case 0: stage_plane<R, CV, NT, NS, 0>(c, j, q); break;
+        case 1: stage_plane<R, CV, NT, NS, 1>(c, j, q); break;
+        case 2: stage_plane<R, CV, NT, NS, 2>(c, j, q); break;
+        case 3: stage_plane<R, CV, NT, NS, 3>(c, j, q); break;
+        case 4: stage_plane<R, CV, NT, NS, 4>(c, j, q); break;
+        case 5: stage_plane<R, CV, NT, NS, 5>(c, j, q); break;
+        case 6: stage_plane<R, CV, NT, NS, 6>(c, j, q); break;
+        case 7: stage_plane<R, CV, NT, NS, 7>(c, j, q); break;
+        default: stage_plane<R, CV, NT, NS, 8>(c, j, q); break;
         }
     }
     cp_async_wait<0>();
 }
 
-template <typename R, int CV, int NS>
-__global__ void __launch_bounds__(512, 1) k_apply_staged(const ApplyArgs<R> a, int nchunks) {
+template <typename R, int CV, int NS, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_apply_staged(const ApplyArgs<R> a, int nchunks) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ SRow srows[kSRows];
-    staged_block<R, CV, NS>(a, a.tiles[blockIdx.x / nchunks], blockIdx.x % nchunks, smraw, srows);
+    staged_block<R, CV, NS, NT>(a, a.tiles[blockIdx.x / nchunks], blockIdx.x % nchunks, smraw, srows);
 }
 
 
@@ -535,16 +535,19 @@ static inline int pow2_at_least(int v) {
 void stage_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
     int v = 1;
     while (v < SV && v < c.cv) v <<= 1;
+    if (c.threads == 256 && v < 2) v = 2;
+    if (c.threads == 256 && v > 4) v = 4;
     *cv = v;
-    *ty = 16;          // fixed geometry: 512 threads = cv x (32 / cv) x 16
-    *nxr = 32 / v;
+    *ty = 16;          // fixed geometry: threads = cv x (threads / 16 / cv) x 16
+    *nxr = c.threads / 16 / v;
 }
 
 size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes) {
     int cv, nxr, ty;
     stage_shape(c, SV, &cv, &nxr, &ty);
     // NS slots of the (ty + 8) x (nxr + 8) halo tile, plus per-thread base and V
-    return (size_t)c.stages * ((size_t)(ty + 8) * (nxr + 8) * cv * vec_bytes + 512 * (vec_bytes + vec_bytes / 2));
+    return (size_t)c.stages *
+           ((size_t)(ty + 8) * (nxr + 8) * cv * vec_bytes + (size_t)c.threads * (vec_bytes + vec_bytes / 2));
 }
 
 // Block shape of the TMA kernel: 512 threads, one point per thread along x,
@@ -564,25 +567,29 @@ void tma_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
 size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes);
 #endif
 
-template <typename R, int CV, int NS>
+template <typename R, int CV, int NS, int NT>
 static cudaError_t launch_staged_t(const ApplyArgs<R> &a, unsigned nblk, size_t smem, int nchunks,
                                    cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply_staged<R, CV, NS>,
+    cudaError_t e = cudaFuncSetAttribute(k_apply_staged<R, CV, NS, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    using G = StagedGeom<CV>;
-    k_apply_staged<R, CV, NS><<<nblk, dim3(CV, G::TX, G::TY), smem, st>>>(a, nchunks);
+    using G = StagedGeom<CV, NT>;
+    k_apply_staged<R, CV, NS, NT><<<nblk, dim3(CV, G::TX, G::TY), smem, st>>>(a, nchunks);
     return cudaGetLastError();
 }
 
 template <typename R, int NS>
-static cudaError_t launch_staged_cv(const ApplyArgs<R> &a, int cv, unsigned nblk, size_t smem, int nchunks,
-                                    cudaStream_t st) {
+static cudaError_t launch_staged_cv(const ApplyArgs<R> &a, int cv, int threads, unsigned nblk, size_t smem,
+                                    int nchunks, cudaStream_t st) {
+    if (threads == 256) {
+        if (cv <= 2) return launch_staged_t<R, 2, NS, 256>(a, nblk, smem, nchunks, st);
+        return launch_staged_t<R, 4, NS, 256>(a, nblk, smem, nchunks, st);
+    }
     switch (cv) {
-    case 1: return launch_staged_t<R, 1, NS>(a, nblk, smem, nchunks, st);
-    case 2: return launch_staged_t<R, 2, NS>(a, nblk, smem, nchunks, st);
-    case 4: return launch_staged_t<R, 4, NS>(a, nblk, smem, nchunks, st);
-    default: return launch_staged_t<R, 8, NS>(a, nblk, smem, nchunks, st);
+    case 1: return launch_staged_t<R, 1, NS, 512>(a, nblk, smem, nchunks, st);
+    case 2: return launch_staged_t<R, 2, NS, 512>(a, nblk, smem, nchunks, st);
+    case 4: return launch_staged_t<R, 4, NS, 512>(a, nblk, smem, nchunks, st);
+    default: return launch_staged_t<R, 8, NS, 512>(a, nblk, smem, nchunks, st);
     }
 }
 
@@ -615,7 +622,7 @@ cudaError_t launch_apply(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, 
     const long long nblk = (long long)ntiles * nchunks;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if ((long long)a.P * a.SV >= 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    return launch_staged_cv<R, 4>(a, cv, (unsigned)nblk, smem, nchunks, st);
+    return launch_staged_cv<R, 4>(a, cv, cfg.threads, (unsigned)nblk, smem, nchunks, st);
 }
 
 // ---------------------------------------------------------- projectors ---
@@ -1125,7 +1132,7 @@ __global__ void __launch_bounds__(512, 1) k_batch_stencil(const SysArgs *__restr
     const BWork w = work[blockIdx.x];
     const SysArgs &S = sys[w.sys];
     const ApplyArgs<float> a = batch_args(S, in_c, out_c, ar, ai);
-    staged_block<float, kBatchCV, 4>(a, S.tiles[w.a], w.b, smraw, srows);
+    staged_block<float, kBatchCV, 4, 512>(a, S.tiles[w.a], w.b, smraw, srows);
 }
 
 cudaError_t launch_batch_stencil(const SysArgs *sys, const BWork *work, int nwork, int in_c, int out_c,
@@ -1138,7 +1145,7 @@ cudaError_t launch_batch_stencil(const SysArgs *sys, const BWork *work, int nwor
     const size_t smem = stage_smem_bytes(c, kBatchCV, sizeof(float4));
     cudaError_t e = cudaFuncSetAttribute(k_batch_stencil, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_batch_stencil<<<nwork, dim3(kBatchCV, StagedGeom<kBatchCV>::TX, StagedGeom<kBatchCV>::TY), smem, st>>>(
+    k_batch_stencil<<<nwork, dim3(kBatchCV, StagedGeom<kBatchCV, 512>::TX, StagedGeom<kBatchCV, 512>::TY), smem, st>>>(
         sys, work, in_c, out_c, ar, ai);
     return cudaGetLastError();
 }
