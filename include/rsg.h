@@ -213,8 +213,10 @@ rsg_status rsg_batch_destroy(rsg_batch b);
  * x: 1, 2 or 4; the staged kernel uses 1 or 2), "ty" (rows per
  * tile: 1, 2, 4, 8 or 16), "zseg" (planes per z segment, 1..120), "cv"
  * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8),
- * "threads" (staged kernel: 512 threads per block, or 256 with two blocks
- * per SM), "adjoint_keep_powers" (rsg_control_gradient: 1 keeps the Taylor powers of
+ * "threads" (staged kernel: 256 threads per block, the default, or 512),
+ * "stages" (staged kernel: shared-memory pipeline depth, 3 or 4),
+ * "blocks_per_sm" (staged kernel with 256 threads: register budget for 2 or
+ * 3 resident blocks per SM), "adjoint_keep_powers" (rsg_control_gradient: 1 keeps the Taylor powers of
  * a whole checkpoint segment, 0 recomputes them per interval, -1 = choose by
  * free device memory, the default).
  * A shape whose shared memory does not fit the SM fails with RSG_ERR_CUDA. */

@@ -697,6 +697,8 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
     else if (k == "adjoint_keep_powers" && value >= -1 && value <= 1) H->adj_keep = (int)value;
     else if (k == "threads" && (value == 256 || value == 512)) H->cfg.threads = (int)value;
+    else if (k == "stages" && (value == 3 || value == 4)) H->cfg.stages = (int)value;
+    else if (k == "blocks_per_sm" && (value == 2 || value == 3)) H->cfg.blocks_per_sm = (int)value;
     else return fail(RSG_ERR_ARG, "unknown option or value: %s=%lld", key, (long long)value);
     return RSG_OK;
 }

@@ -32,7 +32,8 @@ struct TileCfg {
     int ty = 16;      // rows per tile (blockDim.z)
     int zseg = 120;   // planes per z segment
     int cv = 2;       // staged kernel: 16-byte vectors per point in a chunk (1..8)
-    int stages = 4;   // staged kernel: shared-memory pipeline depth (4)
+    int stages = 4;   // staged kernel: shared-memory pipeline depth (3 or 4)
+    int blocks_per_sm = 2;   // staged kernel, 256 threads: register budget for 2 or 3 blocks per SM
     int threads = 256;   // staged kernel: threads per block (256 with two blocks per SM, or 512)
 };
 

@@ -485,11 +485,14 @@ __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile t
     cp_async_wait<0>();
 }
 
-template <typename R, int CV, int NS, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) k_apply_staged(const ApplyArgs<R> a, int nchunks) {
+// The staged kernel keeps its row table in dynamic shared memory after the
+// pipeline slots, sized by the z-segment length (srow_off bytes in), so that
+// MINB blocks fit on one SM.
+template <typename R, int CV, int NS, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_apply_staged(const ApplyArgs<R> a, int nchunks, int srow_off) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ SRow srows[kSRows];
-    staged_block<R, CV, NS, NT>(a, a.tiles[blockIdx.x / nchunks], blockIdx.x % nchunks, smraw, srows);
+    staged_block<R, CV, NS, NT>(a, a.tiles[blockIdx.x / nchunks], blockIdx.x % nchunks, smraw,
+                                (SRow *)(smraw + srow_off));
 }
 
 
@@ -550,6 +553,9 @@ size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes) {
            ((size_t)(ty + 8) * (nxr + 8) * cv * vec_bytes + (size_t)c.threads * (vec_bytes + vec_bytes / 2));
 }
 
+// Row-table bytes of the staged kernel: (ty + 8) rows x (zseg + 8) planes.
+size_t stage_rows_bytes(const TileCfg &c) { return (size_t)(16 + 8) * (c.zseg + 8) * sizeof(SRow); }
+
 // Block shape of the TMA kernel: 512 threads, one point per thread along x,
 // pipeline (4 slots of the halo tile plus the base tile) within 200 KB.
 void tma_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
@@ -565,31 +571,43 @@ void tma_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
 }
 #else
 size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes);
+size_t stage_rows_bytes(const TileCfg &c);
 #endif
 
-template <typename R, int CV, int NS, int NT>
-static cudaError_t launch_staged_t(const ApplyArgs<R> &a, unsigned nblk, size_t smem, int nchunks,
-                                   cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(k_apply_staged<R, CV, NS, NT>,
+template <typename R, int CV, int NS, int NT, int MINB>
+static cudaError_t launch_staged_t(const ApplyArgs<R> &a, unsigned nblk, size_t smem, int srow_off,
+                                   int nchunks, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_apply_staged<R, CV, NS, NT, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     using G = StagedGeom<CV, NT>;
-    k_apply_staged<R, CV, NS, NT><<<nblk, dim3(CV, G::TX, G::TY), smem, st>>>(a, nchunks);
+    k_apply_staged<R, CV, NS, NT, MINB><<<nblk, dim3(CV, G::TX, G::TY), smem, st>>>(a, nchunks, srow_off);
     return cudaGetLastError();
 }
 
-template <typename R, int NS>
-static cudaError_t launch_staged_cv(const ApplyArgs<R> &a, int cv, int threads, unsigned nblk, size_t smem,
-                                    int nchunks, cudaStream_t st) {
-    if (threads == 256) {
-        if (cv <= 2) return launch_staged_t<R, 2, NS, 256>(a, nblk, smem, nchunks, st);
-        return launch_staged_t<R, 4, NS, 256>(a, nblk, smem, nchunks, st);
+template <typename R>
+static cudaError_t launch_staged_cv(const ApplyArgs<R> &a, const TileCfg &cfg, int cv, unsigned nblk, size_t smem,
+                                    int srow_off, int nchunks, cudaStream_t st) {
+    if (cfg.threads == 256) {
+        const bool three = cfg.blocks_per_sm >= 3;
+        if (cfg.stages == 3) {
+            if (cv <= 2)
+                return three ? launch_staged_t<R, 2, 3, 256, 3>(a, nblk, smem, srow_off, nchunks, st)
+                             : launch_staged_t<R, 2, 3, 256, 2>(a, nblk, smem, srow_off, nchunks, st);
+            return three ? launch_staged_t<R, 4, 3, 256, 3>(a, nblk, smem, srow_off, nchunks, st)
+                         : launch_staged_t<R, 4, 3, 256, 2>(a, nblk, smem, srow_off, nchunks, st);
+        }
+        if (cv <= 2)
+            return three ? launch_staged_t<R, 2, 4, 256, 3>(a, nblk, smem, srow_off, nchunks, st)
+                         : launch_staged_t<R, 2, 4, 256, 2>(a, nblk, smem, srow_off, nchunks, st);
+        return three ? launch_staged_t<R, 4, 4, 256, 3>(a, nblk, smem, srow_off, nchunks, st)
+                     : launch_staged_t<R, 4, 4, 256, 2>(a, nblk, smem, srow_off, nchunks, st);
     }
     switch (cv) {
-    case 1: return launch_staged_t<R, 1, NS, 512>(a, nblk, smem, nchunks, st);
-    case 2: return launch_staged_t<R, 2, NS, 512>(a, nblk, smem, nchunks, st);
-    case 4: return launch_staged_t<R, 4, NS, 512>(a, nblk, smem, nchunks, st);
-    default: return launch_staged_t<R, 8, NS, 512>(a, nblk, smem, nchunks, st);
+    case 1: return launch_staged_t<R, 1, 4, 512, 1>(a, nblk, smem, srow_off, nchunks, st);
+    case 2: return launch_staged_t<R, 2, 4, 512, 1>(a, nblk, smem, srow_off, nchunks, st);
+    case 4: return launch_staged_t<R, 4, 4, 512, 1>(a, nblk, smem, srow_off, nchunks, st);
+    default: return launch_staged_t<R, 8, 4, 512, 1>(a, nblk, smem, srow_off, nchunks, st);
     }
 }
 
@@ -617,12 +635,13 @@ cudaError_t launch_apply(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, 
     int cv, nxr, ty;
     stage_shape(cfg, a.SV, &cv, &nxr, &ty);
     const int nchunks = (a.SV + cv - 1) / cv;
-    const size_t smem = stage_smem_bytes(cfg, a.SV, sizeof(typename VT<R>::T));
-    if (smem + sizeof(SRow) * kSRows > 227 * 1024) return cudaErrorInvalidConfiguration;
+    const size_t slots = stage_smem_bytes(cfg, a.SV, sizeof(typename VT<R>::T));
+    const size_t smem = slots + stage_rows_bytes(cfg);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
     const long long nblk = (long long)ntiles * nchunks;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if ((long long)a.P * a.SV >= 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    return launch_staged_cv<R, 4>(a, cv, cfg.threads, (unsigned)nblk, smem, nchunks, st);
+    return launch_staged_cv<R>(a, cfg, cv, (unsigned)nblk, smem, (int)slots, nchunks, st);
 }
 
 // ---------------------------------------------------------- projectors ---
@@ -1138,11 +1157,11 @@ __global__ void __launch_bounds__(512, 1) k_batch_stencil(const SysArgs *__restr
 cudaError_t launch_batch_stencil(const SysArgs *sys, const BWork *work, int nwork, int in_c, int out_c,
                                  float ar, float ai, cudaStream_t st) {
     if (nwork == 0) return cudaSuccess;
-    TileCfg c;
-    c.cv = kBatchCV;
-    c.ty = kBatchTY;
-    c.rx = 1;
-    const size_t smem = stage_smem_bytes(c, kBatchCV, sizeof(float4));
+    // shared memory of the batched block, from its own compile-time geometry
+    // (512 threads, 4 slots): slots of the halo tile plus per-thread base and V
+    using G = StagedGeom<kBatchCV, 512>;
+    const size_t smem = (size_t)4 * ((size_t)G::SLOT * sizeof(float4) + (size_t)G::NTHR * (sizeof(float4) + sizeof(float)));
+    static_assert(G::TX == kBatchNXR && G::TY == kBatchTY, "batch tiles and block geometry must agree");
     cudaError_t e = cudaFuncSetAttribute(k_batch_stencil, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_batch_stencil<<<nwork, dim3(kBatchCV, StagedGeom<kBatchCV, 512>::TX, StagedGeom<kBatchCV, 512>::TY), smem, st>>>(

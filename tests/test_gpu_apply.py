@@ -64,7 +64,10 @@ def test_box_odd_extents(dtype):
                                   {"kernel": 2, "rx": 4}, {"kernel": 2, "ty": 2, "zseg": 5},
                                   {"kernel": 2, "ty": 4, "rx": 4, "zseg": 3},
                                   {"kernel": 0, "threads": 256, "cv": 2}, {"kernel": 0, "threads": 256, "cv": 4},
-                                  {"kernel": 0, "cv": 8, "zseg": 120}, {"kernel": 0, "cv": 1, "zseg": 11}])
+                                  {"kernel": 0, "cv": 8, "zseg": 120, "threads": 512},
+                                  {"kernel": 0, "cv": 1, "zseg": 11, "threads": 512},
+                                  {"kernel": 0, "stages": 3, "blocks_per_sm": 3, "zseg": 40},
+                                  {"kernel": 0, "stages": 3, "blocks_per_sm": 2, "cv": 4, "zseg": 9}])
 def test_kernel_variants_agree(opts):
     p, g = wells_system("sphere", radius=3.3, h=0.25, dtype=torch.complex64, seed=7, natoms=2)
     _check_apply(p, g, 10, opts=opts, expect_kernel=opts["kernel"])
