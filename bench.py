@@ -182,8 +182,8 @@ def extras(mesh, wells, proj, g):
     2000 intervals of dt = 0.05 au, 4 ETRS substeps, checkpoints every 50)."""
     import torch
     import paper_1501_05654_gb300 as rsg
-    from workloads import (control_field, potential_double_well, potential_wells, rng,
-                           white_noise_states)
+    from workloads import (control_field, potential_double_well, potential_wells, projector_atoms,
+                           rng, white_noise_states)
     out = {}
     P, S = mesh.P, 64
     for name, dtype, kernel in (("c64_plain_kernel", torch.complex64, 1),
@@ -201,6 +201,31 @@ def extras(mesh, wells, proj, g):
                      "unit": UNIT}
         del psi, H
         torch.cuda.empty_cache()
+    # batch of 256 uneven systems (cubes 24^3..96^3 at h = 0.25, 1..16 states,
+    # 1..8 atoms x 4 projectors): one launch per Horner stage for all systems
+    from workloads import batch_systems, gaussian_wells
+    gb = rng(3)
+    ns, Ss, nas = batch_systems(gb, 256)
+    hams, psis, pst = [], [], 0
+    for n, S_, na in zip(ns, Ss, nas):
+        m = rsg.Mesh(rsg.CUBE, int(n), spacing=0.25)
+        half = 0.5 * (n - 1) * 0.25
+        c, d, w = gaussian_wells(gb, int(na), 0.0, cube_half=0.6 * half)
+        Hb = rsg.Hamiltonian(m, torch.complex64)
+        Hb.set_potential(potential_wells(m.xyz, c, d, w))
+        Hb.set_projectors(*projector_atoms(gb, int(na), 2.5, 1, cube_half=0.6 * half))
+        hams.append(Hb)
+        psis.append(torch.randn((m.P, rsg.padded_ld(int(S_), torch.complex64)), dtype=torch.complex64,
+                                device="cuda") * 1e-3)
+        pst += m.P * int(S_)
+    batch = rsg.Batch(hams, [int(x) for x in Ss])
+    ms = time_steps(None, psis, 10, lambda xs: batch.propagate(xs, 1, 0.02, scheme=rsg.ETRS))
+    out["batch_256_systems"] = {"ms_per_step": ms, "point_states": pst,
+                                "value": pst * N_APPLY_PER_STEP / (ms * 1e-3) / 1e9, "unit": UNIT,
+                                "workload": "256 cubes n~U{24..96} h=0.25, S~U{1..16}, 1..8 atoms x 4 "
+                                            "projectors, ETRS dt=0.02, one captured graph per step"}
+    del batch, hams, psis
+    torch.cuda.empty_cache()
     # control gradient vs forward (the optimal-control workload)
     cm = rsg.Mesh(rsg.CUBE, 64, spacing=0.3)
     gg = rng(4)

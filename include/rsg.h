@@ -222,6 +222,16 @@ rsg_status rsg_batch_destroy(rsg_batch b);
  * A shape whose shared memory does not fit the SM fails with RSG_ERR_CUDA. */
 rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value);
 
+/* Autotuner: times one Horner stage of H on psi (device, read only) into
+ * work (device, same shape, caller-owned scratch) for every candidate stencil
+ * configuration (the one-thread-per-value kernel and the staged kernel in
+ * several block shapes and z-segment lengths), keeps the fastest as H's
+ * configuration and returns its time per stage in *best_ms (may be NULL).
+ * The choice depends on the mesh, S and ld; rerun it when they change.
+ * Synchronises. */
+rsg_status rsg_ham_autotune(rsg_ham H, const void *psi, void *work, int64_t S, int64_t ld, void *stream,
+                            double *best_ms);
+
 /* Reads an option set above, or "last_kernel": the stencil kernel (0..3)
  * that the last Hamiltonian application actually ran (-1 before any), after
  * automatic fallbacks (small problems, TMA unavailable). */

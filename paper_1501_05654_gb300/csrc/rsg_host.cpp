@@ -669,6 +669,70 @@ rsg_status rsg_ham_kernel_stats(rsg_ham H, double *kernel_ms, int64_t *kernel_la
     return RSG_OK;
 }
 
+rsg_status rsg_ham_autotune(rsg_ham H, const void *psi, void *work, int64_t S, int64_t ld, void *stream,
+                            double *best_ms) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    CKS(check_block(H, psi, S, ld, "psi"));
+    CKS(check_block(H, work, S, ld, "work"));
+    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    const size_t bytes = (size_t)H->m->P * ld * cbytes(H->dtype);
+    if (overlaps(psi, work, bytes)) return fail(RSG_ERR_ARG, "psi and work overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    // candidates: the one-thread-per-value kernel and the staged kernel in
+    // the block shapes that fit the SM (timed as a Horner stage)
+    std::vector<TileCfg> cand;
+    {
+        TileCfg c;
+        c.kernel = 1;
+        cand.push_back(c);
+    }
+    const int shapes[][3] = {{256, 2, 3}, {256, 2, 4}, {256, 4, 4}, {512, 4, 4}, {512, 8, 4}, {512, 2, 4}};
+    for (const auto &sh : shapes)
+        for (int zs : {64, 120}) {
+            TileCfg c;
+            c.kernel = 0;
+            c.threads = sh[0];
+            c.cv = sh[1];
+            c.stages = sh[2];
+            c.zseg = zs;
+            cand.push_back(c);
+        }
+    const TileCfg saved = H->cfg;
+    const bool saved_force = H->force_kernel;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e30;
+    TileCfg pick = saved;
+    const int SV = sv_of(H, ld);
+    for (const TileCfg &c : cand) {
+        H->cfg = c;
+        H->force_kernel = true;
+        Epi ep;
+        ep.ar = 0.0;
+        ep.ai = -1e-3;
+        ep.base = psi;
+        if (apply(H, psi, work, SV, 0.0, nullptr, ep, st) != RSG_OK) continue;   // shape not usable
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; r++) apply(H, psi, work, SV, 0.0, nullptr, ep, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / 3 < best && H->last_kernel == c.kernel) {
+            best = ms / 3;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    H->cfg = best < 1e30 ? pick : saved;
+    H->force_kernel = best < 1e30 ? true : saved_force;
+    if (best_ms) *best_ms = best < 1e30 ? best : -1.0;
+    return best < 1e30 ? read_status(H, st) : fail(RSG_ERR_CUDA, "no candidate ran");
+}
+
 rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value) {
     if (!H || !key || !value) return fail(RSG_ERR_ARG, "NULL argument");
     std::string k(key);
@@ -679,6 +743,8 @@ rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value) {
     else if (k == "zseg") *value = H->cfg.zseg;
     else if (k == "cv") *value = H->cfg.cv;
     else if (k == "threads") *value = H->cfg.threads;
+    else if (k == "stages") *value = H->cfg.stages;
+    else if (k == "blocks_per_sm") *value = H->cfg.blocks_per_sm;
     else return fail(RSG_ERR_ARG, "unknown option: %s", key);
     return RSG_OK;
 }

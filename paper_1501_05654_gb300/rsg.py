@@ -51,6 +51,7 @@ SIGNATURES = {
     "rsg_batch_destroy": [_vp],
     "rsg_ham_set_option": [_vp, C.c_char_p, _i64],
     "rsg_ham_get_option": [_vp, C.c_char_p, _vp],
+    "rsg_ham_autotune": [_vp, _vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_ham_profile": [_vp, _int],
     "rsg_ham_kernel_stats": [_vp, _vp, _vp, _vp, _vp],
     "rsg_last_error": [],
@@ -188,6 +189,41 @@ class Hamiltonian:
         v = C.c_int64()
         _ck(load().rsg_ham_get_option(self._h, key.encode(), C.byref(v)))
         return int(v.value)
+
+    TUNED_KEYS = ("kernel", "threads", "cv", "stages", "zseg", "blocks_per_sm")
+
+    def autotune(self, psi, S=None, cache_path=None, stream=None):
+        """Choose the fastest stencil configuration for this mesh and block.
+
+        With cache_path (a JSON file), a configuration tuned earlier for the
+        same mesh size, state count, leading dimension and dtype is reused
+        without timing, and new results are added to the file.
+        """
+        import json
+        self._check(psi)
+        S = psi.shape[1] if S is None else S
+        key = f"{self.mesh.P}:{self.mesh.h:.6g}:{S}:{psi.shape[1]}:{self.dtype}"
+        cache = {}
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                cache = json.load(f)
+            if key in cache:
+                for k in self.TUNED_KEYS:
+                    self.set_option(k, cache[key][k])
+                return cache[key]
+        work = torch.empty_like(psi)
+        best = C.c_double()
+        _ck(load().rsg_ham_autotune(self._h, C.c_void_p(psi.data_ptr()), C.c_void_p(work.data_ptr()), S,
+                                    psi.shape[1], _stream(stream), C.byref(best)))
+        res = {k: self.get_option(k) for k in self.TUNED_KEYS}
+        res["stage_ms"] = float(best.value)
+        if cache_path:
+            cache[key] = res
+            tmp = cache_path + f".tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1)
+            os.replace(tmp, cache_path)
+        return res
 
     def profile(self, enable: bool):
         _ck(load().rsg_ham_profile(self._h, 1 if enable else 0))

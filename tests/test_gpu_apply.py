@@ -160,3 +160,21 @@ def test_full_size_sphere_sampled(dtype):
     lib_rows = np.argsort(p.idx)[samp]     # library index of each sampled oracle point
     got = y[torch.from_numpy(lib_rows).cuda()].cpu().numpy().astype(np.complex128)
     assert rel_err(got, want) < TOL[dtype]
+
+
+def test_autotune_picks_a_working_configuration(tmp_path):
+    p, g = wells_system("sphere", radius=6.0, h=0.25, dtype=torch.complex64, seed=9, natoms=2)
+    psi = round_c64(white_noise_states(g, p.P, 12))
+    x = p.states_to_gpu(psi)
+    cache = str(tmp_path / "tune.json")
+    res = p.H.autotune(x, S=12, cache_path=cache)
+    assert res["stage_ms"] > 0
+    # the tuned configuration still matches the oracle
+    want = p.O.apply(psi)
+    y = p.H.apply(x, S=12)
+    torch.cuda.synchronize()
+    assert rel_err(p.states_from_gpu(y, 12), want) < TOL[torch.complex64]
+    # a second Hamiltonian reuses the cached choice without timing
+    q, _ = wells_system("sphere", radius=6.0, h=0.25, dtype=torch.complex64, seed=9, natoms=2)
+    res2 = q.H.autotune(q.states_to_gpu(psi), S=12, cache_path=cache)
+    assert {k: res2[k] for k in q.H.TUNED_KEYS} == {k: res[k] for k in q.H.TUNED_KEYS}
