@@ -226,6 +226,40 @@ def extras(mesh, wells, proj, g):
                                             "projectors, ETRS dt=0.02, one captured graph per step"}
     del batch, hams, psis
     torch.cuda.empty_cache()
+    # large cube: 192^3 at h = 0.18, 128 smooth complex64 states, 64 atoms x 9
+    # projectors (s, p, d) on 3-bohr spheres, ETRS dt = 0.01, FP64-checked
+    # Cholesky-QR every 50 steps; drift = max |<psi|psi> - 1| before it
+    gl = rng(5)
+    cm5 = rsg.Mesh(rsg.CUBE, 192, spacing=0.18)
+    half = 0.5 * 191 * 0.18
+    c5, d5, w5 = gaussian_wells(gl, 64, 0.0, cube_half=half - 3.0)
+    H5 = rsg.Hamiltonian(cm5, torch.complex64)
+    H5.set_potential(potential_wells(cm5.xyz, c5, d5, w5))
+    cen, rc, lm, beta, hm = projector_atoms(gl, 64, 3.0, 2, cube_half=half - 3.0)
+    cen[:] = c5                                   # projectors sit on the wells
+    H5.set_projectors(cen, rc, lm, beta, hm)
+    xyz = torch.from_numpy(cm5.xyz).to("cuda", torch.float32)
+    S5 = 128
+    x5 = torch.empty((cm5.P, S5), dtype=torch.complex64, device="cuda")
+    cs = torch.from_numpy(gl.uniform(-0.5 * half, 0.5 * half, (S5, 3))).to("cuda", torch.float32)
+    ks = torch.from_numpy(gl.uniform(-0.5, 0.5, (S5, 3))).to("cuda", torch.float32)
+    sg = torch.from_numpy(gl.uniform(1.0, 2.0, S5)).to("cuda", torch.float32)
+    for s_ in range(S5):
+        r2 = ((xyz - cs[s_]) ** 2).sum(1)
+        x5[:, s_] = torch.polar(torch.exp(-r2 / (4 * sg[s_] ** 2)), xyz @ ks[s_])
+    H5.orthonormalize(x5)
+    ms5 = time_steps(None, x5, 3, lambda x: H5.propagate(x, 1, 0.01, scheme=rsg.ETRS, want_drift=False))
+    torch.cuda.synchronize()
+    g0 = time.perf_counter()
+    H5.orthonormalize(x5)
+    gs_s = time.perf_counter() - g0
+    drift = H5.propagate(x5, 50, 0.01, scheme=rsg.ETRS, gs_every=50)
+    out["large_cube_192"] = {"ms_per_step": ms5, "value": cm5.P * S5 * N_APPLY_PER_STEP / (ms5 * 1e-3) / 1e9,
+                             "unit": UNIT, "gram_schmidt_s": gs_s, "norm_drift_max_50_steps": float(np.max(drift)),
+                             "workload": "192^3 h=0.18, 128 smooth states, 64 atoms x 9 projectors r_c=3, "
+                                         "ETRS dt=0.01, Cholesky-QR every 50 steps"}
+    del H5, x5, xyz
+    torch.cuda.empty_cache()
     # control gradient vs forward (the optimal-control workload)
     cm = rsg.Mesh(rsg.CUBE, 64, spacing=0.3)
     gg = rng(4)

@@ -123,7 +123,7 @@ struct rsg_ham_s {
     DevBuf q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm, nl_ptr, nl_ent, u_pts, u_ptr;
     DevBuf D, partial;
     // workspace
-    DevBuf w0, w1, red, G, W, drift, status, dots, M, ov, grad, Xd, Xdir;
+    DevBuf w0, w1, red, G, W, Wc, drift, status, dots, M, ov, grad, Xd, Xdir;
     double xdir_cached[3] = {NAN, NAN, NAN};
     std::vector<DevBuf> pool;   // control-gradient vectors
     // measurement
@@ -491,9 +491,13 @@ rsg_status orthonormalize_dev(rsg_ham H, void *psi, int64_t S, int64_t ld, doubl
         CK(cudaMemsetAsync(H->status.p, 0, sizeof(int), st));
     }
     if (H->dtype == RSG_C64) {
-        CK(launch_gram<float>(psi, P, (int)ld, (int)S, h3, H->red.as<double>(), nb, H->G.as<double>(), st));
+        // FP64 norms for the diagonal, FP32 runs summed in FP64 elsewhere
+        CK(H->Wc.ensure((size_t)S * S * 8 + (size_t)S * sizeof(double)));
+        double *nrm = (double *)((char *)H->Wc.p + (size_t)S * S * 8);
+        CKS(norms_dev(H, psi, S, ld, nrm, st));
+        CK(launch_gram_c64(psi, P, (int)ld, (int)S, h3, H->red.as<double>(), nb, H->G.as<double>(), nrm, st));
         CK(launch_chol_inv(H->G.as<double>(), H->W.as<double>(), (int)S, drift_dev, H->status.as<int>(), st));
-        CK(launch_tri_apply<float>(psi, P, (int)ld, (int)S, H->W.as<double>(), st));
+        CK(launch_tri_apply_c64(psi, P, (int)ld, (int)S, H->W.as<double>(), H->Wc.p, st));
     } else {
         CK(launch_gram<double>(psi, P, (int)ld, (int)S, h3, H->red.as<double>(), nb, H->G.as<double>(), st));
         CK(launch_chol_inv(H->G.as<double>(), H->W.as<double>(), (int)S, drift_dev, H->status.as<int>(), st));

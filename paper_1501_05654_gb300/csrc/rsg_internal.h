@@ -111,6 +111,13 @@ template <typename R>
 cudaError_t launch_gram(const void *psi, int64_t P, int ld, int S, double h3,
                         double *partial, int nblk, double *G, cudaStream_t st);
 int gram_blocks(int64_t P, int S);
+// complex64 Gram: FP32 products in runs of 8 points, runs summed in FP64;
+// the diagonal is replaced by the given FP64 norms (h3 applied).
+cudaError_t launch_gram_c64(const void *psi, int64_t P, int ld, int S, double h3, double *partial,
+                            int nblk, double *G, const double *norms, cudaStream_t st);
+// complex64 triangular update with W^H rounded to FP32 (Wc_buf: S*S float2).
+cudaError_t launch_tri_apply_c64(void *psi, int64_t P, int ld, int S, const double *W, void *Wc_buf,
+                                 cudaStream_t st);
 // In-place Cholesky of G, inverse of the factor into W (S x S complex double),
 // drift[s] = max(drift[s], |G_ss - 1|), status word set non-zero on failure.
 cudaError_t launch_chol_inv(double *G, double *W, int S, double *drift, int *status,

@@ -100,6 +100,140 @@ cudaError_t launch_gram(const void *psi, int64_t P, int ld, int S, double h3, do
     return cudaGetLastError();
 }
 
+// complex64 Gram matrix: FP32 products summed in FP32 over runs of 8 points,
+// runs summed in FP64.  Tile 32 x 32 of (s, t) per block, 2 x 2 entries per
+// thread (16 x 16 threads); partial[blk][s][t] as in k_gram.
+constexpr int G32 = 32, GRUN = 8;
+__global__ void __launch_bounds__(256) k_gram32(const float2 *__restrict__ psi, int64_t P, int ld, int S,
+                                                double *__restrict__ partial, int nblk) {
+    __shared__ float2 sa[GRUN][G32], sb[GRUN][G32];
+    const int s0 = blockIdx.x * G32, t0 = blockIdx.y * G32;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
+    const int64_t per = (P + nblk - 1) / nblk;
+    const int64_t p0 = blockIdx.z * per;
+    const int64_t p1 = p0 + per < P ? p0 + per : P;
+    double ar[2][2] = {{0, 0}, {0, 0}}, ai[2][2] = {{0, 0}, {0, 0}};
+    for (int64_t pb = p0; pb < p1; pb += GRUN) {
+        // stage GRUN points x 32 columns of both tiles (256 threads, one value each)
+        {
+            const int q = tid / G32, col = tid % G32;
+            const int64_t p = pb + q;
+            float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+            if (p < p1) {
+                if (s0 + col < S) va = psi[p * ld + s0 + col];
+                if (t0 + col < S) vb = psi[p * ld + t0 + col];
+            }
+            sa[q][col] = va;
+            sb[q][col] = vb;
+        }
+        __syncthreads();
+        float fr[2][2] = {{0, 0}, {0, 0}}, fi[2][2] = {{0, 0}, {0, 0}};
+#pragma unroll
+        for (int k = 0; k < GRUN; k++) {
+            const float2 x0 = sa[k][ty], x1 = sa[k][ty + 16];   // psi[p, s]
+            const float2 y0 = sb[k][tx], y1 = sb[k][tx + 16];   // psi[p, t]
+            const float2 xs[2] = {x0, x1}, ys[2] = {y0, y1};
+#pragma unroll
+            for (int a = 0; a < 2; a++)
+#pragma unroll
+                for (int b = 0; b < 2; b++) {
+                    // conj(x) y
+                    fr[a][b] = fmaf(xs[a].x, ys[b].x, fmaf(xs[a].y, ys[b].y, fr[a][b]));
+                    fi[a][b] = fmaf(xs[a].x, ys[b].y, fmaf(-xs[a].y, ys[b].x, fi[a][b]));
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < 2; a++)
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                ar[a][b] += (double)fr[a][b];
+                ai[a][b] += (double)fi[a][b];
+            }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const int s = s0 + ty + 16 * a, t = t0 + tx + 16 * b;
+            if (s < S && t < S) {
+                double *d = partial + (((int64_t)blockIdx.z * S + s) * S + t) * 2;
+                d[0] = ar[a][b];
+                d[1] = ai[a][b];
+            }
+        }
+}
+
+// Replace the Gram diagonal with FP64 norms (h3 already applied to both).
+__global__ void k_set_diag(double *G, const double *norms, int S) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    G[((int64_t)s * S + s) * 2] = norms[s];
+    G[((int64_t)s * S + s) * 2 + 1] = 0.0;
+}
+
+cudaError_t launch_gram_c64(const void *psi, int64_t P, int ld, int S, double h3, double *partial, int nblk,
+                            double *G, const double *norms, cudaStream_t st) {
+    dim3 grid((S + G32 - 1) / G32, (S + G32 - 1) / G32, nblk);
+    k_gram32<<<grid, dim3(16, 16), 0, st>>>((const float2 *)psi, P, ld, S, partial, nblk);
+    const int64_t n = (int64_t)S * S * 2;
+    k_sum_blocks<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, nblk, n, h3, G);
+    k_set_diag<<<(S + 127) / 128, 128, 0, st>>>(G, norms, S);
+    return cudaGetLastError();
+}
+
+// complex64 triangular update psi[p, s] <- sum_{t <= s} psi[p, t] conj(W[s][t])
+// with W rounded to FP32 (the states are FP32): rows staged in shared
+// memory (in place), W^H read from global (L1/L2 resident).
+__global__ void k_wconj32(const double *__restrict__ W, float2 *__restrict__ Wc, int S) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S * S) return;
+    Wc[i] = make_float2((float)W[2 * i], (float)-W[2 * i + 1]);
+}
+
+__global__ void __launch_bounds__(256) k_tri_apply32(float2 *psi, int64_t P, int ld, int S,
+                                                     const float2 *__restrict__ Wc, int pt) {
+    extern __shared__ float2 rows[];   // pt x S
+    const int64_t p0 = (int64_t)blockIdx.x * pt;
+    const int n = pt * S;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int q = e / S, t = e - q * S;
+        const int64_t p = p0 + q;
+        rows[e] = p < P ? psi[p * ld + t] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int s = e % S, q = e / S;
+        const int64_t p = p0 + q;
+        if (p >= P) continue;
+        const float2 *row = rows + q * S;
+        const float2 *w = Wc + (int64_t)s * S;
+        float re = 0.f, im = 0.f;
+        for (int t = 0; t <= s; t++) {
+            const float2 a = row[t], b = w[t];
+            re = fmaf(a.x, b.x, fmaf(-a.y, b.y, re));
+            im = fmaf(a.x, b.y, fmaf(a.y, b.x, im));
+        }
+        psi[p * ld + s] = make_float2(re, im);
+    }
+}
+
+cudaError_t launch_tri_apply_c64(void *psi, int64_t P, int ld, int S, const double *W, void *Wc_buf,
+                                 cudaStream_t st) {
+    k_wconj32<<<(S * S + 255) / 256, 256, 0, st>>>(W, (float2 *)Wc_buf, S);
+    int pt = 8192 / S;
+    if (pt < 1) pt = 1;
+    if (pt > 128) pt = 128;
+    const size_t smem = (size_t)pt * S * sizeof(float2);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_tri_apply32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t nb = (P + pt - 1) / pt;
+    k_tri_apply32<<<(unsigned)nb, 256, smem, st>>>((float2 *)psi, P, ld, S, (const float2 *)Wc_buf, pt);
+    return cudaGetLastError();
+}
+
 // One block.  G (S x S complex double, G[i][j] = <psi_i|psi_j>) is factored
 // in place as G = L L^H (lower L); W = L^-1.  drift (optional) records
 // |G_ss - 1|.  status != 0 if G is not finite or not positive definite.
