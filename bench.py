@@ -43,6 +43,23 @@ def _dist():
     return ws, rank
 
 
+def reduce_max(value, ws, device="cpu"):
+    """Max of a per-rank float over all ranks (identity for one rank)."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(ms_max, ws, units_per_rank_per_step, steps):
+    """Whole-job throughput in 1e9 units/s: every rank did the same work in
+    at most ms_max milliseconds (weak scaling)."""
+    return ws * units_per_rank_per_step * steps / (ms_max * 1e-3) / 1e9
+
+
 def build_inputs(g_seed=2):
     """Seeded inputs of the workload: potential, projector parameters."""
     from workloads import gaussian_wells, projector_atoms, rng
@@ -399,11 +416,8 @@ def main():
     H.profile(False)
     ms = e0.elapsed_time(e1)
     k_ms, k_n, k_bytes, n_launch = H.kernel_stats()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ws * P * S * N_APPLY_PER_STEP * args.steps / (ms_max * 1e-3) / 1e9
+    ms_max = reduce_max(ms, ws, "cuda")
+    value = whole_job_value(ms_max, ws, P * S * N_APPLY_PER_STEP, args.steps)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -424,11 +438,9 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        te = torch.tensor([f0.elapsed_time(f1)], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        te = reduce_max(f0.elapsed_time(f1), ws, "cuda")
         nbytes = psi_h.numel() * psi_h.element_size()
-        e2e = {"value": ws * P * S * N_APPLY_PER_STEP * args.steps / (float(te.item()) * 1e-3) / 1e9,
+        e2e = {"value": whole_job_value(te, ws, P * S * N_APPLY_PER_STEP, args.steps),
                "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
     if rank != 0:
