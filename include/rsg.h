@@ -209,12 +209,16 @@ rsg_status rsg_batch_destroy(rsg_batch b);
 /* Tuning knobs (kernel tile shapes); unknown keys give RSG_ERR_ARG.
  * Keys: "kernel" (0 = shared-memory staged z-march with cp.async, 1 = one
  * thread per point and vector, 2 = z-march through L1, 3 = z-march with
- * plane tiles gathered by the TMA), "rx" (points per thread along
+ * plane tiles gathered by the TMA, 4 = the staged z-march with each tile
+ * row segment copied by one TMA box and off-row entries zeroed in shared
+ * memory; needs cv = 2, else kernel 0 runs), "rx" (points per thread along
  * x: 1, 2 or 4; the staged kernel uses 1 or 2), "ty" (rows per
  * tile: 1, 2, 4, 8 or 16), "zseg" (planes per z segment, 1..120), "cv"
  * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8),
  * "threads" (staged kernel: 256 threads per block, the default, or 512),
- * "stages" (staged kernel: shared-memory pipeline depth, 3 or 4),
+ * "stages" (staged kernels: shared-memory pipeline depth, 3 or 4 for
+ * kernel 0; kernel 4 uses 4, or 5 when set to 5, with 256 threads and 6
+ * with 512),
  * "blocks_per_sm" (staged kernel with 256 threads: register budget for 2 or
  * 3 resident blocks per SM), "adjoint_keep_powers" (rsg_control_gradient: 1 keeps the Taylor powers of
  * a whole checkpoint segment, 0 recomputes them per interval, -1 = choose by
@@ -224,15 +228,15 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value);
 
 /* Autotuner: times one Horner stage of H on psi (device, read only) into
  * work (device, same shape, caller-owned scratch) for every candidate stencil
- * configuration (the one-thread-per-value kernel and the staged kernel in
- * several block shapes and z-segment lengths), keeps the fastest as H's
+ * configuration (the one-thread-per-value kernel and the two staged kernels
+ * in several block shapes and z-segment lengths), keeps the fastest as H's
  * configuration and returns its time per stage in *best_ms (may be NULL).
  * The choice depends on the mesh, S and ld; rerun it when they change.
  * Synchronises. */
 rsg_status rsg_ham_autotune(rsg_ham H, const void *psi, void *work, int64_t S, int64_t ld, void *stream,
                             double *best_ms);
 
-/* Reads an option set above, or "last_kernel": the stencil kernel (0..3)
+/* Reads an option set above, or "last_kernel": the stencil kernel (0..4)
  * that the last Hamiltonian application actually ran (-1 before any), after
  * automatic fallbacks (small problems, TMA unavailable). */
 rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value);

@@ -17,8 +17,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "librsg.so")
-# (source, extra flags): the stencil kernels are compiled once per precision
-SOURCES = [("rsg_kernels.cu", ["-DRSG_ONLY_FLOAT"]), ("rsg_kernels.cu", ["-DRSG_ONLY_DOUBLE"]),
+# (source, extra flags): the stencil kernels are compiled once per precision,
+# the complex64 row-TMA kernels separately (parallel compiles)
+SOURCES = [("rsg_kernels.cu", ["-DRSG_ONLY_FLOAT"]), ("rsg_kernels.cu", ["-DRSG_ONLY_FLOAT", "-DRSG_ROWTMA_TU"]),
+           ("rsg_kernels.cu", ["-DRSG_ONLY_DOUBLE"]),
            ("rsg_linalg.cu", []), ("rsg_noalloc.cu", []), ("rsg_host.cpp", [])]
 HEADERS = ["rsg_internal.h", "rsg_vec.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -27,12 +27,12 @@ struct Tile {
 
 // Kernel tile configuration.
 struct TileCfg {
-    int kernel = 0;   // 0 shared-memory staged, 1 naive, 2 L1 z-march, 3 TMA gather
+    int kernel = 0;   // 0 shared-memory staged, 1 naive, 2 L1 z-march, 3 TMA gather, 4 row-TMA staged
     int rx = 1;       // points per thread along x
     int ty = 16;      // rows per tile (blockDim.z)
     int zseg = 120;   // planes per z segment
     int cv = 2;       // staged kernel: 16-byte vectors per point in a chunk (1..8)
-    int stages = 4;   // staged kernel: shared-memory pipeline depth (3 or 4)
+    int stages = 4;   // staged kernels: shared-memory pipeline depth (3 or 4; kernel 4: 4 or 5 with 256 threads)
     int blocks_per_sm = 2;   // staged kernel, 256 threads: register budget for 2 or 3 blocks per SM
     int threads = 256;   // staged kernel: threads per block (256 with two blocks per SM, or 512)
 };
@@ -91,6 +91,11 @@ void tma_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty);
 template <typename R>
 cudaError_t launch_apply_tma(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
                              bool *launched);
+// Row-TMA staged stencil (kernel 4, the staged block shape); *launched =
+// false when it does not apply.
+template <typename R>
+cudaError_t launch_apply_rowtma(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
+                                bool *launched);
 template <typename R>
 cudaError_t launch_apply(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles,
                          cudaStream_t st);

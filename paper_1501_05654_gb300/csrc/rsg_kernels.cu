@@ -490,7 +490,7 @@ __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile t
 // MINB blocks fit on one SM.
 template <typename R, int CV, int NS, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_apply_staged(const ApplyArgs<R> a, int nchunks, int srow_off) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     staged_block<R, CV, NS, NT>(a, a.tiles[blockIdx.x / nchunks], blockIdx.x % nchunks, smraw,
                                 (SRow *)(smraw + srow_off));
 }
@@ -532,7 +532,7 @@ static inline int pow2_at_least(int v) {
     return p;
 }
 
-#ifndef RSG_ONLY_DOUBLE
+#if !defined(RSG_ONLY_DOUBLE) && !defined(RSG_ROWTMA_TU)
 // Block shape of the staged kernel for SV vectors per point (shared with the
 // host's tile builder through stage_shape()).
 void stage_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
@@ -549,7 +549,7 @@ size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes) {
     int cv, nxr, ty;
     stage_shape(c, SV, &cv, &nxr, &ty);
     // NS slots of the (ty + 8) x (nxr + 8) halo tile, plus per-thread base and V
-    return (size_t)c.stages *
+    return (size_t)(c.stages == 3 ? 3 : 4) *
            ((size_t)(ty + 8) * (nxr + 8) * cv * vec_bytes + (size_t)c.threads * (vec_bytes + vec_bytes / 2));
 }
 
@@ -845,7 +845,6 @@ __global__ void __launch_bounds__(512, 1) k_apply_tma(const ApplyArgs<R> a, cons
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ SRow srows[kSRows];
     __shared__ __align__(8) unsigned long long mbar[NS];
-    __shared__ int s_abort;
     const int NXR = blockDim.y, TY = blockDim.z;
     const int TX = NXR, WX = TX + 8, WY = TY + 8;
     const int chunk = blockIdx.x % nchunks;
@@ -873,7 +872,6 @@ __global__ void __launch_bounds__(512, 1) k_apply_tma(const ApplyArgs<R> a, cons
     if (tid == 0) {
         for (int k = 0; k < NS; k++) mbar_init(mbar0 + 8 * k, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_abort = 0;
     }
     __syncthreads();
     const int slot_elems = WY * WX * CV, bslot_elems = TY * TX * CV;
@@ -955,6 +953,7 @@ __global__ void __launch_bounds__(512, 1) k_apply_tma(const ApplyArgs<R> a, cons
     if (warp == 0)
         for (int j = 0; j < NS - 1 && j < nzr; j++) issue(j);
     const int rs = WX * CV;
+    int abort = 0;
     for (int j = 0; j < nzr; j++) {
         if (warp == 0 && j + NS - 1 < nzr) issue(j + NS - 1);
         const R vq2 = vload(j + 2);
@@ -965,7 +964,7 @@ __global__ void __launch_bounds__(512, 1) k_apply_tma(const ApplyArgs<R> a, cons
                 ok = true;
                 break;
             }
-        if (!ok) s_abort = 1;
+        if (!ok) abort = 1;
         if (ok) {
             const T *sl = slots + (j % NS) * slot_elems;
             const T *cp = sl + ((yi + 4) * WX + xr + 4) * CV + cv;
@@ -1020,13 +1019,20 @@ __global__ void __launch_bounds__(512, 1) k_apply_tma(const ApplyArgs<R> a, cons
         }
         vq0 = vq1;
         vq1 = vq2;
-        __syncthreads();
-        if (s_abort) {
-            if (tid == 0) atomicExch(err, 2);
-            // give copies still in flight a bounded chance to land before leaving
-            for (int k = 0; k < NS; k++)
-                for (long it = 0; it < 4096; ++it)
-                    if (mbar_try(mbar0 + 8 * k, 0) || mbar_try(mbar0 + 8 * k, 1)) break;
+        // barrier-OR: every thread takes the same decision
+        if (__syncthreads_or(abort)) {
+            if (tid == 0) {
+                atomicExch(err, 2);
+                // leave only after the copies still in flight (planes up to
+                // j + NS - 1, one per slot) have landed, each wait bounded
+                const int last = min(nzr - 1, j + NS - 1);
+                for (int jp = max(0, last - NS + 1); jp <= last; jp++) {
+                    const unsigned b = mbar0 + 8 * (jp % NS), par = (unsigned)((jp / NS) & 1);
+                    for (long it = 0; it < kWaitLimit; ++it)
+                        if (mbar_try(b, par)) break;
+                }
+            }
+            __syncthreads();
             return;
         }
     }
@@ -1105,12 +1111,417 @@ cudaError_t launch_apply_tma(const ApplyArgs<R> &a, const TileCfg &cfg, int ntil
     }
 }
 
+// ------------------------------------------------------ row-TMA staged ---
+// k_apply_rowtma: the z-march of k_apply_staged with every state plane
+// brought in by the tensor memory accelerator one mesh row at a time.  In
+// the row-contiguous point order a tile's row segment (WX points in the TY
+// middle rows, the TX interior points in the four halo rows above and below)
+// is a run of consecutive point indices, so one tiled copy of a (CV vectors)
+// x (segment) box over the 2-D view (points, state columns) fetches it.
+// Where a segment runs past an end of its mesh row the copy brings points of
+// the neighbouring rows (or the zero fill beyond the array); warp 1 zeroes
+// those entries one plane ahead, after the copy has landed and before the
+// block barrier that precedes their first read.  Segments that miss their
+// row are not copied and are zeroed whole.  Warp 0 issues the copies (one
+// lane per row) and arms the slot's mbarrier with the byte count; all warps
+// compute.  Per thread and plane the only other memory work is the potential
+// of its point two planes ahead (registers) and one cp.async of the base
+// value of an output retired NS - 1 planes later.  Each thread keeps the
+// point indices of its column in a ring of eight planes in shared memory.
+// Every mbarrier wait is bounded; a wait that gives up makes the whole block
+// leave at the next barrier (a barrier-OR, so the decision is uniform) after
+// a bounded wait for its copies in flight, with err = 2.
+template <int CV, int NS, int NT>
+struct RowTmaSmem {
+    using G = StagedGeom<CV, NT>;
+    static constexpr size_t SLOTS = (size_t)NS * G::SLOT * 16;    // state planes
+    static constexpr size_t BSLOTS = (size_t)NS * NT * 16;        // base values
+    static constexpr size_t IDX = (size_t)8 * NT * 4;              // point-index ring
+    static constexpr size_t ROWS_OFF = SLOTS + BSLOTS + IDX;
+    // 128 bytes of slack: the region is rounded up to a 128-byte boundary
+    static size_t bytes(int zseg) { return 128 + ROWS_OFF + (size_t)G::WY * (zseg + 8) * sizeof(SRow); }
+};
+
+__device__ __forceinline__ void tma_tile2d(unsigned dst, const CUtensorMap *tm, int c0, int c1, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(tm), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+template <typename R, int CV, int NT>
+struct RtCtx {
+    using T = typename VT<R>::T;
+    const T *slots;
+    const T *bslots;
+    const int *idxr;
+    int tid, xr, yi, cv, v;
+    bool vok;
+    int zbase;
+    R fxy;                       // f0 + fx x + fy y of the thread's column
+    R w0, w1, w2, w3, w4;
+};
+
+// Plane j has landed (and been fixed up): add its contributions, retire
+// output j - 4.  Queue slot of output j + (k - 4) is (k + PH) % 9.
+template <typename R, int CV, int NT, int NS, int PH>
+__device__ __forceinline__ void rt_plane(const ApplyArgs<R> &a, const RtCtx<R, CV, NT> &c, int j, bool on,
+                                         R vj, typename VT<R>::T (&q)[9]) {
+    using V = VT<R>;
+    using T = typename V::T;
+    using G = StagedGeom<CV, NT>;
+    constexpr int Q0 = (0 + PH) % 9, Q1 = (1 + PH) % 9, Q2 = (2 + PH) % 9, Q3 = (3 + PH) % 9;
+    constexpr int Q4 = (4 + PH) % 9, Q5 = (5 + PH) % 9, Q6 = (6 + PH) % 9, Q7 = (7 + PH) % 9;
+    constexpr int Q8 = (8 + PH) % 9;
+    constexpr int RS = G::WX * CV;
+    const T *sl = c.slots + (j % NS) * G::SLOT;
+    const T *cp = sl + ((c.yi + 4) * G::WX + c.xr + 4) * CV + c.cv;
+    if (on) {   // the thread's column has a mesh point at plane j
+        const T cval = cp[0];
+        V::fma(q[Q3], c.w1, cval);
+        V::fma(q[Q5], c.w1, cval);
+        V::fma(q[Q2], c.w2, cval);
+        V::fma(q[Q6], c.w2, cval);
+        V::fma(q[Q1], c.w3, cval);
+        V::fma(q[Q7], c.w3, cval);
+        V::fma(q[Q0], c.w4, cval);
+        V::fma(q[Q8], c.w4, cval);
+        T s = V::scale((R)3 * c.w0, cval);
+        V::fma(s, c.w1, V::add(V::add(cp[-CV], cp[CV]), V::add(cp[-RS], cp[RS])));
+        V::fma(s, c.w2, V::add(V::add(cp[-2 * CV], cp[2 * CV]), V::add(cp[-2 * RS], cp[2 * RS])));
+        V::fma(s, c.w3, V::add(V::add(cp[-3 * CV], cp[3 * CV]), V::add(cp[-3 * RS], cp[3 * RS])));
+        V::fma(s, c.w4, V::add(V::add(cp[-4 * CV], cp[4 * CV]), V::add(cp[-4 * RS], cp[4 * RS])));
+        const R diag = vj + c.fxy + a.fz * (R)(c.zbase + j);
+        V::fma(s, diag, cval);
+        q[Q4] = V::add(q[Q4], s);
+    }
+    // output plane j - 4 lies in [zlo, zhi) for j in [8, np)
+    if (j >= 8 && c.vok) {
+        const int id = c.idxr[((j - 4) & 7) * NT + c.tid];
+        if (id >= 0) finish_staged<R>(a, id * a.SV + c.v, q[Q0], c.bslots[(j % NS) * NT + c.tid]);
+    }
+    q[Q0] = V::zero();
+}
+
+template <typename R, int CV, int NS, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
+    k_apply_rowtma(const ApplyArgs<R> a, const __grid_constant__ CUtensorMap tm_mid,
+                   const __grid_constant__ CUtensorMap tm_halo, int nchunks) {
+    using V = VT<R>;
+    using T = typename V::T;
+    using G = StagedGeom<CV, NT>;
+    using L = RowTmaSmem<CV, NS, NT>;
+    static_assert(CV % 2 == 0, "row copies need 128-byte aligned shared-memory rows");
+    static_assert(NS >= 4 && NS <= 7, "base staging distance");
+    constexpr int TX = G::TX, TY = G::TY, WX = G::WX, WY = G::WY;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) unsigned long long mbar[NS];
+    const unsigned raw = (unsigned)__cvta_generic_to_shared(smraw);
+    unsigned char *sm = smraw + ((128u - (raw & 127u)) & 127u);
+    T *slots = (T *)sm;
+    T *bslots = (T *)(sm + L::SLOTS);
+    int *idxr = (int *)(sm + L::SLOTS + L::BSLOTS);
+    SRow *srows = (SRow *)(sm + L::ROWS_OFF);
+
+    const int chunk = blockIdx.x % nchunks;
+    const Tile tl = a.tiles[blockIdx.x / nchunks];
+    const int ny = a.ny, nz = a.nz, SV = a.SV;
+    const int xbase = tl.tx * TX - 4, ybase = tl.ty * TY - 4, zbase = tl.zlo - 4;
+    const int np = tl.zhi - tl.zlo + 8;
+    const int tid = (threadIdx.z * TX + threadIdx.y) * CV + threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < WY * np; i += NT) {
+        const int zz = i / WY;
+        const int yy = ybase + (i - zz * WY);
+        const int zg = zbase + zz;
+        SRow r{0, 1, 0};
+        if (yy >= 0 && yy < ny && zg >= 0 && zg < nz) {
+            const Row g = a.rows[zg * ny + yy];
+            r.start = g.start;
+            r.xmin = (int16_t)g.xmin;
+            r.xmax = (int16_t)g.xmax;
+        }
+        srows[i] = r;
+    }
+    const unsigned mbar0 = (unsigned)__cvta_generic_to_shared(mbar);
+    if (tid == 0) {
+        for (int k = 0; k < NS; k++) mbar_init(mbar0 + 8 * k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const unsigned sh_slots = (unsigned)__cvta_generic_to_shared(slots);
+    const int col = chunk * CV * (int)(16 / sizeof(R));     // element column of this chunk
+    // row yy's segment: first x, width and offset in the slot (16-byte entries)
+    auto seg = [&](int yy, int &xs, int &w, int &off) {
+        const bool mid = yy >= 4 && yy < 4 + TY;
+        xs = mid ? xbase : xbase + 4;
+        w = mid ? WX : TX;
+        off = (yy * WX + (mid ? 0 : 4)) * CV;
+    };
+    // warp 0: copy the row segments of plane jp, arm its mbarrier
+    auto issue = [&](int jp) {
+        const int sl = jp % NS;
+        const unsigned bar = mbar0 + 8u * (unsigned)sl;
+        bool go = false, mid = false;
+        int pidx = 0, off = 0;
+        if (lane < WY) {
+            int xs, w;
+            seg(lane, xs, w, off);
+            mid = w == WX;
+            const SRow rw = srows[jp * WY + lane];
+            go = rw.xmin <= rw.xmax && xs <= rw.xmax && xs + w - 1 >= rw.xmin;
+            pidx = rw.start + (xs - rw.xmin);
+        }
+        const unsigned bm = __ballot_sync(0xffffffffu, go && mid);
+        const unsigned bh = __ballot_sync(0xffffffffu, go && !mid);
+        if (lane == 0) mbar_expect_arrive(bar, (unsigned)((__popc(bm) * WX + __popc(bh) * TX) * CV * 16));
+        if (go) tma_tile2d(sh_slots + (unsigned)((sl * G::SLOT + off) * 16), mid ? &tm_mid : &tm_halo, col, pidx, bar);
+    };
+    auto wait_plane = [&](int jp) -> bool {
+        const unsigned bar = mbar0 + 8u * (unsigned)(jp % NS);
+        const unsigned par = (unsigned)((jp / NS) & 1);
+        for (long it = 0; it < kWaitLimit; ++it)
+            if (mbar_try(bar, par)) return true;
+        return false;
+    };
+    // warp 1: zero the entries of plane jf that are not mesh points of their row
+    auto fix = [&](int jf) {
+        T *sl = slots + (jf % NS) * G::SLOT;
+        int nl = 0, nr = 0, w = 0, off = 0;
+        if (lane < WY) {
+            int xs;
+            seg(lane, xs, w, off);
+            const SRow rw = srows[jf * WY + lane];
+            if (rw.xmin > rw.xmax || xs > rw.xmax || xs + w - 1 < rw.xmin) {
+                nl = w;
+            } else {
+                nl = max(0, rw.xmin - xs);
+                nr = max(0, xs + w - 1 - rw.xmax);
+            }
+        }
+        unsigned need = __ballot_sync(0xffffffffu, (nl | nr) != 0);
+        while (need) {
+            const int r = __ffs(need) - 1;
+            need &= need - 1;
+            const int rl = __shfl_sync(0xffffffffu, nl, r), rr = __shfl_sync(0xffffffffu, nr, r);
+            const int rw = __shfl_sync(0xffffffffu, w, r), ro = __shfl_sync(0xffffffffu, off, r);
+            for (int e = lane; e < rw * CV; e += 32) {
+                const int xx = e / CV;
+                if (xx < rl || xx >= rw - rr) sl[ro + e] = V::zero();
+            }
+        }
+        // order these generic-proxy writes before the slot's next tensor copy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    };
+
+    RtCtx<R, CV, NT> c;
+    c.slots = slots;
+    c.bslots = bslots;
+    c.idxr = idxr;
+    c.tid = tid;
+    c.xr = threadIdx.y;
+    c.yi = threadIdx.z;
+    c.cv = threadIdx.x;
+    c.v = chunk * CV + threadIdx.x;
+    c.vok = c.v < SV;
+    c.zbase = zbase;
+    const int x = tl.tx * TX + threadIdx.y, y = tl.ty * TY + threadIdx.z, yown = threadIdx.z + 4;
+    c.fxy = a.f0 + a.fx * (R)x + a.fy * (R)y;
+    c.w0 = a.w[0];
+    c.w1 = a.w[1];
+    c.w2 = a.w[2];
+    c.w3 = a.w[3];
+    c.w4 = a.w[4];
+    int *my_idx = idxr + tid;
+    auto idx_of = [&](int jp) -> int {
+        if (jp >= np) return -1;
+        const SRow rw = srows[jp * WY + yown];
+        return (x >= rw.xmin && x <= rw.xmax) ? rw.start + (x - rw.xmin) : -1;
+    };
+    const unsigned sh_b = (unsigned)__cvta_generic_to_shared(bslots);
+    const T *__restrict__ basep = (const T *)a.base;
+    // base value of output plane o into the slot its retirement (plane o + 4) reads
+    auto stage_base = [&](int o) {
+        if (basep != nullptr && o >= 4 && o < np - 4) {
+            const int id = my_idx[(o & 7) * NT];
+            const bool ok = id >= 0 && c.vok;
+            cp_async16(sh_b + (unsigned)((((o + 4) % NS) * NT + tid) * 16), basep + (ok ? id * SV + c.v : 0),
+                       ok ? 16 : 0);
+        }
+    };
+
+    T q[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) q[k] = V::zero();
+    int abort = 0;
+    {
+        const int i0 = idx_of(0), i1 = idx_of(1);
+        my_idx[0] = i0;
+        my_idx[NT] = i1;
+    }
+    R vq0 = my_idx[0] >= 0 ? a.V[my_idx[0]] : (R)0;
+    R vq1 = my_idx[NT] >= 0 ? a.V[my_idx[NT]] : (R)0;
+    unsigned okq = (my_idx[0] >= 0 ? 1u : 0u) | (my_idx[NT] >= 0 ? 2u : 0u);
+    if (warp == 0)
+        for (int k = 0; k < NS - 1 && k < np; k++) issue(k);
+    if (warp == 1) {
+        if (wait_plane(0)) fix(0);
+        else abort = 1;
+    }
+    // iteration j: the barrier publishes plane j (landed, fixed) and frees the
+    // slot of plane j - 1 for plane j + NS - 1; warp 1 fixes plane j + 1
+    int last_issued = min(np, NS - 1) - 1;
+    auto pre = [&](int j, R &vq2) -> bool {
+        cp_async_wait<NS - 2>();
+        if (__syncthreads_or(abort)) return true;
+        if (warp == 0 && j + NS - 1 < np) issue(j + NS - 1);
+        last_issued = min(np - 1, j + NS - 1);
+        if (warp == 1 && j + 1 < np) {
+            if (wait_plane(j + 1)) fix(j + 1);
+            else abort = 1;
+        }
+        const int i2 = idx_of(j + 2);
+        my_idx[((j + 2) & 7) * NT] = i2;
+        vq2 = i2 >= 0 ? a.V[i2] : (R)0;
+        okq |= (i2 >= 0 ? 4u : 0u);
+        stage_base(j + NS - 5);
+        cp_async_commit();
+        if (!wait_plane(j)) abort = 1;   // already complete: warp 1 saw it before the barrier
+        return false;
+    };
+    auto post = [&](R vq2) {
+        vq0 = vq1;
+        vq1 = vq2;
+        okq >>= 1;
+    };
+    int j = 0;
+    bool stop = false;
+#define RSG_RT_STEP(PH)                                              \
+    {                                                                \
+        R vq2;                                                       \
+        if (pre(j + PH, vq2)) {                                      \
+            stop = true;                                             \
+            break;                                                   \
+        }                                                            \
+        rt_plane<R, CV, NT, NS, PH>(a, c, j + PH, okq & 1u, vq0, q); \
+        post(vq2);                                                   \
+    }
+#pragma unroll 1
+    for (; j + 9 <= np; j += 9) {
+        RSG_RT_STEP(0)
+        RSG_RT_STEP(1)
+        RSG_RT_STEP(2)
+        RSG_RT_STEP(3)
+        RSG_RT_STEP(4)
+        RSG_RT_STEP(5)
+        RSG_RT_STEP(6)
+        RSG_RT_STEP(7)
+        RSG_RT_STEP(8)
+    }
+#undef RSG_RT_STEP
+    if (!stop) {
+#pragma unroll 1
+        for (; j < np; j++) {
+            R vq2;
+            if (pre(j, vq2)) {
+                stop = true;
+                break;
+            }
+            const bool on = okq & 1u;
+            switch (j % 9) {
+            case 0: rt_plane<R, CV, NT, NS, 0>(a, c, j, on, vq0, q); break;
+            case 1: rt_plane<R, CV, NT, NS, 1>(a, c, j, on, vq0, q); break;
+            case 2: rt_plane<R, CV, NT, NS, 2>(a, c, j, on, vq0, q); break;
+            case 3: rt_plane<R, CV, NT, NS, 3>(a, c, j, on, vq0, q); break;
+            case 4: rt_plane<R, CV, NT, NS, 4>(a, c, j, on, vq0, q); break;
+            case 5: rt_plane<R, CV, NT, NS, 5>(a, c, j, on, vq0, q); break;
+            case 6: rt_plane<R, CV, NT, NS, 6>(a, c, j, on, vq0, q); break;
+            case 7: rt_plane<R, CV, NT, NS, 7>(a, c, j, on, vq0, q); break;
+            default: rt_plane<R, CV, NT, NS, 8>(a, c, j, on, vq0, q); break;
+            }
+            post(vq2);
+        }
+    }
+    cp_async_wait<0>();
+    if (stop) {
+        // leave only after the copies still in flight have landed (bounded)
+        if (tid == 0) {
+            atomicExch(a.err, 2);
+            for (int jp = max(0, last_issued - NS + 1); jp <= last_issued; jp++) wait_plane(jp);
+        }
+        __syncthreads();
+    }
+}
+
+// 2-D view of a (P, SV) block of 16-byte vectors as R elements: rows are
+// points; a box is CV vectors of `rows` consecutive points.
+template <typename R>
+static bool encode_row_box(CUtensorMap *tm, const void *base, int64_t P, int SV, int CV, int rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || !base || rows < 1 || rows > 256) return false;
+    const int epv = 16 / (int)sizeof(R);
+    cuuint64_t dims[2] = {(cuuint64_t)SV * epv, (cuuint64_t)P};
+    cuuint64_t strides[1] = {(cuuint64_t)SV * 16};
+    cuuint32_t box[2] = {(cuuint32_t)(CV * epv), (cuuint32_t)rows};
+    cuuint32_t es[2] = {1, 1};
+    const CUtensorMapDataType dt = sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    return fn(tm, dt, 2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename R, int CV, int NS, int NT, int MINB>
+static cudaError_t launch_rowtma_t(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
+                                   bool *launched) {
+    using G = StagedGeom<CV, NT>;
+    const size_t smem = RowTmaSmem<CV, NS, NT>::bytes(cfg.zseg);
+    if (smem > 227 * 1024) return cudaSuccess;
+    CUtensorMap tm_mid, tm_halo;
+    if (!encode_row_box<R>(&tm_mid, a.in, a.P, a.SV, CV, G::WX)) return cudaSuccess;
+    if (!encode_row_box<R>(&tm_halo, a.in, a.P, a.SV, CV, G::TX)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_apply_rowtma<R, CV, NS, NT, MINB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nchunks = (a.SV + CV - 1) / CV;
+    const long long nblk = (long long)ntiles * nchunks;
+    if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_apply_rowtma<R, CV, NS, NT, MINB><<<(unsigned)nblk, dim3(CV, G::TX, G::TY), smem, st>>>(a, tm_mid, tm_halo,
+                                                                                          nchunks);
+    *launched = true;
+    return cudaGetLastError();
+}
+
+// Row-TMA staged stencil (kernel 4) in the staged kernel's block shape with
+// two vectors per point (cv = 2); *launched = false when it does not apply
+// (no tensor-map encoder, another cv, too much shared memory).
+template <typename R>
+cudaError_t launch_apply_rowtma(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
+                                bool *launched) {
+    *launched = false;
+    if (ntiles == 0 || a.err == nullptr || (long long)a.P * a.SV >= 0x7fffffffLL) return cudaSuccess;
+    int cv, nxr, ty;
+    stage_shape(cfg, a.SV, &cv, &nxr, &ty);
+    if (cv != 2) return cudaSuccess;
+    if constexpr (sizeof(R) == 8) {
+        // complex128 is bound by FP64 arithmetic: one shape (the tiles were
+        // built for cfg.threads, so other shapes fall back to kernel 0)
+        if (cfg.threads != 256) return cudaSuccess;
+        return launch_rowtma_t<R, 2, 4, 256, 2>(a, cfg, ntiles, st, launched);
+    } else {
+        if (cfg.threads == 512) return launch_rowtma_t<R, 2, 6, 512, 1>(a, cfg, ntiles, st, launched);
+        if (cfg.stages >= 5) return launch_rowtma_t<R, 2, 5, 256, 2>(a, cfg, ntiles, st, launched);
+        return launch_rowtma_t<R, 2, 4, 256, 2>(a, cfg, ntiles, st, launched);
+    }
+}
+
 // ------------------------------------------------------------- batches ---
 // One launch per Horner stage for many independent complex64 systems: every
 // block takes a (system, tile, chunk) work item and runs the staged stencil
 // block for that system.  Projector coefficients, their reduction and the
 // projector scatter are batched the same way.
-#ifndef RSG_ONLY_DOUBLE
+#if !defined(RSG_ONLY_DOUBLE) && !defined(RSG_ROWTMA_TU)
 __device__ __forceinline__ ApplyArgs<float> batch_args(const SysArgs &S, int in_c, int out_c, float ar,
                                                        float ai) {
     ApplyArgs<float> a;
@@ -1146,7 +1557,7 @@ __device__ __forceinline__ ApplyArgs<float> batch_args(const SysArgs &S, int in_
 __global__ void __launch_bounds__(512, 1) k_batch_stencil(const SysArgs *__restrict__ sys,
                                                           const BWork *__restrict__ work, int in_c,
                                                           int out_c, float ar, float ai) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ SRow srows[kSRows];
     const BWork w = work[blockIdx.x];
     const SysArgs &S = sys[w.sys];
@@ -1294,7 +1705,10 @@ cudaError_t launch_batch_scatter(const SysArgs *sys, const BWork *work, int nwor
 }
 #endif
 
-#ifndef RSG_ONLY_DOUBLE
+#if defined(RSG_ROWTMA_TU)
+// the complex64 row-TMA kernels compile in a translation unit of their own
+template cudaError_t launch_apply_rowtma<float>(const ApplyArgs<float> &, const TileCfg &, int, cudaStream_t, bool *);
+#elif !defined(RSG_ONLY_DOUBLE)
 template cudaError_t launch_apply_tma<float>(const ApplyArgs<float> &, const TileCfg &, int, cudaStream_t, bool *);
 template cudaError_t launch_apply<float>(const ApplyArgs<float> &, const TileCfg &, int, cudaStream_t);
 template cudaError_t launch_proj_dot<float>(const void *, int, const ProjDev &, double *, cudaStream_t);
@@ -1303,6 +1717,7 @@ template cudaError_t launch_proj_scatter<float>(const ApplyArgs<float> &, const 
 #endif
 #ifndef RSG_ONLY_FLOAT
 template cudaError_t launch_apply_tma<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t, bool *);
+template cudaError_t launch_apply_rowtma<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t, bool *);
 template cudaError_t launch_apply<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t);
 template cudaError_t launch_proj_dot<double>(const void *, int, const ProjDev &, double *, cudaStream_t);
 template cudaError_t launch_proj_reduce<double>(const double *, int, const ProjDev &, double, void *, cudaStream_t);

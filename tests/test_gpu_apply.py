@@ -91,6 +91,35 @@ def test_tma_gather_kernel(dtype, opts):
     assert rel_err(p.states_from_gpu(y, 5), want) < TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", [torch.complex64, torch.complex128])
+@pytest.mark.parametrize("opts", [{"kernel": 4}, {"kernel": 4, "stages": 5}, {"kernel": 4, "threads": 512},
+                                  {"kernel": 4, "zseg": 7}, {"kernel": 4, "zseg": 1}])
+@pytest.mark.parametrize("S", [4, 13])
+def test_row_tma_kernel(dtype, opts, S):
+    """Row-TMA staged stencil on a sphere: rows that end inside a tile and
+    rows absent from the mesh (zeroed in shared memory), a partial last state
+    chunk (S = 13: the copy box runs past the state columns), projectors, a
+    field, and a Horner stage (base values by cp.async)."""
+    p, g = wells_system("sphere", radius=4.6, h=0.25, dtype=dtype, seed=9, natoms=3, lmax=2)
+    want_k = 0 if (dtype == torch.complex128 and opts.get("threads") == 512) else 4
+    _check_apply(p, g, S, eps=0.02, dir=(0.0, 0.6, 0.8), opts=opts, expect_kernel=want_k)
+    psi = white_noise_states(g, p.P, S)
+    if dtype == torch.complex64:
+        psi = round_c64(psi)
+    want = p.O.taylor4(psi, 0.01, eps=0.02, dir=(0.0, 0.6, 0.8))
+    y = p.H.taylor(p.states_to_gpu(psi), 0.01, S=S)
+    torch.cuda.synchronize()
+    assert p.H.get_option("last_kernel") == want_k
+    assert rel_err(p.states_from_gpu(y, S), want) < TOL[dtype]
+
+
+def test_row_tma_kernel_cube_and_box():
+    """Full rows (no fix-ups inside the mesh), ragged tile tails in x, y, z."""
+    for shape, n in (("cube", 37), ("box", (23, 9, 14))):
+        p, g = wells_system(shape, n, h=0.3, dtype=torch.complex64, seed=3, natoms=2, lmax=1)
+        _check_apply(p, g, 10, opts={"kernel": 4}, expect_kernel=4)
+
+
 @pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
 def test_degenerate_meshes(dtype):
     # one point: every neighbour is a ghost
