@@ -78,15 +78,21 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def traffic_record(kernel_src_hash):
+# stencil kernel of each "kernel" option value (rsg_ham_get_option "last_kernel")
+KERNEL_NAMES = {0: "k_apply_staged", 1: "k_apply_naive", 2: "k_apply_zmarch", 3: "k_apply_tma",
+                4: "k_apply_rowtma", 5: "k_apply_quad"}
+KERNEL_SOURCES = ("rsg_kernels.cu", "rsg_quad.cu", "rsg_vec.cuh", "rsg_async.cuh")
+
+
+def traffic_record(kernel_src_hash, kernel_name):
     """DRAM bytes per launch of the stencil kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    summary, if it was taken on the current kernel source and kernel."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("kernel_source_sha256") != kernel_src_hash:
+    if d.get("kernel_source_sha256") != kernel_src_hash or kernel_name not in d.get("kernel", ""):
         return None
     return d.get("bytes_per_launch_full_size")
 
@@ -94,7 +100,7 @@ def traffic_record(kernel_src_hash):
 def kernel_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("rsg_kernels.cu", "rsg_vec.cuh"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1501_05654_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -451,7 +457,8 @@ def main():
     peak, peak_kind = peaks()
     achieved = (k_bytes / k_n) / (k_ms / k_n * 1e-3) / 1e9 if k_n else None
     per_launch_bytes = k_bytes / k_n if k_n else None
-    traffic = traffic_record(kernel_hash())
+    kname = KERNEL_NAMES.get(H.get_option("last_kernel"), "unknown")
+    traffic = traffic_record(kernel_hash(), kname)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -461,7 +468,7 @@ def main():
                    "h_applications_per_step": N_APPLY_PER_STEP,
                    "l2": "state blocks (1.56 GB) exceed L2; no flush",
                    "parallelism": f"replicas x{ws}"},
-        "roofline": {"bound": "hbm", "kernel": "k_apply_staged (Horner stage: stencil + V, base and result streams)",
+        "roofline": {"bound": "hbm", "kernel": f"{kname} (Horner stage: stencil + V, base and result streams)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
                      "peak_kind": f"{peak_kind} copy bandwidth",

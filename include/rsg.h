@@ -211,11 +211,15 @@ rsg_status rsg_batch_destroy(rsg_batch b);
  * thread per point and vector, 2 = z-march through L1, 3 = z-march with
  * plane tiles gathered by the TMA, 4 = the staged z-march with each tile
  * row segment copied by one TMA box and off-row entries zeroed in shared
- * memory; needs cv = 2, else kernel 0 runs), "rx" (points per thread along
+ * memory; needs cv = 2, else kernel 0 runs; 5 = the staged z-march with
+ * register blocking, complex64 only: one complex value at 2 x 2 points per
+ * thread, 16 x 16 tiles with 256 threads or 16 x 12 with 192, else kernel 0
+ * runs), "rx" (points per thread along
  * x: 1, 2 or 4; the staged kernel uses 1 or 2), "ty" (rows per
  * tile: 1, 2, 4, 8 or 16), "zseg" (planes per z segment, 1..120), "cv"
  * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8),
- * "threads" (staged kernel: 256 threads per block, the default, or 512),
+ * "threads" (staged kernels: 256 threads per block, the default, or 512;
+ * 192 selects kernel 5's 16 x 12 tile),
  * "stages" (staged kernels: shared-memory pipeline depth, 3 or 4 for
  * kernel 0; kernel 4 uses 4, or 5 when set to 5, with 256 threads and 6
  * with 512),
@@ -236,7 +240,7 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value);
 rsg_status rsg_ham_autotune(rsg_ham H, const void *psi, void *work, int64_t S, int64_t ld, void *stream,
                             double *best_ms);
 
-/* Reads an option set above, or "last_kernel": the stencil kernel (0..4)
+/* Reads an option set above, or "last_kernel": the stencil kernel (0..5)
  * that the last Hamiltonian application actually ran (-1 before any), after
  * automatic fallbacks (small problems, TMA unavailable). */
 rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value);

@@ -19,6 +19,7 @@
 #include <memory>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "rsg_internal.h"
@@ -244,6 +245,10 @@ int pow2_at_least(int v) {
 // launch_apply): staged kernel cv x nxr x ty threads (512), L1 z-march
 // kernel 256 threads; TX = nxr * rx.
 void block_shape(const TileCfg &c, int SV, int *TX, int *TY) {
+    if (c.kernel == 5) {
+        quad_shape(c, TX, TY);
+        return;
+    }
     if (c.kernel == 3) {
         int cv, nxr, ty;
         tma_shape(c, SV, &cv, &nxr, &ty);
@@ -370,7 +375,7 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         int TX, TY;
         block_shape(cfg, SV, &TX, &TY);
         CKS(get_tiles(m, TX, TY, cfg.zseg, &a.tiles, &ntiles));
-        if ((cfg.kernel == 0 || cfg.kernel == 3 || cfg.kernel == 4) && !H->force_kernel) {
+        if (cfg.kernel != 1 && cfg.kernel != 2 && !H->force_kernel) {
             // the staged kernel runs one block per SM: small problems that
             // give fewer than two blocks per SM go to the one-thread-per-value
             // kernel instead
@@ -393,21 +398,23 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         H->ev_used += 2;
         CK(cudaEventRecord(e0, st));
     }
-    const bool split_nl = (cfg.kernel == 0 || cfg.kernel == 3 || cfg.kernel == 4) && H->pj.natoms > 0;
+    const bool split_nl = cfg.kernel != 1 && cfg.kernel != 2 && H->pj.natoms > 0;
     {
         ApplyArgs<R> b = a;
         if (split_nl) b.nl_ptr = nullptr;
         bool done = false;
         if (cfg.kernel == 3) CK(launch_apply_tma<R>(b, cfg, ntiles, st, &done));
         if (cfg.kernel == 4) CK(launch_apply_rowtma<R>(b, cfg, ntiles, st, &done));
+        if constexpr (std::is_same<R, float>::value)
+            if (cfg.kernel == 5) CK(launch_apply_quad(b, cfg, ntiles, st, &done));
         if (done) {
             H->last_kernel = cfg.kernel;
         } else {
             TileCfg c0 = cfg;
             int n = ntiles;
-            if (c0.kernel == 3 || c0.kernel == 4) {
+            if (c0.kernel >= 3) {
                 // same tiles for kernel 4 (the staged block shape)
-                const bool retile = c0.kernel == 3;
+                const bool retile = c0.kernel != 4;
                 c0.kernel = 0;
                 if (retile) n = tiles_for(H, c0, SV, &b.tiles);
             }
@@ -704,6 +711,15 @@ rsg_status rsg_ham_autotune(rsg_ham H, const void *psi, void *work, int64_t S, i
             c.zseg = zs;
             cand.push_back(c);
         }
+    // the register-blocked staged kernel (complex64): 192 or 256 threads
+    for (int th : {192, 256})
+        for (int zs : {96, 120}) {
+            TileCfg c;
+            c.kernel = 5;
+            c.threads = th;
+            c.zseg = zs;
+            cand.push_back(c);
+        }
     // the row-TMA staged kernel: 256 threads with 4 or 5 slots, 512 with 6
     const int rshapes[][3] = {{256, 2, 4}, {256, 2, 5}, {512, 2, 4}};
     for (const auto &sh : rshapes)
@@ -771,7 +787,7 @@ rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value) {
 rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     if (!H || !key) return fail(RSG_ERR_ARG, "NULL argument");
     std::string k(key);
-    if (k == "kernel" && (value >= 0 && value <= 4)) {
+    if (k == "kernel" && (value >= 0 && value <= 5)) {
         H->cfg.kernel = (int)value;
         H->force_kernel = true;
     }
@@ -781,7 +797,7 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     else if (k == "zseg" && value >= 1 && value <= 120) H->cfg.zseg = (int)value;
     else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
     else if (k == "adjoint_keep_powers" && value >= -1 && value <= 1) H->adj_keep = (int)value;
-    else if (k == "threads" && (value == 256 || value == 512)) H->cfg.threads = (int)value;
+    else if (k == "threads" && (value == 192 || value == 256 || value == 512)) H->cfg.threads = (int)value;
     else if (k == "stages" && value >= 3 && value <= 5) H->cfg.stages = (int)value;
     else if (k == "blocks_per_sm" && (value == 2 || value == 3)) H->cfg.blocks_per_sm = (int)value;
     else return fail(RSG_ERR_ARG, "unknown option or value: %s=%lld", key, (long long)value);

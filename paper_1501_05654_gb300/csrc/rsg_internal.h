@@ -27,7 +27,8 @@ struct Tile {
 
 // Kernel tile configuration.
 struct TileCfg {
-    int kernel = 0;   // 0 shared-memory staged, 1 naive, 2 L1 z-march, 3 TMA gather, 4 row-TMA staged
+    int kernel = 0;   // 0 shared-memory staged, 1 naive, 2 L1 z-march, 3 TMA gather, 4 row-TMA staged,
+                      // 5 register-blocked staged (complex64)
     int rx = 1;       // points per thread along x
     int ty = 16;      // rows per tile (blockDim.z)
     int zseg = 120;   // planes per z segment
@@ -91,6 +92,11 @@ void tma_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty);
 template <typename R>
 cudaError_t launch_apply_tma(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
                              bool *launched);
+// Register-blocked staged stencil (kernel 5, complex64): tile shape and
+// launcher; *launched = false when it does not apply.
+void quad_shape(const TileCfg &cfg, int *TX, int *TY);
+cudaError_t launch_apply_quad(const ApplyArgs<float> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
+                              bool *launched);
 // Row-TMA staged stencil (kernel 4, the staged block shape); *launched =
 // false when it does not apply.
 template <typename R>

@@ -27,6 +27,7 @@
 //                   chunks), k_proj_reduce: h^3 sum over chunks, times h_a.
 #include <cuda.h>
 
+#include "rsg_async.cuh"
 #include "rsg_internal.h"
 #include "rsg_vec.cuh"
 
@@ -80,12 +81,6 @@ __device__ __forceinline__ Row load_row(const Row *rows, int y, int z, int ny, i
 }
 
 // --------------------------------------------------------- z-marching ---
-// Row entry packed for shared memory: start, xmin, xmax (xmin > xmax: empty).
-struct SRow {
-    int32_t start;
-    int16_t xmin, xmax;
-};
-
 constexpr int kMaxTY = 16, kMaxZseg = 120;
 constexpr int kSRows = (kMaxTY + 8) * (kMaxZseg + 8);
 
@@ -208,23 +203,6 @@ __global__ void __launch_bounds__(256, (RX <= 2 ? 2 : 1)) k_apply_zmarch(const A
 // value crosses L2 -> shared memory once per tile (plus the halo); all
 // neighbour reads are fixed-offset shared-memory loads; all offsets are
 // 32-bit (the host checks P * SV < 2^31).
-__device__ __forceinline__ void cp_async16(unsigned smem_addr, const void *gmem, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr), "l"(gmem),
-                 "r"(src_bytes)
-                 : "memory");
-}
-template <int BYTES>
-__device__ __forceinline__ void cp_async_small(unsigned smem_addr, const void *gmem, int src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_addr), "l"(gmem),
-                 "n"(BYTES), "r"(src_bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 // Epilogue of the staged kernel: y = alpha * acc + beta * base (base already
 // in registers), out = y, optional acc += gamma * y.  Projector terms are
 // added afterwards by k_proj_scatter.

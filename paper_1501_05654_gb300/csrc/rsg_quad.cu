@@ -1,0 +1,376 @@
+// Register-blocked staged stencil for complex64 blocks (kernel 5).
+//
+// The operator and epilogue are those of rsg_kernels.cu (8th-order 25-point
+// star Laplacian with zero values outside the mesh, local potential and
+// dipole field on the diagonal, arXiv:1501.05654 Sec. 1 and Sec.
+// "Performance"); projector terms are added afterwards by k_proj_scatter.
+//
+// k_apply_quad: the z-march of k_apply_staged with register blocking.  A
+// block owns a 16 x TY tile of points and one 32-byte chunk of each point's
+// states (four complex64 values).  A thread owns one of those four values at
+// a 2 x 2 group of points (x0, x0 + 1) x (y0, y0 + 1) and keeps four
+// nine-deep z queues.  Per plane it reads two x windows of ten points and two
+// y columns of eight more: 36 eight-byte shared-memory loads for four
+// outputs (9 per output, 72 bytes), against 17 sixteen-byte loads per two
+// outputs in k_apply_staged (136 bytes per output); the wider tile also cuts
+// the halo fill from 2.5x to 2.0x (TY = 16) or 2.17x (TY = 12).
+//
+// Shared-memory slot of one plane: (TY + 8) rows x 24 columns of 32-byte
+// point records; within a row the even x columns come first and the odd ones
+// second, so that for a fixed offset the x-adjacent threads of a warp read
+// consecutive records (no bank conflicts).  Planes stream through NS slots
+// filled with cp.async (ghost points zero-filled), one block barrier per
+// plane, as in k_apply_staged; the potential of each interior point and the
+// base value of each output travel with the plane that uses them.
+#include <cuda.h>
+
+#include "rsg_async.cuh"
+#include "rsg_internal.h"
+#include "rsg_vec.cuh"
+
+namespace rsg {
+
+template <int NYT>
+struct QuadGeom {
+    static constexpr int NXT = 8, NC = 4;                  // x threads, complex values per record
+    static constexpr int NT = NC * NXT * NYT;              // threads
+    static constexpr int TX = 2 * NXT, TY = 2 * NYT;       // tile
+    static constexpr int WX = TX + 8, WY = TY + 8, HW = WX / 2;
+    // the star stencil reads a cross: the TY middle rows at full width and
+    // four rows above and below at the interior width
+    static constexpr int NMID = TY * WX, NCROSS = NMID + 8 * TX;
+    static constexpr int SLOT = WY * WX * NC;              // float2 entries per plane
+    static constexpr int NPTS = TX * TY;                   // interior points
+    static_assert(NPTS == NT, "one interior point per thread for the potential");
+};
+
+// slot column of window column xx (even columns first, then odd)
+__host__ __device__ constexpr int qcol(int xx, int hw) { return (xx >> 1) + (xx & 1) * hw; }
+
+template <int NYT>
+struct QCtx {
+    const float2 *slots;
+    const float2 *bslots;
+    const float *vslots;
+    const SRow *srows;
+    int woff;          // float2 offset of window column 0 of row y0 in a slot
+    int boff, voff;    // this thread's first base / potential entry in a slot
+    int yrow;          // row-table row of y0 (4 + 2 yt)
+    int x0, k, zbase, zlo, zhi, zc0, zc1, ld;
+    bool vok;
+    float fxy[4];      // f0 + fx x + fy y of the four points
+};
+
+// y = alpha * acc + beta * base; out = y; optional acc += gamma * y
+__device__ __forceinline__ void finish_quad(const ApplyArgs<float> &a, int o, float2 acc, float2 bv) {
+    float2 y = f2_fma(make_float2(-a.ai, a.ai), make_float2(acc.y, acc.x), f2_mul(make_float2(a.ar, a.ar), acc));
+    if (a.base != nullptr) {
+        y = f2_fma(make_float2(a.br, a.br), bv, y);
+        y = f2_fma(make_float2(-a.bi, a.bi), make_float2(bv.y, bv.x), y);
+    }
+    ((float2 *)a.out)[o] = y;
+    if (a.acc != nullptr) {
+        float2 s = a.acc_base != nullptr ? ((const float2 *)a.acc_base)[o] : ((float2 *)a.acc)[o];
+        s = f2_fma(make_float2(a.gr, a.gr), y, s);
+        s = f2_fma(make_float2(-a.gi, a.gi), make_float2(y.y, y.x), s);
+        ((float2 *)a.acc)[o] = s;
+    }
+}
+
+// Plane j has landed: add its contributions to the four queues and retire
+// the outputs of plane j - 4.  Queue slot of output j + (k - 4) is (k + PH) % 9.
+template <int NYT, int NS, int PH>
+__device__ __forceinline__ void quad_plane(const ApplyArgs<float> &a, const QCtx<NYT> &c, int j,
+                                           float2 (&q)[4][9]) {
+    using G = QuadGeom<NYT>;
+    constexpr int Q0 = (0 + PH) % 9, Q1 = (1 + PH) % 9, Q2 = (2 + PH) % 9, Q3 = (3 + PH) % 9;
+    constexpr int Q4 = (4 + PH) % 9, Q5 = (5 + PH) % 9, Q6 = (6 + PH) % 9, Q7 = (7 + PH) % 9;
+    constexpr int Q8 = (8 + PH) % 9;
+    constexpr int RW = G::WX * G::NC;     // one slot row, float2 entries
+    const int sl = j % NS;
+    const float2 *pw = c.slots + sl * G::SLOT + c.woff;
+    // window column k (x = x0 - 4 + k) of row r (y = y0 + r)
+#define QW(r, k) pw[(r) * RW + (((k) >> 1) + ((k) & 1) * G::HW) * G::NC]
+    const int p = c.zbase + j;
+    if (p >= c.zc0 && p <= c.zc1) {
+        const float2 w1 = make_float2(a.w[1], a.w[1]), w2 = make_float2(a.w[2], a.w[2]);
+        const float2 w3 = make_float2(a.w[3], a.w[3]), w4 = make_float2(a.w[4], a.w[4]);
+        float2 s[4], cen[4];     // points 0 = (x0, y0), 1 = (x0+1, y0), 2 = (x0, y0+1), 3 = (x0+1, y0+1)
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            float2 W[10];
+#pragma unroll
+            for (int k = 0; k < 10; k++) W[k] = QW(r, k);
+            cen[2 * r] = W[4];
+            cen[2 * r + 1] = W[5];
+            float2 t = f2_mul(w1, f2_add(W[3], W[5]));
+            t = f2_fma(w2, f2_add(W[2], W[6]), t);
+            t = f2_fma(w3, f2_add(W[1], W[7]), t);
+            s[2 * r] = f2_fma(w4, f2_add(W[0], W[8]), t);
+            t = f2_mul(w1, f2_add(W[4], W[6]));
+            t = f2_fma(w2, f2_add(W[3], W[7]), t);
+            t = f2_fma(w3, f2_add(W[2], W[8]), t);
+            s[2 * r + 1] = f2_fma(w4, f2_add(W[1], W[9]), t);
+        }
+#pragma unroll
+        for (int dx = 0; dx < 2; dx++) {
+            // rows y0 - 4 .. y0 - 1 and y0 + 2 .. y0 + 5 of column x0 + dx
+            const float2 m4 = QW(-4, 4 + dx), m3 = QW(-3, 4 + dx), m2 = QW(-2, 4 + dx), m1 = QW(-1, 4 + dx);
+            const float2 p2 = QW(2, 4 + dx), p3 = QW(3, 4 + dx), p4 = QW(4, 4 + dx), p5 = QW(5, 4 + dx);
+            float2 t = f2_fma(w1, f2_add(m1, cen[2 + dx]), s[dx]);
+            t = f2_fma(w2, f2_add(m2, p2), t);
+            t = f2_fma(w3, f2_add(m3, p3), t);
+            s[dx] = f2_fma(w4, f2_add(m4, p4), t);
+            t = f2_fma(w1, f2_add(cen[dx], p2), s[2 + dx]);
+            t = f2_fma(w2, f2_add(m1, p3), t);
+            t = f2_fma(w3, f2_add(m2, p4), t);
+            s[2 + dx] = f2_fma(w4, f2_add(m3, p5), t);
+        }
+        const float fz = a.fz * (float)p + 3.0f * a.w[0];
+        const float *vv = c.vslots + sl * G::NPTS + c.voff;
+#pragma unroll
+        for (int pt = 0; pt < 4; pt++) {
+            // diagonal: staged V (zero outside the mesh, where the value is zero too)
+            const float d = vv[(pt >> 1) * G::TX + (pt & 1)] + c.fxy[pt] + fz;
+            s[pt] = f2_fma(make_float2(d, d), cen[pt], s[pt]);
+            q[pt][Q3] = f2_fma(w1, cen[pt], q[pt][Q3]);
+            q[pt][Q5] = f2_fma(w1, cen[pt], q[pt][Q5]);
+            q[pt][Q2] = f2_fma(w2, cen[pt], q[pt][Q2]);
+            q[pt][Q6] = f2_fma(w2, cen[pt], q[pt][Q6]);
+            q[pt][Q1] = f2_fma(w3, cen[pt], q[pt][Q1]);
+            q[pt][Q7] = f2_fma(w3, cen[pt], q[pt][Q7]);
+            q[pt][Q0] = f2_fma(w4, cen[pt], q[pt][Q0]);
+            q[pt][Q8] = f2_fma(w4, cen[pt], q[pt][Q8]);
+            q[pt][Q4] = f2_add(q[pt][Q4], s[pt]);
+        }
+    }
+#undef QW
+    const int zo = p - 4;
+    if (zo >= c.zlo && zo < c.zhi && c.vok) {
+        const SRow *ro = c.srows + (j - 4) * G::WY + c.yrow;
+        const float2 *bb = c.bslots + sl * G::NPTS * G::NC + c.boff;
+#pragma unroll
+        for (int dy = 0; dy < 2; dy++) {
+            const SRow rw = ro[dy];
+#pragma unroll
+            for (int dx = 0; dx < 2; dx++) {
+                const int x = c.x0 + dx;
+                if (x >= rw.xmin && x <= rw.xmax)
+                    finish_quad(a, (rw.start + (x - rw.xmin)) * c.ld + c.k, q[2 * dy + dx][Q0],
+                                bb[(dy * G::TX + dx) * G::NC]);
+            }
+        }
+    }
+#pragma unroll
+    for (int pt = 0; pt < 4; pt++) q[pt][Q0] = make_float2(0.f, 0.f);
+}
+
+template <int NYT, int NS, int MINB>
+__global__ void __launch_bounds__(QuadGeom<NYT>::NT, MINB) k_apply_quad(const ApplyArgs<float> a, int nchunks) {
+    using G = QuadGeom<NYT>;
+    constexpr int NT = G::NT, TX = G::TX, TY = G::TY, WX = G::WX, WY = G::WY, NC = G::NC;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float2 *slots = (float2 *)smraw;                           // NS x SLOT
+    float2 *bslots = slots + NS * G::SLOT;                     // NS x NPTS x NC
+    float *vslots = (float *)(bslots + NS * G::NPTS * NC);     // NS x NPTS
+    SRow *srows = (SRow *)(vslots + NS * G::NPTS);             // WY x np
+
+    const int chunk = blockIdx.x % nchunks;
+    const Tile tl = a.tiles[blockIdx.x / nchunks];
+    const int ny = a.ny, nz = a.nz, ld = 2 * a.SV;
+    const int xbase = tl.tx * TX - 4, ybase = tl.ty * TY - 4, zbase = tl.zlo - 4;
+    const int np = tl.zhi - tl.zlo + 8;
+    const int cc = threadIdx.x, xt = threadIdx.y, yt = threadIdx.z;
+    const int tid = (yt * G::NXT + xt) * NC + cc;
+    for (int i = tid; i < WY * np; i += NT) {
+        const int zz = i / WY;
+        const int yy = ybase + (i - zz * WY);
+        const int zg = zbase + zz;
+        SRow r{0, 1, 0};
+        if (yy >= 0 && yy < ny && zg >= 0 && zg < nz) {
+            const Row g = a.rows[zg * ny + yy];
+            r.start = g.start;
+            r.xmin = (int16_t)g.xmin;
+            r.xmax = (int16_t)g.xmax;
+        }
+        srows[i] = r;
+    }
+    __syncthreads();
+
+    const float2 *__restrict__ in2 = (const float2 *)a.in;
+    const float2 *__restrict__ base2 = (const float2 *)a.base;
+    const int k0 = NC * chunk;                                  // first complex value of the chunk
+    const unsigned s_slots = (unsigned)__cvta_generic_to_shared(slots);
+    const unsigned s_b = (unsigned)__cvta_generic_to_shared(bslots);
+    const unsigned s_v = (unsigned)__cvta_generic_to_shared(vslots);
+    const int pyy = tid / TX, pxx = tid - pyy * TX;              // this thread's potential point
+    // plane j into slot j % NS: the cross of state records (two 16-byte
+    // halves per point), the potential of the interior points, and the base
+    // values of the outputs of plane j - 4
+    auto stage = [&](int j) {
+        const int sl = j % NS;
+        const SRow *rr = srows + j * WY;
+#pragma unroll
+        for (int m = 0; m < (2 * G::NCROSS + NT - 1) / NT; m++) {
+            const int e = tid + m * NT;
+            if (e < 2 * G::NCROSS) {
+                const int pi = e >> 1, h = e & 1;
+                int yy, xx;
+                if (pi < G::NMID) {
+                    yy = 4 + pi / WX;
+                    xx = pi - (yy - 4) * WX;
+                } else {
+                    const int e2 = pi - G::NMID, r = e2 / TX;
+                    yy = r < 4 ? r : TY + r;
+                    xx = 4 + (e2 - r * TX);
+                }
+                const SRow rw = rr[yy];
+                const int x = xbase + xx, k = k0 + 2 * h;
+                const bool ok = (x >= rw.xmin) & (x <= rw.xmax) & (k < ld);
+                const int off = ok ? (rw.start + (x - rw.xmin)) * ld + k : 0;
+                cp_async16(s_slots + (unsigned)((sl * G::SLOT + (yy * WX + qcol(xx, G::HW)) * NC + 2 * h) * 8),
+                           in2 + off, ok ? 16 : 0);
+            }
+        }
+        {
+            const SRow rw = rr[4 + pyy];
+            const int x = tl.tx * TX + pxx;
+            const bool ok = (x >= rw.xmin) & (x <= rw.xmax);
+            cp_async_small<4>(s_v + (unsigned)((sl * G::NPTS + tid) * 4), a.V + (ok ? rw.start + (x - rw.xmin) : 0),
+                              ok ? 4 : 0);
+        }
+        if (base2 != nullptr && j >= 4) {
+            const SRow *ro = srows + (j - 4) * WY + 4;
+#pragma unroll
+            for (int m = 0; m < 2; m++) {
+                const int e = tid + m * NT, pi = e >> 1, h = e & 1;
+                const int by = pi / TX, bx = pi - by * TX;
+                const SRow rw = ro[by];
+                const int x = tl.tx * TX + bx, k = k0 + 2 * h;
+                const bool ok = (x >= rw.xmin) & (x <= rw.xmax) & (k < ld);
+                const int off = ok ? (rw.start + (x - rw.xmin)) * ld + k : 0;
+                cp_async16(s_b + (unsigned)(((sl * G::NPTS + pi) * NC + 2 * h) * 8), base2 + off, ok ? 16 : 0);
+            }
+        }
+    };
+
+    QCtx<NYT> c;
+    c.slots = slots;
+    c.bslots = bslots;
+    c.vslots = vslots;
+    c.srows = srows;
+    c.woff = ((4 + 2 * yt) * WX + xt) * NC + cc;
+    c.boff = ((2 * yt) * TX + 2 * xt) * NC + cc;
+    c.voff = (2 * yt) * TX + 2 * xt;
+    c.yrow = 4 + 2 * yt;
+    c.x0 = tl.tx * TX + 2 * xt;
+    c.k = k0 + cc;
+    c.vok = c.k < ld;
+    c.ld = ld;
+    c.zbase = zbase;
+    c.zlo = tl.zlo;
+    c.zhi = tl.zhi;
+    const int y0 = tl.ty * TY + 2 * yt;
+#pragma unroll
+    for (int pt = 0; pt < 4; pt++)
+        c.fxy[pt] = a.f0 + a.fx * (float)(c.x0 + (pt & 1)) + a.fy * (float)(y0 + (pt >> 1));
+    // planes where any of the thread's four columns has points
+    c.zc0 = 1 << 30;
+    c.zc1 = -(1 << 30);
+    for (int jj = 0; jj < np; jj++) {
+        const SRow r0 = srows[jj * WY + 4 + 2 * yt], r1 = srows[jj * WY + 5 + 2 * yt];
+        const bool on = (c.x0 + 1 >= r0.xmin && c.x0 <= r0.xmax) || (c.x0 + 1 >= r1.xmin && c.x0 <= r1.xmax);
+        if (on) {
+            c.zc0 = min(c.zc0, zbase + jj);
+            c.zc1 = max(c.zc1, zbase + jj);
+        }
+    }
+    float2 q[4][9];
+#pragma unroll
+    for (int pt = 0; pt < 4; pt++)
+#pragma unroll
+        for (int k = 0; k < 9; k++) q[pt][k] = make_float2(0.f, 0.f);
+
+#pragma unroll 1
+    for (int j = 0; j < NS - 1; j++) {
+        if (j < np) stage(j);
+        cp_async_commit();
+    }
+    // plane j has landed for every thread after the barrier; the slot then
+    // refilled (plane j + NS - 1) was last read at plane j - 1
+    auto pre = [&](int j) {
+        cp_async_wait<NS - 2>();
+        __syncthreads();
+        if (j + NS - 1 < np) stage(j + NS - 1);
+        cp_async_commit();
+    };
+    int j = 0;
+#pragma unroll 1
+    for (; j + 9 <= np; j += 9) {
+        pre(j + 0); quad_plane<NYT, NS, 0>(a, c, j + 0, q);
+        pre(j + 1); quad_plane<NYT, NS, 1>(a, c, j + 1, q);
+        pre(j + 2); quad_plane<NYT, NS, 2>(a, c, j + 2, q);
+        pre(j + 3); quad_plane<NYT, NS, 3>(a, c, j + 3, q);
+        pre(j + 4); quad_plane<NYT, NS, 4>(a, c, j + 4, q);
+        pre(j + 5); quad_plane<NYT, NS, 5>(a, c, j + 5, q);
+        pre(j + 6); quad_plane<NYT, NS, 6>(a, c, j + 6, q);
+        pre(j + 7); quad_plane<NYT, NS, 7>(a, c, j + 7, q);
+        pre(j + 8); quad_plane<NYT, NS, 8>(a, c, j + 8, q);
+    }
+#pragma unroll 1
+    for (; j < np; j++) {
+        pre(j);
+        switch (j % 9) {
+        case 0: quad_plane<NYT, NS, 0>(a, c, j, q); break;
+        case 1: quad_plane<NYT, NS, 1>(a, c, j, q); break;
+        case 2: quad_plane<NYT, NS, 2>(a, c, j, q); break;
+        case 3: quad_plane<NYT, NS, 3>(a, c, j, q); break;
+        case 4: quad_plane<NYT, NS, 4>(a, c, j, q); break;
+        case 5: quad_plane<NYT, NS, 5>(a, c, j, q); break;
+        case 6: quad_plane<NYT, NS, 6>(a, c, j, q); break;
+        case 7: quad_plane<NYT, NS, 7>(a, c, j, q); break;
+        default: quad_plane<NYT, NS, 8>(a, c, j, q); break;
+        }
+    }
+    cp_async_wait<0>();
+}
+
+// Tile of kernel 5: 16 x 16 points with 256 threads, 16 x 12 otherwise (192
+// threads, two blocks per SM at up to 170 registers).
+void quad_shape(const TileCfg &cfg, int *TX, int *TY) {
+    *TX = 16;
+    *TY = cfg.threads == 256 ? 16 : 12;
+}
+
+size_t quad_smem_bytes(int nyt, int ns, int zseg) {
+    const size_t nt = 32 * (size_t)nyt, wy = 2 * (size_t)nyt + 8;
+    return (size_t)ns * (wy * 24 * 4 * 8 + nt * 4 * 8 + nt * 4) + wy * (zseg + 8) * sizeof(SRow);
+}
+
+template <int NYT, int NS, int MINB>
+static cudaError_t launch_quad_t(const ApplyArgs<float> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
+                                 bool *launched) {
+    using G = QuadGeom<NYT>;
+    const size_t smem = quad_smem_bytes(NYT, NS, cfg.zseg);
+    if (smem > 227 * 1024) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_apply_quad<NYT, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nchunks = (2 * a.SV + G::NC - 1) / G::NC;
+    const long long nblk = (long long)ntiles * nchunks;
+    if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    k_apply_quad<NYT, NS, MINB><<<(unsigned)nblk, dim3(G::NC, G::NXT, NYT), smem, st>>>(a, nchunks);
+    *launched = true;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_quad(const ApplyArgs<float> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
+                              bool *launched) {
+    *launched = false;
+    // complex offsets are 32-bit: P * ld < 2^31
+    if (ntiles == 0 || (long long)a.P * 2 * a.SV >= 0x7fffffffLL) return cudaSuccess;
+    if (cfg.threads == 256) return launch_quad_t<8, 3, 2>(a, cfg, ntiles, st, launched);
+    return launch_quad_t<6, 4, 2>(a, cfg, ntiles, st, launched);
+}
+
+}  // namespace rsg

@@ -52,6 +52,19 @@ def test_adjoint_c64_error_reported():
     assert err < 1e-3
 
 
+@pytest.mark.parametrize("kernel", [0, 5])
+def test_adjoint_c64_kernels_agree(kernel):
+    """The adjoint's power sums run through the stencil epilogue's running
+    sum (acc, acc_base): the register-blocked kernel against the oracle."""
+    p, a, b, psi0, phi, eps = _setup(torch.complex64, n=20, h=0.45)
+    p.H.set_option("kernel", kernel)
+    Jw, gw = p.O.control_gradient(a, b, eps, 0.05, checkpoint_every=4)
+    J, gr = p.H.control_gradient(psi0, phi, eps, 0.05, checkpoint_every=4)
+    assert p.H.get_option("last_kernel") == kernel
+    assert abs(J - Jw) < 1e-5 * abs(Jw)
+    assert np.abs(gr - gw).max() < 1e-3 * np.abs(gw).max()
+
+
 def test_adjoint_vs_central_differences_on_device():
     p, a, b, psi0, phi, eps = _setup(torch.complex128, nsteps=8, seed=3)
     J, g = p.H.control_gradient(psi0, phi, eps, 0.05, checkpoint_every=3)

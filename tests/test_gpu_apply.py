@@ -113,6 +113,31 @@ def test_row_tma_kernel(dtype, opts, S):
     assert rel_err(p.states_from_gpu(y, S), want) < TOL[dtype]
 
 
+@pytest.mark.parametrize("opts", [{"kernel": 5}, {"kernel": 5, "threads": 192}, {"kernel": 5, "zseg": 7},
+                                  {"kernel": 5, "threads": 192, "zseg": 1}])
+@pytest.mark.parametrize("S", [1, 2, 5, 13, 16])
+def test_quad_kernel(opts, S):
+    """Register-blocked stencil (complex64): a sphere with projectors and a
+    field; S = 1, 2 and 5 leave part of the last four-value chunk empty."""
+    p, g = wells_system("sphere", radius=4.6, h=0.25, dtype=torch.complex64, seed=10, natoms=3, lmax=2)
+    _check_apply(p, g, S, eps=0.02, dir=(0.0, 0.6, 0.8), opts=opts, expect_kernel=5)
+    psi = round_c64(white_noise_states(g, p.P, S))
+    want = p.O.taylor4(psi, 0.01, eps=0.02, dir=(0.0, 0.6, 0.8))
+    y = p.H.taylor(p.states_to_gpu(psi), 0.01, S=S)
+    torch.cuda.synchronize()
+    assert p.H.get_option("last_kernel") == 5
+    assert rel_err(p.states_from_gpu(y, S), want) < TOL[torch.complex64]
+
+
+def test_quad_kernel_cube_box_and_complex128_fallback():
+    for shape, n in (("cube", 37), ("box", (23, 9, 14)), ("box", (3, 2, 40))):
+        p, g = wells_system(shape, n, h=0.3, dtype=torch.complex64, seed=4, natoms=2, lmax=1)
+        _check_apply(p, g, 10, opts={"kernel": 5}, expect_kernel=5)
+    # complex128 has no register-blocked kernel: the staged kernel runs
+    p, g = wells_system("cube", 20, h=0.3, dtype=torch.complex128, seed=4, natoms=2, lmax=1)
+    _check_apply(p, g, 3, opts={"kernel": 5}, expect_kernel=0)
+
+
 def test_row_tma_kernel_cube_and_box():
     """Full rows (no fix-ups inside the mesh), ragged tile tails in x, y, z."""
     for shape, n in (("cube", 37), ("box", (23, 9, 14))):
