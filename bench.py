@@ -350,7 +350,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--kernel", type=int, default=None, help="stencil variant (0 z-march, 1 naive)")
+    ap.add_argument("--kernel", type=int, default=None,
+                    help="stencil variant (rsg_ham_set_option \"kernel\": 0 staged, 1 naive, 5 register-blocked, ...)")
+    ap.add_argument("--threads", type=int, default=None, help="staged kernels: threads per block")
     ap.add_argument("--rx", type=int, default=None)
     ap.add_argument("--ty", type=int, default=None)
     ap.add_argument("--zseg", type=int, default=None)
@@ -384,7 +386,7 @@ def main():
     H = rsg.Hamiltonian(mesh, dtype)
     H.set_potential(potential_wells(mesh.xyz, *wells))
     H.set_projectors(*proj)
-    for k in ("kernel", "rx", "ty", "zseg"):
+    for k in ("kernel", "threads", "rx", "ty", "zseg"):
         if getattr(args, k) is not None:
             H.set_option(k, getattr(args, k))
     S = 64

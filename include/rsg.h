@@ -218,8 +218,11 @@ rsg_status rsg_batch_destroy(rsg_batch b);
  * x: 1, 2 or 4; the staged kernel uses 1 or 2), "ty" (rows per
  * tile: 1, 2, 4, 8 or 16), "zseg" (planes per z segment, 1..120), "cv"
  * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8),
- * "threads" (staged kernels: 256 threads per block, the default, or 512;
- * 192 selects kernel 5's 16 x 12 tile),
+ * "threads" (staged kernels: 256 or 512 threads per block; kernel 5: 256
+ * gives 16 x 16 tiles, any other value 16 x 12 tiles with 192 threads).
+ * Defaults: complex64 runs kernel 5 with 192 threads and 96-plane z
+ * segments, complex128 kernel 1; kernels 0, 3 and 4 default to 256 threads,
+ * cv 2, 4 stages.
  * "stages" (staged kernels: shared-memory pipeline depth, 3 or 4 for
  * kernel 0; kernel 4 uses 4, or 5 when set to 5, with 256 threads and 6
  * with 512),

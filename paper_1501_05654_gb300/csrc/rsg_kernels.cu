@@ -516,11 +516,13 @@ static inline int pow2_at_least(int v) {
 void stage_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
     int v = 1;
     while (v < SV && v < c.cv) v <<= 1;
-    if (c.threads == 256 && v < 2) v = 2;
-    if (c.threads == 256 && v > 4) v = 4;
+    // 512 threads, or 256 for any other setting (192 is a kernel-5 shape)
+    const int nt = c.threads == 512 ? 512 : 256;
+    if (nt == 256 && v < 2) v = 2;
+    if (nt == 256 && v > 4) v = 4;
     *cv = v;
     *ty = 16;          // fixed geometry: threads = cv x (threads / 16 / cv) x 16
-    *nxr = c.threads / 16 / v;
+    *nxr = nt / 16 / v;
 }
 
 size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes) {
@@ -528,7 +530,7 @@ size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes) {
     stage_shape(c, SV, &cv, &nxr, &ty);
     // NS slots of the (ty + 8) x (nxr + 8) halo tile, plus per-thread base and V
     return (size_t)(c.stages == 3 ? 3 : 4) *
-           ((size_t)(ty + 8) * (nxr + 8) * cv * vec_bytes + (size_t)c.threads * (vec_bytes + vec_bytes / 2));
+           ((size_t)(ty + 8) * (nxr + 8) * cv * vec_bytes + (size_t)cv * nxr * ty * (vec_bytes + vec_bytes / 2));
 }
 
 // Row-table bytes of the staged kernel: (ty + 8) rows x (zseg + 8) planes.
@@ -566,7 +568,7 @@ static cudaError_t launch_staged_t(const ApplyArgs<R> &a, unsigned nblk, size_t 
 template <typename R>
 static cudaError_t launch_staged_cv(const ApplyArgs<R> &a, const TileCfg &cfg, int cv, unsigned nblk, size_t smem,
                                     int srow_off, int nchunks, cudaStream_t st) {
-    if (cfg.threads == 256) {
+    if (cfg.threads != 512) {
         const bool three = cfg.blocks_per_sm >= 3;
         if (cfg.stages == 3) {
             if (cv <= 2)
@@ -1485,7 +1487,7 @@ cudaError_t launch_apply_rowtma(const ApplyArgs<R> &a, const TileCfg &cfg, int n
     if constexpr (sizeof(R) == 8) {
         // complex128 is bound by FP64 arithmetic: one shape (the tiles were
         // built for cfg.threads, so other shapes fall back to kernel 0)
-        if (cfg.threads != 256) return cudaSuccess;
+        if (cfg.threads == 512) return cudaSuccess;
         return launch_rowtma_t<R, 2, 4, 256, 2>(a, cfg, ntiles, st, launched);
     } else {
         if (cfg.threads == 512) return launch_rowtma_t<R, 2, 6, 512, 1>(a, cfg, ntiles, st, launched);

@@ -78,24 +78,26 @@ __device__ __forceinline__ void finish_quad(const ApplyArgs<float> &a, int o, fl
 }
 
 // Plane j has landed: add its contributions to the four queues and retire
-// the outputs of plane j - 4.  Queue slot of output j + (k - 4) is (k + PH) % 9.
-template <int NYT, int NS, int PH>
+// the outputs of plane j - 4.  Entry k of a queue holds output plane
+// j - 4 + k; every entry takes exactly one update per plane, and each update
+// is written one entry down, so the queue shifts without extra moves and the
+// loop body exists once (no unrolling for register renaming, which kept the
+// code out of the instruction cache).
+template <int NYT, int NS>
 __device__ __forceinline__ void quad_plane(const ApplyArgs<float> &a, const QCtx<NYT> &c, int j,
                                            float2 (&q)[4][9]) {
     using G = QuadGeom<NYT>;
-    constexpr int Q0 = (0 + PH) % 9, Q1 = (1 + PH) % 9, Q2 = (2 + PH) % 9, Q3 = (3 + PH) % 9;
-    constexpr int Q4 = (4 + PH) % 9, Q5 = (5 + PH) % 9, Q6 = (6 + PH) % 9, Q7 = (7 + PH) % 9;
-    constexpr int Q8 = (8 + PH) % 9;
     constexpr int RW = G::WX * G::NC;     // one slot row, float2 entries
     const int sl = j % NS;
     const float2 *pw = c.slots + sl * G::SLOT + c.woff;
     // window column k (x = x0 - 4 + k) of row r (y = y0 + r)
 #define QW(r, k) pw[(r) * RW + (((k) >> 1) + ((k) & 1) * G::HW) * G::NC]
     const int p = c.zbase + j;
+    const float2 w1 = make_float2(a.w[1], a.w[1]), w2 = make_float2(a.w[2], a.w[2]);
+    const float2 w3 = make_float2(a.w[3], a.w[3]), w4 = make_float2(a.w[4], a.w[4]);
+    // points 0 = (x0, y0), 1 = (x0+1, y0), 2 = (x0, y0+1), 3 = (x0+1, y0+1)
+    float2 s[4], cen[4];
     if (p >= c.zc0 && p <= c.zc1) {
-        const float2 w1 = make_float2(a.w[1], a.w[1]), w2 = make_float2(a.w[2], a.w[2]);
-        const float2 w3 = make_float2(a.w[3], a.w[3]), w4 = make_float2(a.w[4], a.w[4]);
-        float2 s[4], cen[4];     // points 0 = (x0, y0), 1 = (x0+1, y0), 2 = (x0, y0+1), 3 = (x0+1, y0+1)
 #pragma unroll
         for (int r = 0; r < 2; r++) {
             float2 W[10];
@@ -133,18 +135,29 @@ __device__ __forceinline__ void quad_plane(const ApplyArgs<float> &a, const QCtx
             // diagonal: staged V (zero outside the mesh, where the value is zero too)
             const float d = vv[(pt >> 1) * G::TX + (pt & 1)] + c.fxy[pt] + fz;
             s[pt] = f2_fma(make_float2(d, d), cen[pt], s[pt]);
-            q[pt][Q3] = f2_fma(w1, cen[pt], q[pt][Q3]);
-            q[pt][Q5] = f2_fma(w1, cen[pt], q[pt][Q5]);
-            q[pt][Q2] = f2_fma(w2, cen[pt], q[pt][Q2]);
-            q[pt][Q6] = f2_fma(w2, cen[pt], q[pt][Q6]);
-            q[pt][Q1] = f2_fma(w3, cen[pt], q[pt][Q1]);
-            q[pt][Q7] = f2_fma(w3, cen[pt], q[pt][Q7]);
-            q[pt][Q0] = f2_fma(w4, cen[pt], q[pt][Q0]);
-            q[pt][Q8] = f2_fma(w4, cen[pt], q[pt][Q8]);
-            q[pt][Q4] = f2_add(q[pt][Q4], s[pt]);
         }
+    } else {
+        // no mesh point in the thread's columns at this plane: nothing to add
+#pragma unroll
+        for (int pt = 0; pt < 4; pt++) s[pt] = cen[pt] = make_float2(0.f, 0.f);
     }
 #undef QW
+    float2 done[4];
+#pragma unroll
+    for (int pt = 0; pt < 4; pt++) {
+        float2 *qq = q[pt];
+        const float2 cv = cen[pt];
+        done[pt] = f2_fma(w4, cv, qq[0]);     // output j - 4 is complete
+        qq[0] = f2_fma(w3, cv, qq[1]);
+        qq[1] = f2_fma(w2, cv, qq[2]);
+        qq[2] = f2_fma(w1, cv, qq[3]);
+        qq[3] = f2_add(qq[4], s[pt]);
+        qq[4] = f2_fma(w1, cv, qq[5]);
+        qq[5] = f2_fma(w2, cv, qq[6]);
+        qq[6] = f2_fma(w3, cv, qq[7]);
+        qq[7] = f2_fma(w4, cv, qq[8]);
+        qq[8] = make_float2(0.f, 0.f);
+    }
     const int zo = p - 4;
     if (zo >= c.zlo && zo < c.zhi && c.vok) {
         const SRow *ro = c.srows + (j - 4) * G::WY + c.yrow;
@@ -156,13 +169,11 @@ __device__ __forceinline__ void quad_plane(const ApplyArgs<float> &a, const QCtx
             for (int dx = 0; dx < 2; dx++) {
                 const int x = c.x0 + dx;
                 if (x >= rw.xmin && x <= rw.xmax)
-                    finish_quad(a, (rw.start + (x - rw.xmin)) * c.ld + c.k, q[2 * dy + dx][Q0],
+                    finish_quad(a, (rw.start + (x - rw.xmin)) * c.ld + c.k, done[2 * dy + dx],
                                 bb[(dy * G::TX + dx) * G::NC]);
             }
         }
     }
-#pragma unroll
-    for (int pt = 0; pt < 4; pt++) q[pt][Q0] = make_float2(0.f, 0.f);
 }
 
 template <int NYT, int NS, int MINB>
@@ -204,32 +215,41 @@ __global__ void __launch_bounds__(QuadGeom<NYT>::NT, MINB) k_apply_quad(const Ap
     const unsigned s_b = (unsigned)__cvta_generic_to_shared(bslots);
     const unsigned s_v = (unsigned)__cvta_generic_to_shared(vslots);
     const int pyy = tid / TX, pxx = tid - pyy * TX;              // this thread's potential point
-    // plane j into slot j % NS: the cross of state records (two 16-byte
-    // halves per point), the potential of the interior points, and the base
-    // values of the outputs of plane j - 4
+    // plane j into slot j % NS: the cross of state records, the potential of
+    // the interior points, and the base values of the outputs of plane j - 4.
+    // A staging task is four x-adjacent points of one cross row, taken by two
+    // adjacent threads, one 16-byte half of each record apiece (one row
+    // lookup, four copies; the lanes of a warp still read whole 32-byte
+    // sectors): TY x 6 tasks in the middle rows, 8 x 4 in the halo rows.
+    constexpr int NTASK = TY * (WX / 4) + 8 * (TX / 4);
+    const int hh = tid & 1;
     auto stage = [&](int j) {
         const int sl = j % NS;
         const SRow *rr = srows + j * WY;
+        const unsigned dslot = s_slots + (unsigned)(sl * G::SLOT * 8 + hh * 16);
+        const bool hok = k0 + 2 * hh < ld;
 #pragma unroll
-        for (int m = 0; m < (2 * G::NCROSS + NT - 1) / NT; m++) {
-            const int e = tid + m * NT;
-            if (e < 2 * G::NCROSS) {
-                const int pi = e >> 1, h = e & 1;
-                int yy, xx;
-                if (pi < G::NMID) {
-                    yy = 4 + pi / WX;
-                    xx = pi - (yy - 4) * WX;
+        for (int t0 = 0; t0 < 2 * NTASK; t0 += NT) {
+            const int t = (t0 + tid) >> 1;
+            if (t0 + NT <= 2 * NTASK || t < NTASK) {
+                int yy, xx0;
+                if (t < TY * (WX / 4)) {
+                    yy = 4 + t / (WX / 4);
+                    xx0 = 4 * (t - (yy - 4) * (WX / 4));
                 } else {
-                    const int e2 = pi - G::NMID, r = e2 / TX;
+                    const int t2 = t - TY * (WX / 4), r = t2 / (TX / 4);
                     yy = r < 4 ? r : TY + r;
-                    xx = 4 + (e2 - r * TX);
+                    xx0 = 4 + 4 * (t2 - r * (TX / 4));
                 }
                 const SRow rw = rr[yy];
-                const int x = xbase + xx, k = k0 + 2 * h;
-                const bool ok = (x >= rw.xmin) & (x <= rw.xmax) & (k < ld);
-                const int off = ok ? (rw.start + (x - rw.xmin)) * ld + k : 0;
-                cp_async16(s_slots + (unsigned)((sl * G::SLOT + (yy * WX + qcol(xx, G::HW)) * NC + 2 * h) * 8),
-                           in2 + off, ok ? 16 : 0);
+                const unsigned drow = dslot + (unsigned)(yy * WX * NC * 8);
+#pragma unroll
+                for (int d = 0; d < 4; d++) {
+                    const int x = xbase + xx0 + d;
+                    const bool ok = (x >= rw.xmin) & (x <= rw.xmax) & hok;
+                    const float2 *src = in2 + (ok ? (rw.start + (x - rw.xmin)) * ld + k0 + 2 * hh : 0);
+                    cp_async16(drow + (unsigned)(qcol(xx0 + d, G::HW) * NC * 8), src, ok ? 16 : 0);
+                }
             }
         }
         {
@@ -240,16 +260,16 @@ __global__ void __launch_bounds__(QuadGeom<NYT>::NT, MINB) k_apply_quad(const Ap
                               ok ? 4 : 0);
         }
         if (base2 != nullptr && j >= 4) {
-            const SRow *ro = srows + (j - 4) * WY + 4;
+            // base records of interior points 2 (tid / 2) and 2 (tid / 2) + 1
+            // (same row), half hh of each
+            const int pi0 = 2 * (tid >> 1), by = pi0 / TX, bx = pi0 - by * TX;
+            const SRow rw = srows[(j - 4) * WY + 4 + by];
 #pragma unroll
-            for (int m = 0; m < 2; m++) {
-                const int e = tid + m * NT, pi = e >> 1, h = e & 1;
-                const int by = pi / TX, bx = pi - by * TX;
-                const SRow rw = ro[by];
-                const int x = tl.tx * TX + bx, k = k0 + 2 * h;
-                const bool ok = (x >= rw.xmin) & (x <= rw.xmax) & (k < ld);
-                const int off = ok ? (rw.start + (x - rw.xmin)) * ld + k : 0;
-                cp_async16(s_b + (unsigned)(((sl * G::NPTS + pi) * NC + 2 * h) * 8), base2 + off, ok ? 16 : 0);
+            for (int d = 0; d < 2; d++) {
+                const int x = tl.tx * TX + bx + d;
+                const bool ok = (x >= rw.xmin) & (x <= rw.xmax) & hok;
+                const float2 *src = base2 + (ok ? (rw.start + (x - rw.xmin)) * ld + k0 + 2 * hh : 0);
+                cp_async16(s_b + (unsigned)(((sl * G::NPTS + pi0 + d) * NC + 2 * hh) * 8), src, ok ? 16 : 0);
             }
         }
     };
@@ -304,33 +324,10 @@ __global__ void __launch_bounds__(QuadGeom<NYT>::NT, MINB) k_apply_quad(const Ap
         if (j + NS - 1 < np) stage(j + NS - 1);
         cp_async_commit();
     };
-    int j = 0;
 #pragma unroll 1
-    for (; j + 9 <= np; j += 9) {
-        pre(j + 0); quad_plane<NYT, NS, 0>(a, c, j + 0, q);
-        pre(j + 1); quad_plane<NYT, NS, 1>(a, c, j + 1, q);
-        pre(j + 2); quad_plane<NYT, NS, 2>(a, c, j + 2, q);
-        pre(j + 3); quad_plane<NYT, NS, 3>(a, c, j + 3, q);
-        pre(j + 4); quad_plane<NYT, NS, 4>(a, c, j + 4, q);
-        pre(j + 5); quad_plane<NYT, NS, 5>(a, c, j + 5, q);
-        pre(j + 6); quad_plane<NYT, NS, 6>(a, c, j + 6, q);
-        pre(j + 7); quad_plane<NYT, NS, 7>(a, c, j + 7, q);
-        pre(j + 8); quad_plane<NYT, NS, 8>(a, c, j + 8, q);
-    }
-#pragma unroll 1
-    for (; j < np; j++) {
+    for (int j = 0; j < np; j++) {
         pre(j);
-        switch (j % 9) {
-        case 0: quad_plane<NYT, NS, 0>(a, c, j, q); break;
-        case 1: quad_plane<NYT, NS, 1>(a, c, j, q); break;
-        case 2: quad_plane<NYT, NS, 2>(a, c, j, q); break;
-        case 3: quad_plane<NYT, NS, 3>(a, c, j, q); break;
-        case 4: quad_plane<NYT, NS, 4>(a, c, j, q); break;
-        case 5: quad_plane<NYT, NS, 5>(a, c, j, q); break;
-        case 6: quad_plane<NYT, NS, 6>(a, c, j, q); break;
-        case 7: quad_plane<NYT, NS, 7>(a, c, j, q); break;
-        default: quad_plane<NYT, NS, 8>(a, c, j, q); break;
-        }
+        quad_plane<NYT, NS>(a, c, j, q);
     }
     cp_async_wait<0>();
 }

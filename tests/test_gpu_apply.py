@@ -113,8 +113,8 @@ def test_row_tma_kernel(dtype, opts, S):
     assert rel_err(p.states_from_gpu(y, S), want) < TOL[dtype]
 
 
-@pytest.mark.parametrize("opts", [{"kernel": 5}, {"kernel": 5, "threads": 192}, {"kernel": 5, "zseg": 7},
-                                  {"kernel": 5, "threads": 192, "zseg": 1}])
+@pytest.mark.parametrize("opts", [{"kernel": 5}, {"kernel": 5, "threads": 256}, {"kernel": 5, "zseg": 7},
+                                  {"kernel": 5, "threads": 256, "zseg": 1}, {"kernel": 5, "threads": 512}])
 @pytest.mark.parametrize("S", [1, 2, 5, 13, 16])
 def test_quad_kernel(opts, S):
     """Register-blocked stencil (complex64): a sphere with projectors and a
