@@ -466,7 +466,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if dtype == torch.complex64 else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "points": P, "states": S, "state_dtype": args.dtype,
+        "config": {"workload": WORKLOAD if args.radius == 18.0 else
+                   f"sphere R={args.radius:g} bohr h=0.2 ({P:,} pts), 64 states, 32 wells, 32 atoms x 4 projectors, "
+                   "ETRS Taylor-4 dt=0.01 (smaller than the headline workload)",
+                   "points": P, "states": S, "state_dtype": args.dtype,
                    "h_applications_per_step": N_APPLY_PER_STEP,
                    "l2": "state blocks (1.56 GB) exceed L2; no flush",
                    "parallelism": f"replicas x{ws}"},
