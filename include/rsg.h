@@ -220,7 +220,7 @@ rsg_status rsg_batch_destroy(rsg_batch b);
  * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8),
  * "threads" (staged kernels: 256 or 512 threads per block; kernel 5: 256
  * gives 16 x 16 tiles, any other value 16 x 12 tiles with 192 threads).
- * Defaults: complex64 runs kernel 5 with 192 threads and 96-plane z
+ * Defaults: complex64 runs kernel 5 with 192 threads and 120-plane z
  * segments, complex128 kernel 1; kernels 0, 3 and 4 default to 256 threads,
  * cv 2, 4 stages.
  * "stages" (staged kernels: shared-memory pipeline depth, 3 or 4 for

@@ -121,7 +121,7 @@ struct rsg_ham_s {
     int adj_keep = -1;           // adjoint: keep segment powers (1), recompute (0), by memory (-1)
     // projectors
     ProjDev pj;
-    DevBuf q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm, nl_ptr, nl_ent, u_pts, u_ptr;
+    DevBuf q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm, nl_ptr, nl_ent, u_pts, u_ptr, e_atom, e_p;
     DevBuf D, partial;
     // workspace
     DevBuf w0, w1, red, G, W, Wc, drift, status, dots, M, ov, grad, Xd, Xdir;
@@ -205,6 +205,7 @@ rsg_status get_tiles(rsg_mesh m, int TX, int TY, int zseg, const Tile **out, int
     auto it = m->tiles.find(key);
     if (it == m->tiles.end()) {
         std::vector<Tile> tl;
+        std::vector<int> seg;     // z segment index of each tile
         const int ntx = (m->nx + TX - 1) / TX, nty = (m->ny + TY - 1) / TY;
         for (int ty = 0; ty < nty; ty++)
             for (int tx = 0; tx < ntx; tx++) {
@@ -218,9 +219,38 @@ rsg_status get_tiles(rsg_mesh m, int TX, int TY, int zseg, const Tile **out, int
                             zhi = std::max(zhi, z + 1);
                         }
                     }
-                for (int z0 = zlo; z0 < zhi; z0 += zseg)
+                for (int z0 = zlo; z0 < zhi; z0 += zseg) {
                     tl.push_back(Tile{tx, ty, z0, std::min(zhi, z0 + zseg)});
+                    seg.push_back((z0 - zlo) / zseg);
+                }
             }
+        // launch order: by z segment, then along a Hilbert curve over (tx, ty),
+        // so that the blocks resident at one time cover compact patches of
+        // tiles and read each other's halo rows and columns from L2
+        int side = 1;
+        while (side < ntx || side < nty) side <<= 1;
+        auto hilbert = [side](int x, int y) {
+            long long d = 0;
+            for (int s = side / 2; s > 0; s /= 2) {
+                const int rx = (x & s) > 0, ry = (y & s) > 0;
+                d += (long long)s * s * ((3 * rx) ^ ry);
+                if (ry == 0) {
+                    if (rx == 1) {
+                        x = s - 1 - x;
+                        y = s - 1 - y;
+                    }
+                    std::swap(x, y);
+                }
+            }
+            return d;
+        };
+        std::vector<std::pair<long long, int>> order(tl.size());
+        for (size_t i = 0; i < tl.size(); i++)
+            order[i] = {(long long)seg[i] * side * side + hilbert(tl[i].tx, tl[i].ty), (int)i};
+        std::stable_sort(order.begin(), order.end());
+        std::vector<Tile> sorted(tl.size());
+        for (size_t i = 0; i < tl.size(); i++) sorted[i] = tl[order[i].second];
+        tl.swap(sorted);
         auto &slot = m->tiles[key];
         cudaError_t e = slot.first.upload(tl);
         if (e != cudaSuccess) {
@@ -424,7 +454,7 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     }
     if (H->prof) CK(cudaEventRecord(e1, st));
     if (split_nl) {
-        CK(launch_proj_scatter<R>(a, H->pj.u_pts, H->pj.u_ptr, H->pj.nu, st));
+        CK(launch_proj_scatter<R>(a, H->pj, st));
         H->n_launch++;
     }
     // algorithmic bytes: read u, write out, optional base / acc (read+write),
@@ -646,14 +676,14 @@ rsg_status rsg_ham_create(rsg_mesh m, rsg_dtype dtype, rsg_ham *out) {
     H->dtype = dtype;
     // complex128 is bound by FP64 arithmetic: the one-thread-per-value kernel
     // does the least of it; complex64 runs the register-blocked staged
-    // kernel (16 x 12 tiles, 96-plane segments: fastest on the sphere
+    // kernel (16 x 12 tiles, 120-plane segments: fastest on the sphere
     // workloads measured)
     if (dtype == RSG_C128) {
         H->cfg.kernel = 1;
     } else {
         H->cfg.kernel = 5;
         H->cfg.threads = 192;
-        H->cfg.zseg = 96;
+        H->cfg.zseg = 120;
     }
     *out = H;
     return RSG_OK;
@@ -786,6 +816,7 @@ rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value) {
     else if (k == "zseg") *value = H->cfg.zseg;
     else if (k == "cv") *value = H->cfg.cv;
     else if (k == "threads") *value = H->cfg.threads;
+    else if (k == "sync") *value = H->cfg.sync;
     else if (k == "stages") *value = H->cfg.stages;
     else if (k == "blocks_per_sm") *value = H->cfg.blocks_per_sm;
     else return fail(RSG_ERR_ARG, "unknown option: %s", key);
@@ -806,6 +837,7 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
     else if (k == "adjoint_keep_powers" && value >= -1 && value <= 1) H->adj_keep = (int)value;
     else if (k == "threads" && (value == 192 || value == 256 || value == 512)) H->cfg.threads = (int)value;
+    else if (k == "sync" && value >= 0 && value <= 2) H->cfg.sync = (int)value;
     else if (k == "stages" && value >= 3 && value <= 5) H->cfg.stages = (int)value;
     else if (k == "blocks_per_sm" && (value == 2 || value == 3)) H->cfg.blocks_per_sm = (int)value;
     else return fail(RSG_ERR_ARG, "unknown option or value: %s=%lld", key, (long long)value);
@@ -933,6 +965,20 @@ rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres, cons
         }
     CK(H->u_pts.upload(u_pts));
     CK(H->u_ptr.upload(u_ptr));
+    // point-major copies of each entry's atom and projector values, so the
+    // scatter reads them without going through the entry index
+    std::vector<int32_t> e_atom(nl_ent.size());
+    std::vector<double> e_p(nl_ent.size() * (size_t)std::max(npmax, 1));
+    for (size_t e = 0; e < nl_ent.size(); e++) {
+        const size_t q = (size_t)nl_ent[e];
+        e_atom[e] = q_atom[q];
+        for (int i = 0; i < npmax; i++) e_p[e * npmax + i] = q_p[q * npmax + i];
+    }
+    CK(H->e_atom.upload(e_atom));
+    if (H->dtype == RSG_C64)
+        CK(H->e_p.upload(cast_vec<float>(e_p)));
+    else
+        CK(H->e_p.upload(e_p));
     ProjDev &pj = H->pj;
     pj.natoms = natoms;
     pj.npmax = npmax;
@@ -951,6 +997,8 @@ rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres, cons
     pj.nu = (int)u_pts.size();
     pj.u_pts = H->u_pts.as<int32_t>();
     pj.u_ptr = H->u_ptr.as<int32_t>();
+    pj.e_atom = H->e_atom.as<int32_t>();
+    pj.e_p = H->e_p.p;
     return RSG_OK;
 }
 
@@ -1327,6 +1375,8 @@ rsg_status batch_build(rsg_batch b) {
             A.atom_chunk0 = pj.atom_chunk0;
             A.u_pts = pj.u_pts;
             A.u_ptr = pj.u_ptr;
+            A.e_atom = pj.e_atom;
+            A.e_p = (const float *)pj.e_p;
             A.q_p = (const float *)pj.q_p;
             A.hm = pj.hm;
             CK(b->D[(size_t)i].ensure((size_t)pj.natoms * pj.npmax * ld * 8));

@@ -35,6 +35,7 @@ struct TileCfg {
     int cv = 2;       // staged kernel: 16-byte vectors per point in a chunk (1..8)
     int stages = 4;   // staged kernels: shared-memory pipeline depth (3 or 4; kernel 4: 4 or 5 with 256 threads)
     int blocks_per_sm = 2;   // staged kernel, 256 threads: register budget for 2 or 3 blocks per SM
+    int sync = 0;     // kernel 5, 192 threads: 0 block barrier per plane, 1/2 per-slot mbarriers
     int threads = 256;   // staged kernel: threads per block (256 with two blocks per SM, or 512)
 };
 
@@ -81,6 +82,8 @@ struct ProjDev {
     int32_t *nl_ptr = nullptr, *nl_ent = nullptr;
     int nu = 0;                    // points inside at least one sphere
     int32_t *u_pts = nullptr, *u_ptr = nullptr;   // those points and their CSR rows
+    int32_t *e_atom = nullptr;     // per point-CSR entry: its atom (= q_atom[nl_ent[e]])
+    void *e_p = nullptr;           // per point-CSR entry: its npmax projector values
 };
 
 // ---- launchers (rsg_kernels.cu) ----
@@ -111,10 +114,10 @@ cudaError_t launch_proj_dot(const void *u, int SV, const ProjDev &pj, double *pa
 template <typename R>
 cudaError_t launch_proj_reduce(const double *partial, int SV, const ProjDev &pj,
                                double h3, void *D, cudaStream_t st);
-// out += alpha * (projector terms), acc += gamma * alpha * (same)
+// out += alpha * (projector terms), acc += gamma * alpha * (same), over the
+// union points, reading the point-major entry copies (pj.e_atom, pj.e_p)
 template <typename R>
-cudaError_t launch_proj_scatter(const ApplyArgs<R> &a, const int32_t *upts, const int32_t *uptr,
-                                int nu, cudaStream_t st);
+cudaError_t launch_proj_scatter(const ApplyArgs<R> &a, const ProjDev &pj, cudaStream_t st);
 
 // ---- linear algebra on state blocks (rsg_linalg.cu) ----
 // G (S x S complex double) = h3 * Psi^H Psi; partial needs nblk * S * S * 2 doubles.
@@ -183,8 +186,8 @@ struct SysArgs {
     const float *V;
     float w[5];
     int natoms, npmax, nu;
-    const int32_t *q_pt, *q_atom, *nl_ent, *chunk_q0, *chunk_q1, *atom_chunk0, *u_pts, *u_ptr;
-    const float *q_p;
+    const int32_t *q_pt, *q_atom, *nl_ent, *chunk_q0, *chunk_q1, *atom_chunk0, *u_pts, *u_ptr, *e_atom;
+    const float *q_p, *e_p;
     const double *hm;
     float *D;
     double *partial;

@@ -645,7 +645,23 @@ __global__ void __launch_bounds__(256) k_proj_dot(const typename VT<R>::T *__res
 #pragma unroll
     for (int i = 0; i < NP; i++) acc[i] = V::zero();
     if (v < SV) {
-        for (int q = q0 + threadIdx.y; q < q1; q += blockDim.y) {
+        // four entries per iteration: their point indices, then their values,
+        // are independent loads in flight together
+        const int by = blockDim.y;
+        int q = q0 + threadIdx.y;
+        for (; q + 3 * by < q1; q += 4 * by) {
+            int pt[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) pt[k] = q_pt[q + k * by];
+            T val[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) val[k] = V::ldg(u + (int64_t)pt[k] * SV + v);
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+#pragma unroll
+                for (int i = 0; i < NP; i++) V::fma(acc[i], q_p[(int64_t)(q + k * by) * NP + i], val[k]);
+        }
+        for (; q < q1; q += by) {
             const T val = V::ldg(u + (int64_t)q_pt[q] * SV + v);
 #pragma unroll
             for (int i = 0; i < NP; i++) V::fma(acc[i], q_p[(int64_t)q * NP + i], val);
@@ -705,6 +721,7 @@ __global__ void k_proj_reduce(const double *__restrict__ partial, int SV, int na
     double cr[9], ci[9];
     for (int i = 0; i < npmax; i++) {
         double sr = 0.0, si = 0.0;
+#pragma unroll 4
         for (int c = atom_chunk0[a]; c < atom_chunk0[a + 1]; c++) {
             const double *p = partial + (((int64_t)c * npmax + i) * ldc + s) * 2;
             sr += p[0];
@@ -733,7 +750,9 @@ __global__ void k_proj_reduce(const double *__restrict__ partial, int SV, int na
 // lists come from the point-centric CSR, so there are no atomics.
 template <typename R>
 __global__ void __launch_bounds__(256) k_proj_scatter(const ApplyArgs<R> a, const int32_t *__restrict__ upts,
-                                                      const int32_t *__restrict__ uptr, int nu) {
+                                                      const int32_t *__restrict__ uptr,
+                                                      const int32_t *__restrict__ e_atom,
+                                                      const R *__restrict__ e_p, int nu) {
     using V = VT<R>;
     using T = typename V::T;
     const int u = blockIdx.x * blockDim.y + threadIdx.y;
@@ -744,9 +763,8 @@ __global__ void __launch_bounds__(256) k_proj_scatter(const ApplyArgs<R> a, cons
     for (int v = threadIdx.x; v < a.SV; v += blockDim.x) {
         T sum = V::zero();
         for (int e = e0; e < e1; e++) {
-            const int q = a.nl_ent[e];
-            const int at = a.q_atom[q];
-            const R *pv = a.q_p + q * a.npmax;
+            const int at = e_atom[e];
+            const R *pv = e_p + e * a.npmax;
             const T *Da = D + at * a.npmax * a.SV + v;
             for (int i = 0; i < a.npmax; i++) V::fma(sum, pv[i], Da[i * a.SV]);
         }
@@ -763,12 +781,13 @@ __global__ void __launch_bounds__(256) k_proj_scatter(const ApplyArgs<R> a, cons
 }
 
 template <typename R>
-cudaError_t launch_proj_scatter(const ApplyArgs<R> &a, const int32_t *upts, const int32_t *uptr, int nu,
-                                cudaStream_t st) {
+cudaError_t launch_proj_scatter(const ApplyArgs<R> &a, const ProjDev &pj, cudaStream_t st) {
+    const int nu = pj.nu;
     if (nu == 0) return cudaSuccess;
     const int bx = a.SV < 32 ? a.SV : 32;
     const int by = 256 / bx;
-    k_proj_scatter<R><<<(nu + by - 1) / by, dim3(bx, by), 0, st>>>(a, upts, uptr, nu);
+    k_proj_scatter<R><<<(nu + by - 1) / by, dim3(bx, by), 0, st>>>(a, pj.u_pts, pj.u_ptr, pj.e_atom,
+                                                                   (const R *)pj.e_p, nu);
     return cudaGetLastError();
 }
 
@@ -1575,12 +1594,28 @@ __global__ void __launch_bounds__(256) k_batch_proj_dot(const SysArgs *__restric
     T acc[NP];
 #pragma unroll
     for (int i = 0; i < NP; i++) acc[i] = V::zero();
-    if (v < SV)
-        for (int q = q0 + threadIdx.y; q < q1; q += blockDim.y) {
+    if (v < SV) {
+        // four entries per iteration (independent loads in flight together)
+        const int by = blockDim.y;
+        int q = q0 + threadIdx.y;
+        for (; q + 3 * by < q1; q += 4 * by) {
+            int pt[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) pt[k] = S.q_pt[q + k * by];
+            T val[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) val[k] = V::ldg(u + pt[k] * SV + v);
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+#pragma unroll
+                for (int i = 0; i < NP; i++) V::fma(acc[i], S.q_p[(q + k * by) * NP + i], val[k]);
+        }
+        for (; q < q1; q += by) {
             const T val = V::ldg(u + S.q_pt[q] * SV + v);
 #pragma unroll
             for (int i = 0; i < NP; i++) V::fma(acc[i], S.q_p[q * NP + i], val);
         }
+    }
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     for (int i = 0; i < NP; i++) {
         red[tid * 4 + 0] = acc[i].x;
@@ -1666,9 +1701,8 @@ __global__ void __launch_bounds__(256) k_batch_scatter(const SysArgs *__restrict
     const T *D = (const T *)S.D;
     T sum = V::zero();
     for (int e = S.u_ptr[u]; e < S.u_ptr[u + 1]; e++) {
-        const int q = S.nl_ent[e];
-        const int at = S.q_atom[q];
-        const float *pv = S.q_p + q * S.npmax;
+        const int at = S.e_atom[e];
+        const float *pv = S.e_p + e * S.npmax;
         const T *Da = D + at * S.npmax * SV + v;
         for (int i = 0; i < S.npmax; i++) V::fma(sum, pv[i], Da[i * SV]);
     }
@@ -1693,7 +1727,7 @@ template cudaError_t launch_apply_tma<float>(const ApplyArgs<float> &, const Til
 template cudaError_t launch_apply<float>(const ApplyArgs<float> &, const TileCfg &, int, cudaStream_t);
 template cudaError_t launch_proj_dot<float>(const void *, int, const ProjDev &, double *, cudaStream_t);
 template cudaError_t launch_proj_reduce<float>(const double *, int, const ProjDev &, double, void *, cudaStream_t);
-template cudaError_t launch_proj_scatter<float>(const ApplyArgs<float> &, const int32_t *, const int32_t *, int, cudaStream_t);
+template cudaError_t launch_proj_scatter<float>(const ApplyArgs<float> &, const ProjDev &, cudaStream_t);
 #endif
 #ifndef RSG_ONLY_FLOAT
 template cudaError_t launch_apply_tma<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t, bool *);
@@ -1701,7 +1735,7 @@ template cudaError_t launch_apply_rowtma<double>(const ApplyArgs<double> &, cons
 template cudaError_t launch_apply<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t);
 template cudaError_t launch_proj_dot<double>(const void *, int, const ProjDev &, double *, cudaStream_t);
 template cudaError_t launch_proj_reduce<double>(const double *, int, const ProjDev &, double, void *, cudaStream_t);
-template cudaError_t launch_proj_scatter<double>(const ApplyArgs<double> &, const int32_t *, const int32_t *, int, cudaStream_t);
+template cudaError_t launch_proj_scatter<double>(const ApplyArgs<double> &, const ProjDev &, cudaStream_t);
 #endif
 
 }  // namespace rsg

@@ -61,6 +61,20 @@ struct QCtx {
     float fxy[4];      // f0 + fx x + fy y of the four points
 };
 
+// Bounded mbarrier wait (the pipelined variants): false after 2^22 polls.
+constexpr long kQuadWaitLimit = 1L << 22;
+__device__ __forceinline__ bool qbar_wait(unsigned bar, unsigned parity) {
+    for (long it = 0; it < kQuadWaitLimit; ++it) {
+        unsigned ok;
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // y = alpha * acc + beta * base; out = y; optional acc += gamma * y
 __device__ __forceinline__ void finish_quad(const ApplyArgs<float> &a, int o, float2 acc, float2 bv) {
     float2 y = f2_fma(make_float2(-a.ai, a.ai), make_float2(acc.y, acc.x), f2_mul(make_float2(a.ar, a.ar), acc));
@@ -176,7 +190,14 @@ __device__ __forceinline__ void quad_plane(const ApplyArgs<float> &a, const QCtx
     }
 }
 
-template <int NYT, int NS, int MINB>
+// SYNC selects how a plane's slot is handed between its copies and its
+// readers: 0 = one block barrier per plane; 1 and 2 = per-slot mbarriers, a
+// "full" barrier that every thread's copies arrive on
+// (cp.async.mbarrier.arrive.noinc) and an "empty" barrier that every warp
+// arrives on after its last read of the plane.  With 1 the copies run NS - 1
+// planes ahead (warps stay in step, like the barrier); with 2 they run NS - 2
+// planes ahead and a warp may run one plane ahead of the slowest.
+template <int NYT, int NS, int MINB, int SYNC>
 __global__ void __launch_bounds__(QuadGeom<NYT>::NT, MINB) k_apply_quad(const ApplyArgs<float> a, int nchunks) {
     using G = QuadGeom<NYT>;
     constexpr int NT = G::NT, TX = G::TX, TY = G::TY, WX = G::WX, WY = G::WY, NC = G::NC;
@@ -205,6 +226,19 @@ __global__ void __launch_bounds__(QuadGeom<NYT>::NT, MINB) k_apply_quad(const Ap
             r.xmax = (int16_t)g.xmax;
         }
         srows[i] = r;
+    }
+    // full / empty mbarriers of the NS slots, after the row table
+    const unsigned bar0 =
+        ((unsigned)__cvta_generic_to_shared(srows) + (unsigned)(WY * (tl.zhi - tl.zlo + 8) * sizeof(SRow)) + 7u) & ~7u;
+    if constexpr (SYNC > 0) {
+        if (tid == 0) {
+            for (int k = 0; k < NS; k++) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8 * k), "r"(NT) : "memory");
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8 * (NS + k)), "r"(NYT)
+                             : "memory");
+            }
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
     }
     __syncthreads();
 
@@ -311,25 +345,57 @@ __global__ void __launch_bounds__(QuadGeom<NYT>::NT, MINB) k_apply_quad(const Ap
 #pragma unroll
         for (int k = 0; k < 9; k++) q[pt][k] = make_float2(0.f, 0.f);
 
+    if constexpr (SYNC == 0) {
 #pragma unroll 1
-    for (int j = 0; j < NS - 1; j++) {
-        if (j < np) stage(j);
-        cp_async_commit();
-    }
-    // plane j has landed for every thread after the barrier; the slot then
-    // refilled (plane j + NS - 1) was last read at plane j - 1
-    auto pre = [&](int j) {
-        cp_async_wait<NS - 2>();
-        __syncthreads();
-        if (j + NS - 1 < np) stage(j + NS - 1);
-        cp_async_commit();
-    };
+        for (int j = 0; j < NS - 1; j++) {
+            if (j < np) stage(j);
+            cp_async_commit();
+        }
+        // plane j has landed for every thread after the barrier; the slot then
+        // refilled (plane j + NS - 1) was last read at plane j - 1
 #pragma unroll 1
-    for (int j = 0; j < np; j++) {
-        pre(j);
-        quad_plane<NYT, NS>(a, c, j, q);
+        for (int j = 0; j < np; j++) {
+            cp_async_wait<NS - 2>();
+            __syncthreads();
+            if (j + NS - 1 < np) stage(j + NS - 1);
+            cp_async_commit();
+            quad_plane<NYT, NS>(a, c, j, q);
+        }
+        cp_async_wait<0>();
+    } else {
+        constexpr int D = SYNC == 1 ? NS - 1 : NS - 2;     // planes the copies run ahead
+        const unsigned full0 = bar0, empty0 = bar0 + 8 * NS;
+        const int lane = tid & 31;
+        int bad = 0;
+        auto arrive_full = [&](int p) {
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full0 + 8 * (p % NS))
+                         : "memory");
+        };
+#pragma unroll 1
+        for (int j = 0; j < D && j < np; j++) {
+            stage(j);
+            arrive_full(j);
+        }
+#pragma unroll 1
+        for (int j = 0; j < np; j++) {
+            const int pn = j + D;
+            if (pn < np) {
+                // slot of plane pn last held plane pn - NS: every warp has read it
+                if (pn >= NS && !qbar_wait(empty0 + 8 * (pn % NS), (unsigned)((pn / NS - 1) & 1))) bad = 1;
+                stage(pn);
+                arrive_full(pn);
+            }
+            if (!qbar_wait(full0 + 8 * (j % NS), (unsigned)((j / NS) & 1))) bad = 1;
+            quad_plane<NYT, NS>(a, c, j, q);
+            __syncwarp();
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(empty0 + 8 * (j % NS)) : "memory");
+        }
+        cp_async_wait<0>();
+        // every copy has landed and every full phase up to plane np - 1 was
+        // waited on, so no arrival is left in flight when the block leaves
+        if (bad) atomicExch(a.err, 2);
     }
-    cp_async_wait<0>();
 }
 
 // Tile of kernel 5: 16 x 16 points with 256 threads, 16 x 12 otherwise (192
@@ -341,22 +407,23 @@ void quad_shape(const TileCfg &cfg, int *TX, int *TY) {
 
 size_t quad_smem_bytes(int nyt, int ns, int zseg) {
     const size_t nt = 32 * (size_t)nyt, wy = 2 * (size_t)nyt + 8;
-    return (size_t)ns * (wy * 24 * 4 * 8 + nt * 4 * 8 + nt * 4) + wy * (zseg + 8) * sizeof(SRow);
+    // slots, base and potential rings, row table, then 2 NS mbarriers
+    return (size_t)ns * (wy * 24 * 4 * 8 + nt * 4 * 8 + nt * 4) + wy * (zseg + 8) * sizeof(SRow) + 8 + 16 * (size_t)ns;
 }
 
-template <int NYT, int NS, int MINB>
+template <int NYT, int NS, int MINB, int SYNC>
 static cudaError_t launch_quad_t(const ApplyArgs<float> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
                                  bool *launched) {
     using G = QuadGeom<NYT>;
     const size_t smem = quad_smem_bytes(NYT, NS, cfg.zseg);
     if (smem > 227 * 1024) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_apply_quad<NYT, NS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_apply_quad<NYT, NS, MINB, SYNC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nchunks = (2 * a.SV + G::NC - 1) / G::NC;
     const long long nblk = (long long)ntiles * nchunks;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    k_apply_quad<NYT, NS, MINB><<<(unsigned)nblk, dim3(G::NC, G::NXT, NYT), smem, st>>>(a, nchunks);
+    k_apply_quad<NYT, NS, MINB, SYNC><<<(unsigned)nblk, dim3(G::NC, G::NXT, NYT), smem, st>>>(a, nchunks);
     *launched = true;
     return cudaGetLastError();
 }
@@ -366,8 +433,13 @@ cudaError_t launch_apply_quad(const ApplyArgs<float> &a, const TileCfg &cfg, int
     *launched = false;
     // complex offsets are 32-bit: P * ld < 2^31
     if (ntiles == 0 || (long long)a.P * 2 * a.SV >= 0x7fffffffLL) return cudaSuccess;
-    if (cfg.threads == 256) return launch_quad_t<8, 3, 2>(a, cfg, ntiles, st, launched);
-    return launch_quad_t<6, 4, 2>(a, cfg, ntiles, st, launched);
+    if (a.err == nullptr && cfg.sync != 0) return cudaSuccess;
+    if (cfg.threads == 256) return launch_quad_t<8, 3, 2, 0>(a, cfg, ntiles, st, launched);
+    switch (cfg.sync) {
+    case 1: return launch_quad_t<6, 4, 2, 1>(a, cfg, ntiles, st, launched);
+    case 2: return launch_quad_t<6, 4, 2, 2>(a, cfg, ntiles, st, launched);
+    default: return launch_quad_t<6, 4, 2, 0>(a, cfg, ntiles, st, launched);
+    }
 }
 
 }  // namespace rsg
