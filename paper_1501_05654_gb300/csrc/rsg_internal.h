@@ -198,10 +198,11 @@ struct SysArgs {
 struct BWork {
     int32_t sys, a, b, pad;
 };
-// Staged stencil over every system's tiles (block 2 x 16 x 16, cv = 2).
+// Register-blocked stencil over every system's tiles (16 x 12 tiles, chunks
+// of four complex values = two 16-byte vectors; rsg_quad.cu).
 cudaError_t launch_batch_stencil(const SysArgs *sys, const BWork *work, int nwork, int in_c, int out_c,
                                  float ar, float ai, cudaStream_t st);
-constexpr int kBatchCV = 2, kBatchTY = 16, kBatchNXR = 16, kBatchZseg = 120;
+constexpr int kBatchCV = 2, kBatchTY = 12, kBatchNXR = 16, kBatchZseg = 120;
 cudaError_t launch_batch_proj(const SysArgs *sys, const BWork *dot_work, int ndot, const BWork *red_work,
                               int nred, int in_c, int npmax, cudaStream_t st);
 cudaError_t launch_batch_scatter(const SysArgs *sys, const BWork *work, int nwork, int out_c, float ar,

@@ -28,6 +28,7 @@
 #include <cuda.h>
 
 #include "rsg_async.cuh"
+#include "rsg_batch.cuh"
 #include "rsg_internal.h"
 #include "rsg_vec.cuh"
 
@@ -298,7 +299,7 @@ __device__ __forceinline__ void stage_plane(const StageCtx<R, CV, NT> &c, int j,
 }
 
 // One block of the staged kernel: tile tl, state chunk `chunk` of the
-// system described by a.  Shared by the single-system and batched kernels.
+// system described by a.
 template <typename R, int CV, int NS, int NT = 512>
 __device__ __forceinline__ void staged_block(const ApplyArgs<R> &a, const Tile tl, const int chunk,
                                              unsigned char *smraw, SRow *srows) {
@@ -1516,68 +1517,11 @@ cudaError_t launch_apply_rowtma(const ApplyArgs<R> &a, const TileCfg &cfg, int n
 }
 
 // ------------------------------------------------------------- batches ---
-// One launch per Horner stage for many independent complex64 systems: every
-// block takes a (system, tile, chunk) work item and runs the staged stencil
-// block for that system.  Projector coefficients, their reduction and the
-// projector scatter are batched the same way.
+// One launch per Horner stage for many independent complex64 systems: the
+// stencil takes (system, tile, chunk) work items (k_batch_quad, rsg_quad.cu);
+// projector coefficients, their reduction and the projector scatter are
+// batched the same way here.
 #if !defined(RSG_ONLY_DOUBLE) && !defined(RSG_ROWTMA_TU)
-__device__ __forceinline__ ApplyArgs<float> batch_args(const SysArgs &S, int in_c, int out_c, float ar,
-                                                       float ai) {
-    ApplyArgs<float> a;
-    a.in = S.vec[in_c];
-    a.out = S.vec[out_c];
-    a.base = S.vec[0];
-    a.acc = nullptr;
-    a.acc_base = nullptr;
-    a.rows = S.rows;
-    a.tiles = S.tiles;
-    a.nx = S.nx;
-    a.ny = S.ny;
-    a.nz = S.nz;
-    a.SV = S.SV;
-    a.V = S.V;
-    a.f0 = a.fx = a.fy = a.fz = 0.f;
-    for (int k = 0; k < 5; k++) a.w[k] = S.w[k];
-    a.ar = ar;
-    a.ai = ai;
-    a.br = 1.f;
-    a.bi = 0.f;
-    a.gr = a.gi = 0.f;
-    a.nl_ptr = nullptr;
-    a.nl_ent = nullptr;
-    a.q_atom = nullptr;
-    a.q_p = nullptr;
-    a.D = nullptr;
-    a.npmax = 0;
-    a.P = S.P;
-    return a;
-}
-
-__global__ void __launch_bounds__(512, 1) k_batch_stencil(const SysArgs *__restrict__ sys,
-                                                          const BWork *__restrict__ work, int in_c,
-                                                          int out_c, float ar, float ai) {
-    extern __shared__ __align__(128) unsigned char smraw[];
-    __shared__ SRow srows[kSRows];
-    const BWork w = work[blockIdx.x];
-    const SysArgs &S = sys[w.sys];
-    const ApplyArgs<float> a = batch_args(S, in_c, out_c, ar, ai);
-    staged_block<float, kBatchCV, 4, 512>(a, S.tiles[w.a], w.b, smraw, srows);
-}
-
-cudaError_t launch_batch_stencil(const SysArgs *sys, const BWork *work, int nwork, int in_c, int out_c,
-                                 float ar, float ai, cudaStream_t st) {
-    if (nwork == 0) return cudaSuccess;
-    // shared memory of the batched block, from its own compile-time geometry
-    // (512 threads, 4 slots): slots of the halo tile plus per-thread base and V
-    using G = StagedGeom<kBatchCV, 512>;
-    const size_t smem = (size_t)4 * ((size_t)G::SLOT * sizeof(float4) + (size_t)G::NTHR * (sizeof(float4) + sizeof(float)));
-    static_assert(G::TX == kBatchNXR && G::TY == kBatchTY, "batch tiles and block geometry must agree");
-    cudaError_t e = cudaFuncSetAttribute(k_batch_stencil, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_batch_stencil<<<nwork, dim3(kBatchCV, StagedGeom<kBatchCV, 512>::TX, StagedGeom<kBatchCV, 512>::TY), smem, st>>>(
-        sys, work, in_c, out_c, ar, ai);
-    return cudaGetLastError();
-}
 
 // <p_ai|u> partial sums over one sphere chunk of one system (block 8 x 32).
 template <int NP>

@@ -25,6 +25,7 @@
 #include <cuda.h>
 
 #include "rsg_async.cuh"
+#include "rsg_batch.cuh"
 #include "rsg_internal.h"
 #include "rsg_vec.cuh"
 
@@ -197,18 +198,19 @@ __device__ __forceinline__ void quad_plane(const ApplyArgs<float> &a, const QCtx
 // arrives on after its last read of the plane.  With 1 the copies run NS - 1
 // planes ahead (warps stay in step, like the barrier); with 2 they run NS - 2
 // planes ahead and a warp may run one plane ahead of the slowest.
-template <int NYT, int NS, int MINB, int SYNC>
-__global__ void __launch_bounds__(QuadGeom<NYT>::NT, MINB) k_apply_quad(const ApplyArgs<float> a, int nchunks) {
+// One block of the register-blocked stencil: tile tl, four-value chunk
+// `chunk` of the system described by a.  Shared by the single-system and
+// batched kernels.
+template <int NYT, int NS, int SYNC>
+__device__ __forceinline__ void quad_block(const ApplyArgs<float> &a, const Tile tl, const int chunk,
+                                           unsigned char *smraw) {
     using G = QuadGeom<NYT>;
     constexpr int NT = G::NT, TX = G::TX, TY = G::TY, WX = G::WX, WY = G::WY, NC = G::NC;
-    extern __shared__ __align__(128) unsigned char smraw[];
     float2 *slots = (float2 *)smraw;                           // NS x SLOT
     float2 *bslots = slots + NS * G::SLOT;                     // NS x NPTS x NC
     float *vslots = (float *)(bslots + NS * G::NPTS * NC);     // NS x NPTS
     SRow *srows = (SRow *)(vslots + NS * G::NPTS);             // WY x np
 
-    const int chunk = blockIdx.x % nchunks;
-    const Tile tl = a.tiles[blockIdx.x / nchunks];
     const int ny = a.ny, nz = a.nz, ld = 2 * a.SV;
     const int xbase = tl.tx * TX - 4, ybase = tl.ty * TY - 4, zbase = tl.zlo - 4;
     const int np = tl.zhi - tl.zlo + 8;
@@ -398,6 +400,24 @@ __global__ void __launch_bounds__(QuadGeom<NYT>::NT, MINB) k_apply_quad(const Ap
     }
 }
 
+template <int NYT, int NS, int MINB, int SYNC>
+__global__ void __launch_bounds__(QuadGeom<NYT>::NT, MINB) k_apply_quad(const ApplyArgs<float> a, int nchunks) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    quad_block<NYT, NS, SYNC>(a, a.tiles[blockIdx.x / nchunks], blockIdx.x % nchunks, smraw);
+}
+
+// Batches: every block takes a (system, tile, chunk) work item and runs the
+// register-blocked block for that system (16 x 12 tiles, 192 threads).
+__global__ void __launch_bounds__(QuadGeom<kBatchTY / 2>::NT, 2)
+    k_batch_quad(const SysArgs *__restrict__ sys, const BWork *__restrict__ work, int in_c, int out_c, float ar,
+                 float ai) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    const BWork w = work[blockIdx.x];
+    const SysArgs &S = sys[w.sys];
+    const ApplyArgs<float> a = batch_args(S, in_c, out_c, ar, ai);
+    quad_block<kBatchTY / 2, 4, 0>(a, S.tiles[w.a], w.b, smraw);
+}
+
 // Tile of kernel 5: 16 x 16 points with 256 threads, 16 x 12 otherwise (192
 // threads, two blocks per SM at up to 170 registers).
 void quad_shape(const TileCfg &cfg, int *TX, int *TY) {
@@ -425,6 +445,19 @@ static cudaError_t launch_quad_t(const ApplyArgs<float> &a, const TileCfg &cfg, 
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     k_apply_quad<NYT, NS, MINB, SYNC><<<(unsigned)nblk, dim3(G::NC, G::NXT, NYT), smem, st>>>(a, nchunks);
     *launched = true;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_stencil(const SysArgs *sys, const BWork *work, int nwork, int in_c, int out_c,
+                                 float ar, float ai, cudaStream_t st) {
+    if (nwork == 0) return cudaSuccess;
+    using G = QuadGeom<kBatchTY / 2>;
+    static_assert(G::TX == kBatchNXR && G::TY == kBatchTY && G::NC == 2 * kBatchCV,
+                  "batch tiles and chunks must match the block geometry");
+    const size_t smem = quad_smem_bytes(kBatchTY / 2, 4, kBatchZseg);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_batch_quad<<<nwork, dim3(G::NC, G::NXT, kBatchTY / 2), smem, st>>>(sys, work, in_c, out_c, ar, ai);
     return cudaGetLastError();
 }
 
