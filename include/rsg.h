@@ -224,8 +224,8 @@ rsg_status rsg_batch_destroy(rsg_batch b);
  * segments, complex128 kernel 1; kernels 0, 3 and 4 default to 256 threads,
  * cv 2, 4 stages.
  * "stages" (staged kernels: shared-memory pipeline depth, 3 or 4 for
- * kernel 0; kernel 4 uses 4, or 5 when set to 5, with 256 threads and 6
- * with 512),
+ * kernel 0 and for kernel 5 with 192 threads (default 4; 256 threads use 3);
+ * kernel 4 uses 4, or 5 when set to 5, with 256 threads and 6 with 512),
  * "blocks_per_sm" (staged kernel with 256 threads: register budget for 2 or
  * 3 resident blocks per SM), "adjoint_keep_powers" (rsg_control_gradient: 1 keeps the Taylor powers of
  * a whole checkpoint segment, 0 recomputes them per interval, -1 = choose by

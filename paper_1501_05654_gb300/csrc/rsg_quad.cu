@@ -471,7 +471,9 @@ cudaError_t launch_apply_quad(const ApplyArgs<float> &a, const TileCfg &cfg, int
     switch (cfg.sync) {
     case 1: return launch_quad_t<6, 4, 2, 1>(a, cfg, ntiles, st, launched);
     case 2: return launch_quad_t<6, 4, 2, 2>(a, cfg, ntiles, st, launched);
-    default: return launch_quad_t<6, 4, 2, 0>(a, cfg, ntiles, st, launched);
+    default:
+        if (cfg.stages == 3) return launch_quad_t<6, 3, 2, 0>(a, cfg, ntiles, st, launched);
+        return launch_quad_t<6, 4, 2, 0>(a, cfg, ntiles, st, launched);
     }
 }
 
