@@ -684,6 +684,7 @@ rsg_status rsg_ham_create(rsg_mesh m, rsg_dtype dtype, rsg_ham *out) {
         H->cfg.kernel = 5;
         H->cfg.threads = 192;
         H->cfg.zseg = 120;
+        H->cfg.stages = 3;
     }
     *out = H;
     return RSG_OK;
@@ -836,7 +837,8 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     else if (k == "zseg" && value >= 1 && value <= 120) H->cfg.zseg = (int)value;
     else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
     else if (k == "adjoint_keep_powers" && value >= -1 && value <= 1) H->adj_keep = (int)value;
-    else if (k == "threads" && (value == 192 || value == 256 || value == 512)) H->cfg.threads = (int)value;
+    else if (k == "threads" && (value == 160 || value == 192 || value == 256 || value == 512))
+        H->cfg.threads = (int)value;
     else if (k == "sync" && value >= 0 && value <= 2) H->cfg.sync = (int)value;
     else if (k == "stages" && value >= 3 && value <= 5) H->cfg.stages = (int)value;
     else if (k == "blocks_per_sm" && (value == 2 || value == 3)) H->cfg.blocks_per_sm = (int)value;

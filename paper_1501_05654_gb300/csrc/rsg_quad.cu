@@ -418,11 +418,12 @@ __global__ void __launch_bounds__(QuadGeom<kBatchTY / 2>::NT, 2)
     quad_block<kBatchTY / 2, 4, 0>(a, S.tiles[w.a], w.b, smraw);
 }
 
-// Tile of kernel 5: 16 x 16 points with 256 threads, 16 x 12 otherwise (192
+// Tile of kernel 5: 16 x 16 points with 256 threads, 16 x 10 with 160
+// (three blocks per SM at up to 136 registers), 16 x 12 otherwise (192
 // threads, two blocks per SM at up to 170 registers).
 void quad_shape(const TileCfg &cfg, int *TX, int *TY) {
     *TX = 16;
-    *TY = cfg.threads == 256 ? 16 : 12;
+    *TY = cfg.threads == 256 ? 16 : cfg.threads == 160 ? 10 : 12;
 }
 
 size_t quad_smem_bytes(int nyt, int ns, int zseg) {
@@ -468,6 +469,7 @@ cudaError_t launch_apply_quad(const ApplyArgs<float> &a, const TileCfg &cfg, int
     if (ntiles == 0 || (long long)a.P * 2 * a.SV >= 0x7fffffffLL) return cudaSuccess;
     if (a.err == nullptr && cfg.sync != 0) return cudaSuccess;
     if (cfg.threads == 256) return launch_quad_t<8, 3, 2, 0>(a, cfg, ntiles, st, launched);
+    if (cfg.threads == 160) return launch_quad_t<5, 3, 3, 0>(a, cfg, ntiles, st, launched);
     switch (cfg.sync) {
     case 1: return launch_quad_t<6, 4, 2, 1>(a, cfg, ntiles, st, launched);
     case 2: return launch_quad_t<6, 4, 2, 2>(a, cfg, ntiles, st, launched);

@@ -116,7 +116,7 @@ def test_row_tma_kernel(dtype, opts, S):
 @pytest.mark.parametrize("opts", [{"kernel": 5}, {"kernel": 5, "threads": 256}, {"kernel": 5, "zseg": 7},
                                   {"kernel": 5, "threads": 256, "zseg": 1}, {"kernel": 5, "threads": 512},
                                   {"kernel": 5, "sync": 1}, {"kernel": 5, "sync": 2}, {"kernel": 5, "sync": 2, "zseg": 3},
-                                  {"kernel": 5, "stages": 3, "zseg": 9}])
+                                  {"kernel": 5, "stages": 3, "zseg": 9}, {"kernel": 5, "threads": 160, "zseg": 96}])
 @pytest.mark.parametrize("S", [1, 2, 5, 13, 16])
 def test_quad_kernel(opts, S):
     """Register-blocked stencil (complex64): a sphere with projectors and a
