@@ -148,6 +148,29 @@ rsg_status rsg_propagate_steps(rsg_ham H, void *psi, int64_t S, int64_t ld,
 rsg_status rsg_orthonormalize(rsg_ham H, void *psi, int64_t S, int64_t ld,
                               double *norms2_out, void *stream);
 
+/* Lowest S eigenpairs of H (the ground-state step before a propagation: the
+ * paper's closing section on parallelisation names orthogonalisation and
+ * subspace diagonalisation as the ground-state building blocks, and its
+ * few-electron section tabulates the 1-D lithium eigenvalues this solves
+ * for as one particle in 3-D).  Chebyshev-filtered subspace iteration: each
+ * of max_iter iterations applies a degree-`degree` Chebyshev polynomial of H
+ * (degree applications of H - c, damping the spectrum above the largest
+ * current Ritz value), re-orthonormalises (FP64 Cholesky-QR) and does a
+ * Rayleigh-Ritz step on the FP64 S x S matrix X^H H X.  It stops when every
+ * residual |H x_s - lambda_s x_s| (h^3-weighted 2-norm, FP64) is <= tol.
+ * psi (device, P x ld, S <= 256): in, the starting block (any full-rank
+ * block, e.g. seeded random values); out, the orthonormal Ritz vectors in
+ * ascending order.  evals_out (host, S) receives the Ritz values, resid_out
+ * (host, S, may be NULL) the residual norms, iters_out (may be NULL) the
+ * iterations taken.  The current field (rsg_field_set) is part of H.
+ * Uses the Hamiltonian's work blocks; synchronises once per iteration.
+ * Errors: as rsg_hamiltonian_apply; RSG_ERR_ARG for degree outside 1..64,
+ * max_iter < 0 or tol <= 0; RSG_ERR_UNSUPPORTED for S > 256;
+ * RSG_ERR_NONFINITE if the block loses rank or a matrix is not finite. */
+rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t max_iter, int degree,
+                          double tol, double *evals_out, double *resid_out, int64_t *iters_out,
+                          void *stream);
+
 /* FP64 <psi_s|psi_s> for S states into norms2_out (host, S doubles);
  * synchronises. */
 rsg_status rsg_state_norms(rsg_ham H, const void *psi, int64_t S, int64_t ld,

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <complex>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -115,6 +116,8 @@ struct rsg_ham_s {
     bool has_V = false;
     DevBuf V;
     double eps = 0.0, dir[3] = {1, 0, 0};
+    double vmin = 0.0, vmax = 0.0;     // range of the potential (spectral bounds of the eigensolver)
+    double proj_norm = 0.0;            // bound on the non-local operator: sum over atoms of sum |h_ij|
     TileCfg cfg;
     bool force_kernel = false;   // set when the caller chose the kernel explicitly
     int last_kernel = -1;        // stencil kernel of the last application
@@ -333,6 +336,7 @@ struct Epi {
     void *acc = nullptr;
     const void *acc_base = nullptr;
     double ar = 1, ai = 0, br = 1, bi = 0, gr = 0, gi = 0;
+    double shift = 0;   // applies H - shift (folded into the diagonal's constant term)
 };
 
 rsg_status ensure_rows(rsg_mesh m) {
@@ -375,7 +379,7 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
             fd[d] = eps * dir[d] * h;
         }
     }
-    a.f0 = (R)f0;
+    a.f0 = (R)(f0 - ep.shift);
     a.fx = (R)fd[0];
     a.fy = (R)fd[1];
     a.fz = (R)fd[2];
@@ -861,6 +865,8 @@ rsg_status rsg_potential_set(rsg_ham H, const double *v, int v_on_device) {
     else
         CK(H->V.upload(hv));
     H->has_V = true;
+    H->vmin = P ? *std::min_element(hv.begin(), hv.end()) : 0.0;
+    H->vmax = P ? *std::max_element(hv.begin(), hv.end()) : 0.0;
     return RSG_OK;
 }
 
@@ -878,6 +884,7 @@ rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres, cons
     if (!H) return fail(RSG_ERR_ARG, "NULL handle");
     if (natoms < 0) return fail(RSG_ERR_ARG, "natoms < 0");
     H->pj = ProjDev();
+    H->proj_norm = 0.0;
     if (natoms == 0) return RSG_OK;
     if (!centres || !rcut || !lmax || !beta || !hmats) return fail(RSG_ERR_ARG, "NULL array");
     rsg_mesh m = H->m;
@@ -934,7 +941,10 @@ rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres, cons
         }
         atom_ch0.push_back((int32_t)ch_q0.size());
         for (int i = 0; i < np; i++)
-            for (int j = 0; j < np; j++) hm[((size_t)a * npmax + i) * npmax + j] = hmats[hoff + i * np + j];
+            for (int j = 0; j < np; j++) {
+                hm[((size_t)a * npmax + i) * npmax + j] = hmats[hoff + i * np + j];
+                H->proj_norm += std::fabs(hmats[hoff + i * np + j]);
+            }
         hoff += (int64_t)np * np;
     }
     // point-centric CSR of entries (for the fused scatter in the epilogue)
@@ -1107,6 +1117,212 @@ rsg_status rsg_propagate_steps(rsg_ham H, void *psi, int64_t S, int64_t ld, int6
     }
     if (gs_every > 0 || norm_drift_out) return read_status(H, st);
     return RSG_OK;
+}
+
+// ------------------------------------------------------- eigensolver ----
+// Lowest eigenpairs of H by Chebyshev-filtered subspace iteration.  Each
+// filter step is one application of H - c through the stencil epilogue (the
+// shift folded into the diagonal, the previous iterate added as the base);
+// each iteration ends with the FP64 Cholesky-QR, a Rayleigh-Ritz step on the
+// S x S FP64 matrix X^H H X (cyclic complex Jacobi on the host) and FP64
+// residual norms.
+
+}  // extern "C"
+
+namespace {
+
+// Cyclic Jacobi for a Hermitian n x n matrix A (row-major complex double,
+// overwritten): eigenvalues ascending in w, eigenvectors in the columns of
+// V (row-major, V[t][s] = component t of vector s).
+void jacobi_hermitian(int n, std::vector<std::complex<double>> &A, std::vector<double> &w,
+                      std::vector<std::complex<double>> &V) {
+    using cd = std::complex<double>;
+    V.assign((size_t)n * n, cd(0, 0));
+    for (int i = 0; i < n; i++) V[(size_t)i * n + i] = 1.0;
+    double scale = 0.0;
+    for (const cd &x : A) scale += std::norm(x);
+    scale = std::sqrt(scale);
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < n; p++)
+            for (int q = 0; q < n; q++)
+                if (p != q) off += std::norm(A[(size_t)p * n + q]);
+        if (std::sqrt(off) <= 1e-15 * scale || off == 0.0) break;
+        for (int p = 0; p < n - 1; p++)
+            for (int q = p + 1; q < n; q++) {
+                const cd b = A[(size_t)p * n + q];
+                const double ab = std::abs(b);
+                if (ab <= 1e-300) continue;
+                // U = diag(1, e^{-i phi}) R(theta): zeroes A_pq, phi = arg A_pq
+                const cd ph = b / ab;
+                const double th = 0.5 * std::atan2(2.0 * ab, A[(size_t)p * n + p].real() - A[(size_t)q * n + q].real());
+                const double c = std::cos(th), s = std::sin(th);
+                const cd u00 = c, u01 = -s, u10 = s * std::conj(ph), u11 = c * std::conj(ph);
+                for (int k = 0; k < n; k++) {     // A <- A U
+                    const cd ap = A[(size_t)k * n + p], aq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = ap * u00 + aq * u10;
+                    A[(size_t)k * n + q] = ap * u01 + aq * u11;
+                }
+                for (int k = 0; k < n; k++) {     // A <- U^H A
+                    const cd ap = A[(size_t)p * n + k], aq = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = std::conj(u00) * ap + std::conj(u10) * aq;
+                    A[(size_t)q * n + k] = std::conj(u01) * ap + std::conj(u11) * aq;
+                }
+                A[(size_t)p * n + q] = A[(size_t)q * n + p] = 0.0;
+                for (int k = 0; k < n; k++) {     // V <- V U
+                    const cd vp = V[(size_t)k * n + p], vq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = vp * u00 + vq * u10;
+                    V[(size_t)k * n + q] = vp * u01 + vq * u11;
+                }
+            }
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return A[(size_t)x * n + x].real() < A[(size_t)y * n + y].real(); });
+    std::vector<cd> Vs((size_t)n * n);
+    w.resize(n);
+    for (int j = 0; j < n; j++) {
+        w[j] = A[(size_t)order[j] * n + order[j]].real();
+        for (int t = 0; t < n; t++) Vs[(size_t)t * n + j] = V[(size_t)t * n + order[j]];
+    }
+    V.swap(Vs);
+}
+
+}  // namespace
+
+extern "C" {
+
+rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t max_iter, int degree,
+                          double tol, double *evals_out, double *resid_out, int64_t *iters_out, void *stream) {
+    if (!H || !evals_out) return fail(RSG_ERR_ARG, "NULL argument");
+    CKS(check_block(H, psi, S, ld, "psi"));
+    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (S > 256) return fail(RSG_ERR_UNSUPPORTED, "S > 256");
+    if (degree < 1 || degree > 64) return fail(RSG_ERR_ARG, "degree must be in 1..64");
+    if (max_iter < 0 || !(tol > 0)) return fail(RSG_ERR_ARG, "need max_iter >= 0 and tol > 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    rsg_mesh m = H->m;
+    const int64_t P = m->P;
+    const double h = m->h, h3 = h * h * h;
+    const int SV = sv_of(H, ld);
+    const size_t bytes = (size_t)P * ld * cbytes(H->dtype);
+    CK(H->w0.ensure(bytes));
+    CK(H->w1.ensure(bytes));
+    const int nbg = gram_blocks(P, (int)S), nbn = norm_blocks(P);
+    CK(H->red.ensure(std::max((size_t)nbg * S * S * 2, (size_t)nbn * S) * sizeof(double)));
+    CK(H->G.ensure((size_t)S * S * 2 * sizeof(double)));
+    CK(H->W.ensure((size_t)S * S * 2 * sizeof(double)));
+    CK(H->drift.ensure((size_t)2 * S * sizeof(double)));
+    double *lam_dev = H->drift.as<double>(), *res_dev = H->drift.as<double>() + S;
+    // upper bound of the spectrum: Gershgorin for the 8th-order Laplacian
+    // (the row sum of |c_k| is the largest value of its symbol), the largest
+    // potential, the projector bound and the field over the mesh box
+    double csum = 0.0;
+    for (int k = 0; k < 5; k++) csum += (k ? 2.0 : 1.0) * std::fabs(kFD[k]);
+    double field = 0.0;
+    for (int corner = 0; corner < 8; corner++) {
+        double v = 0.0;
+        for (int d = 0; d < 3; d++) {
+            const int ext = d == 0 ? m->nx : d == 1 ? m->ny : m->nz;
+            const int idx = (corner >> d) & 1 ? ext - 1 : 0;
+            v += H->dir[d] * (m->origin[d] + h * (idx + m->lo[d]));
+        }
+        field = std::max(field, std::fabs(H->eps * v));
+    }
+    const double upper = 3.0 * csum / (2.0 * h * h) + H->vmax + H->proj_norm + field;
+
+    std::vector<std::complex<double>> A((size_t)S * S), Q;
+    std::vector<double> lam, res((size_t)S);
+    auto rayleigh_ritz = [&]() -> rsg_status {
+        Epi ep;
+        CKS(apply(H, psi, H->w0.p, SV, H->eps, H->dir, ep, st));
+        if (H->dtype == RSG_C64)
+            CK(launch_cross_gram<float>(psi, H->w0.p, P, (int)ld, (int)S, h3, H->red.as<double>(), nbg,
+                                        H->G.as<double>(), st));
+        else
+            CK(launch_cross_gram<double>(psi, H->w0.p, P, (int)ld, (int)S, h3, H->red.as<double>(), nbg,
+                                         H->G.as<double>(), st));
+        CK(cudaMemcpyAsync(A.data(), H->G.p, (size_t)S * S * 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < S; i++)
+            for (int64_t j = 0; j < S; j++)
+                if (!std::isfinite(A[(size_t)i * S + j].real()) || !std::isfinite(A[(size_t)i * S + j].imag()))
+                    return fail(RSG_ERR_NONFINITE, "Rayleigh-Ritz matrix not finite");
+        for (int64_t i = 0; i < S; i++)      // exact Hermitian part
+            for (int64_t j = i; j < S; j++) {
+                const std::complex<double> x = 0.5 * (A[(size_t)i * S + j] + std::conj(A[(size_t)j * S + i]));
+                A[(size_t)i * S + j] = x;
+                A[(size_t)j * S + i] = std::conj(x);
+            }
+        jacobi_hermitian((int)S, A, lam, Q);
+        CK(cudaMemcpyAsync(H->W.p, Q.data(), (size_t)S * S * 2 * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(lam_dev, lam.data(), (size_t)S * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (H->dtype == RSG_C64) {
+            CK(launch_rotate<float>(psi, P, (int)ld, (int)S, H->W.as<double>(), st));
+            CK(launch_rotate<float>(H->w0.p, P, (int)ld, (int)S, H->W.as<double>(), st));
+            CK(launch_resid<float>(psi, H->w0.p, P, (int)ld, (int)S, lam_dev, h3, H->red.as<double>(), nbn, res_dev,
+                                   st));
+        } else {
+            CK(launch_rotate<double>(psi, P, (int)ld, (int)S, H->W.as<double>(), st));
+            CK(launch_rotate<double>(H->w0.p, P, (int)ld, (int)S, H->W.as<double>(), st));
+            CK(launch_resid<double>(psi, H->w0.p, P, (int)ld, (int)S, lam_dev, h3, H->red.as<double>(), nbn,
+                                    res_dev, st));
+        }
+        CK(cudaMemcpyAsync(res.data(), res_dev, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (double &r : res) r = std::sqrt(std::max(r, 0.0));
+        H->n_launch += 7;
+        return RSG_OK;
+    };
+    auto converged = [&]() {
+        for (double r : res)
+            if (!(r <= tol)) return false;
+        return true;
+    };
+
+    CKS(orthonormalize_dev(H, psi, S, ld, nullptr, st));
+    CKS(read_status(H, st));
+    CKS(rayleigh_ritz());
+    int64_t it = 0;
+    while (it < max_iter && !converged()) {
+        // damp [a, upper] and amplify below a = the largest Ritz value
+        const double a = lam[(size_t)S - 1], lo = lam[0];
+        if (!(a < upper)) return fail(RSG_ERR_NONFINITE, "Ritz values above the spectral bound");
+        const double e = 0.5 * (upper - a), c = 0.5 * (upper + a);
+        double sigma = e / (lo - c);
+        const double sigma1 = sigma, gamma = 2.0 / sigma1;
+        void *X = psi, *Y = H->w0.p, *Z = H->w1.p;
+        {
+            Epi ep;                      // Y = (sigma1 / e) (H - c) X
+            ep.ar = sigma1 / e;
+            ep.shift = c;
+            CKS(apply(H, X, Y, SV, H->eps, H->dir, ep, st));
+        }
+        for (int k = 2; k <= degree; k++) {
+            const double sigma2 = 1.0 / (gamma - sigma);
+            Epi ep;                      // Z = (2 sigma2 / e) (H - c) Y - sigma sigma2 X
+            ep.ar = 2.0 * sigma2 / e;
+            ep.shift = c;
+            ep.base = X;
+            ep.br = -sigma * sigma2;
+            CKS(apply(H, Y, Z, SV, H->eps, H->dir, ep, st));
+            void *t = X;
+            X = Y;
+            Y = Z;
+            Z = t;
+            sigma = sigma2;
+        }
+        if (Y != psi) CK(cudaMemcpyAsync(psi, Y, bytes, cudaMemcpyDeviceToDevice, st));
+        CKS(orthonormalize_dev(H, psi, S, ld, nullptr, st));
+        CKS(read_status(H, st));
+        CKS(rayleigh_ritz());
+        it++;
+    }
+    std::memcpy(evals_out, lam.data(), (size_t)S * sizeof(double));
+    if (resid_out) std::memcpy(resid_out, res.data(), (size_t)S * sizeof(double));
+    if (iters_out) *iters_out = it;
+    return read_status(H, st);
 }
 
 }  // extern "C"

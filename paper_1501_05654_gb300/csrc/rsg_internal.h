@@ -120,6 +120,17 @@ template <typename R>
 cudaError_t launch_proj_scatter(const ApplyArgs<R> &a, const ProjDev &pj, cudaStream_t st);
 
 // ---- linear algebra on state blocks (rsg_linalg.cu) ----
+// G (S x S complex double) = h3 * Psi^H Phi (cross Gram; partial as launch_gram).
+template <typename R>
+cudaError_t launch_cross_gram(const void *psi, const void *phi, int64_t P, int ld, int S, double h3,
+                              double *partial, int nblk, double *G, cudaStream_t st);
+// psi <- psi Q (in place; Q S x S complex double).
+template <typename R>
+cudaError_t launch_rotate(void *psi, int64_t P, int ld, int S, const double *Q, cudaStream_t st);
+// out[s] = h3 sum_p |hx[p,s] - lam[s] x[p,s]|^2 (FP64; partial nblk * S doubles).
+template <typename R>
+cudaError_t launch_resid(const void *x, const void *hx, int64_t P, int ld, int S, const double *lam, double h3,
+                         double *partial, int nblk, double *out, cudaStream_t st);
 // G (S x S complex double) = h3 * Psi^H Psi; partial needs nblk * S * S * 2 doubles.
 template <typename R>
 cudaError_t launch_gram(const void *psi, int64_t P, int ld, int S, double h3,

@@ -40,10 +40,11 @@ int norm_blocks(int64_t P) {
 }
 
 // partial[blk][s][t] (complex double) = sum over the block's points of
-// conj(psi[p,s]) psi[p,t] for one GT x GT tile of (s, t).
+// conj(psi[p,s]) phi[p,t] for one GT x GT tile of (s, t) (phi = psi: the Gram
+// matrix; phi = H psi: the Rayleigh-Ritz matrix of the eigensolver).
 template <typename R>
-__global__ void __launch_bounds__(GT *GT) k_gram(const R *__restrict__ psi, int64_t P, int ld, int S,
-                                                 double *__restrict__ partial, int nblk) {
+__global__ void __launch_bounds__(GT *GT) k_gram(const R *__restrict__ psi, const R *__restrict__ phi, int64_t P,
+                                                 int ld, int S, double *__restrict__ partial, int nblk) {
     __shared__ double sa[GT][GT][2], sb[GT][GT][2];
     const int s0 = blockIdx.x * GT, t0 = blockIdx.y * GT;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(GT *GT) k_gram(const R *__restrict__ psi, int6
         double ar = 0, ai = 0, br = 0, bi = 0;
         if (p < p1) {
             if (s0 + tx < S) ld_c(psi + (p * ld + s0 + tx) * 2, ar, ai);
-            if (t0 + tx < S) ld_c(psi + (p * ld + t0 + tx) * 2, br, bi);
+            if (t0 + tx < S) ld_c(phi + (p * ld + t0 + tx) * 2, br, bi);
         }
         sa[ty][tx][0] = ar;
         sa[ty][tx][1] = ai;
@@ -94,9 +95,102 @@ template <typename R>
 cudaError_t launch_gram(const void *psi, int64_t P, int ld, int S, double h3, double *partial,
                         int nblk, double *G, cudaStream_t st) {
     dim3 grid((S + GT - 1) / GT, (S + GT - 1) / GT, nblk);
-    k_gram<R><<<grid, dim3(GT, GT), 0, st>>>((const R *)psi, P, ld, S, partial, nblk);
+    k_gram<R><<<grid, dim3(GT, GT), 0, st>>>((const R *)psi, (const R *)psi, P, ld, S, partial, nblk);
     const int64_t n = (int64_t)S * S * 2;
     k_sum_blocks<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, nblk, n, h3, G);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_cross_gram(const void *psi, const void *phi, int64_t P, int ld, int S, double h3,
+                              double *partial, int nblk, double *G, cudaStream_t st) {
+    dim3 grid((S + GT - 1) / GT, (S + GT - 1) / GT, nblk);
+    k_gram<R><<<grid, dim3(GT, GT), 0, st>>>((const R *)psi, (const R *)phi, P, ld, S, partial, nblk);
+    const int64_t n = (int64_t)S * S * 2;
+    k_sum_blocks<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, nblk, n, h3, G);
+    return cudaGetLastError();
+}
+
+// psi[p, s] <- sum_t psi[p, t] Q[t][s] (Q: S x S complex double, the Ritz
+// rotation), in place: each block stages its full rows in shared memory.
+template <typename R>
+__global__ void __launch_bounds__(256) k_rotate(R *psi, int64_t P, int ld, int S, const double *__restrict__ Q,
+                                                int pt) {
+    extern __shared__ double rowbuf[];   // pt * S complex double
+    const int64_t p0 = (int64_t)blockIdx.x * pt;
+    const int n = pt * S;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int q = e / S, t = e % S;
+        const int64_t p = p0 + q;
+        double re = 0.0, im = 0.0;
+        if (p < P) ld_c(psi + (p * ld + t) * 2, re, im);
+        rowbuf[e * 2] = re;
+        rowbuf[e * 2 + 1] = im;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int q = e / S, s = e % S;
+        const int64_t p = p0 + q;
+        if (p >= P) continue;
+        double re = 0.0, im = 0.0;
+        const double *row = rowbuf + (int64_t)q * S * 2;
+        for (int t = 0; t < S; t++) {
+            const double qr = Q[((int64_t)t * S + s) * 2], qi = Q[((int64_t)t * S + s) * 2 + 1];
+            re += row[2 * t] * qr - row[2 * t + 1] * qi;
+            im += row[2 * t] * qi + row[2 * t + 1] * qr;
+        }
+        psi[(p * ld + s) * 2] = (R)re;
+        psi[(p * ld + s) * 2 + 1] = (R)im;
+    }
+}
+
+template <typename R>
+cudaError_t launch_rotate(void *psi, int64_t P, int ld, int S, const double *Q, cudaStream_t st) {
+    int pt = 4096 / S;
+    if (pt < 1) pt = 1;
+    if (pt > 64) pt = 64;
+    const size_t smem = (size_t)pt * S * 2 * sizeof(double);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_rotate<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t nb = (P + pt - 1) / pt;
+    k_rotate<R><<<(unsigned)nb, 256, smem, st>>>((R *)psi, P, ld, S, Q, pt);
+    return cudaGetLastError();
+}
+
+// partial[blk][s] = sum over the block's points of |hx[p,s] - lam[s] x[p,s]|^2
+template <typename R>
+__global__ void __launch_bounds__(256) k_resid(const R *__restrict__ x, const R *__restrict__ hx, int64_t P,
+                                               int ld, int S, const double *__restrict__ lam,
+                                               double *__restrict__ partial, int nblk) {
+    __shared__ double red[256];
+    const int s = blockIdx.y;
+    const int64_t per = (P + nblk - 1) / nblk;
+    const int64_t p0 = blockIdx.x * per, p1 = p0 + per < P ? p0 + per : P;
+    const double l = lam[s];
+    double acc = 0.0;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        double xr, xi, yr, yi;
+        ld_c(x + (p * ld + s) * 2, xr, xi);
+        ld_c(hx + (p * ld + s) * 2, yr, yi);
+        const double rr = yr - l * xr, ri = yi - l * xi;
+        acc += rr * rr + ri * ri;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * S + s] = red[0];
+}
+
+template <typename R>
+cudaError_t launch_resid(const void *x, const void *hx, int64_t P, int ld, int S, const double *lam, double h3,
+                         double *partial, int nblk, double *out, cudaStream_t st) {
+    k_resid<R><<<dim3(nblk, S), 256, 0, st>>>((const R *)x, (const R *)hx, P, ld, S, lam, partial, nblk);
+    k_sum_blocks<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(partial, nblk, S, h3, out);
     return cudaGetLastError();
 }
 
@@ -672,6 +766,11 @@ cudaError_t launch_grad_accum(const double *M, double tau, double *grad_k, cudaS
 #define RSG_INST(R)                                                                               \
     template cudaError_t launch_gram<R>(const void *, int64_t, int, int, double, double *, int,      \
                                         double *, cudaStream_t);                                     \
+    template cudaError_t launch_cross_gram<R>(const void *, const void *, int64_t, int, int, double, \
+                                              double *, int, double *, cudaStream_t);                \
+    template cudaError_t launch_rotate<R>(void *, int64_t, int, int, const double *, cudaStream_t);  \
+    template cudaError_t launch_resid<R>(const void *, const void *, int64_t, int, int, const double *, \
+                                         double, double *, int, double *, cudaStream_t);             \
     template cudaError_t launch_tri_apply<R>(void *, int64_t, int, int, const double *,              \
                                              cudaStream_t);                                          \
     template cudaError_t launch_norms<R>(const void *, int64_t, int, int, double, double *, int,     \
