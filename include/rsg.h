@@ -156,8 +156,12 @@ rsg_status rsg_orthonormalize(rsg_ham H, void *psi, int64_t S, int64_t ld,
  * of max_iter iterations applies a degree-`degree` Chebyshev polynomial of H
  * (degree applications of H - c, damping the spectrum above the largest
  * current Ritz value), re-orthonormalises (FP64 Cholesky-QR) and does a
- * Rayleigh-Ritz step on the FP64 S x S matrix X^H H X.  It stops when every
- * residual |H x_s - lambda_s x_s| (h^3-weighted 2-norm, FP64) is <= tol.
+ * Rayleigh-Ritz step on the FP64 S x S matrix X^H H X.  It stops when the
+ * residuals |H x_s - lambda_s x_s| (h^3-weighted 2-norm, FP64) of the nwant
+ * lowest states are <= tol.  The S - nwant states above them are a buffer:
+ * the filter damps the spectrum above the largest Ritz value, so wanted
+ * states converge at a rate set by their distance from the buffer's top
+ * (a few buffer states past the next gap in the spectrum are enough).
  * psi (device, P x ld, S <= 256): in, the starting block (any full-rank
  * block, e.g. seeded random values); out, the orthonormal Ritz vectors in
  * ascending order.  evals_out (host, S) receives the Ritz values, resid_out
@@ -165,10 +169,10 @@ rsg_status rsg_orthonormalize(rsg_ham H, void *psi, int64_t S, int64_t ld,
  * iterations taken.  The current field (rsg_field_set) is part of H.
  * Uses the Hamiltonian's work blocks; synchronises once per iteration.
  * Errors: as rsg_hamiltonian_apply; RSG_ERR_ARG for degree outside 1..64,
- * max_iter < 0 or tol <= 0; RSG_ERR_UNSUPPORTED for S > 256;
+ * nwant outside 1..S, max_iter < 0 or tol <= 0; RSG_ERR_UNSUPPORTED for S > 256;
  * RSG_ERR_NONFINITE if the block loses rank or a matrix is not finite. */
-rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t max_iter, int degree,
-                          double tol, double *evals_out, double *resid_out, int64_t *iters_out,
+rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t nwant, int64_t max_iter,
+                          int degree, double tol, double *evals_out, double *resid_out, int64_t *iters_out,
                           void *stream);
 
 /* FP64 <psi_s|psi_s> for S states into norms2_out (host, S doubles);

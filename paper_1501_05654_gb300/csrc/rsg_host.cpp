@@ -1193,10 +1193,12 @@ void jacobi_hermitian(int n, std::vector<std::complex<double>> &A, std::vector<d
 
 extern "C" {
 
-rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t max_iter, int degree,
-                          double tol, double *evals_out, double *resid_out, int64_t *iters_out, void *stream) {
+rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t nwant, int64_t max_iter,
+                          int degree, double tol, double *evals_out, double *resid_out, int64_t *iters_out,
+                          void *stream) {
     if (!H || !evals_out) return fail(RSG_ERR_ARG, "NULL argument");
     CKS(check_block(H, psi, S, ld, "psi"));
+    if (nwant < 1 || nwant > S) return fail(RSG_ERR_ARG, "need 1 <= nwant <= S");
     if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
     if (S > 256) return fail(RSG_ERR_UNSUPPORTED, "S > 256");
     if (degree < 1 || degree > 64) return fail(RSG_ERR_ARG, "degree must be in 1..64");
@@ -1276,8 +1278,8 @@ rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t m
         return RSG_OK;
     };
     auto converged = [&]() {
-        for (double r : res)
-            if (!(r <= tol)) return false;
+        for (int64_t s = 0; s < nwant; s++)
+            if (!(res[(size_t)s] <= tol)) return false;
         return true;
     };
 
@@ -1286,7 +1288,8 @@ rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t m
     CKS(rayleigh_ritz());
     int64_t it = 0;
     while (it < max_iter && !converged()) {
-        // damp [a, upper] and amplify below a = the largest Ritz value
+        // damp [a, upper] and amplify below a = the largest Ritz value (the
+        // top of the buffer states above the nwant wanted ones)
         const double a = lam[(size_t)S - 1], lo = lam[0];
         if (!(a < upper)) return fail(RSG_ERR_NONFINITE, "Ritz values above the spectral bound");
         const double e = 0.5 * (upper - a), c = 0.5 * (upper + a);

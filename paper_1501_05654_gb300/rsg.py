@@ -43,7 +43,7 @@ SIGNATURES = {
     "rsg_taylor_apply": [_vp, _vp, _vp, _i64, _i64, _dbl, _vp],
     "rsg_propagate_steps": [_vp, _vp, _i64, _i64, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp],
     "rsg_orthonormalize": [_vp, _vp, _i64, _i64, _vp, _vp],
-    "rsg_eigensolve": [_vp, _vp, _i64, _i64, _i64, _int, _dbl, _vp, _vp, _vp, _vp],
+    "rsg_eigensolve": [_vp, _vp, _i64, _i64, _i64, _i64, _int, _dbl, _vp, _vp, _vp, _vp],
     "rsg_state_norms": [_vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_state_norms_noalloc": [_vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_control_gradient": [_vp, _vp, _vp, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp, _vp],
@@ -283,14 +283,17 @@ class Hamiltonian:
                                        None if drift is None else _ptr(drift), _stream(stream)))
         return drift
 
-    def eigensolve(self, psi, max_iter: int = 200, degree: int = 10, tol: float = 1e-8, S=None, stream=None):
-        """Lowest S eigenpairs (rsg_eigensolve): psi (in, starting block; out,
-        Ritz vectors) and (eigenvalues, residual norms, iterations)."""
+    def eigensolve(self, psi, nwant=None, max_iter: int = 200, degree: int = 10, tol: float = 1e-8, S=None,
+                   stream=None):
+        """Lowest eigenpairs (rsg_eigensolve): psi (in, starting block of S
+        states; out, Ritz vectors); the nwant lowest (default S) must reach
+        tol.  Returns (eigenvalues, residual norms, iterations) for all S."""
         self._check(psi)
         S = psi.shape[1] if S is None else S
+        nwant = S if nwant is None else nwant
         ev, res = np.zeros(S), np.zeros(S)
         it = C.c_int64()
-        _ck(load().rsg_eigensolve(self._h, C.c_void_p(psi.data_ptr()), S, psi.shape[1], int(max_iter),
+        _ck(load().rsg_eigensolve(self._h, C.c_void_p(psi.data_ptr()), S, psi.shape[1], int(nwant), int(max_iter),
                                   int(degree), float(tol), _ptr(ev), _ptr(res), C.byref(it), _stream(stream)))
         return ev, res, int(it.value)
 

@@ -57,14 +57,15 @@ def test_harmonic_oscillator_exact_discrete_levels(dtype, tol, etol):
     lv = np.sort([a + b + c for a in e1 for b in e1 for c in e1])
     want = lv[:10]
     assert lv[10] - lv[9] > 0.3          # a gap after the ten lowest: the block is well defined
-    x = _start(p, 10)
-    ev, res, it = p.H.eigensolve(x, max_iter=300, degree=12, tol=tol)
-    assert np.all(res <= tol), (res, it)
-    assert np.abs(ev - want).max() < etol * np.abs(want).max(), (ev, want)
+    # ten wanted states and four buffer states from the next multiplet
+    x = _start(p, 14)
+    ev, res, it = p.H.eigensolve(x, nwant=10, max_iter=300, degree=12, tol=tol)
+    assert np.all(res[:10] <= tol), (res, it)
+    assert np.abs(ev[:10] - want).max() < etol * np.abs(want).max(), (ev, want)
     # the vectors are orthonormal in the h^3 inner product
-    got = p.states_from_gpu(x, 10)
+    got = p.states_from_gpu(x, 14)
     G = h ** 3 * got.conj().T @ got
-    assert np.abs(G - np.eye(10)).max() < (1e-12 if dtype == torch.complex128 else 1e-5)
+    assert np.abs(G - np.eye(14)).max() < (1e-12 if dtype == torch.complex128 else 1e-5)
 
 
 def test_sphere_with_projectors_and_field_against_arpack():
@@ -77,10 +78,9 @@ def test_sphere_with_projectors_and_field_against_arpack():
     want = np.sort(sla.eigsh(op, k=6, which="SA", tol=1e-11, ncv=40, v0=np.ones(P),
                              return_eigenvectors=False))[:4]
     x = _start(p, 8, seed=2)
-    # eight states: the lowest four are compared, the rest are a buffer whose
-    # convergence may lag (the solver runs until all meet tol or max_iter)
-    ev, res, it = p.H.eigensolve(x, max_iter=300, degree=12, tol=1e-10)
-    assert np.all(res[:4] <= 1e-9), (res, it)
+    # four wanted states and four buffer states
+    ev, res, it = p.H.eigensolve(x, nwant=4, max_iter=300, degree=12, tol=1e-10)
+    assert np.all(res[:4] <= 1e-10), (res, it)
     assert np.abs(ev[:4] - want).max() < 1e-9 * np.abs(want).max(), (ev[:4], want)
     # residuals of the returned pairs, recomputed by the FP64 oracle
     got = p.states_from_gpu(x, 8)
@@ -97,8 +97,8 @@ def test_lithium_table():
     p = Pair("cube", n, h=h, dtype=torch.complex128)
     p.set_potential(potential_soft_coulomb_li(p.om.xyz))
     x = _start(p, 8, seed=5)
-    ev, res, it = p.H.eigensolve(x, max_iter=300, degree=16, tol=1e-8)
-    assert np.all(res[:4] <= 1e-7), (res, it)
+    ev, res, it = p.H.eigensolve(x, nwant=4, max_iter=300, degree=16, tol=1e-8)
+    assert np.all(res[:4] <= 1e-8), (res, it)
     want = np.array(gold["energies_hartree"])
     assert np.all(np.abs(ev[:4] - want) < 1.5 * gold["printed_precision"]), (ev[:4], want)
     # the same discrete operator through the oracle (ARPACK)
@@ -114,4 +114,6 @@ def test_argument_errors():
         p.H.eigensolve(x, degree=0)
     with pytest.raises(rsg.RSGError):
         p.H.eigensolve(x, tol=0.0)
+    with pytest.raises(rsg.RSGError):
+        p.H.eigensolve(x, nwant=3)
     _ = oracle
