@@ -529,8 +529,11 @@ void stage_shape(const TileCfg &c, int SV, int *cv, int *nxr, int *ty) {
 size_t stage_smem_bytes(const TileCfg &c, int SV, size_t vec_bytes) {
     int cv, nxr, ty;
     stage_shape(c, SV, &cv, &nxr, &ty);
-    // NS slots of the (ty + 8) x (nxr + 8) halo tile, plus per-thread base and V
-    return (size_t)(c.stages == 3 ? 3 : 4) *
+    // NS slots of the (ty + 8) x (nxr + 8) halo tile, plus per-thread base and V;
+    // NS as launch_staged_cv picks it: 3 only with 256 threads and stages = 3
+    // (the 512-thread instantiations always have 4)
+    const int ns = (c.threads != 512 && c.stages == 3) ? 3 : 4;
+    return (size_t)ns *
            ((size_t)(ty + 8) * (nxr + 8) * cv * vec_bytes + (size_t)cv * nxr * ty * (vec_bytes + vec_bytes / 2));
 }
 
