@@ -308,6 +308,25 @@ def extras(mesh, wells, proj, g):
             "forward_s": tf, "gradient_s": tg, "ratio": tg / tf,
             "workload": "64^3 h=0.3 double well, 2000 intervals dt=0.05, ETRS nsub=4, K=50"}
         del H, blk
+    # optimal control loop on the control workload's operator (64^3 double
+    # well, 200 intervals of 0.05 au, 4 ETRS substeps): from the ground to the
+    # first excited state of H_0 (both from the eigensolver), 8 L-BFGS steps
+    Hc = rsg.Hamiltonian(cm, torch.complex128)
+    Hc.set_potential(potential_double_well(cm.xyz, 0.02, 2.0, 0.5))
+    xb = torch.from_numpy(white_noise_states(rng(7), cm.P, 4)).cuda()
+    Hc.eigensolve(xb, nwant=2, max_iter=300, degree=16, tol=1e-9)
+    phi0, phi1 = xb[:, 0].contiguous(), xb[:, 1].contiguous()
+    eps0 = control_field(rng(4), 200, 0.05)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, Jopt, hist, nit, nev = Hc.control_optimize(phi0, phi1, eps0, 0.05, scheme=rsg.ETRS, nsub=4,
+                                                  checkpoint_every=50, max_iter=8, gtol=1e-9)
+    to = time.perf_counter() - t0
+    out["control_optimize_c128"] = {"s": to, "steps": nit, "gradient_evaluations": nev, "J_start": float(hist[0]),
+                                    "J_end": Jopt, "s_per_evaluation": to / nev,
+                                    "workload": "64^3 h=0.3 double well, 200 intervals dt=0.05, ETRS nsub=4, K=50, "
+                                                "ground -> first excited state, L-BFGS 8 steps"}
+    del Hc, xb
     # ground state (Chebyshev-filtered subspace iteration): the four lowest
     # levels of the 1-D lithium model as one particle in 3-D (61^3, h = 0.4,
     # complex128), four buffer states, residuals <= 1e-8

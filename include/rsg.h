@@ -213,6 +213,26 @@ rsg_status rsg_control_gradient(rsg_ham H, const void *psi0, const void *target,
                                 int checkpoint_every, double *J_out,
                                 double *grad_out, void *stream);
 
+/* Optimal control loop (Sec. "Quantum optimal control": the gradient of
+ * Eq. (qoctgradient) drives a gradient-based optimiser; the paper uses
+ * conjugate-gradient and BFGS schemes): maximises J = |<target|psi(T)>|^2
+ * over the piecewise-constant control eps (host, nsteps doubles: in, the
+ * starting field; out, the best field found) by limited-memory BFGS
+ * (memory 8) on -J with an Armijo backtracking line search.  Every
+ * evaluation is one rsg_control_gradient call with the same psi0, target,
+ * nsteps, dt, scheme, nsub, dir and checkpoint_every.  Stops after max_iter
+ * accepted steps, when max_k |dJ/deps_k| <= gtol, or when no step along the
+ * search direction increases J.  *J_out = J at the returned field; J_hist
+ * (host, max_iter + 1 doubles, may be NULL) receives J at the start and
+ * after each accepted step (non-decreasing); iters_out / evals_out (may be
+ * NULL) the accepted steps and the gradient evaluations.  Synchronises.
+ * Errors: as rsg_control_gradient; RSG_ERR_ARG for max_iter < 0 or gtol < 0;
+ * RSG_ERR_NONFINITE if J is not finite. */
+rsg_status rsg_control_optimize(rsg_ham H, const void *psi0, const void *target, int64_t nsteps, double dt,
+                                rsg_scheme scheme, int nsub, double *eps, const double dir[3],
+                                int checkpoint_every, int64_t max_iter, double gtol, double *J_out,
+                                double *J_hist, int64_t *iters_out, int64_t *evals_out, void *stream);
+
 /* -------------------------------------------------------------- batches ---
  * Many independent systems (Sec. "Performance": groups of states as the
  * unit of work) propagated together: one launch per Taylor stage covers the

@@ -1508,6 +1508,120 @@ extern "C" rsg_status rsg_control_gradient(rsg_ham H, const void *psi0, const vo
                                       checkpoint_every, J_out, grad_out, st);
 }
 
+// Optimal control loop (Sec. "Quantum optimal control": the gradient of
+// Eq. (qoctgradient) feeds a gradient-based optimiser; the paper uses
+// conjugate-gradient and BFGS schemes).  Limited-memory BFGS (two-loop
+// recursion, memory 8) on f = -J with an Armijo backtracking line search;
+// every evaluation of J and its gradient is one rsg_control_gradient call.
+extern "C" rsg_status rsg_control_optimize(rsg_ham H, const void *psi0, const void *target, int64_t nsteps,
+                                           double dt, rsg_scheme scheme, int nsub, double *eps,
+                                           const double dir[3], int checkpoint_every, int64_t max_iter,
+                                           double gtol, double *J_out, double *J_hist, int64_t *iters_out,
+                                           int64_t *evals_out, void *stream) {
+    if (!H || !eps || !J_out) return fail(RSG_ERR_ARG, "NULL argument");
+    if (max_iter < 0 || !(gtol >= 0)) return fail(RSG_ERR_ARG, "need max_iter >= 0 and gtol >= 0");
+    if (nsteps < 1) return fail(RSG_ERR_ARG, "nsteps < 1");
+    const size_t n = (size_t)nsteps;
+    constexpr int kMem = 8;
+    auto dot = [n](const std::vector<double> &a, const std::vector<double> &b) {
+        double s = 0.0;
+        for (size_t i = 0; i < n; i++) s += a[i] * b[i];
+        return s;
+    };
+    auto inf_norm = [n](const std::vector<double> &a) {
+        double m = 0.0;
+        for (size_t i = 0; i < n; i++) m = std::max(m, std::fabs(a[i]));
+        return m;
+    };
+    std::vector<double> x(eps, eps + n), g(n), xt(n), gt(n), d(n);
+    int64_t evals = 0;
+    double J = 0.0, Jt = 0.0;
+    // f = -J, gradient -dJ/deps
+    auto evaluate = [&](const std::vector<double> &at, double &Jv, std::vector<double> &grad) -> rsg_status {
+        CKS(rsg_control_gradient(H, psi0, target, nsteps, dt, scheme, nsub, at.data(), dir, checkpoint_every, &Jv,
+                                 grad.data(), stream));
+        for (size_t i = 0; i < n; i++) grad[i] = -grad[i];
+        evals++;
+        if (!std::isfinite(Jv)) return fail(RSG_ERR_NONFINITE, "objective not finite");
+        return RSG_OK;
+    };
+    CKS(evaluate(x, J, g));
+    if (J_hist) J_hist[0] = J;
+    std::vector<std::vector<double>> S, Y;
+    std::vector<double> rho;
+    int64_t it = 0;
+    while (it < max_iter && inf_norm(g) > gtol) {
+        // two-loop recursion: d = -H_k g
+        d = g;
+        std::vector<double> alpha(S.size());
+        for (int k = (int)S.size() - 1; k >= 0; k--) {
+            alpha[(size_t)k] = rho[(size_t)k] * dot(S[(size_t)k], d);
+            for (size_t i = 0; i < n; i++) d[i] -= alpha[(size_t)k] * Y[(size_t)k][i];
+        }
+        double gamma = 1.0;
+        if (!S.empty()) {
+            gamma = dot(S.back(), Y.back()) / dot(Y.back(), Y.back());
+        } else {
+            // first step: a move of at most 1e-2 in the largest component
+            gamma = 1e-2 / std::max(inf_norm(g), 1e-300);
+        }
+        for (size_t i = 0; i < n; i++) d[i] *= gamma;
+        for (size_t k = 0; k < S.size(); k++) {
+            const double beta = rho[k] * dot(Y[k], d);
+            for (size_t i = 0; i < n; i++) d[i] += S[k][i] * (alpha[k] - beta);
+        }
+        for (size_t i = 0; i < n; i++) d[i] = -d[i];
+        double slope = dot(g, d);
+        if (!(slope < 0)) {       // not a descent direction: restart from steepest descent
+            S.clear();
+            Y.clear();
+            rho.clear();
+            const double sc = 1e-2 / std::max(inf_norm(g), 1e-300);
+            for (size_t i = 0; i < n; i++) d[i] = -sc * g[i];
+            slope = dot(g, d);
+        }
+        // Armijo backtracking on f = -J
+        double step = 1.0;
+        bool accepted = false;
+        for (int ls = 0; ls < 40; ls++) {
+            for (size_t i = 0; i < n; i++) xt[i] = x[i] + step * d[i];
+            CKS(evaluate(xt, Jt, gt));
+            if (-Jt <= -J + 1e-4 * step * slope) {
+                accepted = true;
+                break;
+            }
+            step *= 0.5;
+        }
+        if (!accepted) break;     // no decrease along d: stationary to working precision
+        std::vector<double> sv(n), yv(n);
+        for (size_t i = 0; i < n; i++) {
+            sv[i] = xt[i] - x[i];
+            yv[i] = gt[i] - g[i];
+        }
+        const double sy = dot(sv, yv);
+        if (sy > 1e-12 * std::sqrt(dot(sv, sv) * dot(yv, yv))) {
+            if ((int)S.size() == kMem) {
+                S.erase(S.begin());
+                Y.erase(Y.begin());
+                rho.erase(rho.begin());
+            }
+            S.push_back(sv);
+            Y.push_back(yv);
+            rho.push_back(1.0 / sy);
+        }
+        x.swap(xt);
+        g.swap(gt);
+        J = Jt;
+        it++;
+        if (J_hist) J_hist[it] = J;
+    }
+    std::memcpy(eps, x.data(), n * sizeof(double));
+    *J_out = J;
+    if (iters_out) *iters_out = it;
+    if (evals_out) *evals_out = evals;
+    return RSG_OK;
+}
+
 // ============================================================== batch ====
 namespace {
 

@@ -47,6 +47,8 @@ SIGNATURES = {
     "rsg_state_norms": [_vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_state_norms_noalloc": [_vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_control_gradient": [_vp, _vp, _vp, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp, _vp],
+    "rsg_control_optimize": [_vp, _vp, _vp, _i64, _dbl, _int, _int, _vp, _vp, _int, _i64, _dbl, _vp, _vp, _vp,
+                             _vp, _vp],
     "rsg_batch_create": [_vp, _vp, _int, _vp],
     "rsg_batch_propagate": [_vp, _vp, _i64, _dbl, _int, _int, _vp],
     "rsg_batch_destroy": [_vp],
@@ -330,6 +332,26 @@ class Hamiltonian:
                                         int(checkpoint_every), C.byref(J), _ptr(g),
                                         _stream(stream)))
         return float(J.value), g
+
+    def control_optimize(self, psi0, target, eps, dt: float, scheme: int = ETRS, nsub: int = 1,
+                         dir=(1.0, 0.0, 0.0), checkpoint_every: int = 50, max_iter: int = 50,
+                         gtol: float = 1e-8, stream=None):
+        """Maximise J over the control (rsg_control_optimize).  Returns
+        (eps (numpy, the best field), J, J history, accepted steps, evaluations)."""
+        for t in (psi0, target):
+            if not (t.is_cuda and t.dtype == self.dtype and t.numel() == self.mesh.P
+                    and t.is_contiguous()):
+                raise ValueError("psi0/target: contiguous cuda vectors of P values")
+        e = _np(eps, np.float64).copy()
+        d = _np(dir, np.float64)
+        hist = np.zeros(int(max_iter) + 1)
+        J = C.c_double()
+        it, ev = C.c_int64(), C.c_int64()
+        _ck(load().rsg_control_optimize(self._h, C.c_void_p(psi0.data_ptr()), C.c_void_p(target.data_ptr()),
+                                        e.shape[0], float(dt), int(scheme), int(nsub), _ptr(e), _ptr(d),
+                                        int(checkpoint_every), int(max_iter), float(gtol), C.byref(J),
+                                        _ptr(hist), C.byref(it), C.byref(ev), _stream(stream)))
+        return e, float(J.value), hist[:it.value + 1], int(it.value), int(ev.value)
 
 
 class ControlObjective(torch.autograd.Function):
