@@ -1583,7 +1583,8 @@ extern "C" rsg_status rsg_control_optimize(rsg_ham H, const void *psi0, const vo
         // Armijo backtracking on f = -J
         double step = 1.0;
         bool accepted = false;
-        for (int ls = 0; ls < 40; ls++) {
+        int ls = 0;
+        for (; ls < 40; ls++) {
             for (size_t i = 0; i < n; i++) xt[i] = x[i] + step * d[i];
             CKS(evaluate(xt, Jt, gt));
             if (-Jt <= -J + 1e-4 * step * slope) {
@@ -1593,6 +1594,22 @@ extern "C" rsg_status rsg_control_optimize(rsg_ham H, const void *psi0, const vo
             step *= 0.5;
         }
         if (!accepted) break;     // no decrease along d: stationary to working precision
+        // a scaled steepest-descent direction (no usable curvature pair yet,
+        // e.g. while -J is concave along the path) is only a guess at the step
+        // length: expand while J keeps increasing
+        if (S.empty() && ls == 0) {
+            std::vector<double> xe(n), ge(n);
+            double Je = 0.0;
+            for (int k = 0; k < 20; k++) {
+                step *= 2.0;
+                for (size_t i = 0; i < n; i++) xe[i] = x[i] + step * d[i];
+                CKS(evaluate(xe, Je, ge));
+                if (!(Je > Jt)) break;
+                xt.swap(xe);
+                gt.swap(ge);
+                Jt = Je;
+            }
+        }
         std::vector<double> sv(n), yv(n);
         for (size_t i = 0; i < n; i++) {
             sv[i] = xt[i] - x[i];
