@@ -8,11 +8,11 @@
  * (arXiv:1501.05654):
  *   - Sec. 1: fields on uniform grids, integrals as grid sums, high-order
  *     finite-difference Laplacian; finite boxes of arbitrary shape.
- *   - Sec. "Performance": the building blocks include "the application of a
+ *   - Sec. "Parallelization, optimizations and graphics processing units": the building blocks include "the application of a
  *     Hamiltonian"; the basic object is a group of several states; a field is
  *     a linear array plus tables describing the grid; the point order in
  *     memory is the library's business.
- *   - Sec. "Magnetic response": pseudopotentials act as a non-local operator
+ *   - Sec. "Magnetic response and gauge invariance in real-space grids": pseudopotentials act as a non-local operator
  *     (here separable projectors |p_ai> h_ij <p_aj|).
  *   - Sec. "Quantum optimal control", Eq. (qoctgradient): gradient of a
  *     final-time objective with respect to the control, through a costate
@@ -66,7 +66,7 @@ typedef enum { RSG_SHAPE_CUBE = 0, RSG_SHAPE_SPHERE = 1, RSG_SHAPE_BOX = 2 } rsg
 typedef enum { RSG_EXPMID = 0, RSG_ETRS = 1 } rsg_scheme;
 
 /* ---------------------------------------------------------------- mesh ---
- * Uniform mesh (Sec. 1; Sec. "Performance": field = linear array + grid
+ * Uniform mesh (Sec. 1; Sec. "Parallelization, optimizations and graphics processing units": field = linear array + grid
  * tables).  CUBE: n[0]^3 points, lattice i = 0..n-1, origin -(n-1)h/2 per
  * axis (centred box).  BOX: n[0] x n[1] x n[2], same centring.  SPHERE:
  * lattice points with i^2+j^2+k^2 <= (radius/spacing)^2 (inclusive,
@@ -97,7 +97,7 @@ rsg_status rsg_ham_destroy(rsg_ham H);
  * host array; 1: device array.  Copied; the caller keeps ownership. */
 rsg_status rsg_potential_set(rsg_ham H, const double *v, int v_on_device);
 
-/* Separable projectors (Sec. "Magnetic response": non-local pseudopotential).
+/* Separable projectors (Sec. "Magnetic response and gauge invariance in real-space grids": non-local pseudopotential).
  * Atom a at centres[3a..3a+2] (bohr) carries (lmax[a]+1)^2 projectors,
  * lmax in {0,1,2}: p_ai(r) = Y_i(r-R_a) exp(-|r-R_a|^2/(2 beta_a^2)) on the
  * mesh points with |r-R_a| <= rcut[a], Y = {1; x,y,z; xy,yz,zx,x^2-y^2,
@@ -112,7 +112,7 @@ rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres,
  * rsg_taylor_apply (default 0).  dir may be NULL when eps = 0. */
 rsg_status rsg_field_set(rsg_ham H, double eps, const double dir[3]);
 
-/* hpsi = H psi for S states (Sec. "Performance": application of a
+/* hpsi = H psi for S states (Sec. "Parallelization, optimizations and graphics processing units": application of a
  * Hamiltonian to a group of states).  psi and hpsi: device (P, ld) blocks of
  * the Hamiltonian's dtype; they must not overlap.  Asynchronous on stream.
  * Errors: RSG_ERR_ARG (NULL, S < 1, ld < S, odd ld for complex64, misaligned
@@ -175,6 +175,26 @@ rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t n
                           int degree, double tol, double *evals_out, double *resid_out, int64_t *iters_out,
                           void *stream);
 
+/* Shifted linear solves (H - z) x = b for S right-hand sides at one complex
+ * shift z = zr + i zi: the linear problem of the Sternheimer equation
+ * (Sec. "The Sternheimer formulation of linear-response": a shifted
+ * Kohn-Sham Hamiltonian is inverted at every step; a complex shift needs a
+ * non-Hermitian solver).  Conjugate-orthogonal conjugate gradients for the
+ * complex symmetric H - z (H is real symmetric: real stencil, potential,
+ * field and projector matrices), each right-hand side its own system; A x
+ * is one Hamiltonian application with -z x added in the epilogue; inner
+ * products are FP64.  b (device, P x ld, read only); x (device, same
+ * shape): in, the initial guess (zeros for none); out, the solution.  Stops
+ * when every |b_s - (H - z) x_s| <= tol |b_s| or after max_iter iterations;
+ * resid_out (host, S, may be NULL) receives the true relative residuals,
+ * iters_out (may be NULL) the iterations.  Uses three work blocks of the
+ * Hamiltonian; synchronises twice per iteration.
+ * Errors: as rsg_hamiltonian_apply; RSG_ERR_ARG for overlapping b and x,
+ * max_iter < 0, tol <= 0 or a non-finite shift; RSG_ERR_NONFINITE on a
+ * breakdown (p^T (H - z) p = 0). */
+rsg_status rsg_shifted_solve(rsg_ham H, const void *b, void *x, int64_t S, int64_t ld, double zr, double zi,
+                             int64_t max_iter, double tol, double *resid_out, int64_t *iters_out, void *stream);
+
 /* FP64 <psi_s|psi_s> for S states into norms2_out (host, S doubles);
  * synchronises. */
 rsg_status rsg_state_norms(rsg_ham H, const void *psi, int64_t S, int64_t ld,
@@ -234,7 +254,7 @@ rsg_status rsg_control_optimize(rsg_ham H, const void *psi0, const void *target,
                                 double *J_hist, int64_t *iters_out, int64_t *evals_out, void *stream);
 
 /* -------------------------------------------------------------- batches ---
- * Many independent systems (Sec. "Performance": groups of states as the
+ * Many independent systems (Sec. "Parallelization, optimizations and graphics processing units": groups of states as the
  * unit of work) propagated together: one launch per Taylor stage covers the
  * tiles of every system.  hams: nsys Hamiltonians (all complex64), S[i]
  * states per system.  The handles must outlive the batch. */

@@ -13,12 +13,12 @@
  *   - Sec. 1 (introduction): fields sampled on a uniform real-space grid,
  *     integrals become grid sums, derivatives become high-order finite
  *     differences; the error is controlled by the spacing and the box.
- *   - Sec. "Magnetic response"/hyper-virial passage: pseudopotentials enter
+ *   - Sec. "Magnetic response and gauge invariance in real-space grids"/hyper-virial passage: pseudopotentials enter
  *     as a non-local operator v_nl (separable projectors here).
  *   - Sec. "Quantum optimal control", Eq. (qoctgradient) and the costate
  *     equations: gradient = 2 Im int <chi| dH/du |psi> dt, costate
  *     propagated backwards with the forward propagators.
- *   - Sec. "Performance": a block of states is the basic object; fields are
+ *   - Sec. "Parallelization, optimizations and graphics processing units": a block of states is the basic object; fields are
  *     linear arrays plus tables describing the grid.
  *
  * Readings the paper leaves open (restated in the design notes):

@@ -4,9 +4,9 @@
 // re-orthonormalisation and the discrete adjoint of the control gradient.
 //
 // Method passages (arXiv:1501.05654): Sec. 1 (uniform grids, finite
-// differences), Sec. "Performance" (Hamiltonian application on groups of
+// differences), Sec. "Parallelization, optimizations and graphics processing units" (Hamiltonian application on groups of
 // states; linear arrays plus grid tables; re-orthonormalisation only rarely
-// needed in real time), Sec. "Magnetic response" (non-local pseudopotential),
+// needed in real time), Sec. "Magnetic response and gauge invariance in real-space grids" (non-local pseudopotential),
 // Sec. "Quantum optimal control" (Eq. (qoctgradient), costate propagation).
 #include <cuda_runtime.h>
 
@@ -128,6 +128,7 @@ struct rsg_ham_s {
     DevBuf D, partial;
     // workspace
     DevBuf w0, w1, red, G, W, Wc, drift, status, dots, M, ov, grad, Xd, Xdir;
+    DevBuf w2, cg;     // shifted solver: third work block, per-state scalars
     double xdir_cached[3] = {NAN, NAN, NAN};
     std::vector<DevBuf> pool;   // control-gradient vectors
     // measurement
@@ -1324,6 +1325,140 @@ rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t n
     }
     std::memcpy(evals_out, lam.data(), (size_t)S * sizeof(double));
     if (resid_out) std::memcpy(resid_out, res.data(), (size_t)S * sizeof(double));
+    if (iters_out) *iters_out = it;
+    return read_status(H, st);
+}
+
+// -------------------------------------------------- shifted solves ----
+// (H - z) x = b for S right-hand sides at one complex shift z: the linear
+// problem of the Sternheimer equation (Sec. "The Sternheimer formulation of
+// linear-response"), solved by
+// conjugate-orthogonal conjugate gradients for the complex symmetric matrix
+// H - z (H is real symmetric here).  A x is one application with the base
+// term -z x folded into the epilogue; every inner product is FP64.
+rsg_status rsg_shifted_solve(rsg_ham H, const void *b, void *x, int64_t S, int64_t ld, double zr, double zi,
+                             int64_t max_iter, double tol, double *resid_out, int64_t *iters_out, void *stream) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    CKS(check_block(H, b, S, ld, "b"));
+    CKS(check_block(H, x, S, ld, "x"));
+    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (max_iter < 0 || !(tol > 0) || !std::isfinite(zr) || !std::isfinite(zi))
+        return fail(RSG_ERR_ARG, "need max_iter >= 0, tol > 0 and a finite shift");
+    rsg_mesh m = H->m;
+    const int64_t P = m->P;
+    const size_t bytes = (size_t)P * ld * cbytes(H->dtype);
+    if (overlaps(b, x, bytes)) return fail(RSG_ERR_ARG, "b and x overlap");
+    cudaStream_t st = (cudaStream_t)stream;
+    const double h3 = std::pow(m->h, 3);
+    const int SV = sv_of(H, ld);
+    CK(H->w0.ensure(bytes));
+    CK(H->w1.ensure(bytes));
+    CK(H->w2.ensure(bytes));
+    const int nbn = norm_blocks(P);
+    CK(H->red.ensure((size_t)nbn * S * 2 * sizeof(double)));
+    CK(H->cg.ensure((size_t)S * 10 * sizeof(double)));
+    double *cgb = H->cg.as<double>();
+    double *d_dot = cgb, *d_nrm = cgb + 2 * S, *d_a = cgb + 3 * S, *d_b = cgb + 5 * S, *d_one = cgb + 7 * S;
+    void *r = H->w0.p, *p = H->w1.p, *q = H->w2.p;
+    const bool c64 = H->dtype == RSG_C64;
+    std::vector<double> one((size_t)2 * S, 0.0), coef((size_t)4 * S);
+    for (int64_t s = 0; s < S; s++) one[(size_t)2 * s] = 1.0;
+    CK(cudaMemcpyAsync(d_one, one.data(), (size_t)2 * S * sizeof(double), cudaMemcpyHostToDevice, st));
+    auto Ax = [&](const void *in, void *out) -> rsg_status {     // out = (H - z) in
+        Epi ep;
+        ep.base = in;
+        ep.br = -zr;
+        ep.bi = -zi;
+        return apply(H, in, out, SV, H->eps, H->dir, ep, st);
+    };
+    auto comb = [&](const void *u, const void *v, void *w, const double *a, const double *bb) -> rsg_status {
+        if (c64) CK(launch_comb<float>(u, v, w, P, (int)ld, (int)S, a, bb, st));
+        else CK(launch_comb<double>(u, v, w, P, (int)ld, (int)S, a, bb, st));
+        return RSG_OK;
+    };
+    std::vector<double> dot((size_t)2 * S), nrm((size_t)S), bn((size_t)S);
+    auto bilinear = [&](const void *u, const void *v) -> rsg_status {    // dot = u^T v (host)
+        if (c64) CK(launch_bilinear<float>(u, v, P, (int)ld, (int)S, h3, H->red.as<double>(), nbn, d_dot, st));
+        else CK(launch_bilinear<double>(u, v, P, (int)ld, (int)S, h3, H->red.as<double>(), nbn, d_dot, st));
+        CK(cudaMemcpyAsync(dot.data(), d_dot, (size_t)2 * S * sizeof(double), cudaMemcpyDeviceToHost, st));
+        return RSG_OK;
+    };
+    auto norms = [&](const void *u, std::vector<double> &out) -> rsg_status {
+        CKS(norms_dev(H, u, S, ld, d_nrm, st));
+        CK(cudaMemcpyAsync(out.data(), d_nrm, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return RSG_OK;
+    };
+    auto upload = [&](const std::vector<std::complex<double>> &v, double *dst) -> rsg_status {
+        for (int64_t s = 0; s < S; s++) {
+            coef[(size_t)2 * s] = v[(size_t)s].real();
+            coef[(size_t)2 * s + 1] = v[(size_t)s].imag();
+        }
+        CK(cudaMemcpyAsync(dst, coef.data(), (size_t)2 * S * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));     // coef is reused by the next upload
+        return RSG_OK;
+    };
+    using cd = std::complex<double>;
+    std::vector<cd> rho((size_t)S), mu((size_t)S), alpha((size_t)S), beta((size_t)S), neg((size_t)S);
+    // r = b - A x, p = r
+    CKS(Ax(x, q));
+    for (int64_t s = 0; s < S; s++) neg[(size_t)s] = -1.0;
+    CKS(upload(neg, d_a));
+    CKS(comb(b, q, r, d_one, d_a));
+    CK(cudaMemcpyAsync(p, r, bytes, cudaMemcpyDeviceToDevice, st));
+    CKS(norms(b, bn));
+    CKS(bilinear(r, r));
+    CKS(norms(r, nrm));
+    for (int64_t s = 0; s < S; s++) rho[(size_t)s] = cd(dot[(size_t)2 * s], dot[(size_t)2 * s + 1]);
+    std::vector<char> done((size_t)S, 0);
+    auto check = [&]() {
+        bool all = true;
+        for (int64_t s = 0; s < S; s++) {
+            done[(size_t)s] = std::sqrt(nrm[(size_t)s]) <= tol * std::sqrt(bn[(size_t)s]);
+            all = all && done[(size_t)s];
+        }
+        return all;
+    };
+    int64_t it = 0;
+    while (it < max_iter && !check()) {
+        CKS(Ax(p, q));
+        CKS(bilinear(p, q));
+        CK(cudaStreamSynchronize(st));
+        for (int64_t s = 0; s < S; s++) {
+            mu[(size_t)s] = cd(dot[(size_t)2 * s], dot[(size_t)2 * s + 1]);
+            if (done[(size_t)s]) {
+                alpha[(size_t)s] = 0.0;
+            } else {
+                if (std::abs(mu[(size_t)s]) == 0.0 || !std::isfinite(std::abs(mu[(size_t)s])))
+                    return fail(RSG_ERR_NONFINITE, "breakdown: p^T (H - z) p = 0 for state %lld", (long long)s);
+                alpha[(size_t)s] = rho[(size_t)s] / mu[(size_t)s];
+            }
+            neg[(size_t)s] = -alpha[(size_t)s];
+        }
+        CKS(upload(alpha, d_a));
+        CKS(comb(x, p, x, d_one, d_a));          // x += alpha p
+        CKS(upload(neg, d_b));
+        CKS(comb(r, q, r, d_one, d_b));          // r -= alpha q
+        CKS(bilinear(r, r));
+        CKS(norms(r, nrm));
+        for (int64_t s = 0; s < S; s++) {
+            const cd rn(dot[(size_t)2 * s], dot[(size_t)2 * s + 1]);
+            beta[(size_t)s] = done[(size_t)s] || std::abs(rho[(size_t)s]) == 0.0 ? cd(0.0) : rn / rho[(size_t)s];
+            rho[(size_t)s] = rn;
+        }
+        CKS(upload(beta, d_b));
+        CKS(comb(r, p, p, d_one, d_b));          // p = r + beta p
+        it++;
+    }
+    // true residual |b - (H - z) x| / |b|
+    CKS(Ax(x, q));
+    for (int64_t s = 0; s < S; s++) neg[(size_t)s] = -1.0;
+    CKS(upload(neg, d_a));
+    CKS(comb(b, q, r, d_one, d_a));
+    CKS(norms(r, nrm));
+    if (resid_out)
+        for (int64_t s = 0; s < S; s++)
+            resid_out[s] = bn[(size_t)s] > 0 ? std::sqrt(nrm[(size_t)s] / bn[(size_t)s]) : std::sqrt(nrm[(size_t)s]);
     if (iters_out) *iters_out = it;
     return read_status(H, st);
 }

@@ -127,6 +127,14 @@ cudaError_t launch_cross_gram(const void *psi, const void *phi, int64_t P, int l
 // psi <- psi Q (in place; Q S x S complex double).
 template <typename R>
 cudaError_t launch_rotate(void *psi, int64_t P, int ld, int S, const double *Q, cudaStream_t st);
+// out[s] (complex double) = h3 sum_p x[p,s] y[p,s] (no conjugate; partial nblk * S * 2 doubles).
+template <typename R>
+cudaError_t launch_bilinear(const void *x, const void *y, int64_t P, int ld, int S, double h3, double *partial,
+                            int nblk, double *out, cudaStream_t st);
+// z = a x + b y per state, complex a[s], b[s] (device, interleaved doubles); z may alias x or y.
+template <typename R>
+cudaError_t launch_comb(const void *x, const void *y, void *z, int64_t P, int ld, int S, const double *a,
+                        const double *b, cudaStream_t st);
 // out[s] = h3 sum_p |hx[p,s] - lam[s] x[p,s]|^2 (FP64; partial nblk * S doubles).
 template <typename R>
 cudaError_t launch_resid(const void *x, const void *hx, int64_t P, int ld, int S, const double *lam, double h3,

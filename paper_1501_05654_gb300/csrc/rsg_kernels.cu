@@ -4,7 +4,7 @@
 // on a uniform mesh stored as rows of contiguous points (z slowest, x
 // fastest), with the 8th-order 25-point star Laplacian (radius 4 per axis)
 // and zero values outside the mesh (arXiv:1501.05654, Sec. 1: high-order
-// finite differences on a real-space grid; Sec. "Performance": Hamiltonian
+// finite differences on a real-space grid; Sec. "Parallelization, optimizations and graphics processing units": Hamiltonian
 // application on a group of states, fields as linear arrays plus grid
 // tables).
 //

@@ -2,7 +2,7 @@
 //
 // Norms, Gram matrices, the Cholesky factor of the Gram matrix and its
 // inverse are kept in FP64 for both compute types (arXiv:1501.05654,
-// Sec. "Performance": real-time propagation preserves orthogonality, so the
+// Sec. "Parallelization, optimizations and graphics processing units": real-time propagation preserves orthogonality, so the
 // states are re-orthonormalised only now and then; here Cholesky-QR, which
 // equals Gram-Schmidt in index order).  The adjoint inner products of the
 // control gradient (Sec. "Quantum optimal control", Eq. (qoctgradient)) are
@@ -184,6 +184,72 @@ __global__ void __launch_bounds__(256) k_resid(const R *__restrict__ x, const R 
         __syncthreads();
     }
     if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * S + s] = red[0];
+}
+
+// partial[blk][s] (complex double) = sum over the block's points of
+// x[p,s] y[p,s] (the bilinear form of complex symmetric systems, no conjugate)
+template <typename R>
+__global__ void __launch_bounds__(256) k_bilinear(const R *__restrict__ x, const R *__restrict__ y, int64_t P,
+                                                  int ld, int S, double *__restrict__ partial, int nblk) {
+    __shared__ double red[2][256];
+    const int s = blockIdx.y;
+    const int64_t per = (P + nblk - 1) / nblk;
+    const int64_t p0 = blockIdx.x * per, p1 = p0 + per < P ? p0 + per : P;
+    double ar = 0.0, ai = 0.0;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        double xr, xi, yr, yi;
+        ld_c(x + (p * ld + s) * 2, xr, xi);
+        ld_c(y + (p * ld + s) * 2, yr, yi);
+        ar += xr * yr - xi * yi;
+        ai += xr * yi + xi * yr;
+    }
+    red[0][threadIdx.x] = ar;
+    red[1][threadIdx.x] = ai;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + w];
+            red[1][threadIdx.x] += red[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[((int64_t)blockIdx.x * S + s) * 2] = red[0][0];
+        partial[((int64_t)blockIdx.x * S + s) * 2 + 1] = red[1][0];
+    }
+}
+
+template <typename R>
+cudaError_t launch_bilinear(const void *x, const void *y, int64_t P, int ld, int S, double h3, double *partial,
+                            int nblk, double *out, cudaStream_t st) {
+    k_bilinear<R><<<dim3(nblk, S), 256, 0, st>>>((const R *)x, (const R *)y, P, ld, S, partial, nblk);
+    k_sum_blocks<<<(unsigned)((2 * S + 255) / 256), 256, 0, st>>>(partial, nblk, 2 * (int64_t)S, h3, out);
+    return cudaGetLastError();
+}
+
+// z[p,s] = a[s] x[p,s] + b[s] y[p,s] with complex per-state a, b (device,
+// interleaved doubles); z may alias x or y (each element is read before it
+// is written, by the same thread)
+template <typename R>
+__global__ void __launch_bounds__(256) k_comb(const R *x, const R *y, R *z, int64_t P, int ld, int S,
+                                              const double *__restrict__ a, const double *__restrict__ b) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= P * S) return;
+    const int64_t p = i / S;
+    const int s = (int)(i - p * S);
+    const int64_t o = (p * ld + s) * 2;
+    const double xr = (double)x[o], xi = (double)x[o + 1], yr = (double)y[o], yi = (double)y[o + 1];
+    const double ar = a[2 * s], ai = a[2 * s + 1], br = b[2 * s], bi = b[2 * s + 1];
+    z[o] = (R)(ar * xr - ai * xi + br * yr - bi * yi);
+    z[o + 1] = (R)(ar * xi + ai * xr + br * yi + bi * yr);
+}
+
+template <typename R>
+cudaError_t launch_comb(const void *x, const void *y, void *z, int64_t P, int ld, int S, const double *a,
+                        const double *b, cudaStream_t st) {
+    const int64_t n = P * S;
+    k_comb<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const R *)x, (const R *)y, (R *)z, P, ld, S, a, b);
+    return cudaGetLastError();
 }
 
 template <typename R>
@@ -771,6 +837,10 @@ cudaError_t launch_grad_accum(const double *M, double tau, double *grad_k, cudaS
     template cudaError_t launch_rotate<R>(void *, int64_t, int, int, const double *, cudaStream_t);  \
     template cudaError_t launch_resid<R>(const void *, const void *, int64_t, int, int, const double *, \
                                          double, double *, int, double *, cudaStream_t);             \
+    template cudaError_t launch_bilinear<R>(const void *, const void *, int64_t, int, int, double,   \
+                                            double *, int, double *, cudaStream_t);                  \
+    template cudaError_t launch_comb<R>(const void *, const void *, void *, int64_t, int, int,       \
+                                        const double *, const double *, cudaStream_t);               \
     template cudaError_t launch_tri_apply<R>(void *, int64_t, int, int, const double *,              \
                                              cudaStream_t);                                          \
     template cudaError_t launch_norms<R>(const void *, int64_t, int, int, double, double *, int,     \

@@ -3,7 +3,7 @@
 // The operator and epilogue are those of rsg_kernels.cu (8th-order 25-point
 // star Laplacian with zero values outside the mesh, local potential and
 // dipole field on the diagonal, arXiv:1501.05654 Sec. 1 and Sec.
-// "Performance"); projector terms are added afterwards by k_proj_scatter.
+// "Parallelization, optimizations and graphics processing units"); projector terms are added afterwards by k_proj_scatter.
 //
 // k_apply_quad: the z-march of k_apply_staged with register blocking.  A
 // block owns a 16 x TY tile of points and one 32-byte chunk of each point's

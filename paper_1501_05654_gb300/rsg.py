@@ -43,6 +43,7 @@ SIGNATURES = {
     "rsg_taylor_apply": [_vp, _vp, _vp, _i64, _i64, _dbl, _vp],
     "rsg_propagate_steps": [_vp, _vp, _i64, _i64, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp],
     "rsg_orthonormalize": [_vp, _vp, _i64, _i64, _vp, _vp],
+    "rsg_shifted_solve": [_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _i64, _dbl, _vp, _vp, _vp],
     "rsg_eigensolve": [_vp, _vp, _i64, _i64, _i64, _i64, _int, _dbl, _vp, _vp, _vp, _vp],
     "rsg_state_norms": [_vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_state_norms_noalloc": [_vp, _vp, _i64, _i64, _vp, _vp],
@@ -298,6 +299,20 @@ class Hamiltonian:
         _ck(load().rsg_eigensolve(self._h, C.c_void_p(psi.data_ptr()), S, psi.shape[1], int(nwant), int(max_iter),
                                   int(degree), float(tol), _ptr(ev), _ptr(res), C.byref(it), _stream(stream)))
         return ev, res, int(it.value)
+
+    def shifted_solve(self, b, x, z: complex, max_iter: int = 500, tol: float = 1e-10, S=None, stream=None):
+        """Solve (H - z) x = b (rsg_shifted_solve); x holds the initial guess
+        and receives the solution.  Returns (relative residuals, iterations)."""
+        self._check(b)
+        self._check(x)
+        S = b.shape[1] if S is None else S
+        res = np.zeros(S)
+        it = C.c_int64()
+        z = complex(z)
+        _ck(load().rsg_shifted_solve(self._h, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), S, b.shape[1],
+                                     z.real, z.imag, int(max_iter), float(tol), _ptr(res), C.byref(it),
+                                     _stream(stream)))
+        return res, int(it.value)
 
     def orthonormalize(self, psi, S=None, stream=None):
         self._check(psi)
