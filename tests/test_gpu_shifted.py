@@ -2,7 +2,9 @@
 complex symmetric H - z) against references independent of the library:
 dense LAPACK solves with the oracle's assembled FP64 matrix on a small cube
 (wells, projectors and a field), and on a larger sphere the true residual
-recomputed by the oracle's FP64 operator."""
+recomputed by the oracle's FP64 operator.  complex64 solves stop near the
+FP32 floor of applying H - z (|H| eps_32 |x| / |b|, ~1e-5 for a shift 0.05
+from the real axis), so their tolerance is 1e-4."""
 import numpy as np
 import pytest
 import torch
@@ -16,7 +18,7 @@ from workloads import white_noise_states
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("dtype,tol,etol", [(torch.complex128, 1e-11, 1e-9), (torch.complex64, 1e-6, 1e-4)])
+@pytest.mark.parametrize("dtype,tol,etol", [(torch.complex128, 1e-11, 1e-9), (torch.complex64, 1e-4, 1e-3)])
 @pytest.mark.parametrize("z", [-0.4 + 0.05j, 1.3 + 0.1j])
 def test_small_cube_against_dense_solve(dtype, tol, etol, z):
     p, g = wells_system("cube", 10, h=0.4, dtype=dtype, seed=12, natoms=2, lmax=1)
