@@ -175,6 +175,17 @@ rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t n
                           int degree, double tol, double *evals_out, double *resid_out, int64_t *iters_out,
                           void *stream);
 
+/* Mask absorber (Sec. "Photoemission", Eq. (mask_split): an orbital splits
+ * into a bounded part M(r) phi and an unbounded part (1 - M(r)) phi; keeping
+ * the bounded part removes the charge that reaches the boundary region).
+ * mask: P values in [0, 1] in library point order (host, or device when
+ * mask_on_device != 0); after every time step of rsg_propagate_steps each
+ * state is multiplied by it pointwise.  NULL removes the absorber.  With an
+ * absorber set, rsg_control_gradient and rsg_control_optimize (whose adjoint
+ * is that of the propagator without it) and rsg_batch_create return
+ * RSG_ERR_UNSUPPORTED.  Errors: RSG_ERR_ARG for a value outside [0, 1]. */
+rsg_status rsg_absorber_set(rsg_ham H, const double *mask, int mask_on_device);
+
 /* Shifted linear solves (H - z) x = b for S right-hand sides at one complex
  * shift z = zr + i zi: the linear problem of the Sternheimer equation
  * (Sec. "The Sternheimer formulation of linear-response": a shifted

@@ -129,6 +129,8 @@ struct rsg_ham_s {
     // workspace
     DevBuf w0, w1, red, G, W, Wc, drift, status, dots, M, ov, grad, Xd, Xdir;
     DevBuf w2, cg;     // shifted solver: third work block, per-state scalars
+    DevBuf mask;       // mask absorber M(r) (compute type), applied after each time step
+    bool has_mask = false;
     double xdir_cached[3] = {NAN, NAN, NAN};
     std::vector<DevBuf> pool;   // control-gradient vectors
     // measurement
@@ -871,6 +873,29 @@ rsg_status rsg_potential_set(rsg_ham H, const double *v, int v_on_device) {
     return RSG_OK;
 }
 
+rsg_status rsg_absorber_set(rsg_ham H, const double *mask, int mask_on_device) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    if (!mask) {
+        H->has_mask = false;
+        return RSG_OK;
+    }
+    const int64_t P = H->m->P;
+    std::vector<double> hm((size_t)P);
+    if (mask_on_device)
+        CK(cudaMemcpy(hm.data(), mask, (size_t)P * sizeof(double), cudaMemcpyDeviceToHost));
+    else
+        std::memcpy(hm.data(), mask, (size_t)P * sizeof(double));
+    for (int64_t p = 0; p < P; p++)
+        if (!(hm[(size_t)p] >= 0.0 && hm[(size_t)p] <= 1.0))
+            return fail(RSG_ERR_ARG, "mask value outside [0, 1] at %lld", (long long)p);
+    if (H->dtype == RSG_C64)
+        CK(H->mask.upload(cast_vec<float>(hm)));
+    else
+        CK(H->mask.upload(hm));
+    H->has_mask = true;
+    return RSG_OK;
+}
+
 rsg_status rsg_field_set(rsg_ham H, double eps, const double dir[3]) {
     if (!H) return fail(RSG_ERR_ARG, "NULL handle");
     if (eps != 0.0 && !dir) return fail(RSG_ERR_ARG, "dir is NULL");
@@ -1094,6 +1119,12 @@ rsg_status rsg_propagate_steps(rsg_ham H, void *psi, int64_t S, int64_t ld, int6
                 CKS(taylor(H, psi, psi, ld, 0.5 * tsub, e, d, st));
                 CKS(taylor(H, psi, psi, ld, 0.5 * tsub, e, d, st));
             }
+        }
+        if (H->has_mask) {
+            // mask absorber: keep the bounded part M psi of every state
+            if (H->dtype == RSG_C64) CK(launch_mask<float>(psi, H->m->P, (int)ld, (int)S, H->mask.p, st));
+            else CK(launch_mask<double>(psi, H->m->P, (int)ld, (int)S, H->mask.p, st));
+            H->n_launch++;
         }
         const bool gs_now = gs_every > 0 && (k + 1) % gs_every == 0;
         if (gs_now) {
@@ -1630,6 +1661,8 @@ extern "C" rsg_status rsg_control_gradient(rsg_ham H, const void *psi0, const vo
                                            double *J_out, double *grad_out, void *stream) {
     if (!H || !psi0 || !target || !eps || !J_out || !grad_out) return fail(RSG_ERR_ARG, "NULL argument");
     if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (H->has_mask)
+        return fail(RSG_ERR_UNSUPPORTED, "a mask absorber is set: the adjoint is that of the propagator without it");
     if (nsteps < 1 || nsub < 1 || !std::isfinite(dt)) return fail(RSG_ERR_ARG, "bad nsteps/nsub/dt");
     if (scheme != RSG_EXPMID && scheme != RSG_ETRS) return fail(RSG_ERR_ARG, "unknown scheme");
     if (((uintptr_t)psi0) % 8 || ((uintptr_t)target) % 8) return fail(RSG_ERR_ARG, "misaligned state");
@@ -1897,6 +1930,7 @@ rsg_status rsg_batch_create(const rsg_ham *hams, const int64_t *S, int nsys, rsg
     for (int i = 0; i < nsys; i++) {
         if (!hams[i]) return fail(RSG_ERR_ARG, "NULL Hamiltonian %d", i);
         if (hams[i]->dtype != RSG_C64) return fail(RSG_ERR_UNSUPPORTED, "batches are complex64");
+        if (hams[i]->has_mask) return fail(RSG_ERR_UNSUPPORTED, "batches do not apply mask absorbers");
         if (S[i] < 1) return fail(RSG_ERR_ARG, "S[%d] < 1", i);
         b->hams.push_back(hams[i]);
         b->S.push_back(S[i]);

@@ -131,6 +131,9 @@ cudaError_t launch_rotate(void *psi, int64_t P, int ld, int S, const double *Q, 
 template <typename R>
 cudaError_t launch_bilinear(const void *x, const void *y, int64_t P, int ld, int S, double h3, double *partial,
                             int nblk, double *out, cudaStream_t st);
+// psi[p, s] *= M[p] (M: P values of the compute type), the first S states.
+template <typename R>
+cudaError_t launch_mask(void *psi, int64_t P, int ld, int S, const void *M, cudaStream_t st);
 // z = a x + b y per state, complex a[s], b[s] (device, interleaved doubles); z may alias x or y.
 template <typename R>
 cudaError_t launch_comb(const void *x, const void *y, void *z, int64_t P, int ld, int S, const double *a,

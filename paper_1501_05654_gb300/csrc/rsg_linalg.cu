@@ -252,6 +252,26 @@ cudaError_t launch_comb(const void *x, const void *y, void *z, int64_t P, int ld
     return cudaGetLastError();
 }
 
+// psi[p, s] *= M[p] for the first S states (mask absorber)
+template <typename R>
+__global__ void __launch_bounds__(256) k_mask(R *psi, int64_t P, int ld, int S, const R *__restrict__ M) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= P * S) return;
+    const int64_t p = i / S;
+    const int s = (int)(i - p * S);
+    const R m = M[p];
+    R *v = psi + (p * ld + s) * 2;
+    v[0] *= m;
+    v[1] *= m;
+}
+
+template <typename R>
+cudaError_t launch_mask(void *psi, int64_t P, int ld, int S, const void *M, cudaStream_t st) {
+    const int64_t n = P * S;
+    k_mask<R><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((R *)psi, P, ld, S, (const R *)M);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_resid(const void *x, const void *hx, int64_t P, int ld, int S, const double *lam, double h3,
                          double *partial, int nblk, double *out, cudaStream_t st) {
@@ -841,6 +861,7 @@ cudaError_t launch_grad_accum(const double *M, double tau, double *grad_k, cudaS
                                             double *, int, double *, cudaStream_t);                  \
     template cudaError_t launch_comb<R>(const void *, const void *, void *, int64_t, int, int,       \
                                         const double *, const double *, cudaStream_t);               \
+    template cudaError_t launch_mask<R>(void *, int64_t, int, int, const void *, cudaStream_t);      \
     template cudaError_t launch_tri_apply<R>(void *, int64_t, int, int, const double *,              \
                                              cudaStream_t);                                          \
     template cudaError_t launch_norms<R>(const void *, int64_t, int, int, double, double *, int,     \

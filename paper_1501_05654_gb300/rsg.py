@@ -43,6 +43,7 @@ SIGNATURES = {
     "rsg_taylor_apply": [_vp, _vp, _vp, _i64, _i64, _dbl, _vp],
     "rsg_propagate_steps": [_vp, _vp, _i64, _i64, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp],
     "rsg_orthonormalize": [_vp, _vp, _i64, _i64, _vp, _vp],
+    "rsg_absorber_set": [_vp, _vp, _int],
     "rsg_shifted_solve": [_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _i64, _dbl, _vp, _vp, _vp],
     "rsg_eigensolve": [_vp, _vp, _i64, _i64, _i64, _i64, _int, _dbl, _vp, _vp, _vp, _vp],
     "rsg_state_norms": [_vp, _vp, _i64, _i64, _vp, _vp],
@@ -185,6 +186,18 @@ class Hamiltonian:
     def set_field(self, eps: float, dir=(1.0, 0.0, 0.0)):
         d = _np(dir, np.float64)
         _ck(load().rsg_field_set(self._h, float(eps), _ptr(d)))
+
+    def set_absorber(self, mask):
+        """Mask absorber M (P values in [0, 1], library point order) applied
+        after every time step; None removes it (rsg_absorber_set)."""
+        if mask is None:
+            _ck(load().rsg_absorber_set(self._h, None, 0))
+        elif isinstance(mask, torch.Tensor) and mask.is_cuda:
+            m = mask.to(torch.float64).contiguous()
+            _ck(load().rsg_absorber_set(self._h, C.c_void_p(m.data_ptr()), 1))
+        else:
+            m = _np(mask if not isinstance(mask, torch.Tensor) else mask.numpy(), np.float64)
+            _ck(load().rsg_absorber_set(self._h, _ptr(m), 0))
 
     def set_option(self, key: str, value: int):
         _ck(load().rsg_ham_set_option(self._h, key.encode(), int(value)))
