@@ -7,6 +7,7 @@ import re
 
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import paper_1501_05654_gb300 as rsg
@@ -98,3 +99,29 @@ def test_odd_ld_rejected_for_complex64(lib):
     fake_mis = C.c_void_p(8)
     assert lib.rsg_hamiltonian_apply(H._h, fake_mis, C.c_void_p(4096), 2, 2, None) == -1
     assert b"aligned" in lib.rsg_last_error()
+
+
+def test_solver_entry_points_argument_errors(lib):
+    """Host-side checks of the eigensolver, shifted solver, control loop and
+    absorber, which fail before any device work (no GPU needed)."""
+    m = rsg.Mesh(rsg.CUBE, 6, spacing=0.3)
+    H = rsg.Hamiltonian(m, torch.complex128)
+    fake, fake2 = C.c_void_p(4096), C.c_void_p(1 << 30)   # never dereferenced
+    ev = np.zeros(2)
+    it = C.c_int64()
+    # NULL eigenvalue output, then no potential
+    assert lib.rsg_eigensolve(H._h, fake, 2, 2, 2, 10, 8, 1e-8, None, None, None, None) == -1
+    assert lib.rsg_eigensolve(H._h, fake, 2, 2, 2, 10, 8, 1e-8, ev.ctypes.data_as(C.c_void_p), None,
+                              C.byref(it), None) == -7
+    assert lib.rsg_shifted_solve(H._h, fake, None, 2, 2, 0.1, 0.1, 10, 1e-8, None, None, None) == -1
+    assert lib.rsg_shifted_solve(H._h, fake, fake2, 2, 2, 0.1, 0.1, 10, 1e-8, None, None, None) == -7
+    J = C.c_double()
+    assert lib.rsg_control_optimize(H._h, fake, fake2, 4, 0.05, 1, 1, None, None, 50, 5, 1e-8, C.byref(J),
+                                    None, None, None, None) == -1
+    eps = np.zeros(4)
+    assert lib.rsg_control_optimize(H._h, fake, fake2, 4, 0.05, 1, 1, eps.ctypes.data_as(C.c_void_p), None, 50,
+                                    -1, 1e-8, C.byref(J), None, None, None, None) == -1
+    bad = np.full(m.P, 2.0)
+    assert lib.rsg_absorber_set(H._h, bad.ctypes.data_as(C.c_void_p), 0) == -1
+    assert b"[0, 1]" in lib.rsg_last_error()
+    assert lib.rsg_absorber_set(H._h, None, 0) == 0
