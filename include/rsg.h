@@ -294,7 +294,8 @@ rsg_status rsg_batch_destroy(rsg_batch b);
  * thread, 16 x 16 tiles with 256 threads or 16 x 12 with 192, else kernel 0
  * runs), "rx" (points per thread along
  * x: 1, 2 or 4; the staged kernel uses 1 or 2), "ty" (rows per
- * tile: 1, 2, 4, 8 or 16), "zseg" (planes per z segment, 1..120), "cv"
+ * tile: 1, 2, 4, 8 or 16), "zseg" (planes per z segment, 1..256; kernels 2
+ * and 3 use at most 120), "cv"
  * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8),
  * "threads" (staged kernels: 256 or 512 threads per block; kernel 5: 256
  * gives 16 x 16 tiles, any other value 16 x 12 tiles with 192 threads).

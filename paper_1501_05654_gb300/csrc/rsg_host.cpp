@@ -408,6 +408,8 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     int ntiles = 0;
     a.tiles = nullptr;
     TileCfg cfg = H->cfg;
+    // kernels 2 and 3 keep a static row table of at most 120-plane segments
+    if ((cfg.kernel == 2 || cfg.kernel == 3) && cfg.zseg > 120) cfg.zseg = 120;
     if (cfg.kernel != 1) {
         int TX, TY;
         block_shape(cfg, SV, &TX, &TY);
@@ -841,7 +843,7 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     else if (k == "rx" && (value == 1 || value == 2 || value == 4)) H->cfg.rx = (int)value;
     else if (k == "ty" && (value == 1 || value == 2 || value == 4 || value == 8 || value == 16))
         H->cfg.ty = (int)value;
-    else if (k == "zseg" && value >= 1 && value <= 120) H->cfg.zseg = (int)value;
+    else if (k == "zseg" && value >= 1 && value <= 256) H->cfg.zseg = (int)value;
     else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
     else if (k == "adjoint_keep_powers" && value >= -1 && value <= 1) H->adj_keep = (int)value;
     else if (k == "threads" && (value == 160 || value == 192 || value == 256 || value == 512))

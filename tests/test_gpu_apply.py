@@ -140,6 +140,16 @@ def test_quad_kernel_cube_box_and_complex128_fallback():
     _check_apply(p, g, 3, opts={"kernel": 5}, expect_kernel=0)
 
 
+@pytest.mark.parametrize("opts", [{"kernel": 5, "zseg": 256}, {"kernel": 5, "zseg": 200, "threads": 256},
+                                  {"kernel": 0, "zseg": 200}, {"kernel": 4, "zseg": 256},
+                                  {"kernel": 3, "zseg": 200}])
+def test_long_z_segments(opts):
+    """A 260-plane box: z segments beyond 120 planes (kernels 0, 4, 5 size
+    their row tables dynamically; kernel 3 caps its segments at 120)."""
+    p, g = wells_system("box", (12, 10, 260), h=0.3, dtype=torch.complex64, seed=14, natoms=2, lmax=1)
+    _check_apply(p, g, 6, opts=opts, expect_kernel=opts["kernel"])
+
+
 def test_row_tma_kernel_cube_and_box():
     """Full rows (no fix-ups inside the mesh), ragged tile tails in x, y, z."""
     for shape, n in (("cube", 37), ("box", (23, 9, 14))):
