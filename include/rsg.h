@@ -299,7 +299,7 @@ rsg_status rsg_batch_destroy(rsg_batch b);
  * (staged kernel: 16-byte vectors per point per block, 1, 2, 4 or 8),
  * "threads" (staged kernels: 256 or 512 threads per block; kernel 5: 256
  * gives 16 x 16 tiles, any other value 16 x 12 tiles with 192 threads).
- * Defaults: complex64 runs kernel 5 with 192 threads, 3 stages and 120-plane
+ * Defaults: complex64 runs kernel 5 with 192 threads, 3 stages and 150-plane
  * z segments, complex128 kernel 1; kernels 0, 3 and 4 default to 256
  * threads, cv 2; 160 threads give kernel 5 16 x 10 tiles, three blocks per
  * SM (z segments up to 96 planes keep the three in shared memory).

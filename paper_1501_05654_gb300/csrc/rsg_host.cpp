@@ -685,14 +685,14 @@ rsg_status rsg_ham_create(rsg_mesh m, rsg_dtype dtype, rsg_ham *out) {
     H->dtype = dtype;
     // complex128 is bound by FP64 arithmetic: the one-thread-per-value kernel
     // does the least of it; complex64 runs the register-blocked staged
-    // kernel (16 x 12 tiles, 120-plane segments: fastest on the sphere
+    // kernel (16 x 12 tiles, 150-plane segments: fastest on the sphere
     // workloads measured)
     if (dtype == RSG_C128) {
         H->cfg.kernel = 1;
     } else {
         H->cfg.kernel = 5;
         H->cfg.threads = 192;
-        H->cfg.zseg = 120;
+        H->cfg.zseg = 150;
         H->cfg.stages = 3;
     }
     *out = H;
