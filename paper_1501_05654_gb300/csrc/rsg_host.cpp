@@ -230,10 +230,10 @@ rsg_status get_tiles(rsg_mesh m, int TX, int TY, int zseg, const Tile **out, int
                     seg.push_back((z0 - zlo) / zseg);
                 }
             }
-        // launch order: by z segment, then along a Hilbert curve over (tx, ty),
-        // so that the blocks resident at one time cover compact patches of
-        // tiles and read each other's halo rows and columns from L2 (with
-        // longer tiles first inside each segment index, see below)
+        // launch order: longest tiles first, then by z segment and along a
+        // Hilbert curve over (tx, ty), so that the blocks resident at one time
+        // cover compact patches of tiles and read each other's halo rows and
+        // columns from L2
         int side = 1;
         while (side < ntx || side < nty) side <<= 1;
         auto hilbert = [side](int x, int y) {
@@ -251,13 +251,13 @@ rsg_status get_tiles(rsg_mesh m, int TX, int TY, int zseg, const Tile **out, int
             }
             return d;
         };
-        // within a segment index, longer tiles first (16-plane buckets) so that
-        // the last blocks of a launch are short ones, then the Hilbert order
+        // longest tiles first (8-plane buckets) so that the last blocks of a
+        // launch are short ones; then the segment index and the Hilbert order
         std::vector<std::pair<long long, int>> order(tl.size());
         const long long hs = (long long)side * side;
         for (size_t i = 0; i < tl.size(); i++) {
-            const long long len_bucket = 64 - std::min(63, (tl[i].zhi - tl[i].zlo) / 16);
-            order[i] = {((long long)seg[i] * 64 + len_bucket) * hs + hilbert(tl[i].tx, tl[i].ty), (int)i};
+            const long long len_bucket = 64 - std::min(63, (tl[i].zhi - tl[i].zlo) / 8);
+            order[i] = {(len_bucket * 64 + seg[i]) * hs + hilbert(tl[i].tx, tl[i].ty), (int)i};
         }
         std::stable_sort(order.begin(), order.end());
         std::vector<Tile> sorted(tl.size());
