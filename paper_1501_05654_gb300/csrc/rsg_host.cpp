@@ -108,6 +108,7 @@ struct rsg_mesh_s {
     DevBuf d_rows;
     // tile lists keyed by (TX, TY, zseg): device tiles and their count
     std::map<std::tuple<int, int, int>, std::pair<DevBuf, int>> tiles;
+    std::map<std::tuple<int, int, int>, std::vector<Tile>> tiles_host;   // the same lists on the host
 };
 
 struct rsg_ham_s {
@@ -263,6 +264,7 @@ rsg_status get_tiles(rsg_mesh m, int TX, int TY, int zseg, const Tile **out, int
         std::vector<Tile> sorted(tl.size());
         for (size_t i = 0; i < tl.size(); i++) sorted[i] = tl[order[i].second];
         tl.swap(sorted);
+        m->tiles_host[key] = tl;
         auto &slot = m->tiles[key];
         cudaError_t e = slot.first.upload(tl);
         if (e != cudaSuccess) {
@@ -1845,6 +1847,7 @@ rsg_status batch_build(rsg_batch b) {
     b->D.resize((size_t)n);
     b->partial.resize((size_t)n);
     std::vector<BWork> work, dot, red, sca;
+    std::vector<int> work_len;   // planes of each stencil work item's tile
     int npmax = 0;
     bool uniform = true;
     for (int i = 0; i < n; i++) {
@@ -1888,8 +1891,12 @@ rsg_status batch_build(rsg_batch b) {
         for (int k = 0; k < 5; k++) A.w[k] = (float)(-0.5 * kFD[k] / (m->h * m->h));
         A.h3 = m->h * m->h * m->h;
         const int nch = (SV + kBatchCV - 1) / kBatchCV;
+        const std::vector<Tile> &ht = m->tiles_host[std::make_tuple(kBatchNXR, kBatchTY, kBatchZseg)];
         for (int t = 0; t < ntiles; t++)
-            for (int c = 0; c < nch; c++) work.push_back(BWork{i, t, c, 0});
+            for (int c = 0; c < nch; c++) {
+                work.push_back(BWork{i, t, c, 0});
+                work_len.push_back(ht[(size_t)t].zhi - ht[(size_t)t].zlo);
+            }
         const ProjDev &pj = H->pj;
         A.natoms = pj.natoms;
         A.npmax = pj.npmax;
@@ -1915,6 +1922,17 @@ rsg_status batch_build(rsg_batch b) {
             for (int at = 0; at < pj.natoms; at++) red.push_back(BWork{i, at, 0, 0});
             for (int u = 0; u < pj.nu; u += 32) sca.push_back(BWork{i, u, std::min(32, pj.nu - u), 0});
         }
+    }
+    {
+        // longest stencil work items first, across systems, so that the last
+        // blocks of a launch are short ones (stable: systems and tile order
+        // are kept among equal lengths)
+        std::vector<size_t> idx(work.size());
+        for (size_t k = 0; k < idx.size(); k++) idx[k] = k;
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return work_len[x] > work_len[y]; });
+        std::vector<BWork> sorted(work.size());
+        for (size_t k = 0; k < idx.size(); k++) sorted[k] = work[idx[k]];
+        work.swap(sorted);
     }
     CK(b->d_work.upload(work));
     CK(b->d_dot.upload(dot));
