@@ -297,15 +297,19 @@ def extras(mesh, wells, proj, g):
         blk = torch.zeros((cm.P, ld), dtype=dtype, device="cuda")
         blk[:, 0] = x
         torch.cuda.synchronize()
+        H.kernel_stats()                  # reset the library's counters
         t0 = time.perf_counter()
         H.propagate(blk, 2000, 0.05, scheme=rsg.ETRS, nsub=4, eps=eps, want_drift=False, S=1)
         torch.cuda.synchronize()
         tf = time.perf_counter() - t0
+        nf = H.kernel_stats()[1]          # Hamiltonian applications of the forward propagation
         t0 = time.perf_counter()
         J, grad = H.control_gradient(x, tgt, eps, 0.05, scheme=rsg.ETRS, nsub=4, checkpoint_every=50)
         tg = time.perf_counter() - t0
+        ng = H.kernel_stats()[1]          # ... of the gradient (forward, recompute, costate)
         out[f"control_gradient_{'c128' if dtype == torch.complex128 else 'c64'}"] = {
             "forward_s": tf, "gradient_s": tg, "ratio": tg / tf,
+            "h_applications_forward": nf, "h_applications_gradient": ng, "h_application_ratio": ng / nf,
             "workload": "64^3 h=0.3 double well, 2000 intervals dt=0.05, ETRS nsub=4, K=50"}
         del H, blk
     # optimal control loop on the control workload's operator (64^3 double
