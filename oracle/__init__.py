@@ -73,6 +73,7 @@ def _load():
         L.orc_ham_atom_nproj.argtypes = [vp, C.c_int]
         L.orc_ham_atom_values.argtypes = [vp, C.c_int, vp, vp]
         L.orc_apply.argtypes = [vp, dbl, vp, vp, vp, i64]
+        L.orc_apply_scaled.argtypes = [vp, dbl, vp, vp, vp, i64]
         L.orc_apply_sampled.argtypes = [vp, dbl, vp, vp, i64, i64, vp, vp, vp]
         L.orc_taylor4.argtypes = [vp, dbl, vp, dbl, vp, vp, i64]
         L.orc_norms2.argtypes = [vp, vp, i64, vp]
@@ -129,6 +130,16 @@ class Mesh:
         psi = np.ascontiguousarray(psi, dtype=np.complex128)
         out = np.empty(psi.shape[1])
         _load().orc_norms2(self._m, _p(psi), psi.shape[1], _p(out))
+        return out
+
+    def apply_scaled(self, psi, theta: float, vtheta):
+        """Complex-scaled operator -1/2 e^{-2 i theta} lap + V(r e^{i theta})
+        (vtheta: the caller's complex values of V(r e^{i theta}) per point)."""
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        vt = np.ascontiguousarray(vtheta, dtype=np.complex128)
+        assert vt.shape == (self.P,)
+        out = np.empty_like(psi)
+        _load().orc_apply_scaled(self._m, float(theta), _p(vt), _p(psi), _p(out), psi.shape[1])
         return out
 
     def mgs(self, psi):

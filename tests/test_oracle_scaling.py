@@ -1,0 +1,75 @@
+"""Pins of the oracle's complex-scaled operator (Sec. "Complex scaling and
+resonances": H_theta = -1/2 e^{-2 i theta} lap + V(r e^{i theta})):
+
+- closed form: with antisymmetric-image walls and V = v0 constant, products
+  of sines are exact eigenvectors with eigenvalue e^{-2 i theta} E + v0, E
+  the closed-form discrete free spectrum sum_d sigma(pi m_d / (N+1)) / (2 h^2),
+  sigma(phi) = -c0 - 2 sum_k c_k cos(k phi);
+- complex symmetry: x^T H_theta y = y^T H_theta x (no conjugate) on a sphere
+  with random complex potential values;
+- the paper's one-dimensional example v(x) = 3 (x^2 - 2) e^{-x^2/4}: its
+  two bound-state energies do not move with theta (the rotated continuum
+  does), checked between theta = 0 and theta = 0.5 on a 301-point line.
+"""
+import numpy as np
+
+import oracle
+
+C = [-205 / 72, 8 / 5, -1 / 5, 8 / 315, -1 / 560]
+
+
+def _sigma(phi):
+    return -C[0] - 2 * sum(C[k] * np.cos(k * phi) for k in range(1, 5))
+
+
+def test_closed_form_rotated_spectrum():
+    n, h, v0, theta = 9, 0.35, 0.7, 0.4
+    m = oracle.Mesh(oracle.CUBE, n, h=h, bc=oracle.ODD)
+    for modes in ((1, 1, 1), (2, 3, 1), (4, 1, 7)):
+        f = np.ones(m.P)
+        for d, md in enumerate(modes):
+            f = f * np.sin(np.pi * md * (m.ijk[:, d] + 1) / (n + 1))
+        E = sum(_sigma(np.pi * md / (n + 1)) for md in modes) / (2 * h * h)
+        hf = m.apply_scaled(f.reshape(-1, 1).astype(np.complex128), theta, np.full(m.P, v0 + 0j))[:, 0]
+        big = np.abs(f) > 0.1 * np.abs(f).max()
+        ratio = hf[big] / f[big]
+        want = np.exp(-2j * theta) * E + v0
+        assert np.abs(ratio - want).max() < 1e-11 * abs(want), (ratio[:3], want)
+
+
+def test_complex_symmetric():
+    g = np.random.default_rng(21)
+    m = oracle.Mesh(oracle.SPHERE, radius=2.0, h=0.3)
+    vt = g.standard_normal(m.P) + 1j * g.standard_normal(m.P)
+    x = g.standard_normal((m.P, 1)) + 1j * g.standard_normal((m.P, 1))
+    y = g.standard_normal((m.P, 1)) + 1j * g.standard_normal((m.P, 1))
+    a = (x[:, 0] * m.apply_scaled(y, 0.3, vt)[:, 0]).sum()
+    b = (y[:, 0] * m.apply_scaled(x, 0.3, vt)[:, 0]).sum()
+    assert abs(a - b) < 1e-12 * abs(a)
+    # and not Hermitian once theta != 0
+    c = (np.conj(x[:, 0]) * m.apply_scaled(y, 0.3, vt)[:, 0]).sum()
+    d = np.conj((np.conj(y[:, 0]) * m.apply_scaled(x, 0.3, vt)[:, 0]).sum())
+    assert abs(c - d) > 1e-3 * abs(c)
+
+
+def test_paper_1d_example_bound_states_do_not_rotate():
+    N, h = 301, 0.1
+    m = oracle.Mesh(oracle.BOX, (N, 1, 1), h=h)
+    x = m.xyz[:, 0]
+    levels = []
+    for theta in (0.0, 0.5):
+        z = x * np.exp(1j * theta)
+        vt = 3 * (z * z - 2) * np.exp(-z * z / 4)
+        A = m.apply_scaled(np.eye(m.P, dtype=np.complex128), theta, vt)
+        w = np.linalg.eigvals(A)
+        # the single-point y and z directions add -1/2 e^{-2 i theta} 2 c0 / h^2
+        w = w - np.exp(-2j * theta) * (-C[0] / h ** 2)
+        levels.append(w)
+    w0 = np.sort(levels[0].real)
+    bound = w0[w0 < -0.05][:2]
+    assert len(bound) == 2, w0[:5]
+    for e in bound:
+        near = levels[1][np.argmin(np.abs(levels[1] - e))]
+        assert abs(near - e) < 1e-5, (e, near)
+    # the continuum rotates into the lower half plane
+    assert np.sum(levels[1].imag < -0.1) > N // 2
