@@ -186,13 +186,36 @@ rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t n
  * RSG_ERR_UNSUPPORTED.  Errors: RSG_ERR_ARG for a value outside [0, 1]. */
 rsg_status rsg_absorber_set(rsg_ham H, const double *mask, int mask_on_device);
 
+/* Complex scaling (Sec. "Complex scaling and resonances": the transform
+ * R_theta maps H to H_theta, and the single-particle equation there takes
+ * the kinetic term times e^{-2i theta} and the potential at the rotated
+ * coordinates).  While set, every Hamiltonian application uses
+ *   H_theta = -1/2 e^{-2i theta} lap + v_theta(r),
+ * which is complex symmetric, not Hermitian: bound-state energies stay on
+ * the real axis, the continuum turns by -2 theta, resonances appear as
+ * eigenvalues eps0 - i Gamma/2.  v_theta: 2P doubles, the values
+ * v(r e^{i theta}) of every point as (re, im) pairs in library point order
+ * (host, or device when v_on_device != 0), computed by the caller, who
+ * knows v analytically; copied, and used in place of rsg_potential_set's
+ * V (which may be left unset).  theta in [0, pi/4].  v_theta = NULL
+ * removes the scaling.  rsg_hamiltonian_apply, rsg_taylor_apply,
+ * rsg_propagate_steps (without a field) and rsg_shifted_solve use H_theta;
+ * rsg_eigensolve, rsg_control_gradient, rsg_control_optimize and
+ * rsg_batch_create return RSG_ERR_UNSUPPORTED, as do rsg_projectors_set
+ * with atoms and rsg_field_set or rsg_propagate_steps with a nonzero field
+ * (and this call, while either is set).  Applications run the stencil
+ * kernel 6 (one thread per point and 16-byte vector).
+ * Errors: RSG_ERR_ARG for theta outside [0, pi/4] or a non-finite value. */
+rsg_status rsg_complex_scaling_set(rsg_ham H, double theta, const double *v_theta, int v_on_device);
+
 /* Shifted linear solves (H - z) x = b for S right-hand sides at one complex
  * shift z = zr + i zi: the linear problem of the Sternheimer equation
  * (Sec. "The Sternheimer formulation of linear-response": a shifted
  * Kohn-Sham Hamiltonian is inverted at every step; a complex shift needs a
  * non-Hermitian solver).  Conjugate-orthogonal conjugate gradients for the
  * complex symmetric H - z (H is real symmetric: real stencil, potential,
- * field and projector matrices), each right-hand side its own system; A x
+ * field and projector matrices; or the complex-symmetric H_theta of
+ * rsg_complex_scaling_set), each right-hand side its own system; A x
  * is one Hamiltonian application with -z x added in the epilogue; inner
  * products are FP64.  b (device, P x ld, read only); x (device, same
  * shape): in, the initial guess (zeros for none); out, the solution.  Stops
@@ -323,7 +346,8 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value);
 rsg_status rsg_ham_autotune(rsg_ham H, const void *psi, void *work, int64_t S, int64_t ld, void *stream,
                             double *best_ms);
 
-/* Reads an option set above, or "last_kernel": the stencil kernel (0..5)
+/* Reads an option set above, or "last_kernel": the stencil kernel (0..5, or
+ * 6 for the complex-scaled operator)
  * that the last Hamiltonian application actually ran (-1 before any), after
  * automatic fallbacks (small problems, TMA unavailable). */
 rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value);

@@ -132,6 +132,9 @@ struct rsg_ham_s {
     DevBuf w2, cg;     // shifted solver: third work block, per-state scalars
     DevBuf mask;       // mask absorber M(r) (compute type), applied after each time step
     bool has_mask = false;
+    DevBuf vtheta;     // complex scaling: v(r e^{i theta}) per point, interleaved (compute type)
+    bool has_scaling = false;
+    double theta = 0.0;
     double xdir_cached[3] = {NAN, NAN, NAN};
     std::vector<DevBuf> pool;   // control-gradient vectors
     // measurement
@@ -350,6 +353,9 @@ struct Epi {
     double shift = 0;   // applies H - shift (folded into the diagonal's constant term)
 };
 
+// A potential is set: the real V, or the complex v_theta of complex scaling.
+bool has_potential(rsg_ham H) { return H->has_V || H->has_scaling; }
+
 rsg_status ensure_rows(rsg_mesh m) {
     if (m->d_rows.p) return RSG_OK;
     CK(m->d_rows.upload(m->rows));
@@ -445,8 +451,12 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         H->ev_used += 2;
         CK(cudaEventRecord(e0, st));
     }
-    const bool split_nl = cfg.kernel != 1 && cfg.kernel != 2 && H->pj.natoms > 0;
-    {
+    const bool split_nl = !H->has_scaling && cfg.kernel != 1 && cfg.kernel != 2 && H->pj.natoms > 0;
+    if (H->has_scaling) {
+        // complex-scaled operator (no projectors, no field: refused while set)
+        CK(launch_apply_scaled<R>(a, H->vtheta.as<R>(), H->theta, st));
+        H->last_kernel = 6;
+    } else {
         ApplyArgs<R> b = a;
         if (split_nl) b.nl_ptr = nullptr;
         bool done = false;
@@ -478,7 +488,8 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     // the potential, and (with projectors) the per-point entry lists,
     // entry values and the coefficient block
     const double P = (double)m->P, row = 16.0 * SV;
-    double bytes = P * row * (2.0 + (ep.base ? 1.0 : 0.0) + (ep.acc ? 2.0 : 0.0)) + P * sizeof(R);
+    double bytes = P * row * (2.0 + (ep.base ? 1.0 : 0.0) + (ep.acc ? 2.0 : 0.0)) +
+                   P * sizeof(R) * (H->has_scaling ? 2.0 : 1.0);
     if (H->pj.natoms > 0 && !split_nl)
         bytes += 4.0 * (P + 1) + (double)H->pj.nq * (8.0 + H->pj.npmax * sizeof(R)) +
                  (double)H->pj.natoms * H->pj.npmax * row;
@@ -744,7 +755,7 @@ rsg_status rsg_ham_autotune(rsg_ham H, const void *psi, void *work, int64_t S, i
     if (!H) return fail(RSG_ERR_ARG, "NULL handle");
     CKS(check_block(H, psi, S, ld, "psi"));
     CKS(check_block(H, work, S, ld, "work"));
-    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (!has_potential(H)) return fail(RSG_ERR_STATE, "potential not set");
     const size_t bytes = (size_t)H->m->P * ld * cbytes(H->dtype);
     if (overlaps(psi, work, bytes)) return fail(RSG_ERR_ARG, "psi and work overlap");
     cudaStream_t st = (cudaStream_t)stream;
@@ -906,9 +917,37 @@ rsg_status rsg_absorber_set(rsg_ham H, const double *mask, int mask_on_device) {
     return RSG_OK;
 }
 
+rsg_status rsg_complex_scaling_set(rsg_ham H, double theta, const double *v_theta, int v_on_device) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    if (!v_theta) {
+        H->has_scaling = false;
+        H->theta = 0.0;
+        return RSG_OK;
+    }
+    if (!(theta >= 0.0 && theta <= 0.78539816339744830962)) return fail(RSG_ERR_ARG, "theta outside [0, pi/4]");
+    if (H->pj.natoms > 0) return fail(RSG_ERR_UNSUPPORTED, "projectors are set: complex scaling takes none");
+    if (H->eps != 0.0) return fail(RSG_ERR_UNSUPPORTED, "a dipole field is set: complex scaling takes none");
+    const int64_t P = H->m->P;
+    std::vector<double> hv((size_t)(2 * P));
+    if (v_on_device)
+        CK(cudaMemcpy(hv.data(), v_theta, (size_t)(2 * P) * sizeof(double), cudaMemcpyDeviceToHost));
+    else
+        std::memcpy(hv.data(), v_theta, (size_t)(2 * P) * sizeof(double));
+    for (int64_t i = 0; i < 2 * P; i++)
+        if (!std::isfinite(hv[(size_t)i])) return fail(RSG_ERR_ARG, "v_theta not finite at %lld", (long long)(i / 2));
+    if (H->dtype == RSG_C64)
+        CK(H->vtheta.upload(cast_vec<float>(hv)));
+    else
+        CK(H->vtheta.upload(hv));
+    H->theta = theta;
+    H->has_scaling = true;
+    return RSG_OK;
+}
+
 rsg_status rsg_field_set(rsg_ham H, double eps, const double dir[3]) {
     if (!H) return fail(RSG_ERR_ARG, "NULL handle");
     if (eps != 0.0 && !dir) return fail(RSG_ERR_ARG, "dir is NULL");
+    if (eps != 0.0 && H->has_scaling) return fail(RSG_ERR_UNSUPPORTED, "complex scaling is set: no dipole field");
     H->eps = eps;
     if (dir)
         for (int d = 0; d < 3; d++) H->dir[d] = dir[d];
@@ -919,6 +958,7 @@ rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres, cons
                               const int32_t *lmax, const double *beta, const double *hmats) {
     if (!H) return fail(RSG_ERR_ARG, "NULL handle");
     if (natoms < 0) return fail(RSG_ERR_ARG, "natoms < 0");
+    if (natoms > 0 && H->has_scaling) return fail(RSG_ERR_UNSUPPORTED, "complex scaling is set: no projectors");
     H->pj = ProjDev();
     H->proj_norm = 0.0;
     if (natoms == 0) return RSG_OK;
@@ -1055,7 +1095,7 @@ rsg_status rsg_hamiltonian_apply(rsg_ham H, const void *psi, void *hpsi, int64_t
     if (!H) return fail(RSG_ERR_ARG, "NULL handle");
     CKS(check_block(H, psi, S, ld, "psi"));
     CKS(check_block(H, hpsi, S, ld, "hpsi"));
-    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (!has_potential(H)) return fail(RSG_ERR_STATE, "potential not set");
     const size_t bytes = (size_t)H->m->P * ld * cbytes(H->dtype);
     if (overlaps(psi, hpsi, bytes)) return fail(RSG_ERR_ARG, "psi and hpsi overlap");
     Epi ep;
@@ -1067,7 +1107,7 @@ rsg_status rsg_taylor_apply(rsg_ham H, const void *psi, void *out, int64_t S, in
     if (!H) return fail(RSG_ERR_ARG, "NULL handle");
     CKS(check_block(H, psi, S, ld, "psi"));
     CKS(check_block(H, out, S, ld, "out"));
-    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (!has_potential(H)) return fail(RSG_ERR_STATE, "potential not set");
     const size_t bytes = (size_t)H->m->P * ld * cbytes(H->dtype);
     if (out != psi && overlaps(psi, out, bytes)) return fail(RSG_ERR_ARG, "psi and out partially overlap");
     if (!std::isfinite(tau)) return fail(RSG_ERR_ARG, "tau not finite");
@@ -1106,11 +1146,14 @@ rsg_status rsg_propagate_steps(rsg_ham H, void *psi, int64_t S, int64_t ld, int6
                                int gs_every, double *norm_drift_out, void *stream) {
     if (!H) return fail(RSG_ERR_ARG, "NULL handle");
     CKS(check_block(H, psi, S, ld, "psi"));
-    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (!has_potential(H)) return fail(RSG_ERR_STATE, "potential not set");
     if (nsteps < 0 || nsub < 1 || gs_every < 0 || !std::isfinite(dt))
         return fail(RSG_ERR_ARG, "bad nsteps/nsub/gs_every/dt");
     if (scheme != RSG_EXPMID && scheme != RSG_ETRS) return fail(RSG_ERR_ARG, "unknown scheme");
     if (S > 1024 && gs_every > 0) return fail(RSG_ERR_UNSUPPORTED, "S > 1024 with Gram-Schmidt");
+    if (H->has_scaling && eps)
+        for (int64_t k = 0; k < nsteps; k++)
+            if (eps[k] != 0.0) return fail(RSG_ERR_UNSUPPORTED, "complex scaling is set: no dipole field");
     cudaStream_t st = (cudaStream_t)stream;
     const double xdir[3] = {1.0, 0.0, 0.0};
     const double *d = dir ? dir : xdir;
@@ -1241,8 +1284,10 @@ rsg_status rsg_eigensolve(rsg_ham H, void *psi, int64_t S, int64_t ld, int64_t n
     if (!H || !evals_out) return fail(RSG_ERR_ARG, "NULL argument");
     CKS(check_block(H, psi, S, ld, "psi"));
     if (nwant < 1 || nwant > S) return fail(RSG_ERR_ARG, "need 1 <= nwant <= S");
-    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (!has_potential(H)) return fail(RSG_ERR_STATE, "potential not set");
     if (S > 256) return fail(RSG_ERR_UNSUPPORTED, "S > 256");
+    if (H->has_scaling)
+        return fail(RSG_ERR_UNSUPPORTED, "complex scaling is set: the eigensolver needs a Hermitian operator");
     if (degree < 1 || degree > 64) return fail(RSG_ERR_ARG, "degree must be in 1..64");
     if (max_iter < 0 || !(tol > 0)) return fail(RSG_ERR_ARG, "need max_iter >= 0 and tol > 0");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1382,7 +1427,7 @@ rsg_status rsg_shifted_solve(rsg_ham H, const void *b, void *x, int64_t S, int64
     if (!H) return fail(RSG_ERR_ARG, "NULL handle");
     CKS(check_block(H, b, S, ld, "b"));
     CKS(check_block(H, x, S, ld, "x"));
-    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (!has_potential(H)) return fail(RSG_ERR_STATE, "potential not set");
     if (max_iter < 0 || !(tol > 0) || !std::isfinite(zr) || !std::isfinite(zi))
         return fail(RSG_ERR_ARG, "need max_iter >= 0, tol > 0 and a finite shift");
     rsg_mesh m = H->m;
@@ -1670,9 +1715,11 @@ extern "C" rsg_status rsg_control_gradient(rsg_ham H, const void *psi0, const vo
                                            const double *eps, const double dir[3], int checkpoint_every,
                                            double *J_out, double *grad_out, void *stream) {
     if (!H || !psi0 || !target || !eps || !J_out || !grad_out) return fail(RSG_ERR_ARG, "NULL argument");
-    if (!H->has_V) return fail(RSG_ERR_STATE, "potential not set");
+    if (!has_potential(H)) return fail(RSG_ERR_STATE, "potential not set");
     if (H->has_mask)
         return fail(RSG_ERR_UNSUPPORTED, "a mask absorber is set: the adjoint is that of the propagator without it");
+    if (H->has_scaling)
+        return fail(RSG_ERR_UNSUPPORTED, "complex scaling is set: the control field is a dipole field");
     if (nsteps < 1 || nsub < 1 || !std::isfinite(dt)) return fail(RSG_ERR_ARG, "bad nsteps/nsub/dt");
     if (scheme != RSG_EXPMID && scheme != RSG_ETRS) return fail(RSG_ERR_ARG, "unknown scheme");
     if (((uintptr_t)psi0) % 8 || ((uintptr_t)target) % 8) return fail(RSG_ERR_ARG, "misaligned state");
@@ -1697,6 +1744,8 @@ extern "C" rsg_status rsg_control_optimize(rsg_ham H, const void *psi0, const vo
                                            double gtol, double *J_out, double *J_hist, int64_t *iters_out,
                                            int64_t *evals_out, void *stream) {
     if (!H || !eps || !J_out) return fail(RSG_ERR_ARG, "NULL argument");
+    if (H->has_scaling)
+        return fail(RSG_ERR_UNSUPPORTED, "complex scaling is set: the control field is a dipole field");
     if (max_iter < 0 || !(gtol >= 0)) return fail(RSG_ERR_ARG, "need max_iter >= 0 and gtol >= 0");
     if (nsteps < 1) return fail(RSG_ERR_ARG, "nsteps < 1");
     const size_t n = (size_t)nsteps;
@@ -1957,6 +2006,7 @@ rsg_status rsg_batch_create(const rsg_ham *hams, const int64_t *S, int nsys, rsg
         if (!hams[i]) return fail(RSG_ERR_ARG, "NULL Hamiltonian %d", i);
         if (hams[i]->dtype != RSG_C64) return fail(RSG_ERR_UNSUPPORTED, "batches are complex64");
         if (hams[i]->has_mask) return fail(RSG_ERR_UNSUPPORTED, "batches do not apply mask absorbers");
+        if (hams[i]->has_scaling) return fail(RSG_ERR_UNSUPPORTED, "batches do not apply complex scaling");
         if (S[i] < 1) return fail(RSG_ERR_ARG, "S[%d] < 1", i);
         b->hams.push_back(hams[i]);
         b->S.push_back(S[i]);

@@ -108,6 +108,11 @@ cudaError_t launch_apply_rowtma(const ApplyArgs<R> &a, const TileCfg &cfg, int n
 template <typename R>
 cudaError_t launch_apply(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles,
                          cudaStream_t st);
+// Complex-scaled operator -1/2 e^{-2i theta} lap + v_theta (+ the real
+// constant a.f0): vt holds the interleaved complex v_theta of every point;
+// a.nl_ptr and the field terms are ignored (rsg_scaled.cu).
+template <typename R>
+cudaError_t launch_apply_scaled(const ApplyArgs<R> &a, const R *vt, double theta, cudaStream_t st);
 template <typename R>
 cudaError_t launch_proj_dot(const void *u, int SV, const ProjDev &pj, double *partial,
                             cudaStream_t st);

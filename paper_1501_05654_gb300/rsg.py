@@ -44,6 +44,7 @@ SIGNATURES = {
     "rsg_propagate_steps": [_vp, _vp, _i64, _i64, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp],
     "rsg_orthonormalize": [_vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_absorber_set": [_vp, _vp, _int],
+    "rsg_complex_scaling_set": [_vp, _dbl, _vp, _int],
     "rsg_shifted_solve": [_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _i64, _dbl, _vp, _vp, _vp],
     "rsg_eigensolve": [_vp, _vp, _i64, _i64, _i64, _i64, _int, _dbl, _vp, _vp, _vp, _vp],
     "rsg_state_norms": [_vp, _vp, _i64, _i64, _vp, _vp],
@@ -198,6 +199,20 @@ class Hamiltonian:
         else:
             m = _np(mask if not isinstance(mask, torch.Tensor) else mask.numpy(), np.float64)
             _ck(load().rsg_absorber_set(self._h, _ptr(m), 0))
+
+    def set_complex_scaling(self, theta, v_theta):
+        """Complex scaling: from now on H is -1/2 e^{-2i theta} lap + v_theta,
+        v_theta the P complex values v(r e^{i theta}) in library point order;
+        v_theta None removes it (rsg_complex_scaling_set)."""
+        if v_theta is None:
+            _ck(load().rsg_complex_scaling_set(self._h, float(theta), None, 0))
+        elif isinstance(v_theta, torch.Tensor) and v_theta.is_cuda:
+            v = torch.view_as_real(v_theta.to(torch.complex128).contiguous()).contiguous()
+            _ck(load().rsg_complex_scaling_set(self._h, float(theta), C.c_void_p(v.data_ptr()), 1))
+        else:
+            a = v_theta.numpy() if isinstance(v_theta, torch.Tensor) else np.asarray(v_theta)
+            v = np.ascontiguousarray(a.astype(np.complex128)).view(np.float64)
+            _ck(load().rsg_complex_scaling_set(self._h, float(theta), _ptr(v), 0))
 
     def set_option(self, key: str, value: int):
         _ck(load().rsg_ham_set_option(self._h, key.encode(), int(value)))

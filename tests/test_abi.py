@@ -125,3 +125,25 @@ def test_solver_entry_points_argument_errors(lib):
     assert lib.rsg_absorber_set(H._h, bad.ctypes.data_as(C.c_void_p), 0) == -1
     assert b"[0, 1]" in lib.rsg_last_error()
     assert lib.rsg_absorber_set(H._h, None, 0) == 0
+
+
+def test_complex_scaling_argument_errors(lib):
+    """Host-side checks of rsg_complex_scaling_set (no device work)."""
+    m = rsg.Mesh(rsg.CUBE, 6, spacing=0.3)
+    H = rsg.Hamiltonian(m, torch.complex64)
+    vt = np.zeros(2 * m.P)
+    p = vt.ctypes.data_as(C.c_void_p)
+    assert lib.rsg_complex_scaling_set(None, 0.3, p, 0) == -1
+    assert lib.rsg_complex_scaling_set(H._h, -0.1, p, 0) == -1
+    assert lib.rsg_complex_scaling_set(H._h, 0.8, p, 0) == -1
+    assert b"pi/4" in lib.rsg_last_error()
+    assert lib.rsg_complex_scaling_set(H._h, float("nan"), p, 0) == -1
+    assert lib.rsg_complex_scaling_set(H._h, 0.3, None, 0) == 0     # removal
+    d = np.array([1.0, 0.0, 0.0])
+    assert lib.rsg_field_set(H._h, 0.05, d.ctypes.data_as(C.c_void_p)) == 0
+    assert lib.rsg_complex_scaling_set(H._h, 0.3, p, 0) == -4
+    assert b"dipole field" in lib.rsg_last_error()
+    assert lib.rsg_field_set(H._h, 0.0, d.ctypes.data_as(C.c_void_p)) == 0
+    vt[5] = np.inf
+    assert lib.rsg_complex_scaling_set(H._h, 0.3, p, 0) == -1
+    assert b"not finite" in lib.rsg_last_error()

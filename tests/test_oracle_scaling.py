@@ -9,7 +9,12 @@ resonances": H_theta = -1/2 e^{-2 i theta} lap + V(r e^{i theta})):
   with random complex potential values;
 - the paper's one-dimensional example v(x) = 3 (x^2 - 2) e^{-x^2/4}: its
   two bound-state energies do not move with theta (the rotated continuum
-  does), checked between theta = 0 and theta = 0.5 on a 301-point line.
+  does), checked between theta = 0 and theta = 0.5 on a 301-point line;
+- the same example's lowest resonance (spectrum figure of the section: an
+  isolated eigenvalue near the origin, imaginary part of order -1e-5): the
+  first non-real eigenvalue that stays put between theta = 0.4 and 0.5 has
+  0 < Re < 1 and -1e-4 < Im < -1e-6 (this discretisation converges in h
+  to 0.35448 - 4.70e-5 i).
 """
 import numpy as np
 
@@ -73,3 +78,20 @@ def test_paper_1d_example_bound_states_do_not_rotate():
         assert abs(near - e) < 1e-5, (e, near)
     # the continuum rotates into the lower half plane
     assert np.sum(levels[1].imag < -0.1) > N // 2
+
+
+def _spectrum_1d(N, h, theta):
+    m = oracle.Mesh(oracle.BOX, (N, 1, 1), h=h)
+    z = m.xyz[:, 0] * np.exp(1j * theta)
+    vt = 3 * (z * z - 2) * np.exp(-z * z / 4)
+    w = np.linalg.eigvals(m.apply_scaled(np.eye(m.P, dtype=np.complex128), theta, vt))
+    return w - np.exp(-2j * theta) * (-C[0] / h ** 2)
+
+
+def test_paper_1d_example_lowest_resonance():
+    a, b = _spectrum_1d(301, 0.1, 0.5), _spectrum_1d(301, 0.1, 0.4)
+    stable = np.array(sorted((e for e in a if np.abs(b - e).min() < 1e-4 and e.real < 3), key=lambda e: e.real))
+    assert len(stable) >= 3, stable
+    assert np.all(np.abs(stable[:2].imag) < 1e-6) and np.all(stable[:2].real < 0)
+    r = stable[2]
+    assert 0 < r.real < 1 and -1e-4 < r.imag < -1e-6, r
