@@ -287,6 +287,29 @@ rsg_status rsg_control_optimize(rsg_ham H, const void *psi0, const void *target,
                                 int checkpoint_every, int64_t max_iter, double gtol, double *J_out,
                                 double *J_hist, int64_t *iters_out, int64_t *evals_out, void *stream);
 
+/* The optimal control loop over a linear parametrisation of the field
+ * (Sec. "Quantum optimal control": the parameters that shape the field can
+ * be, for example, the Fourier coefficients of its amplitude):
+ * eps_k = sum_m basis[k * nparam + m] u_m, and the gradient in u is
+ * B^T dJ/deps.  basis: host, nsteps x nparam, row-major, read only (e.g.
+ * from rsg_fourier_basis).  u: host, nparam; in, the start; out, the
+ * optimum.  Everything else as rsg_control_optimize (J_hist: max_iter + 1
+ * values).  Errors: as rsg_control_optimize; RSG_ERR_ARG for nparam < 1 or
+ * a non-finite basis value. */
+rsg_status rsg_control_optimize_basis(rsg_ham H, const void *psi0, const void *target, int64_t nsteps,
+                                      double dt, rsg_scheme scheme, int nsub, int64_t nparam,
+                                      const double *basis, double *u, const double dir[3],
+                                      int checkpoint_every, int64_t max_iter, double gtol, double *J_out,
+                                      double *J_hist, int64_t *iters_out, int64_t *evals_out, void *stream);
+
+/* Fourier (sine-series) basis for rsg_control_optimize_basis: mode m =
+ * 1..nparam of a field that vanishes at t = 0 and t = T = nsteps dt,
+ * sin(m pi t / T), sampled at the interval midpoints t = (k + 1/2) dt:
+ * basis_out[k * nparam + (m - 1)] (host, nsteps x nparam).  The highest
+ * frequency is nparam pi / T.  Errors: RSG_ERR_ARG for NULL, nsteps < 1
+ * or nparam < 1. */
+rsg_status rsg_fourier_basis(int64_t nsteps, int64_t nparam, double *basis_out);
+
 /* -------------------------------------------------------------- batches ---
  * Many independent systems (Sec. "Parallelization, optimizations and graphics processing units": groups of states as the
  * unit of work) propagated together: one launch per Taylor stage covers the

@@ -7,5 +7,5 @@ the CUDA library in-tree.
 """
 from .build import build  # noqa: F401
 from .rsg import (BOX, C64, C128, CUBE, ETRS, EXPMID, SPHERE, Batch,  # noqa: F401
-                  ControlObjective, Hamiltonian, Mesh, RSGError, empty_states, load,
+                  ControlObjective, Hamiltonian, Mesh, RSGError, empty_states, fourier_basis, load,
                   padded_ld)

@@ -1733,22 +1733,15 @@ extern "C" rsg_status rsg_control_gradient(rsg_ham H, const void *psi0, const vo
                                       checkpoint_every, J_out, grad_out, st);
 }
 
-// Optimal control loop (Sec. "Quantum optimal control": the gradient of
-// Eq. (qoctgradient) feeds a gradient-based optimiser; the paper uses
-// conjugate-gradient and BFGS schemes).  Limited-memory BFGS (two-loop
-// recursion, memory 8) on f = -J with an Armijo backtracking line search;
-// every evaluation of J and its gradient is one rsg_control_gradient call.
-extern "C" rsg_status rsg_control_optimize(rsg_ham H, const void *psi0, const void *target, int64_t nsteps,
-                                           double dt, rsg_scheme scheme, int nsub, double *eps,
-                                           const double dir[3], int checkpoint_every, int64_t max_iter,
-                                           double gtol, double *J_out, double *J_hist, int64_t *iters_out,
-                                           int64_t *evals_out, void *stream) {
-    if (!H || !eps || !J_out) return fail(RSG_ERR_ARG, "NULL argument");
-    if (H->has_scaling)
-        return fail(RSG_ERR_UNSUPPORTED, "complex scaling is set: the control field is a dipole field");
-    if (max_iter < 0 || !(gtol >= 0)) return fail(RSG_ERR_ARG, "need max_iter >= 0 and gtol >= 0");
-    if (nsteps < 1) return fail(RSG_ERR_ARG, "nsteps < 1");
-    const size_t n = (size_t)nsteps;
+namespace {
+
+// Limited-memory BFGS (two-loop recursion, memory 8) maximising J over x
+// (n values, in/out) with an Armijo backtracking line search on f = -J.
+// evaluate(at, J, grad) sets J(at) and grad = -dJ/dat and counts itself.
+// J_hist (may be NULL) receives J after every accepted iteration.
+template <typename Eval>
+rsg_status lbfgs_maximise(size_t n, std::vector<double> &x, Eval &&evaluate, int64_t max_iter, double gtol,
+                          double *J_out, double *J_hist, int64_t *iters_out) {
     constexpr int kMem = 8;
     auto dot = [n](const std::vector<double> &a, const std::vector<double> &b) {
         double s = 0.0;
@@ -1760,18 +1753,8 @@ extern "C" rsg_status rsg_control_optimize(rsg_ham H, const void *psi0, const vo
         for (size_t i = 0; i < n; i++) m = std::max(m, std::fabs(a[i]));
         return m;
     };
-    std::vector<double> x(eps, eps + n), g(n), xt(n), gt(n), d(n);
-    int64_t evals = 0;
+    std::vector<double> g(n), xt(n), gt(n), d(n);
     double J = 0.0, Jt = 0.0;
-    // f = -J, gradient -dJ/deps
-    auto evaluate = [&](const std::vector<double> &at, double &Jv, std::vector<double> &grad) -> rsg_status {
-        CKS(rsg_control_gradient(H, psi0, target, nsteps, dt, scheme, nsub, at.data(), dir, checkpoint_every, &Jv,
-                                 grad.data(), stream));
-        for (size_t i = 0; i < n; i++) grad[i] = -grad[i];
-        evals++;
-        if (!std::isfinite(Jv)) return fail(RSG_ERR_NONFINITE, "objective not finite");
-        return RSG_OK;
-    };
     CKS(evaluate(x, J, g));
     if (J_hist) J_hist[0] = J;
     std::vector<std::vector<double>> S, Y;
@@ -1859,10 +1842,97 @@ extern "C" rsg_status rsg_control_optimize(rsg_ham H, const void *psi0, const vo
         it++;
         if (J_hist) J_hist[it] = J;
     }
-    std::memcpy(eps, x.data(), n * sizeof(double));
     *J_out = J;
     if (iters_out) *iters_out = it;
+    return RSG_OK;
+}
+
+rsg_status check_optimize_args(rsg_ham H, int64_t nsteps, int64_t max_iter, double gtol) {
+    if (H->has_scaling)
+        return fail(RSG_ERR_UNSUPPORTED, "complex scaling is set: the control field is a dipole field");
+    if (max_iter < 0 || !(gtol >= 0)) return fail(RSG_ERR_ARG, "need max_iter >= 0 and gtol >= 0");
+    if (nsteps < 1) return fail(RSG_ERR_ARG, "nsteps < 1");
+    return RSG_OK;
+}
+
+}  // namespace
+
+// Optimal control loop (Sec. "Quantum optimal control": the gradient of
+// Eq. (qoctgradient) feeds a gradient-based optimiser; the paper uses
+// conjugate-gradient and BFGS schemes).  The parameters are the interval
+// values of the field; every evaluation of J and its gradient is one
+// rsg_control_gradient call.
+extern "C" rsg_status rsg_control_optimize(rsg_ham H, const void *psi0, const void *target, int64_t nsteps,
+                                           double dt, rsg_scheme scheme, int nsub, double *eps,
+                                           const double dir[3], int checkpoint_every, int64_t max_iter,
+                                           double gtol, double *J_out, double *J_hist, int64_t *iters_out,
+                                           int64_t *evals_out, void *stream) {
+    if (!H || !eps || !J_out) return fail(RSG_ERR_ARG, "NULL argument");
+    CKS(check_optimize_args(H, nsteps, max_iter, gtol));
+    const size_t n = (size_t)nsteps;
+    std::vector<double> x(eps, eps + n);
+    int64_t evals = 0;
+    auto evaluate = [&](const std::vector<double> &at, double &Jv, std::vector<double> &grad) -> rsg_status {
+        CKS(rsg_control_gradient(H, psi0, target, nsteps, dt, scheme, nsub, at.data(), dir, checkpoint_every, &Jv,
+                                 grad.data(), stream));
+        for (size_t i = 0; i < n; i++) grad[i] = -grad[i];
+        evals++;
+        if (!std::isfinite(Jv)) return fail(RSG_ERR_NONFINITE, "objective not finite");
+        return RSG_OK;
+    };
+    CKS(lbfgs_maximise(n, x, evaluate, max_iter, gtol, J_out, J_hist, iters_out));
+    std::memcpy(eps, x.data(), n * sizeof(double));
     if (evals_out) *evals_out = evals;
+    return RSG_OK;
+}
+
+// The same loop over a linear parametrisation eps = B u of the field (the
+// section's example: Fourier coefficients of the amplitude); the gradient
+// in u is B^T dJ/deps.
+extern "C" rsg_status rsg_control_optimize_basis(rsg_ham H, const void *psi0, const void *target, int64_t nsteps,
+                                                 double dt, rsg_scheme scheme, int nsub, int64_t nparam,
+                                                 const double *basis, double *u, const double dir[3],
+                                                 int checkpoint_every, int64_t max_iter, double gtol, double *J_out,
+                                                 double *J_hist, int64_t *iters_out, int64_t *evals_out,
+                                                 void *stream) {
+    if (!H || !basis || !u || !J_out) return fail(RSG_ERR_ARG, "NULL argument");
+    CKS(check_optimize_args(H, nsteps, max_iter, gtol));
+    if (nparam < 1) return fail(RSG_ERR_ARG, "nparam < 1");
+    const size_t n = (size_t)nsteps, m = (size_t)nparam;
+    for (size_t i = 0; i < n * m; i++)
+        if (!std::isfinite(basis[i])) return fail(RSG_ERR_ARG, "basis not finite");
+    std::vector<double> x(u, u + m), eps(n), ge(n);
+    int64_t evals = 0;
+    auto evaluate = [&](const std::vector<double> &at, double &Jv, std::vector<double> &grad) -> rsg_status {
+        for (size_t k = 0; k < n; k++) {
+            double e = 0.0;
+            for (size_t j = 0; j < m; j++) e += basis[k * m + j] * at[j];
+            eps[k] = e;
+        }
+        CKS(rsg_control_gradient(H, psi0, target, nsteps, dt, scheme, nsub, eps.data(), dir, checkpoint_every, &Jv,
+                                 ge.data(), stream));
+        for (size_t j = 0; j < m; j++) {
+            double s = 0.0;
+            for (size_t k = 0; k < n; k++) s += basis[k * m + j] * ge[k];
+            grad[j] = -s;
+        }
+        evals++;
+        if (!std::isfinite(Jv)) return fail(RSG_ERR_NONFINITE, "objective not finite");
+        return RSG_OK;
+    };
+    CKS(lbfgs_maximise(m, x, evaluate, max_iter, gtol, J_out, J_hist, iters_out));
+    std::memcpy(u, x.data(), m * sizeof(double));
+    if (evals_out) *evals_out = evals;
+    return RSG_OK;
+}
+
+// Sine series on [0, T], T = nsteps intervals, at the interval midpoints.
+extern "C" rsg_status rsg_fourier_basis(int64_t nsteps, int64_t nparam, double *basis_out) {
+    if (!basis_out || nsteps < 1 || nparam < 1) return fail(RSG_ERR_ARG, "bad basis arguments");
+    const double pi = 3.14159265358979323846;
+    for (int64_t k = 0; k < nsteps; k++)
+        for (int64_t j = 0; j < nparam; j++)
+            basis_out[k * nparam + j] = std::sin(pi * (double)(j + 1) * ((double)k + 0.5) / (double)nsteps);
     return RSG_OK;
 }
 

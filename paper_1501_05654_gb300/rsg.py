@@ -52,6 +52,9 @@ SIGNATURES = {
     "rsg_control_gradient": [_vp, _vp, _vp, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp, _vp],
     "rsg_control_optimize": [_vp, _vp, _vp, _i64, _dbl, _int, _int, _vp, _vp, _int, _i64, _dbl, _vp, _vp, _vp,
                              _vp, _vp],
+    "rsg_control_optimize_basis": [_vp, _vp, _vp, _i64, _dbl, _int, _int, _i64, _vp, _vp, _vp, _int, _i64, _dbl,
+                                   _vp, _vp, _vp, _vp, _vp],
+    "rsg_fourier_basis": [_i64, _i64, _vp],
     "rsg_batch_create": [_vp, _vp, _int, _vp],
     "rsg_batch_propagate": [_vp, _vp, _i64, _dbl, _int, _int, _vp],
     "rsg_batch_destroy": [_vp],
@@ -395,6 +398,40 @@ class Hamiltonian:
                                         int(checkpoint_every), int(max_iter), float(gtol), C.byref(J),
                                         _ptr(hist), C.byref(it), C.byref(ev), _stream(stream)))
         return e, float(J.value), hist[:it.value + 1], int(it.value), int(ev.value)
+
+    def control_optimize_basis(self, psi0, target, basis, u, dt: float, scheme: int = ETRS, nsub: int = 1,
+                               dir=(1.0, 0.0, 0.0), checkpoint_every: int = 50, max_iter: int = 50,
+                               gtol: float = 1e-8, stream=None):
+        """Maximise J over the coefficients u of eps = basis @ u
+        (rsg_control_optimize_basis; basis of shape (nsteps, nparam)).
+        Returns (u (numpy), J, J history, accepted steps, evaluations)."""
+        for t in (psi0, target):
+            if not (t.is_cuda and t.dtype == self.dtype and t.numel() == self.mesh.P
+                    and t.is_contiguous()):
+                raise ValueError("psi0/target: contiguous cuda vectors of P values")
+        B = _np(basis, np.float64)
+        if B.ndim != 2:
+            raise ValueError("basis: (nsteps, nparam)")
+        x = _np(u, np.float64).copy()
+        if x.shape != (B.shape[1],):
+            raise ValueError("u: nparam values")
+        d = _np(dir, np.float64)
+        hist = np.zeros(int(max_iter) + 1)
+        J = C.c_double()
+        it, ev = C.c_int64(), C.c_int64()
+        _ck(load().rsg_control_optimize_basis(self._h, C.c_void_p(psi0.data_ptr()), C.c_void_p(target.data_ptr()),
+                                              B.shape[0], float(dt), int(scheme), int(nsub), B.shape[1], _ptr(B),
+                                              _ptr(x), _ptr(d), int(checkpoint_every), int(max_iter), float(gtol),
+                                              C.byref(J), _ptr(hist), C.byref(it), C.byref(ev), _stream(stream)))
+        return x, float(J.value), hist[:it.value + 1], int(it.value), int(ev.value)
+
+
+def fourier_basis(nsteps: int, nparam: int) -> np.ndarray:
+    """Sine-series basis sin(m pi t / T) at the interval midpoints,
+    shape (nsteps, nparam) (rsg_fourier_basis)."""
+    B = np.zeros((int(nsteps), int(nparam)))
+    _ck(load().rsg_fourier_basis(int(nsteps), int(nparam), _ptr(B)))
+    return B
 
 
 class ControlObjective(torch.autograd.Function):

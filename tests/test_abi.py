@@ -147,3 +147,30 @@ def test_complex_scaling_argument_errors(lib):
     vt[5] = np.inf
     assert lib.rsg_complex_scaling_set(H._h, 0.3, p, 0) == -1
     assert b"not finite" in lib.rsg_last_error()
+
+
+def test_fourier_basis(lib):
+    """Sine series at interval midpoints: the discrete sine transform's
+    orthogonality (sum_k s_m s_m' = n/2 delta) and the field's zeros at the
+    ends of [0, T] (values at the first and last midpoints shrink as
+    sin(m pi / 2n))."""
+    n, M = 40, 7
+    B = rsg.fourier_basis(n, M)
+    assert B.shape == (n, M)
+    assert np.abs(B.T @ B - 0.5 * n * np.eye(M)).max() < 1e-12
+    for m in range(1, M + 1):
+        assert abs(abs(B[0, m - 1]) - np.sin(m * np.pi / (2 * n))) < 1e-13
+        assert abs(abs(B[-1, m - 1]) - np.sin(m * np.pi / (2 * n))) < 1e-13
+    assert lib.rsg_fourier_basis(0, 3, B.ctypes.data_as(C.c_void_p)) == -1
+    assert lib.rsg_fourier_basis(4, 0, B.ctypes.data_as(C.c_void_p)) == -1
+    assert lib.rsg_fourier_basis(4, 3, None) == -1
+    m = rsg.Mesh(rsg.CUBE, 6, spacing=0.3)
+    H = rsg.Hamiltonian(m, torch.complex128)
+    u = np.zeros(3)
+    J = C.c_double()
+    # NULL basis, nparam < 1 (both before any device work)
+    assert lib.rsg_control_optimize_basis(H._h, None, None, 4, 0.05, 1, 1, 3, None, u.ctypes.data_as(C.c_void_p),
+                                          None, 50, 5, 1e-8, C.byref(J), None, None, None, None) == -1
+    assert lib.rsg_control_optimize_basis(H._h, None, None, 4, 0.05, 1, 1, 0, B.ctypes.data_as(C.c_void_p),
+                                          u.ctypes.data_as(C.c_void_p), None, 50, 5, 1e-8, C.byref(J), None, None,
+                                          None, None) == -1
