@@ -224,6 +224,22 @@ def extras(mesh, wells, proj, g):
                      "unit": UNIT}
         del psi, H
         torch.cuda.empty_cache()
+    # complex scaling on the headline mesh: the same wells at r e^{0.3 i}, no
+    # projectors (refused while scaling is set), 64 complex64 states, ETRS
+    from workloads import potential_wells_scaled
+    Hz = rsg.Hamiltonian(mesh, torch.complex64)
+    Hz.set_complex_scaling(0.3, potential_wells_scaled(mesh.xyz, *wells, 0.3))
+    psi = torch.from_numpy(white_noise_states(g, P, S, dtype=np.complex64)).cuda()
+    Hz.profile(True)
+    ms = time_steps(Hz, psi, 2, lambda x: Hz.propagate(x, 1, 0.01, scheme=rsg.ETRS, want_drift=False))
+    kms, kn, kbytes, _ = Hz.kernel_stats()
+    Hz.profile(False)
+    out["complex_scaling_c64"] = {"ms_per_step": ms, "value": P * S * N_APPLY_PER_STEP / (ms * 1e-3) / 1e9,
+                                  "unit": UNIT, "kernel": "k_apply_scaled",
+                                  "kernel_GBps": kbytes / (kms * 1e-3) / 1e9 if kms > 0 else None,
+                                  "workload": "sphere R=18 h=0.2, 32 wells at r e^{0.3i}, 64 states, ETRS dt=0.01"}
+    del psi, Hz
+    torch.cuda.empty_cache()
     # batch of 256 uneven systems (cubes 24^3..96^3 at h = 0.25, 1..16 states,
     # 1..8 atoms x 4 projectors): one launch per Horner stage for all systems
     from workloads import batch_systems, gaussian_wells

@@ -95,3 +95,19 @@ def test_paper_1d_example_lowest_resonance():
     assert np.all(np.abs(stable[:2].imag) < 1e-6) and np.all(stable[:2].real < 0)
     r = stable[2]
     assert 0 < r.real < 1 and -1e-4 < r.imag < -1e-6, r
+
+
+def test_rotated_wells_generator():
+    """workloads.potential_wells_scaled: theta = 0 gives the real wells, and
+    for small theta v(r e^{i theta}) = v(r) + i theta r.grad v(r) + O(theta^2)."""
+    from workloads import gaussian_wells, potential_wells, potential_wells_scaled, rng
+    g = rng(40)
+    c, d, w = gaussian_wells(g, 5, 2.0)
+    xyz = g.uniform(-3, 3, size=(200, 3))
+    assert np.abs(potential_wells_scaled(xyz, c, d, w, 0.0) - potential_wells(xyz, c, d, w)).max() < 1e-15
+    t, dx = 1e-4, 1e-6
+    v = potential_wells(xyz, c, d, w)
+    rgrad = (potential_wells(xyz * (1 + dx), c, d, w) - potential_wells(xyz * (1 - dx), c, d, w)) / (2 * dx)
+    want = v + 1j * t * rgrad
+    got = potential_wells_scaled(xyz, c, d, w, t)
+    assert np.abs(got - want).max() < 1e-7 * max(1.0, np.abs(v).max())

@@ -91,6 +91,18 @@ def potential_wells(xyz: np.ndarray, centres, depths, widths) -> np.ndarray:
     return v
 
 
+def potential_wells_scaled(xyz: np.ndarray, centres, depths, widths, theta: float) -> np.ndarray:
+    """The Gaussian wells of potential_wells at the rotated coordinates
+    r e^{i theta} (complex values; the square |r e^{i theta} - R|^2 taken
+    without conjugation, as the analytic continuation requires)."""
+    z = np.asarray(xyz, dtype=np.float64) * np.exp(1j * theta)
+    v = np.zeros(z.shape[0], dtype=np.complex128)
+    for c, d, w in zip(centres, depths, widths):
+        dz = z - np.asarray(c, dtype=np.float64)
+        v -= d * np.exp(-np.einsum("pi,pi->p", dz, dz) / (2.0 * w * w))
+    return v
+
+
 def _uniform_ball(g: np.random.Generator, n: int, radius: float) -> np.ndarray:
     out = np.empty((n, 3))
     k = 0
