@@ -67,6 +67,7 @@ def _load():
         L.orc_ham_new.argtypes = [vp, vp]
         L.orc_ham_free.argtypes = [vp]
         L.orc_ham_set_projectors.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
+        L.orc_ham_set_projectors_raw.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
         L.orc_ham_atom_npoints.restype = i64
         L.orc_ham_atom_npoints.argtypes = [vp, C.c_int]
         L.orc_ham_atom_nproj.restype = C.c_int
@@ -173,6 +174,21 @@ class Hamiltonian:
                                                      for h in hmats]) if n else np.zeros(1))
         _load().orc_ham_set_projectors(self._h, n, _p(centres), _p(rcut), _p(lmax), _p(beta),
                                        _p(hflat))
+        self.natoms = n
+
+    def set_projectors_raw(self, points, values, hmats):
+        """Projectors as sampled values: per atom the point indices (n_a,),
+        values (n_a, nproj_a) and the matrix h_a (orc_ham_set_projectors_raw)."""
+        n = len(points)
+        npts = np.array([len(p) for p in points], dtype=np.int64)
+        vals = [np.asarray(v, dtype=np.float64).reshape(len(p), -1) for p, v in zip(points, values)]
+        nproj = np.array([v.shape[1] for v in vals], dtype=np.int32)
+        pidx = np.ascontiguousarray(np.concatenate([np.asarray(p, np.int64) for p in points]) if n
+                                    else np.zeros(1, np.int64))
+        pv = np.ascontiguousarray(np.concatenate([v.ravel() for v in vals]) if n else np.zeros(1))
+        hflat = np.ascontiguousarray(np.concatenate([np.asarray(h, dtype=np.float64).ravel() for h in hmats])
+                                     if n else np.zeros(1))
+        _load().orc_ham_set_projectors_raw(self._h, n, _p(npts), _p(pidx), _p(nproj), _p(pv), _p(hflat))
         self.natoms = n
 
     def atom(self, a: int):

@@ -320,6 +320,37 @@ void orc_ham_set_projectors(void *hv, int natoms, const double *centres,
     }
 }
 
+/* The same non-local term from projector values the caller has sampled:
+ * atom a covers npts[a] mesh points point_idx[...] (concatenated over
+ * atoms) with nproj[a] values per point (pvals, point-major), taken as
+ * given, and the nproj x nproj coupling matrix h_a (concatenated). */
+void orc_ham_set_projectors_raw(void *hv, int natoms, const int64_t *npts, const int64_t *point_idx,
+                                const int32_t *nproj, const double *pvals, const double *hmats)
+{
+    orc_ham *H = (orc_ham *)hv;
+    free_atoms(H);
+    H->natoms = natoms;
+    H->atoms = (orc_atom *)calloc(natoms ? natoms : 1, sizeof(orc_atom));
+    int64_t off = 0, voff = 0, hoff = 0;
+    for (int a = 0; a < natoms; a++) {
+        orc_atom *A = &H->atoms[a];
+        int64_t n = npts[a];
+        A->npts = n;
+        A->nproj = nproj[a];
+        A->pt = (int64_t *)malloc(sizeof(int64_t) * (n ? n : 1));
+        A->p = (double *)malloc(sizeof(double) * A->nproj * (n ? n : 1));
+        for (int64_t k = 0; k < n; k++) {
+            A->pt[k] = point_idx[off + k];
+            for (int i = 0; i < A->nproj; i++) A->p[i * n + k] = pvals[voff + k * A->nproj + i];
+        }
+        A->hm = (double *)malloc(sizeof(double) * A->nproj * A->nproj);
+        memcpy(A->hm, hmats + hoff, sizeof(double) * A->nproj * A->nproj);
+        off += n;
+        voff += n * A->nproj;
+        hoff += (int64_t)A->nproj * A->nproj;
+    }
+}
+
 int64_t orc_ham_atom_npoints(void *hv, int a) { return ((orc_ham *)hv)->atoms[a].npts; }
 int orc_ham_atom_nproj(void *hv, int a) { return ((orc_ham *)hv)->atoms[a].nproj; }
 

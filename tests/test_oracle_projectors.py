@@ -108,3 +108,46 @@ def test_projectors_act_linearly_on_state_blocks():
     lin = H.apply(psi @ np.array([[1.0], [2.0 - 1j], [0.5j]]))
     assert np.abs(lin.ravel() - blk @ np.array([1.0, 2.0 - 1j, 0.5j])).max() < 1e-11 * np.abs(blk).max()
     _ = wdot  # keep the helper import used across the suite
+
+
+def test_raw_projectors_reproduce_the_sampled_set():
+    """Feeding the oracle's own sampled projectors back as raw values gives
+    the same operator."""
+    m = oracle.Mesh(oracle.SPHERE, radius=2.5, h=0.3)
+    g = rng(41)
+    V = g.standard_normal(m.P)
+    Ha = oracle.Hamiltonian(m, V)
+    hm = [np.diag(g.uniform(-1, 1, 4)), np.diag(g.uniform(-1, 1, 9))]
+    Ha.set_projectors([[0.2, -0.1, 0.3], [-0.6, 0.5, -0.2]], [1.3, 1.6], [1, 2], [0.33, 0.4], hm)
+    pts, vals = zip(*(Ha.atom(a) for a in range(2)))
+    Hr = oracle.Hamiltonian(m, V)
+    Hr.set_projectors_raw(list(pts), [v.T for v in vals], hm)
+    psi = white_noise_states(g, m.P, 3)
+    assert np.abs(Ha.apply(psi) - Hr.apply(psi)).max() == 0.0
+
+
+def test_raw_projectors_spectrum_from_small_problem():
+    """Arbitrary sampled projectors on scattered point sets: the non-local
+    operator h^3 sum_a P_a h_a P_a^T is real symmetric with rank
+    sum nproj_a, and (disjoint supports) its nonzero eigenvalues are those of
+    the small problems h_a G_a, G_a = h^3 P_a^T P_a (similar matrices)."""
+    m = oracle.Mesh(oracle.CUBE, 6, h=0.4)
+    g = rng(42)
+    perm = g.permutation(m.P)
+    sets = [np.sort(perm[:40]), np.sort(perm[40:95])]
+    vals = [g.standard_normal((40, 3)), g.standard_normal((55, 2))]
+    hs = []
+    for k in (3, 2):
+        A = g.standard_normal((k, k))
+        hs.append(A + A.T)
+    H0 = oracle.Hamiltonian(m, np.zeros(m.P))
+    H1 = oracle.Hamiltonian(m, np.zeros(m.P))
+    H1.set_projectors_raw(sets, vals, hs)
+    D = dense_h(H1, m.P) - dense_h(H0, m.P)
+    assert np.abs(D.imag).max() == 0.0 and np.abs(D - D.T).max() < 1e-13 * np.abs(D).max()
+    w = np.linalg.eigvalsh(D.real)
+    big = np.sort(w[np.abs(w) > 1e-9 * np.abs(w).max()])
+    assert len(big) == 5
+    h3 = m.h ** 3
+    small = np.sort(np.concatenate([np.linalg.eigvals(hh @ (h3 * v.T @ v)).real for hh, v in zip(hs, vals)]))
+    assert np.abs(big - small).max() < 1e-10 * np.abs(small).max(), (big, small)
