@@ -108,6 +108,23 @@ rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres,
                               const double *rcut, const int32_t *lmax,
                               const double *beta, const double *hmats);
 
+/* Separable projectors given as values (the same non-local term,
+ * sum_a sum_ij |p_ai> h_a,ij <p_aj|, for projectors the caller samples
+ * itself, e.g. from a pseudopotential table).  Atom a covers npts[a] mesh
+ * points: point_idx (concatenated over atoms, library point order, each
+ * point at most once per atom) and, for each of them in the same order,
+ * nproj[a] values (pvals, concatenated, point-major: value i of the k-th
+ * point of atom a at offset_a + k * nproj[a] + i).  The values are used as
+ * given (no normalisation); hmats as in rsg_projectors_set (nproj x nproj
+ * per atom, symmetric to 1e-12 of its largest entry).  Host arrays, copied;
+ * replaces any projector set; natoms = 0 removes all projectors.
+ * Errors: RSG_ERR_ARG for a NULL array, nproj < 1, npts < 0, a point index
+ * outside the mesh or repeated within an atom, a non-finite value or an
+ * asymmetric h; RSG_ERR_UNSUPPORTED for nproj > 9 or while complex scaling
+ * is set. */
+rsg_status rsg_projectors_set_raw(rsg_ham H, int natoms, const int64_t *npts, const int64_t *point_idx,
+                                  const int32_t *nproj, const double *pvals, const double *hmats);
+
 /* Static dipole field eps * (dir . r) used by rsg_hamiltonian_apply and
  * rsg_taylor_apply (default 0).  dir may be NULL when eps = 0. */
 rsg_status rsg_field_set(rsg_ham H, double eps, const double dir[3]);

@@ -954,6 +954,84 @@ rsg_status rsg_field_set(rsg_ham H, double eps, const double dir[3]) {
     return RSG_OK;
 }
 
+// Device tables of a projector set from its entry list: entry q is point
+// q_pt[q] of atom q_atom[q] with the npmax values q_p[q * npmax + i]; the
+// entries of each atom are contiguous and cut into chunks of at most kChunk
+// (ch_atom, ch_q0, ch_q1; atom_ch0 = per-atom prefix of chunks); hm holds the
+// zero-padded npmax x npmax coupling matrices.
+static rsg_status upload_projectors(rsg_ham H, int natoms, int npmax, const std::vector<int32_t> &q_pt,
+                                    const std::vector<int32_t> &q_atom, const std::vector<double> &q_p,
+                                    const std::vector<int32_t> &ch_atom, const std::vector<int32_t> &ch_q0,
+                                    const std::vector<int32_t> &ch_q1, const std::vector<int32_t> &atom_ch0,
+                                    const std::vector<double> &hm) {
+    rsg_mesh m = H->m;
+    // point-centric CSR of entries (for the fused scatter in the epilogue)
+    const int64_t P = m->P;
+    std::vector<int32_t> nl_ptr((size_t)P + 1, 0), nl_ent(q_pt.size());
+    for (int32_t p : q_pt) nl_ptr[(size_t)p + 1]++;
+    for (int64_t p = 0; p < P; p++) nl_ptr[(size_t)p + 1] += nl_ptr[(size_t)p];
+    {
+        std::vector<int32_t> fill(nl_ptr.begin(), nl_ptr.end() - 1);
+        for (size_t q = 0; q < q_pt.size(); q++) nl_ent[(size_t)fill[(size_t)q_pt[q]]++] = (int32_t)q;
+    }
+    CK(H->q_pt.upload(q_pt));
+    CK(H->q_atom.upload(q_atom));
+    if (H->dtype == RSG_C64)
+        CK(H->q_p.upload(cast_vec<float>(q_p)));
+    else
+        CK(H->q_p.upload(q_p));
+    CK(H->ch_atom.upload(ch_atom));
+    CK(H->ch_q0.upload(ch_q0));
+    CK(H->ch_q1.upload(ch_q1));
+    CK(H->atom_ch0.upload(atom_ch0));
+    CK(H->hm.upload(hm));
+    CK(H->nl_ptr.upload(nl_ptr));
+    CK(H->nl_ent.upload(nl_ent));
+    std::vector<int32_t> u_pts, u_ptr(1, 0);
+    for (int64_t p = 0; p < P; p++)
+        if (nl_ptr[(size_t)p + 1] > nl_ptr[(size_t)p]) {
+            u_pts.push_back((int32_t)p);
+            u_ptr.push_back(nl_ptr[(size_t)p + 1]);
+        }
+    CK(H->u_pts.upload(u_pts));
+    CK(H->u_ptr.upload(u_ptr));
+    // point-major copies of each entry's atom and projector values, so the
+    // scatter reads them without going through the entry index
+    std::vector<int32_t> e_atom(nl_ent.size());
+    std::vector<double> e_p(nl_ent.size() * (size_t)std::max(npmax, 1));
+    for (size_t e = 0; e < nl_ent.size(); e++) {
+        const size_t q = (size_t)nl_ent[e];
+        e_atom[e] = q_atom[q];
+        for (int i = 0; i < npmax; i++) e_p[e * npmax + i] = q_p[q * npmax + i];
+    }
+    CK(H->e_atom.upload(e_atom));
+    if (H->dtype == RSG_C64)
+        CK(H->e_p.upload(cast_vec<float>(e_p)));
+    else
+        CK(H->e_p.upload(e_p));
+    ProjDev &pj = H->pj;
+    pj.natoms = natoms;
+    pj.npmax = npmax;
+    pj.nq = (int64_t)q_pt.size();
+    pj.nchunks = (int)ch_q0.size();
+    pj.q_pt = H->q_pt.as<int32_t>();
+    pj.q_atom = H->q_atom.as<int32_t>();
+    pj.q_p = H->q_p.p;
+    pj.chunk_atom = H->ch_atom.as<int32_t>();
+    pj.chunk_q0 = H->ch_q0.as<int32_t>();
+    pj.chunk_q1 = H->ch_q1.as<int32_t>();
+    pj.atom_chunk0 = H->atom_ch0.as<int32_t>();
+    pj.hm = H->hm.as<double>();
+    pj.nl_ptr = H->nl_ptr.as<int32_t>();
+    pj.nl_ent = H->nl_ent.as<int32_t>();
+    pj.nu = (int)u_pts.size();
+    pj.u_pts = H->u_pts.as<int32_t>();
+    pj.u_ptr = H->u_ptr.as<int32_t>();
+    pj.e_atom = H->e_atom.as<int32_t>();
+    pj.e_p = H->e_p.p;
+    return RSG_OK;
+}
+
 rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres, const double *rcut,
                               const int32_t *lmax, const double *beta, const double *hmats) {
     if (!H) return fail(RSG_ERR_ARG, "NULL handle");
@@ -1023,70 +1101,96 @@ rsg_status rsg_projectors_set(rsg_ham H, int natoms, const double *centres, cons
             }
         hoff += (int64_t)np * np;
     }
-    // point-centric CSR of entries (for the fused scatter in the epilogue)
-    const int64_t P = m->P;
-    std::vector<int32_t> nl_ptr((size_t)P + 1, 0), nl_ent(q_pt.size());
-    for (int32_t p : q_pt) nl_ptr[(size_t)p + 1]++;
-    for (int64_t p = 0; p < P; p++) nl_ptr[(size_t)p + 1] += nl_ptr[(size_t)p];
-    {
-        std::vector<int32_t> fill(nl_ptr.begin(), nl_ptr.end() - 1);
-        for (size_t q = 0; q < q_pt.size(); q++) nl_ent[(size_t)fill[(size_t)q_pt[q]]++] = (int32_t)q;
+    return upload_projectors(H, natoms, npmax, q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm);
+}
+
+rsg_status rsg_projectors_set_raw(rsg_ham H, int natoms, const int64_t *npts, const int64_t *point_idx,
+                                  const int32_t *nproj, const double *pvals, const double *hmats) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    if (natoms < 0) return fail(RSG_ERR_ARG, "natoms < 0");
+    if (natoms > 0 && H->has_scaling) return fail(RSG_ERR_UNSUPPORTED, "complex scaling is set: no projectors");
+    if (natoms == 0) {
+        H->pj = ProjDev();
+        H->proj_norm = 0.0;
+        return RSG_OK;
     }
-    CK(H->q_pt.upload(q_pt));
-    CK(H->q_atom.upload(q_atom));
-    if (H->dtype == RSG_C64)
-        CK(H->q_p.upload(cast_vec<float>(q_p)));
-    else
-        CK(H->q_p.upload(q_p));
-    CK(H->ch_atom.upload(ch_atom));
-    CK(H->ch_q0.upload(ch_q0));
-    CK(H->ch_q1.upload(ch_q1));
-    CK(H->atom_ch0.upload(atom_ch0));
-    CK(H->hm.upload(hm));
-    CK(H->nl_ptr.upload(nl_ptr));
-    CK(H->nl_ent.upload(nl_ent));
-    std::vector<int32_t> u_pts, u_ptr(1, 0);
-    for (int64_t p = 0; p < P; p++)
-        if (nl_ptr[(size_t)p + 1] > nl_ptr[(size_t)p]) {
-            u_pts.push_back((int32_t)p);
-            u_ptr.push_back(nl_ptr[(size_t)p + 1]);
+    if (!npts || !point_idx || !nproj || !pvals || !hmats) return fail(RSG_ERR_ARG, "NULL array");
+    const int64_t P = H->m->P;
+    int npmax = 1;
+    int64_t nq = 0;
+    for (int a = 0; a < natoms; a++) {
+        if (nproj[a] < 1) return fail(RSG_ERR_ARG, "nproj[%d] < 1", a);
+        if (nproj[a] > 9) return fail(RSG_ERR_UNSUPPORTED, "at most 9 projectors per atom");
+        if (npts[a] < 0) return fail(RSG_ERR_ARG, "npts[%d] < 0", a);
+        npmax = std::max(npmax, (int)nproj[a]);
+        nq += npts[a];
+    }
+    if (nq >= (int64_t)INT32_MAX) return fail(RSG_ERR_UNSUPPORTED, "more than 2^31 projector entries");
+    std::vector<int32_t> q_pt, q_atom, ch_atom, ch_q0, ch_q1, atom_ch0(1, 0);
+    std::vector<double> q_p, hm((size_t)natoms * npmax * npmax, 0.0);
+    q_pt.reserve((size_t)nq);
+    q_atom.reserve((size_t)nq);
+    q_p.reserve((size_t)nq * npmax);
+    double proj_norm = 0.0;
+    int64_t off = 0, voff = 0, hoff = 0;
+    std::vector<int64_t> order;
+    std::vector<char> seen((size_t)P, 0);
+    for (int a = 0; a < natoms; a++) {
+        const int np = nproj[a];
+        const int64_t n = npts[a];
+        // entries in ascending point order (coalesced gathers); a point may
+        // appear once per atom
+        order.resize((size_t)n);
+        for (int64_t k = 0; k < n; k++) {
+            const int64_t pt = point_idx[off + k];
+            if (pt < 0 || pt >= P) return fail(RSG_ERR_ARG, "atom %d: point index %lld outside the mesh", a,
+                                               (long long)pt);
+            order[(size_t)k] = k;
         }
-    CK(H->u_pts.upload(u_pts));
-    CK(H->u_ptr.upload(u_ptr));
-    // point-major copies of each entry's atom and projector values, so the
-    // scatter reads them without going through the entry index
-    std::vector<int32_t> e_atom(nl_ent.size());
-    std::vector<double> e_p(nl_ent.size() * (size_t)std::max(npmax, 1));
-    for (size_t e = 0; e < nl_ent.size(); e++) {
-        const size_t q = (size_t)nl_ent[e];
-        e_atom[e] = q_atom[q];
-        for (int i = 0; i < npmax; i++) e_p[e * npmax + i] = q_p[q * npmax + i];
+        std::sort(order.begin(), order.end(),
+                  [&](int64_t x, int64_t y) { return point_idx[off + x] < point_idx[off + y]; });
+        const size_t q_begin = q_pt.size();
+        for (int64_t k : order) {
+            const int64_t pt = point_idx[off + k];
+            if (seen[(size_t)pt]) return fail(RSG_ERR_ARG, "atom %d: point %lld listed twice", a, (long long)pt);
+            seen[(size_t)pt] = 1;
+            q_pt.push_back((int32_t)pt);
+            q_atom.push_back(a);
+            for (int i = 0; i < npmax; i++) {
+                const double v = i < np ? pvals[voff + k * np + i] : 0.0;
+                if (!std::isfinite(v)) return fail(RSG_ERR_ARG, "atom %d: projector value not finite", a);
+                q_p.push_back(v);
+            }
+        }
+        for (size_t q = q_begin; q < q_pt.size(); q++) seen[(size_t)q_pt[q]] = 0;
+        const size_t q_end = q_pt.size();
+        for (size_t q0 = q_begin; q0 < q_end; q0 += kChunk) {
+            ch_atom.push_back(a);
+            ch_q0.push_back((int32_t)q0);
+            ch_q1.push_back((int32_t)std::min(q_end, q0 + kChunk));
+        }
+        atom_ch0.push_back((int32_t)ch_q0.size());
+        double hmax = 0.0;
+        for (int i = 0; i < np * np; i++) {
+            if (!std::isfinite(hmats[hoff + i])) return fail(RSG_ERR_ARG, "atom %d: h not finite", a);
+            hmax = std::max(hmax, std::fabs(hmats[hoff + i]));
+        }
+        for (int i = 0; i < np; i++)
+            for (int j = 0; j < np; j++) {
+                const double hij = hmats[hoff + i * np + j];
+                if (std::fabs(hij - hmats[hoff + j * np + i]) > 1e-12 * hmax)
+                    return fail(RSG_ERR_ARG, "atom %d: h is not symmetric", a);
+                hm[((size_t)a * npmax + i) * npmax + j] = hij;
+                proj_norm += std::fabs(hij);
+            }
+        off += n;
+        voff += n * np;
+        hoff += (int64_t)np * np;
     }
-    CK(H->e_atom.upload(e_atom));
-    if (H->dtype == RSG_C64)
-        CK(H->e_p.upload(cast_vec<float>(e_p)));
-    else
-        CK(H->e_p.upload(e_p));
-    ProjDev &pj = H->pj;
-    pj.natoms = natoms;
-    pj.npmax = npmax;
-    pj.nq = (int64_t)q_pt.size();
-    pj.nchunks = (int)ch_q0.size();
-    pj.q_pt = H->q_pt.as<int32_t>();
-    pj.q_atom = H->q_atom.as<int32_t>();
-    pj.q_p = H->q_p.p;
-    pj.chunk_atom = H->ch_atom.as<int32_t>();
-    pj.chunk_q0 = H->ch_q0.as<int32_t>();
-    pj.chunk_q1 = H->ch_q1.as<int32_t>();
-    pj.atom_chunk0 = H->atom_ch0.as<int32_t>();
-    pj.hm = H->hm.as<double>();
-    pj.nl_ptr = H->nl_ptr.as<int32_t>();
-    pj.nl_ent = H->nl_ent.as<int32_t>();
-    pj.nu = (int)u_pts.size();
-    pj.u_pts = H->u_pts.as<int32_t>();
-    pj.u_ptr = H->u_ptr.as<int32_t>();
-    pj.e_atom = H->e_atom.as<int32_t>();
-    pj.e_p = H->e_p.p;
+    H->pj = ProjDev();
+    H->proj_norm = 0.0;
+    CKS(upload_projectors(H, natoms, npmax, q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm));
+    H->proj_norm = proj_norm;
     return RSG_OK;
 }
 

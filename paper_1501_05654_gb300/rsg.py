@@ -44,6 +44,7 @@ SIGNATURES = {
     "rsg_propagate_steps": [_vp, _vp, _i64, _i64, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp],
     "rsg_orthonormalize": [_vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_absorber_set": [_vp, _vp, _int],
+    "rsg_projectors_set_raw": [_vp, _int, _vp, _vp, _vp, _vp, _vp],
     "rsg_complex_scaling_set": [_vp, _dbl, _vp, _int],
     "rsg_shifted_solve": [_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _i64, _dbl, _vp, _vp, _vp],
     "rsg_eigensolve": [_vp, _vp, _i64, _i64, _i64, _i64, _int, _dbl, _vp, _vp, _vp, _vp],
@@ -186,6 +187,23 @@ class Hamiltonian:
                     if n else np.zeros(1), np.float64)
         _ck(load().rsg_projectors_set(self._h, n, _ptr(centres), _ptr(rcut), _ptr(lmax),
                                       _ptr(beta), _ptr(hflat)))
+
+    def set_projectors_raw(self, points, values, hmats):
+        """Projectors as sampled values (rsg_projectors_set_raw): per atom a
+        list of library point indices (n_a,), values of shape (n_a, nproj_a)
+        and the nproj_a x nproj_a matrix h_a."""
+        n = len(points)
+        if not (len(values) == n and len(hmats) == n):
+            raise ValueError("points, values and hmats: one entry per atom")
+        npts = np.array([len(p) for p in points], dtype=np.int64)
+        vals = [np.asarray(v, np.float64).reshape(len(p), -1) for p, v in zip(points, values)]
+        nproj = np.array([v.shape[1] for v in vals], dtype=np.int32)
+        pidx = _np(np.concatenate([np.asarray(p, np.int64) for p in points]) if n else np.zeros(1), np.int64)
+        pv = _np(np.concatenate([v.ravel() for v in vals]) if n else np.zeros(1), np.float64)
+        hflat = _np(np.concatenate([np.asarray(h, np.float64).ravel() for h in hmats]) if n else np.zeros(1),
+                    np.float64)
+        _ck(load().rsg_projectors_set_raw(self._h, n, _ptr(npts), _ptr(pidx), _ptr(nproj), _ptr(pv),
+                                          _ptr(hflat)))
 
     def set_field(self, eps: float, dir=(1.0, 0.0, 0.0)):
         d = _np(dir, np.float64)

@@ -174,3 +174,31 @@ def test_fourier_basis(lib):
     assert lib.rsg_control_optimize_basis(H._h, None, None, 4, 0.05, 1, 1, 0, B.ctypes.data_as(C.c_void_p),
                                           u.ctypes.data_as(C.c_void_p), None, 50, 5, 1e-8, C.byref(J), None, None,
                                           None, None) == -1
+
+
+def test_raw_projector_argument_errors(lib):
+    """rsg_projectors_set_raw validates everything before any device work."""
+    m = rsg.Mesh(rsg.CUBE, 6, spacing=0.3)
+    H = rsg.Hamiltonian(m, torch.complex128)
+
+    def call(pts, vals, nproj, hm):
+        npts = np.array([len(pts)], dtype=np.int64)
+        pi = np.asarray(pts, dtype=np.int64)
+        pv = np.asarray(vals, dtype=np.float64).ravel()
+        npj = np.array([nproj], dtype=np.int32)
+        hf = np.asarray(hm, dtype=np.float64).ravel()
+        return lib.rsg_projectors_set_raw(H._h, 1, npts.ctypes.data_as(C.c_void_p), pi.ctypes.data_as(C.c_void_p),
+                                          npj.ctypes.data_as(C.c_void_p), pv.ctypes.data_as(C.c_void_p),
+                                          hf.ctypes.data_as(C.c_void_p))
+
+    assert lib.rsg_projectors_set_raw(H._h, 1, None, None, None, None, None) == -1
+    assert call([0, 1, 1], np.ones(3), 1, [1.0]) == -1
+    assert b"twice" in lib.rsg_last_error()
+    assert call([0, m.P], np.ones(2), 1, [1.0]) == -1
+    assert b"outside" in lib.rsg_last_error()
+    assert call([0, 1], np.ones(20), 10, np.eye(10)) == -4
+    assert call([0, 1], np.ones(4), 2, [[1.0, 0.5], [0.4, 1.0]]) == -1
+    assert b"symmetric" in lib.rsg_last_error()
+    assert call([0, 1], [1.0, np.inf], 1, [1.0]) == -1
+    assert call([0, 1], np.ones(2), 0, [1.0]) == -1
+    assert lib.rsg_projectors_set_raw(H._h, 0, None, None, None, None, None) == 0
