@@ -81,7 +81,7 @@ def peaks():
 # stencil kernel of each "kernel" option value (rsg_ham_get_option "last_kernel")
 KERNEL_NAMES = {0: "k_apply_staged", 1: "k_apply_naive", 2: "k_apply_zmarch", 3: "k_apply_tma",
                 4: "k_apply_rowtma", 5: "k_apply_quad"}
-KERNEL_SOURCES = ("rsg_kernels.cu", "rsg_quad.cu", "rsg_vec.cuh", "rsg_async.cuh", "rsg_batch.cuh")
+KERNEL_SOURCES = ("rsg_kernels.cu", "rsg_quad.cu", "rsg_vec.cuh", "rsg_async.cuh", "rsg_batch.cuh", "rsg_internal.h")
 
 
 def traffic_record(kernel_src_hash, kernel_name):
@@ -234,8 +234,10 @@ def extras(mesh, wells, proj, g):
     ms = time_steps(Hz, psi, 2, lambda x: Hz.propagate(x, 1, 0.01, scheme=rsg.ETRS, want_drift=False))
     kms, kn, kbytes, _ = Hz.kernel_stats()
     Hz.profile(False)
+    zk = Hz.get_option("last_kernel")
     out["complex_scaling_c64"] = {"ms_per_step": ms, "value": P * S * N_APPLY_PER_STEP / (ms * 1e-3) / 1e9,
-                                  "unit": UNIT, "kernel": "k_apply_scaled",
+                                  "unit": UNIT,
+                                  "kernel": "k_apply_quad (complex diagonal)" if zk == 5 else "k_apply_scaled",
                                   "kernel_GBps": kbytes / (kms * 1e-3) / 1e9 if kms > 0 else None,
                                   "workload": "sphere R=18 h=0.2, 32 wells at r e^{0.3i}, 64 states, ETRS dt=0.01"}
     del psi, Hz

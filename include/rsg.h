@@ -220,8 +220,11 @@ rsg_status rsg_absorber_set(rsg_ham H, const double *mask, int mask_on_device);
  * rsg_eigensolve, rsg_control_gradient, rsg_control_optimize and
  * rsg_batch_create return RSG_ERR_UNSUPPORTED, as do rsg_projectors_set
  * with atoms and rsg_field_set or rsg_propagate_steps with a nonzero field
- * (and this call, while either is set).  Applications run the stencil
- * kernel 6 (one thread per point and 16-byte vector).
+ * (and this call, while either is set).  complex64 applications with the
+ * default kernel run the register-blocked stencil (kernel 5) with the
+ * complex diagonal v_theta e^{2i theta} and e^{-2i theta} folded into the
+ * output scaling; otherwise they run kernel 6 (one thread per point and
+ * 16-byte vector).
  * Errors: RSG_ERR_ARG for theta outside [0, pi/4] or a non-finite value. */
 rsg_status rsg_complex_scaling_set(rsg_ham H, double theta, const double *v_theta, int v_on_device);
 

@@ -133,6 +133,7 @@ struct rsg_ham_s {
     DevBuf mask;       // mask absorber M(r) (compute type), applied after each time step
     bool has_mask = false;
     DevBuf vtheta;     // complex scaling: v(r e^{i theta}) per point, interleaved (compute type)
+    DevBuf vtheta_rot; // complex64: v(r e^{i theta}) e^{2i theta}, the register-blocked kernel's diagonal
     bool has_scaling = false;
     double theta = 0.0;
     double xdir_cached[3] = {NAN, NAN, NAN};
@@ -454,8 +455,25 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     const bool split_nl = !H->has_scaling && cfg.kernel != 1 && cfg.kernel != 2 && H->pj.natoms > 0;
     if (H->has_scaling) {
         // complex-scaled operator (no projectors, no field: refused while set)
-        CK(launch_apply_scaled<R>(a, H->vtheta.as<R>(), H->theta, st));
-        H->last_kernel = 6;
+        bool done = false;
+        if constexpr (std::is_same<R, float>::value) {
+            // register-blocked kernel: alpha (lap + v_theta e^{2i theta} u) with
+            // alpha rotated by e^{-2i theta}, without a diagonal constant
+            if (cfg.kernel == 5 && a.f0 == 0.f && a.fx == 0.f && a.fy == 0.f && a.fz == 0.f) {
+                ApplyArgs<R> b = a;
+                b.Vc = H->vtheta_rot.p;
+                b.nl_ptr = nullptr;
+                const double kr = std::cos(2.0 * H->theta), ki = -std::sin(2.0 * H->theta);
+                b.ar = (R)(ep.ar * kr - ep.ai * ki);
+                b.ai = (R)(ep.ar * ki + ep.ai * kr);
+                CK(launch_apply_quad(b, cfg, ntiles, st, &done));
+                if (done) H->last_kernel = 5;
+            }
+        }
+        if (!done) {
+            CK(launch_apply_scaled<R>(a, H->vtheta.as<R>(), H->theta, st));
+            H->last_kernel = 6;
+        }
     } else {
         ApplyArgs<R> b = a;
         if (split_nl) b.nl_ptr = nullptr;
@@ -935,10 +953,19 @@ rsg_status rsg_complex_scaling_set(rsg_ham H, double theta, const double *v_thet
         std::memcpy(hv.data(), v_theta, (size_t)(2 * P) * sizeof(double));
     for (int64_t i = 0; i < 2 * P; i++)
         if (!std::isfinite(hv[(size_t)i])) return fail(RSG_ERR_ARG, "v_theta not finite at %lld", (long long)(i / 2));
-    if (H->dtype == RSG_C64)
+    if (H->dtype == RSG_C64) {
         CK(H->vtheta.upload(cast_vec<float>(hv)));
-    else
+        const double cr = std::cos(2.0 * theta), ci = std::sin(2.0 * theta);
+        std::vector<float> rot((size_t)(2 * P));
+        for (int64_t p = 0; p < P; p++) {
+            const double re = hv[(size_t)(2 * p)], im = hv[(size_t)(2 * p + 1)];
+            rot[(size_t)(2 * p)] = (float)(re * cr - im * ci);
+            rot[(size_t)(2 * p + 1)] = (float)(re * ci + im * cr);
+        }
+        CK(H->vtheta_rot.upload(rot));
+    } else {
         CK(H->vtheta.upload(hv));
+    }
     H->theta = theta;
     H->has_scaling = true;
     return RSG_OK;

@@ -66,6 +66,10 @@ struct ApplyArgs {
     int npmax;
     int64_t P;
     int *err;                // device status word (bounded waits record timeouts)
+    // complex scaling in the register-blocked kernel: the complex diagonal
+    // v_theta e^{2i theta} per point (interleaved); the caller folds the
+    // kinetic rotation e^{-2i theta} into (ar, ai); nullptr otherwise
+    const void *Vc = nullptr;
 };
 
 // Projector tables on the device (entry-major, see rsg_host.cpp).

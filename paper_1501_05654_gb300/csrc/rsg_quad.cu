@@ -22,6 +22,11 @@
 // filled with cp.async (ghost points zero-filled), one block barrier per
 // plane, as in k_apply_staged; the potential of each interior point and the
 // base value of each output travel with the plane that uses them.
+//
+// Complex scaling (CS = true): the diagonal is the complex v_theta e^{2i theta}
+// of each point (staged like V, 8 bytes per point) and the caller folds the
+// kinetic rotation e^{-2i theta} into alpha, so the rest of the kernel is the
+// same.
 #include <cuda.h>
 
 #include "rsg_async.cuh"
@@ -98,7 +103,7 @@ __device__ __forceinline__ void finish_quad(const ApplyArgs<float> &a, int o, fl
 // is written one entry down, so the queue shifts without extra moves and the
 // loop body exists once (no unrolling for register renaming, which kept the
 // code out of the instruction cache).
-template <int NYT, int NS>
+template <int NYT, int NS, bool CS>
 __device__ __forceinline__ void quad_plane(const ApplyArgs<float> &a, const QCtx<NYT> &c, int j,
                                            float2 (&q)[4][9]) {
     using G = QuadGeom<NYT>;
@@ -143,13 +148,27 @@ __device__ __forceinline__ void quad_plane(const ApplyArgs<float> &a, const QCtx
             t = f2_fma(w3, f2_add(m2, p4), t);
             s[2 + dx] = f2_fma(w4, f2_add(m3, p5), t);
         }
-        const float fz = a.fz * (float)p + 3.0f * a.w[0];
-        const float *vv = c.vslots + sl * G::NPTS + c.voff;
+        if constexpr (CS) {
+            // complex diagonal v_theta e^{2i theta} plus the stencil's real
+            // centre weight (no field terms under complex scaling)
+            const float2 *vv = (const float2 *)c.vslots + sl * G::NPTS + c.voff;
+            const float w0 = 3.0f * a.w[0];
 #pragma unroll
-        for (int pt = 0; pt < 4; pt++) {
-            // diagonal: staged V (zero outside the mesh, where the value is zero too)
-            const float d = vv[(pt >> 1) * G::TX + (pt & 1)] + c.fxy[pt] + fz;
-            s[pt] = f2_fma(make_float2(d, d), cen[pt], s[pt]);
+            for (int pt = 0; pt < 4; pt++) {
+                const float2 d = vv[(pt >> 1) * G::TX + (pt & 1)];
+                const float dr = d.x + w0;
+                s[pt] = f2_fma(make_float2(dr, dr), cen[pt], s[pt]);
+                s[pt] = f2_fma(make_float2(-d.y, d.y), make_float2(cen[pt].y, cen[pt].x), s[pt]);
+            }
+        } else {
+            const float fz = a.fz * (float)p + 3.0f * a.w[0];
+            const float *vv = c.vslots + sl * G::NPTS + c.voff;
+#pragma unroll
+            for (int pt = 0; pt < 4; pt++) {
+                // diagonal: staged V (zero outside the mesh, where the value is zero too)
+                const float d = vv[(pt >> 1) * G::TX + (pt & 1)] + c.fxy[pt] + fz;
+                s[pt] = f2_fma(make_float2(d, d), cen[pt], s[pt]);
+            }
         }
     } else {
         // no mesh point in the thread's columns at this plane: nothing to add
@@ -201,15 +220,15 @@ __device__ __forceinline__ void quad_plane(const ApplyArgs<float> &a, const QCtx
 // One block of the register-blocked stencil: tile tl, four-value chunk
 // `chunk` of the system described by a.  Shared by the single-system and
 // batched kernels.
-template <int NYT, int NS, int SYNC>
+template <int NYT, int NS, int SYNC, bool CS = false>
 __device__ __forceinline__ void quad_block(const ApplyArgs<float> &a, const Tile tl, const int chunk,
                                            unsigned char *smraw) {
     using G = QuadGeom<NYT>;
     constexpr int NT = G::NT, TX = G::TX, TY = G::TY, WX = G::WX, WY = G::WY, NC = G::NC;
     float2 *slots = (float2 *)smraw;                           // NS x SLOT
     float2 *bslots = slots + NS * G::SLOT;                     // NS x NPTS x NC
-    float *vslots = (float *)(bslots + NS * G::NPTS * NC);     // NS x NPTS
-    SRow *srows = (SRow *)(vslots + NS * G::NPTS);             // WY x np
+    float *vslots = (float *)(bslots + NS * G::NPTS * NC);     // NS x NPTS (x 2 with CS: complex)
+    SRow *srows = (SRow *)(vslots + NS * G::NPTS * (CS ? 2 : 1));   // WY x np
 
     const int ny = a.ny, nz = a.nz, ld = 2 * a.SV;
     const int xbase = tl.tx * TX - 4, ybase = tl.ty * TY - 4, zbase = tl.zlo - 4;
@@ -292,8 +311,12 @@ __device__ __forceinline__ void quad_block(const ApplyArgs<float> &a, const Tile
             const SRow rw = rr[4 + pyy];
             const int x = tl.tx * TX + pxx;
             const bool ok = (x >= rw.xmin) & (x <= rw.xmax);
-            cp_async_small<4>(s_v + (unsigned)((sl * G::NPTS + tid) * 4), a.V + (ok ? rw.start + (x - rw.xmin) : 0),
-                              ok ? 4 : 0);
+            if constexpr (CS)
+                cp_async_small<8>(s_v + (unsigned)((sl * G::NPTS + tid) * 8),
+                                  (const float2 *)a.Vc + (ok ? rw.start + (x - rw.xmin) : 0), ok ? 8 : 0);
+            else
+                cp_async_small<4>(s_v + (unsigned)((sl * G::NPTS + tid) * 4),
+                                  a.V + (ok ? rw.start + (x - rw.xmin) : 0), ok ? 4 : 0);
         }
         if (base2 != nullptr && j >= 4) {
             // base records of interior points 2 (tid / 2) and 2 (tid / 2) + 1
@@ -361,7 +384,7 @@ __device__ __forceinline__ void quad_block(const ApplyArgs<float> &a, const Tile
             __syncthreads();
             if (j + NS - 1 < np) stage(j + NS - 1);
             cp_async_commit();
-            quad_plane<NYT, NS>(a, c, j, q);
+            quad_plane<NYT, NS, CS>(a, c, j, q);
         }
         cp_async_wait<0>();
     } else {
@@ -388,7 +411,7 @@ __device__ __forceinline__ void quad_block(const ApplyArgs<float> &a, const Tile
                 arrive_full(pn);
             }
             if (!qbar_wait(full0 + 8 * (j % NS), (unsigned)((j / NS) & 1))) bad = 1;
-            quad_plane<NYT, NS>(a, c, j, q);
+            quad_plane<NYT, NS, CS>(a, c, j, q);
             __syncwarp();
             if (lane == 0)
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(empty0 + 8 * (j % NS)) : "memory");
@@ -400,10 +423,10 @@ __device__ __forceinline__ void quad_block(const ApplyArgs<float> &a, const Tile
     }
 }
 
-template <int NYT, int NS, int MINB, int SYNC>
+template <int NYT, int NS, int MINB, int SYNC, bool CS = false>
 __global__ void __launch_bounds__(QuadGeom<NYT>::NT, MINB) k_apply_quad(const ApplyArgs<float> a, int nchunks) {
     extern __shared__ __align__(128) unsigned char smraw[];
-    quad_block<NYT, NS, SYNC>(a, a.tiles[blockIdx.x / nchunks], blockIdx.x % nchunks, smraw);
+    quad_block<NYT, NS, SYNC, CS>(a, a.tiles[blockIdx.x / nchunks], blockIdx.x % nchunks, smraw);
 }
 
 // Batches: every block takes a (system, tile, chunk) work item and runs the
@@ -426,25 +449,27 @@ void quad_shape(const TileCfg &cfg, int *TX, int *TY) {
     *TY = cfg.threads == 256 ? 16 : cfg.threads == 160 ? 10 : 12;
 }
 
-size_t quad_smem_bytes(int nyt, int ns, int zseg) {
+size_t quad_smem_bytes(int nyt, int ns, int zseg, bool cs = false) {
     const size_t nt = 32 * (size_t)nyt, wy = 2 * (size_t)nyt + 8;
-    // slots, base and potential rings, row table, then 2 NS mbarriers
-    return (size_t)ns * (wy * 24 * 4 * 8 + nt * 4 * 8 + nt * 4) + wy * (zseg + 8) * sizeof(SRow) + 8 + 16 * (size_t)ns;
+    // slots, base and potential rings (complex potential with cs), row
+    // table, then 2 NS mbarriers
+    return (size_t)ns * (wy * 24 * 4 * 8 + nt * 4 * 8 + nt * 4 * (cs ? 2 : 1)) + wy * (zseg + 8) * sizeof(SRow) + 8 +
+           16 * (size_t)ns;
 }
 
-template <int NYT, int NS, int MINB, int SYNC>
+template <int NYT, int NS, int MINB, int SYNC, bool CS = false>
 static cudaError_t launch_quad_t(const ApplyArgs<float> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
                                  bool *launched) {
     using G = QuadGeom<NYT>;
-    const size_t smem = quad_smem_bytes(NYT, NS, cfg.zseg);
+    const size_t smem = quad_smem_bytes(NYT, NS, cfg.zseg, CS);
     if (smem > 227 * 1024) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_apply_quad<NYT, NS, MINB, SYNC>,
+    cudaError_t e = cudaFuncSetAttribute(k_apply_quad<NYT, NS, MINB, SYNC, CS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nchunks = (2 * a.SV + G::NC - 1) / G::NC;
     const long long nblk = (long long)ntiles * nchunks;
     if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    k_apply_quad<NYT, NS, MINB, SYNC><<<(unsigned)nblk, dim3(G::NC, G::NXT, NYT), smem, st>>>(a, nchunks);
+    k_apply_quad<NYT, NS, MINB, SYNC, CS><<<(unsigned)nblk, dim3(G::NC, G::NXT, NYT), smem, st>>>(a, nchunks);
     *launched = true;
     return cudaGetLastError();
 }
@@ -468,6 +493,11 @@ cudaError_t launch_apply_quad(const ApplyArgs<float> &a, const TileCfg &cfg, int
     // complex offsets are 32-bit: P * ld < 2^31
     if (ntiles == 0 || (long long)a.P * 2 * a.SV >= 0x7fffffffLL) return cudaSuccess;
     if (a.err == nullptr && cfg.sync != 0) return cudaSuccess;
+    if (a.Vc != nullptr) {
+        // complex scaling: the default block shape (16 x 12 tiles, 3 slots) only
+        if (cfg.threads == 256 || cfg.threads == 160 || cfg.sync != 0 || cfg.stages != 3) return cudaSuccess;
+        return launch_quad_t<6, 3, 2, 0, true>(a, cfg, ntiles, st, launched);
+    }
     if (cfg.threads == 256) return launch_quad_t<8, 3, 2, 0>(a, cfg, ntiles, st, launched);
     if (cfg.threads == 160) return launch_quad_t<5, 3, 3, 0>(a, cfg, ntiles, st, launched);
     switch (cfg.sync) {

@@ -187,3 +187,46 @@ def test_refusals_and_removal():
     assert p.H.get_option("last_kernel") == 6
     assert np.abs(p.states_from_gpu(y, S) - want).max() < 1e-12 * np.abs(want).max()
     _ = oracle
+
+
+@pytest.mark.parametrize("shape,n,radius,S", [("sphere", 0, 3.3, 4), ("box", (37, 23, 29), 0.0, 6),
+                                              ("sphere", 0, 3.0, 64)])
+def test_register_blocked_scaled_kernel(shape, n, radius, S):
+    """complex64 with the register-blocked kernel forced: the complex
+    diagonal v_theta e^{2i theta} in shared memory and e^{-2i theta} folded
+    into alpha; apply, a Taylor stage (alpha, base) and a shifted solve."""
+    theta = 0.35
+    p, vt = _scaled_pair(shape, n, radius, dtype=torch.complex64, theta=theta)
+    p.H.set_option("kernel", 5)
+    psi = _states(p, S, seed=S + 3)
+    x = p.states_to_gpu(psi)
+    y = p.H.apply(x, S=S)
+    assert p.H.get_option("last_kernel") == 5
+    want = p.om.apply_scaled(psi, theta, vt)
+    got = p.states_from_gpu(y, S)
+    assert np.abs(got - want).max() < 2e-6 * np.abs(want).max()
+    out = torch.zeros_like(x)
+    p.H.taylor(x, 0.01, out=out, S=S)
+    assert p.H.get_option("last_kernel") == 5
+    app = lambda u: p.om.apply_scaled(u, theta, vt)  # noqa: E731
+    tw = _series(app, psi, 0.01)
+    assert np.abs(p.states_from_gpu(out, S) - tw).max() < 2e-6 * np.abs(tw).max()
+    # the same results as the one-thread-per-value kernel
+    p.H.set_option("kernel", 1)
+    y1 = p.H.apply(x, S=S)
+    assert p.H.get_option("last_kernel") == 6
+    assert np.abs(p.states_from_gpu(y1, S) - got).max() < 2e-6 * np.abs(want).max()
+
+
+def test_register_blocked_scaled_shifted_solve():
+    theta, z = 0.3, 0.4 + 0.15j
+    p, vt = _scaled_pair("cube", 12, h=0.35, dtype=torch.complex64, theta=theta)
+    p.H.set_option("kernel", 5)
+    A = p.om.apply_scaled(np.eye(p.P, dtype=np.complex128), theta, vt) - z * np.eye(p.P)
+    b = _states(p, 3, seed=12)
+    want = np.linalg.solve(A, b)
+    x = torch.zeros_like(p.states_to_gpu(b))
+    res, it = p.H.shifted_solve(p.states_to_gpu(b), x, z, max_iter=3000, tol=1e-4, S=3)
+    assert p.H.get_option("last_kernel") == 5
+    assert np.all(res <= 1e-4), (res, it)
+    assert np.abs(p.states_from_gpu(x, 3) - want).max() < 1e-3 * np.abs(want).max()
