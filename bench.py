@@ -506,23 +506,27 @@ def main():
     # end to end through the public API with host buffers: every step copies
     # its input from pinned host memory, runs one ETRS step and copies the
     # result back.  The steps are independent (each propagates the same host
-    # input), so they are pipelined over two device buffers and three streams:
-    # step k's copy in and step k-1's copy out overlap step k-1's / k's
-    # compute.  The serial form (one stream, no overlap) is reported beside it.
+    # input), so they are pipelined over three device buffers and three
+    # streams: step k+1's copy in and step k-1's copy out overlap step k's
+    # compute, each on its own buffer (with two buffers a copy in would wait
+    # for the previous copy out of its buffer, and the step would take the
+    # sum of both copies).  The serial form (one stream, no overlap) is
+    # reported beside it.
     e2e = None
     if not args.no_e2e:
         nbytes = psi_h.numel() * psi_h.element_size()
-        dev = [psi, torch.empty_like(psi)]
-        out_h = [torch.empty_like(psi_h).pin_memory() for _ in range(2)]
+        NBUF = 3
+        dev = [psi] + [torch.empty_like(psi) for _ in range(NBUF - 1)]
+        out_h = [torch.empty_like(psi_h).pin_memory() for _ in range(NBUF)]
         s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
 
         def e2e_steps(n):
-            ev_in = [torch.cuda.Event() for _ in range(2)]
-            ev_cmp = [torch.cuda.Event() for _ in range(2)]
-            ev_out = [torch.cuda.Event() for _ in range(2)]
-            used = [False, False]
+            ev_in = [torch.cuda.Event() for _ in range(NBUF)]
+            ev_cmp = [torch.cuda.Event() for _ in range(NBUF)]
+            ev_out = [torch.cuda.Event() for _ in range(NBUF)]
+            used = [False] * NBUF
             for k in range(n):
-                b = k % 2
+                b = k % NBUF
                 if used[b]:
                     s_in.wait_event(ev_out[b])          # buffer b's previous result is home
                 with torch.cuda.stream(s_in):
@@ -562,9 +566,9 @@ def main():
         ts = reduce_max(g0.elapsed_time(g1), ws, "cuda")
         e2e = {"value": whole_job_value(te, ws, P * S * N_APPLY_PER_STEP, args.steps),
                "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "pipelining": "2 device buffers, copy-in / compute / copy-out streams",
+               "pipelining": "3 device buffers, copy-in / compute / copy-out streams",
                "serial_value": whole_job_value(ts, ws, P * S * N_APPLY_PER_STEP, args.steps)}
-        del dev[1]
+        del dev[1:]
 
     if rank != 0:
         if ws > 1:
