@@ -190,7 +190,8 @@ def test_refusals_and_removal():
 
 
 @pytest.mark.parametrize("shape,n,radius,S", [("sphere", 0, 3.3, 4), ("box", (37, 23, 29), 0.0, 6),
-                                              ("sphere", 0, 3.0, 64)])
+                                              ("sphere", 0, 3.0, 64), ("sphere", 0, 2.7, 1),
+                                              ("box", (21, 30, 17), 0.0, 13)])
 def test_register_blocked_scaled_kernel(shape, n, radius, S):
     """complex64 with the register-blocked kernel forced: the complex
     diagonal v_theta e^{2i theta} in shared memory and e^{-2i theta} folded
