@@ -23,6 +23,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -112,7 +113,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # raw samples: a temporary file unless RSG_CLOCK_LOG_DIR names a folder to keep them in
+        folder = os.environ.get("RSG_CLOCK_LOG_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -208,6 +211,7 @@ def extras(mesh, wells, proj, g):
     from workloads import (control_field, potential_double_well, potential_wells, projector_atoms,
                            rng, white_noise_states)
     out = {}
+    peak, _ = peaks()
     P, S = mesh.P, 64
     for name, dtype, kernel in (("c64_plain_kernel", torch.complex64, 1),
                                 ("c128_default", torch.complex128, None),
@@ -261,8 +265,14 @@ def extras(mesh, wells, proj, g):
         pst += m.P * int(S_)
     batch = rsg.Batch(hams, [int(x) for x in Ss])
     ms = time_steps(None, psis, 10, lambda xs: batch.propagate(xs, 1, 0.02, scheme=rsg.ETRS))
+    # algorithmic stencil bytes of one step (read u, read psi, write, V per
+    # Horner stage) over the whole step time: a lower bound on the batched
+    # stencil's own fraction, since the step also holds the projector kernels
+    sbytes = N_APPLY_PER_STEP * sum(h.mesh.P * (3 * x.shape[1] * 8 + 4) for h, x in zip(hams, psis))
     out["batch_256_systems"] = {"ms_per_step": ms, "point_states": pst,
                                 "value": pst * N_APPLY_PER_STEP / (ms * 1e-3) / 1e9, "unit": UNIT,
+                                "step_stencil_GBps": sbytes / (ms * 1e-3) / 1e9,
+                                "step_frac_of_measured_hbm": sbytes / (ms * 1e-3) / 1e9 / peak,
                                 "workload": "256 cubes n~U{24..96} h=0.25, S~U{1..16}, 1..8 atoms x 4 "
                                             "projectors, ETRS dt=0.02, one captured graph per step"}
     del batch, hams, psis
@@ -289,14 +299,21 @@ def extras(mesh, wells, proj, g):
         r2 = ((xyz - cs[s_]) ** 2).sum(1)
         x5[:, s_] = torch.polar(torch.exp(-r2 / (4 * sg[s_] ** 2)), xyz @ ks[s_])
     H5.orthonormalize(x5)
+    H5.profile(True)
     ms5 = time_steps(None, x5, 3, lambda x: H5.propagate(x, 1, 0.01, scheme=rsg.ETRS, want_drift=False))
+    k5_ms, _, k5_bytes, _ = H5.kernel_stats()
+    H5.profile(False)
+    k5_name = KERNEL_NAMES.get(H5.get_option("last_kernel"), "unknown")
     torch.cuda.synchronize()
     g0 = time.perf_counter()
     H5.orthonormalize(x5)
     gs_s = time.perf_counter() - g0
     drift = H5.propagate(x5, 50, 0.01, scheme=rsg.ETRS, gs_every=50)
+    k5_gbs = k5_bytes / (k5_ms * 1e-3) / 1e9 if k5_ms > 0 else None
     out["large_cube_192"] = {"ms_per_step": ms5, "value": cm5.P * S5 * N_APPLY_PER_STEP / (ms5 * 1e-3) / 1e9,
-                             "unit": UNIT, "gram_schmidt_s": gs_s, "norm_drift_max_50_steps": float(np.max(drift)),
+                             "unit": UNIT, "kernel": k5_name, "kernel_GBps": k5_gbs,
+                             "kernel_frac_of_measured_hbm": k5_gbs / peak if k5_gbs else None,
+                             "gram_schmidt_s": gs_s, "norm_drift_max_50_steps": float(np.max(drift)),
                              "workload": "192^3 h=0.18, 128 smooth states, 64 atoms x 9 projectors r_c=3, "
                                          "ETRS dt=0.01, Cholesky-QR every 50 steps"}
     del H5, x5, xyz
