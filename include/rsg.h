@@ -407,6 +407,20 @@ rsg_status rsg_ham_profile(rsg_ham H, int enable);
 rsg_status rsg_ham_kernel_stats(rsg_ham H, double *kernel_ms, int64_t *kernel_launches,
                                 double *kernel_bytes, int64_t *all_launches);
 
+/* Failure-path support (no counterpart in the paper).
+ * rsg_selftest_bounded_wait runs the bounded-wait path of the pipelined
+ * stencil kernels on purpose: one warp waits on an mbarrier phase that
+ * cannot complete, polling `polls` times (1..65536, each poll suspending
+ * for at most about a microsecond), records the timeout in the handle's
+ * status word and returns; the call then reports RSG_ERR_TIMEOUT, and the
+ * handle and the CUDA context stay usable.  Synchronises the stream.
+ * rsg_debug_fail_allocations(n) makes the library's next n device
+ * allocations fail as if the device were out of memory (RSG_ERR_OOM from
+ * the call that needed them); 0 clears it.  Errors: RSG_ERR_ARG for polls
+ * outside 1..65536 or n < 0. */
+rsg_status rsg_selftest_bounded_wait(rsg_ham H, int polls, void *stream);
+rsg_status rsg_debug_fail_allocations(int n);
+
 /* Thread-local description of the last error (empty if none). */
 const char *rsg_last_error(void);
 

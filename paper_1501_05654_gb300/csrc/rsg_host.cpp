@@ -8,6 +8,7 @@
 // states; linear arrays plus grid tables; re-orthonormalisation only rarely
 // needed in real time), Sec. "Magnetic response and gauge invariance in real-space grids" (non-local pseudopotential),
 // Sec. "Quantum optimal control" (Eq. (qoctgradient), costate propagation).
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,6 +59,10 @@ rsg_status fail(rsg_status s, const char *fmt, ...) {
 // 8th-order central second difference weights, |k| = 0..4 (times 1/h^2).
 const double kFD[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
 
+// Simulated allocation failures (rsg_debug_fail_allocations): the next
+// g_fail_allocs device allocations report cudaErrorMemoryAllocation.
+std::atomic<int> g_fail_allocs{0};
+
 // Device buffer that only grows.
 struct DevBuf {
     void *p = nullptr;
@@ -77,6 +82,8 @@ struct DevBuf {
     }
     cudaError_t ensure(size_t bytes) {
         if (bytes <= n && p) return cudaSuccess;
+        for (int f = g_fail_allocs.load(); f > 0;)
+            if (g_fail_allocs.compare_exchange_weak(f, f - 1)) return cudaErrorMemoryAllocation;
         release();
         cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
         if (e == cudaSuccess) n = bytes ? bytes : 16;
@@ -601,7 +608,7 @@ rsg_status read_status(rsg_ham H, cudaStream_t st) {
     if (s != 0) {
         CK(cudaMemsetAsync(H->status.p, 0, sizeof(int), st));
         CK(cudaStreamSynchronize(st));
-        if (s == 2) return fail(RSG_ERR_TIMEOUT, "a bounded wait in the stencil kernel gave up");
+        if (s == 2) return fail(RSG_ERR_TIMEOUT, "a bounded device wait gave up");
         if (s == 3) return fail(RSG_ERR_CUDA, "TMA destination not 128-byte aligned (copy skipped)");
         return fail(RSG_ERR_NONFINITE, "Gram matrix not finite or not positive definite");
     }
@@ -642,6 +649,12 @@ rsg_status set_error(rsg_status s, const char *msg) { return fail(s, "%s", msg);
 }  // namespace rsg
 
 // ===================================================================== ABI
+
+namespace rsg {
+// Bounded-wait self-test kernel (rsg_selftest.cu): one warp waits `polls`
+// times on an mbarrier phase that cannot complete and records 2 in *err.
+cudaError_t launch_selftest_wait(int polls, int *err, cudaStream_t st);
+}  // namespace rsg
 
 extern "C" {
 
@@ -1255,6 +1268,25 @@ rsg_status rsg_state_norms(rsg_ham H, const void *psi, int64_t S, int64_t ld, do
     CK(cudaMemcpyAsync(norms2_out, H->drift.p, (size_t)S * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return read_status(H, st);
+}
+
+rsg_status rsg_selftest_bounded_wait(rsg_ham H, int polls, void *stream) {
+    if (!H) return fail(RSG_ERR_ARG, "NULL handle");
+    if (polls < 1 || polls > 65536) return fail(RSG_ERR_ARG, "polls must be in 1..65536");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!H->status.p) {
+        CK(H->status.ensure(sizeof(int)));
+        CK(cudaMemsetAsync(H->status.p, 0, sizeof(int), st));
+    }
+    CK(launch_selftest_wait(polls, H->status.as<int>(), st));
+    H->n_launch++;
+    return read_status(H, st);
+}
+
+rsg_status rsg_debug_fail_allocations(int n) {
+    if (n < 0) return fail(RSG_ERR_ARG, "n < 0");
+    g_fail_allocs.store(n);
+    return RSG_OK;
 }
 
 rsg_status rsg_orthonormalize(rsg_ham H, void *psi, int64_t S, int64_t ld, double *norms2_out,

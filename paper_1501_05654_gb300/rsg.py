@@ -64,6 +64,8 @@ SIGNATURES = {
     "rsg_ham_autotune": [_vp, _vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_ham_profile": [_vp, _int],
     "rsg_ham_kernel_stats": [_vp, _vp, _vp, _vp, _vp],
+    "rsg_selftest_bounded_wait": [_vp, _int, _vp],
+    "rsg_debug_fail_allocations": [_int],
     "rsg_last_error": [],
 }
 

@@ -202,3 +202,21 @@ def test_raw_projector_argument_errors(lib):
     assert call([0, 1], [1.0, np.inf], 1, [1.0]) == -1
     assert call([0, 1], np.ones(2), 0, [1.0]) == -1
     assert lib.rsg_projectors_set_raw(H._h, 0, None, None, None, None, None) == 0
+
+
+def test_failure_path_support_arguments(lib):
+    """rsg_selftest_bounded_wait and rsg_debug_fail_allocations reject bad
+    arguments before any device work; a simulated allocation failure is
+    reported as RSG_ERR_OOM by the call that allocates (here the potential
+    upload), and it is consumed."""
+    m = rsg.Mesh(rsg.CUBE, 6, spacing=0.3)
+    H = rsg.Hamiltonian(m, torch.complex64)
+    assert lib.rsg_selftest_bounded_wait(None, 10, None) == -1
+    assert lib.rsg_selftest_bounded_wait(H._h, 0, None) == -1
+    assert lib.rsg_selftest_bounded_wait(H._h, 65537, None) == -1
+    assert lib.rsg_debug_fail_allocations(-1) == -1
+    V = np.zeros(m.P)
+    assert lib.rsg_debug_fail_allocations(1) == 0
+    assert lib.rsg_potential_set(H._h, V.ctypes.data_as(C.c_void_p), 0) == -2
+    assert b"memory" in lib.rsg_last_error().lower()
+    assert lib.rsg_debug_fail_allocations(0) == 0
