@@ -17,10 +17,11 @@ pytestmark = pytest.mark.gpu
 SPECS = [(9, 1, 1), (14, 3, 2), (20, 4, 0), (24, 6, 3), (11, 2, 1), (17, 5, 2)]   # (n, S, atoms)
 
 
-def _systems(lmax_of=lambda i: 1, seed=0):
+def _systems(lmax_of=lambda i: 1, seed=0, atoms=True):
     g = rng(3, seed)
     out = []
     for i, (n, S, na) in enumerate(SPECS):
+        na = na if atoms else 0
         p = Pair("cube", n, h=0.25, dtype=torch.complex64)
         half = 0.5 * (n - 1) * 0.25
         c, d, w = gaussian_wells(g, 2, 0.0, cube_half=0.6 * half)
@@ -53,6 +54,21 @@ def test_batch_matches_single_system_and_oracle():
     p, psi, S = systems[3]
     want, _ = p.O.propagate(psi, 4, 0.02, scheme=oracle.ETRS)
     assert rel_err(p.states_from_gpu(xs[3], S), want) < 2e-5
+
+
+def test_batch_bitwise_equals_single_register_blocked_systems():
+    """Without projectors the batched stencil runs the same register-blocked
+    block, tiles, plane order and epilogue constants as the single-system
+    kernel 5, so each system's result is bit-for-bit that of its own run."""
+    systems = _systems(seed=3, atoms=False)
+    _, xs = _run_batch(systems, 3, 0.02, rsg.ETRS)
+    for (p, psi, S), x in zip(systems, xs):
+        p.H.set_option("kernel", 5)
+        y = p.states_to_gpu(psi)
+        p.H.propagate(y, 3, 0.02, scheme=rsg.ETRS)
+        torch.cuda.synchronize()
+        assert p.H.get_option("last_kernel") == 5
+        assert torch.equal(x, y), (p.P, S, (x - y).abs().max().item())
 
 
 def test_batch_expmid_and_recapture_on_new_buffers():
