@@ -82,7 +82,10 @@ def peaks():
 # stencil kernel of each "kernel" option value (rsg_ham_get_option "last_kernel")
 KERNEL_NAMES = {0: "k_apply_staged", 1: "k_apply_naive", 2: "k_apply_zmarch", 3: "k_apply_tma",
                 4: "k_apply_rowtma", 5: "k_apply_quad"}
-KERNEL_SOURCES = ("rsg_kernels.cu", "rsg_quad.cu", "rsg_vec.cuh", "rsg_async.cuh", "rsg_batch.cuh", "rsg_internal.h")
+# the files the dominant stencil kernel (k_apply_quad) is compiled from; the
+# public header it also includes holds only C declarations the kernel does
+# not use
+KERNEL_SOURCES = ("rsg_quad.cu", "rsg_vec.cuh", "rsg_async.cuh", "rsg_batch.cuh", "rsg_internal.h")
 
 
 def traffic_record(kernel_src_hash, kernel_name):
