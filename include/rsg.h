@@ -64,6 +64,9 @@ typedef enum {
 typedef enum { RSG_C64 = 0, RSG_C128 = 1 } rsg_dtype;
 typedef enum { RSG_SHAPE_CUBE = 0, RSG_SHAPE_SPHERE = 1, RSG_SHAPE_BOX = 2 } rsg_shape;
 typedef enum { RSG_EXPMID = 0, RSG_ETRS = 1 } rsg_scheme;
+/* Boundary rule of the Laplacian: zero values outside the mesh (finite
+ * systems, the default), or antisymmetric images for a cube or box. */
+typedef enum { RSG_BC_ZERO = 0, RSG_BC_ODD = 1 } rsg_bc;
 
 /* ---------------------------------------------------------------- mesh ---
  * Uniform mesh (Sec. 1; Sec. "Parallelization, optimizations and graphics processing units": field = linear array + grid
@@ -76,6 +79,21 @@ typedef enum { RSG_EXPMID = 0, RSG_ETRS = 1 } rsg_scheme;
  * Errors: RSG_ERR_ARG for spacing <= 0, extents outside 1..1024, NULL out. */
 rsg_status rsg_mesh_create(rsg_shape shape, const int32_t n[3], double radius,
                            double spacing, rsg_mesh *out);
+
+/* Boundary rule of a cube or box mesh (Sec. 1: finite boxes; the image
+ * rule is a test aid).  RSG_BC_ZERO (default): neighbours outside the mesh
+ * are zero.  RSG_BC_ODD: a neighbour outside the mesh takes the value of
+ * its mirror image about a wall one spacing outside the mesh, with the sign
+ * flipped, and a neighbour on a wall is zero; minus the Laplacian then has
+ * the closed-form eigenvalues sum_d sigma(pi m_d / (n_d + 1)) / h^2 with
+ * products of sines as eigenvectors, so box eigenvalues converge at the
+ * stencil's order.  Applications on an image-wall mesh run the
+ * one-thread-per-value kernels (1, or 6 with complex scaling); batches
+ * refuse such meshes.  Set it before building Hamiltonians' work on the
+ * mesh or between calls (not while a call on the mesh is in flight).
+ * Errors: RSG_ERR_ARG for an unknown rule, RSG_ERR_UNSUPPORTED for RSG_BC_ODD
+ * on a sphere. */
+rsg_status rsg_mesh_set_boundary(rsg_mesh m, int bc);
 /* Number of mesh points P. */
 rsg_status rsg_mesh_num_points(rsg_mesh m, int64_t *P);
 /* Host array ijk (P x 3 int32, caller-owned): lattice integers of every point

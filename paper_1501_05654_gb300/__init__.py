@@ -6,6 +6,6 @@ Public API: ``Mesh``, ``Hamiltonian``, ``Batch``, ``ControlObjective`` and
 the CUDA library in-tree.
 """
 from .build import build  # noqa: F401
-from .rsg import (BOX, C64, C128, CUBE, ETRS, EXPMID, SPHERE, Batch,  # noqa: F401
+from .rsg import (BC_ODD, BC_ZERO, BOX, C64, C128, CUBE, ETRS, EXPMID, SPHERE, Batch,  # noqa: F401
                   ControlObjective, Hamiltonian, Mesh, RSGError, empty_states, fourier_basis, load,
                   padded_ld)

@@ -26,6 +26,18 @@
 
 #include "rsg_internal.h"
 
+namespace rsg {
+// Bounded-wait self-test kernel (rsg_selftest.cu): one warp waits `polls`
+// times on an mbarrier phase that cannot complete and records 2 in *err.
+cudaError_t launch_selftest_wait(int polls, int *err, cudaStream_t st);
+// Antisymmetric-image boundary (rsg_odd.cuh): the one-thread-per-value
+// kernel (rsg_kernels.cu) and the complex-scaled kernel (rsg_scaled.cu).
+template <typename R>
+cudaError_t launch_apply_naive_odd(const ApplyArgs<R> &a, cudaStream_t st);
+template <typename R>
+cudaError_t launch_apply_scaled_odd(const ApplyArgs<R> &a, const R *vt, double theta, cudaStream_t st);
+}  // namespace rsg
+
 using namespace rsg;
 
 namespace {
@@ -110,6 +122,7 @@ struct rsg_mesh_s {
     int32_t lo[3] = {0, 0, 0};     // lattice coordinate of bbox index 0
     int nx = 0, ny = 0, nz = 0;
     int64_t P = 0;
+    int bc = RSG_BC_ZERO;           // boundary rule (image walls for cube/box only)
     std::vector<int32_t> ijk;       // P x 3 lattice integers
     std::vector<Row> rows;          // ny * nz
     DevBuf d_rows;
@@ -459,8 +472,18 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         H->ev_used += 2;
         CK(cudaEventRecord(e0, st));
     }
-    const bool split_nl = !H->has_scaling && cfg.kernel != 1 && cfg.kernel != 2 && H->pj.natoms > 0;
-    if (H->has_scaling) {
+    const bool odd = m->bc == RSG_BC_ODD;
+    const bool split_nl = !odd && !H->has_scaling && cfg.kernel != 1 && cfg.kernel != 2 && H->pj.natoms > 0;
+    if (odd) {
+        // image walls: the one-thread-per-value kernels, neighbours through the image rule
+        if (H->has_scaling) {
+            CK(launch_apply_scaled_odd<R>(a, H->vtheta.as<R>(), H->theta, st));
+            H->last_kernel = 6;
+        } else {
+            CK(launch_apply_naive_odd<R>(a, st));
+            H->last_kernel = 1;
+        }
+    } else if (H->has_scaling) {
         // complex-scaled operator (no projectors, no field: refused while set)
         bool done = false;
         if constexpr (std::is_same<R, float>::value) {
@@ -650,15 +673,18 @@ rsg_status set_error(rsg_status s, const char *msg) { return fail(s, "%s", msg);
 
 // ===================================================================== ABI
 
-namespace rsg {
-// Bounded-wait self-test kernel (rsg_selftest.cu): one warp waits `polls`
-// times on an mbarrier phase that cannot complete and records 2 in *err.
-cudaError_t launch_selftest_wait(int polls, int *err, cudaStream_t st);
-}  // namespace rsg
-
 extern "C" {
 
 const char *rsg_last_error(void) { return g_err.c_str(); }
+
+rsg_status rsg_mesh_set_boundary(rsg_mesh m, int bc) {
+    if (!m) return fail(RSG_ERR_ARG, "NULL mesh");
+    if (bc != RSG_BC_ZERO && bc != RSG_BC_ODD) return fail(RSG_ERR_ARG, "unknown boundary rule %d", bc);
+    if (bc == RSG_BC_ODD && m->shape == RSG_SHAPE_SPHERE)
+        return fail(RSG_ERR_UNSUPPORTED, "image walls need a cube or a box");
+    m->bc = bc;
+    return RSG_OK;
+}
 
 rsg_status rsg_mesh_create(rsg_shape shape, const int32_t n[3], double radius, double spacing,
                            rsg_mesh *out) {
@@ -2240,6 +2266,7 @@ rsg_status rsg_batch_create(const rsg_ham *hams, const int64_t *S, int nsys, rsg
         if (hams[i]->dtype != RSG_C64) return fail(RSG_ERR_UNSUPPORTED, "batches are complex64");
         if (hams[i]->has_mask) return fail(RSG_ERR_UNSUPPORTED, "batches do not apply mask absorbers");
         if (hams[i]->has_scaling) return fail(RSG_ERR_UNSUPPORTED, "batches do not apply complex scaling");
+        if (hams[i]->m->bc != RSG_BC_ZERO) return fail(RSG_ERR_UNSUPPORTED, "batches use zero ghosts only");
         if (S[i] < 1) return fail(RSG_ERR_ARG, "S[%d] < 1", i);
         b->hams.push_back(hams[i]);
         b->S.push_back(S[i]);

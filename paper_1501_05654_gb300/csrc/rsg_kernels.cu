@@ -30,6 +30,7 @@
 #include "rsg_async.cuh"
 #include "rsg_batch.cuh"
 #include "rsg_internal.h"
+#include "rsg_odd.cuh"
 #include "rsg_vec.cuh"
 
 namespace rsg {
@@ -503,6 +504,46 @@ __global__ void __launch_bounds__(256) k_apply_naive(const ApplyArgs<R> a) {
         }
         finish_point<R>(a, idx, x, y, z, v, c, acc);
     }
+}
+
+// One thread per (point, vector) with the antisymmetric-image boundary of a
+// box mesh (rsg_odd.cuh): every neighbour goes through the image rule; the
+// diagonal, projectors and epilogue are those of the other kernels.
+template <typename R>
+__global__ void __launch_bounds__(256) k_apply_naive_odd(const ApplyArgs<R> a) {
+    using V = VT<R>;
+    using T = typename V::T;
+    const int row = blockIdx.x;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, SV = a.SV;
+    const int y = row % ny, z = row / ny;
+    const Row rc = a.rows[row];
+    if (rc.xmin > rc.xmax) return;
+    const T *__restrict__ in = (const T *)a.in;
+    const int n = (rc.xmax - rc.xmin + 1) * SV;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int xo = t / SV, v = t - xo * SV;
+        const int x = rc.xmin + xo;
+        const int64_t idx = (int64_t)rc.start + xo;
+        const T c = V::ldg(in + idx * SV + v);
+        T acc = V::scale((R)3 * a.w[0], c);
+        for (int k = 1; k <= 4; k++) {
+            T s = V::add(odd_site<R>(in, a.rows, x - k, y, z, nx, ny, nz, SV, v),
+                         odd_site<R>(in, a.rows, x + k, y, z, nx, ny, nz, SV, v));
+            s = V::add(s, odd_site<R>(in, a.rows, x, y - k, z, nx, ny, nz, SV, v));
+            s = V::add(s, odd_site<R>(in, a.rows, x, y + k, z, nx, ny, nz, SV, v));
+            s = V::add(s, odd_site<R>(in, a.rows, x, y, z - k, nx, ny, nz, SV, v));
+            s = V::add(s, odd_site<R>(in, a.rows, x, y, z + k, nx, ny, nz, SV, v));
+            V::fma(acc, a.w[k], s);
+        }
+        finish_point<R>(a, idx, x, y, z, v, c, acc);
+    }
+}
+
+template <typename R>
+cudaError_t launch_apply_naive_odd(const ApplyArgs<R> &a, cudaStream_t st) {
+    if (a.ny * a.nz == 0) return cudaSuccess;
+    k_apply_naive_odd<R><<<a.ny * a.nz, 256, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 static inline int pow2_at_least(int v) {
@@ -1672,6 +1713,7 @@ template cudaError_t launch_apply_rowtma<float>(const ApplyArgs<float> &, const 
 #elif !defined(RSG_ONLY_DOUBLE)
 template cudaError_t launch_apply_tma<float>(const ApplyArgs<float> &, const TileCfg &, int, cudaStream_t, bool *);
 template cudaError_t launch_apply<float>(const ApplyArgs<float> &, const TileCfg &, int, cudaStream_t);
+template cudaError_t launch_apply_naive_odd<float>(const ApplyArgs<float> &, cudaStream_t);
 template cudaError_t launch_proj_dot<float>(const void *, int, const ProjDev &, double *, cudaStream_t);
 template cudaError_t launch_proj_reduce<float>(const double *, int, const ProjDev &, double, void *, cudaStream_t);
 template cudaError_t launch_proj_scatter<float>(const ApplyArgs<float> &, const ProjDev &, cudaStream_t);
@@ -1680,6 +1722,7 @@ template cudaError_t launch_proj_scatter<float>(const ApplyArgs<float> &, const 
 template cudaError_t launch_apply_tma<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t, bool *);
 template cudaError_t launch_apply_rowtma<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t, bool *);
 template cudaError_t launch_apply<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t);
+template cudaError_t launch_apply_naive_odd<double>(const ApplyArgs<double> &, cudaStream_t);
 template cudaError_t launch_proj_dot<double>(const void *, int, const ProjDev &, double *, cudaStream_t);
 template cudaError_t launch_proj_reduce<double>(const double *, int, const ProjDev &, double, void *, cudaStream_t);
 template cudaError_t launch_proj_scatter<double>(const ApplyArgs<double> &, const ProjDev &, cudaStream_t);

@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "rsg_internal.h"
+#include "rsg_odd.cuh"
 #include "rsg_vec.cuh"
 
 namespace rsg {
@@ -34,7 +35,8 @@ __device__ __forceinline__ Row scaled_row(const Row *rows, int y, int z, int ny,
     return rows[(int64_t)z * ny + y];
 }
 
-template <typename R>
+// ODD: the antisymmetric-image boundary of a box mesh (rsg_odd.cuh)
+template <typename R, bool ODD>
 __global__ void __launch_bounds__(256) k_apply_scaled(const ApplyArgs<R> a, const R *__restrict__ vt, R kr,
                                                       R ki) {
     using V = VT<R>;
@@ -53,11 +55,22 @@ __global__ void __launch_bounds__(256) k_apply_scaled(const ApplyArgs<R> a, cons
         const T c = V::ldg(in + idx * SV + v);
         T lap = V::scale((R)3 * a.w[0], c);
         for (int k = 1; k <= 4; k++) {
-            T s = V::add(scaled_value<R>(in, rc, x - k, SV, v), scaled_value<R>(in, rc, x + k, SV, v));
-            s = V::add(s, scaled_value<R>(in, scaled_row(a.rows, y - k, z, ny, nz), x, SV, v));
-            s = V::add(s, scaled_value<R>(in, scaled_row(a.rows, y + k, z, ny, nz), x, SV, v));
-            s = V::add(s, scaled_value<R>(in, scaled_row(a.rows, y, z - k, ny, nz), x, SV, v));
-            s = V::add(s, scaled_value<R>(in, scaled_row(a.rows, y, z + k, ny, nz), x, SV, v));
+            T s;
+            if constexpr (ODD) {
+                const int nx = a.nx;
+                s = V::add(odd_site<R>(in, a.rows, x - k, y, z, nx, ny, nz, SV, v),
+                           odd_site<R>(in, a.rows, x + k, y, z, nx, ny, nz, SV, v));
+                s = V::add(s, odd_site<R>(in, a.rows, x, y - k, z, nx, ny, nz, SV, v));
+                s = V::add(s, odd_site<R>(in, a.rows, x, y + k, z, nx, ny, nz, SV, v));
+                s = V::add(s, odd_site<R>(in, a.rows, x, y, z - k, nx, ny, nz, SV, v));
+                s = V::add(s, odd_site<R>(in, a.rows, x, y, z + k, nx, ny, nz, SV, v));
+            } else {
+                s = V::add(scaled_value<R>(in, rc, x - k, SV, v), scaled_value<R>(in, rc, x + k, SV, v));
+                s = V::add(s, scaled_value<R>(in, scaled_row(a.rows, y - k, z, ny, nz), x, SV, v));
+                s = V::add(s, scaled_value<R>(in, scaled_row(a.rows, y + k, z, ny, nz), x, SV, v));
+                s = V::add(s, scaled_value<R>(in, scaled_row(a.rows, y, z - k, ny, nz), x, SV, v));
+                s = V::add(s, scaled_value<R>(in, scaled_row(a.rows, y, z + k, ny, nz), x, SV, v));
+            }
             V::fma(lap, a.w[k], s);
         }
         T acc = V::cmul(kr, ki, lap);
@@ -78,11 +91,23 @@ __global__ void __launch_bounds__(256) k_apply_scaled(const ApplyArgs<R> a, cons
 template <typename R>
 cudaError_t launch_apply_scaled(const ApplyArgs<R> &a, const R *vt, double theta, cudaStream_t st) {
     if (a.ny * a.nz == 0) return cudaSuccess;
-    k_apply_scaled<R><<<a.ny * a.nz, 256, 0, st>>>(a, vt, (R)std::cos(2.0 * theta), (R)-std::sin(2.0 * theta));
+    k_apply_scaled<R, false>
+        <<<a.ny * a.nz, 256, 0, st>>>(a, vt, (R)std::cos(2.0 * theta), (R)-std::sin(2.0 * theta));
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_apply_scaled_odd(const ApplyArgs<R> &a, const R *vt, double theta, cudaStream_t st) {
+    if (a.ny * a.nz == 0) return cudaSuccess;
+    k_apply_scaled<R, true>
+        <<<a.ny * a.nz, 256, 0, st>>>(a, vt, (R)std::cos(2.0 * theta), (R)-std::sin(2.0 * theta));
     return cudaGetLastError();
 }
 
 template cudaError_t launch_apply_scaled<float>(const ApplyArgs<float> &, const float *, double, cudaStream_t);
 template cudaError_t launch_apply_scaled<double>(const ApplyArgs<double> &, const double *, double, cudaStream_t);
+template cudaError_t launch_apply_scaled_odd<float>(const ApplyArgs<float> &, const float *, double, cudaStream_t);
+template cudaError_t launch_apply_scaled_odd<double>(const ApplyArgs<double> &, const double *, double,
+                                                     cudaStream_t);
 
 }  // namespace rsg

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "librsg.so")
 CUBE, SPHERE, BOX = 0, 1, 2
 C64, C128 = 0, 1
 EXPMID, ETRS = 0, 1
+BC_ZERO, BC_ODD = 0, 1
 
 _STATUS = {0: "RSG_OK", -1: "RSG_ERR_ARG", -2: "RSG_ERR_OOM", -3: "RSG_ERR_CUDA",
            -4: "RSG_ERR_UNSUPPORTED", -5: "RSG_ERR_TIMEOUT", -6: "RSG_ERR_NONFINITE",
@@ -44,6 +45,7 @@ SIGNATURES = {
     "rsg_propagate_steps": [_vp, _vp, _i64, _i64, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp],
     "rsg_orthonormalize": [_vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_absorber_set": [_vp, _vp, _int],
+    "rsg_mesh_set_boundary": [_vp, _int],
     "rsg_projectors_set_raw": [_vp, _int, _vp, _vp, _vp, _vp, _vp],
     "rsg_complex_scaling_set": [_vp, _dbl, _vp, _int],
     "rsg_shifted_solve": [_vp, _vp, _vp, _i64, _i64, _dbl, _dbl, _i64, _dbl, _vp, _vp, _vp],
@@ -147,6 +149,11 @@ class Mesh:
         self.origin = org
         self.h = float(sp.value)
         self.xyz = org[None, :] + self.h * self.ijk.astype(np.float64)
+
+    def set_boundary(self, bc: int):
+        """BC_ZERO (zero values outside the mesh) or BC_ODD (antisymmetric
+        images about walls one spacing outside a cube or box)."""
+        _ck(load().rsg_mesh_set_boundary(self._h, int(bc)))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

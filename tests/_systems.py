@@ -14,11 +14,14 @@ from workloads import (gaussian_wells, potential_double_well, potential_harmonic
 
 
 class Pair:
-    def __init__(self, shape, n=0, radius=0.0, h=0.3, dtype=torch.complex64):
+    def __init__(self, shape, n=0, radius=0.0, h=0.3, dtype=torch.complex64, odd=False):
         self.lm = rsg.Mesh({"cube": rsg.CUBE, "box": rsg.BOX, "sphere": rsg.SPHERE}[shape], n,
                            radius=radius, spacing=h)
+        if odd:
+            self.lm.set_boundary(rsg.BC_ODD)
         self.om = oracle.Mesh({"cube": oracle.CUBE, "box": oracle.BOX,
-                               "sphere": oracle.SPHERE}[shape], n, radius=radius, h=h)
+                               "sphere": oracle.SPHERE}[shape], n, radius=radius, h=h,
+                              bc=oracle.ODD if odd else oracle.ZERO)
         self.idx = perm_lib_to_oracle(self.lm.ijk, self.om.ijk)
         self.P = self.lm.P
         self.h = h

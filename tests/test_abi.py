@@ -220,3 +220,14 @@ def test_failure_path_support_arguments(lib):
     assert lib.rsg_potential_set(H._h, V.ctypes.data_as(C.c_void_p), 0) == -2
     assert b"memory" in lib.rsg_last_error().lower()
     assert lib.rsg_debug_fail_allocations(0) == 0
+
+
+def test_mesh_boundary_rule(lib):
+    """Image walls are for cubes and boxes; the rule is validated on the host."""
+    sph = rsg.Mesh(rsg.SPHERE, radius=1.0, spacing=0.3)
+    assert lib.rsg_mesh_set_boundary(sph._h, rsg.BC_ODD) == -4
+    cube = rsg.Mesh(rsg.CUBE, 6, spacing=0.3)
+    assert lib.rsg_mesh_set_boundary(cube._h, 2) == -1
+    assert lib.rsg_mesh_set_boundary(None, 0) == -1
+    assert lib.rsg_mesh_set_boundary(cube._h, rsg.BC_ODD) == 0
+    assert lib.rsg_mesh_set_boundary(cube._h, rsg.BC_ZERO) == 0
