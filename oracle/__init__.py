@@ -75,6 +75,7 @@ def _load():
         L.orc_ham_atom_values.argtypes = [vp, C.c_int, vp, vp]
         L.orc_apply.argtypes = [vp, dbl, vp, vp, vp, i64]
         L.orc_apply_scaled.argtypes = [vp, dbl, vp, vp, vp, i64]
+        L.orc_apply_scaled_sampled.argtypes = [vp, dbl, vp, vp, i64, i64, vp, vp, vp]
         L.orc_apply_sampled.argtypes = [vp, dbl, vp, vp, i64, i64, vp, vp, vp]
         L.orc_taylor4.argtypes = [vp, dbl, vp, dbl, vp, vp, i64]
         L.orc_norms2.argtypes = [vp, vp, i64, vp]
@@ -141,6 +142,17 @@ class Mesh:
         assert vt.shape == (self.P,)
         out = np.empty_like(psi)
         _load().orc_apply_scaled(self._m, float(theta), _p(vt), _p(psi), _p(out), psi.shape[1])
+        return out
+
+    def apply_scaled_sampled(self, psi, theta: float, vtheta, pidx, sidx):
+        """(H_theta psi) at the (point, state) pairs (pidx[t], sidx[t])."""
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        vt = np.ascontiguousarray(vtheta, dtype=np.complex128)
+        pidx = np.ascontiguousarray(pidx, dtype=np.int64)
+        sidx = np.ascontiguousarray(sidx, dtype=np.int64)
+        out = np.empty(pidx.shape[0], dtype=np.complex128)
+        _load().orc_apply_scaled_sampled(self._m, float(theta), _p(vt), _p(psi), psi.shape[1], pidx.shape[0],
+                                         _p(pidx), _p(sidx), _p(out))
         return out
 
     def mgs(self, psi):

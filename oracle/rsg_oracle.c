@@ -453,24 +453,38 @@ void orc_apply(void *hv, double eps, const double *dir, const cplx *psi,
  * vtheta psi, with vtheta the caller's values of V(r e^{i theta}) on the
  * mesh (no projectors, no field).  The Laplacian is the mesh's 8th-order
  * stencil with the mesh's boundary rule. */
+static cplx scaled_point(const orc_mesh *m, cplx rot, const cplx *vtheta, const cplx *psi, int64_t S,
+                         int64_t p, int64_t s)
+{
+    const double ih2 = 1.0 / (m->h * m->h);
+    cplx lap = 0.0;
+    for (int d = 0; d < 3; d++)
+        for (int k = -4; k <= 4; k++) {
+            int32_t c[3] = {m->ijk[3 * p], m->ijk[3 * p + 1], m->ijk[3 * p + 2]};
+            c[d] += k;
+            lap += FD_C[abs(k)] * ih2 * site_value(m, psi, S, s, c);
+        }
+    return -0.5 * rot * lap + vtheta[p] * psi[p * S + s];
+}
+
 void orc_apply_scaled(void *mv, double theta, const cplx *vtheta, const cplx *psi, cplx *hpsi,
                       int64_t S)
 {
     const orc_mesh *m = (const orc_mesh *)mv;
-    const double ih2 = 1.0 / (m->h * m->h);
     const cplx rot = cexp(-2.0 * I * theta);
 #pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < m->P; p++)
-        for (int64_t s = 0; s < S; s++) {
-            cplx lap = 0.0;
-            for (int d = 0; d < 3; d++)
-                for (int k = -4; k <= 4; k++) {
-                    int32_t c[3] = {m->ijk[3 * p], m->ijk[3 * p + 1], m->ijk[3 * p + 2]};
-                    c[d] += k;
-                    lap += FD_C[abs(k)] * ih2 * site_value(m, psi, S, s, c);
-                }
-            hpsi[p * S + s] = -0.5 * rot * lap + vtheta[p] * psi[p * S + s];
-        }
+        for (int64_t s = 0; s < S; s++) hpsi[p * S + s] = scaled_point(m, rot, vtheta, psi, S, p, s);
+}
+
+/* (H_theta psi) at nsamp chosen (point, state) pairs only; for full-size checks. */
+void orc_apply_scaled_sampled(void *mv, double theta, const cplx *vtheta, const cplx *psi, int64_t S,
+                              int64_t nsamp, const int64_t *pidx, const int64_t *sidx, cplx *out)
+{
+    const orc_mesh *m = (const orc_mesh *)mv;
+    const cplx rot = cexp(-2.0 * I * theta);
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < nsamp; t++) out[t] = scaled_point(m, rot, vtheta, psi, S, pidx[t], sidx[t]);
 }
 
 /* (H psi) at nsamp chosen (point, state) pairs only; for full-size checks. */
