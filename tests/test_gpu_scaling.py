@@ -20,6 +20,7 @@ import torch
 
 import oracle
 import paper_1501_05654_gb300 as rsg
+from tests._parity import rel_err
 from tests._systems import Pair
 from workloads import rng, white_noise_states
 
@@ -231,3 +232,29 @@ def test_register_blocked_scaled_shifted_solve():
     assert p.H.get_option("last_kernel") == 5
     assert np.all(res <= 1e-4), (res, it)
     assert np.abs(p.states_from_gpu(x, 3) - want).max() < 1e-3 * np.abs(want).max()
+
+
+def test_full_size_sphere_sampled_register_blocked():
+    """The benchmark's complex-scaled configuration: R = 18 bohr, h = 0.2
+    (3,053,617 points), 64 complex64 states, 32 wells at r e^{0.3i}, the
+    default register-blocked kernel; every state of 4096 sampled points
+    against the oracle."""
+    from workloads import gaussian_wells, potential_wells_scaled
+    g = rng(2)
+    theta = 0.3
+    p = Pair("sphere", radius=18.0, h=0.2, dtype=torch.complex64)
+    c, d, w = gaussian_wells(g, 32, 18.0 - 2.5)
+    vt = potential_wells_scaled(p.om.xyz, c, d, w, theta).astype(np.complex64).astype(np.complex128)
+    p.H.set_complex_scaling(theta, p.to_lib(vt))
+    S = 64
+    psi = white_noise_states(g, p.P, S, dtype=np.complex64).astype(np.complex128)
+    y = p.H.apply(p.states_to_gpu(psi))
+    torch.cuda.synchronize()
+    assert p.H.get_option("last_kernel") == 5
+    samp = g.choice(p.P, 4096, replace=False)
+    pidx = np.repeat(samp, S)
+    sidx = np.tile(np.arange(S), len(samp))
+    want = p.om.apply_scaled_sampled(psi, theta, vt, pidx, sidx).reshape(len(samp), S)
+    lib_rows = np.argsort(p.idx)[samp]     # library index of each sampled oracle point
+    got = y[torch.from_numpy(lib_rows).cuda()].cpu().numpy().astype(np.complex128)
+    assert rel_err(got, want) < 2e-5
