@@ -267,6 +267,23 @@ rsg_status rsg_complex_scaling_set(rsg_ham H, double theta, const double *v_thet
 rsg_status rsg_shifted_solve(rsg_ham H, const void *b, void *x, int64_t S, int64_t ld, double zr, double zi,
                              int64_t max_iter, double tol, double *resid_out, int64_t *iters_out, void *stream);
 
+/* Checkpoint and resume of a state block, e.g. part-way through a long
+ * propagation.  rsg_states_save writes the S live columns of psi ((P, ld)
+ * block of the Hamiltonian's dtype, device memory when psi_on_device != 0,
+ * else host) to `path` as a NumPy .npy array of shape (P, S) in library
+ * point order (complex64 '<c8' or complex128 '<c16', C order), and writes
+ * `path`.json with the point and state counts, the dtype, `step`, `time`
+ * and the caller's `seed`.  rsg_states_load reads such a file back into
+ * psi, zeroing the columns S..ld-1, and returns the metadata through any
+ * non-NULL output pointer (then the .json file must exist and match).
+ * Both synchronise; neither needs a stream.  Errors: RSG_ERR_ARG for NULL,
+ * S outside 1..ld, an unreadable or unwritable file, or a file whose dtype,
+ * shape or metadata do not match H and S. */
+rsg_status rsg_states_save(rsg_ham H, const char *path, const void *psi, int64_t S, int64_t ld,
+                           int psi_on_device, int64_t step, double time, uint64_t seed);
+rsg_status rsg_states_load(rsg_ham H, const char *path, void *psi, int64_t S, int64_t ld, int psi_on_device,
+                           int64_t *step, double *time, uint64_t *seed);
+
 /* FP64 <psi_s|psi_s> for S states into norms2_out (host, S doubles);
  * synchronises. */
 rsg_status rsg_state_norms(rsg_ham H, const void *psi, int64_t S, int64_t ld,

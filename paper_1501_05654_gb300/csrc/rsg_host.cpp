@@ -1284,6 +1284,123 @@ rsg_status rsg_taylor_apply(rsg_ham H, const void *psi, void *out, int64_t S, in
     return taylor(H, psi, out, ld, tau, H->eps, H->dir, (cudaStream_t)stream);
 }
 
+// ------------------------------------------------ checkpoint / resume ----
+// A state block is stored as a NumPy .npy file (format 1.0: magic, version,
+// little-endian header length, a Python-literal header dict padded to a
+// multiple of 64 bytes) holding the live (P, S) columns in library point
+// order, plus `path`.json with the step counter, time and the caller's seed.
+
+static std::string npy_descr(rsg_dtype t) { return t == RSG_C64 ? "<c8" : "<c16"; }
+
+rsg_status rsg_states_save(rsg_ham H, const char *path, const void *psi, int64_t S, int64_t ld,
+                           int psi_on_device, int64_t step, double time, uint64_t seed) {
+    if (!H || !path || !psi) return fail(RSG_ERR_ARG, "NULL argument");
+    if (S < 1 || ld < S) return fail(RSG_ERR_ARG, "need 1 <= S <= ld");
+    const size_t cb = cbytes(H->dtype);
+    const int64_t P = H->m->P;
+    std::vector<char> host;
+    const char *src = (const char *)psi;
+    if (psi_on_device) {
+        host.resize((size_t)P * ld * cb);
+        CK(cudaMemcpy(host.data(), psi, host.size(), cudaMemcpyDeviceToHost));
+        src = host.data();
+    }
+    char dict[256];
+    std::snprintf(dict, sizeof dict, "{'descr': '%s', 'fortran_order': False, 'shape': (%lld, %lld), }",
+                  npy_descr(H->dtype).c_str(), (long long)P, (long long)S);
+    std::string hdr(dict);
+    const size_t unpadded = 10 + hdr.size() + 1;
+    hdr.append((64 - unpadded % 64) % 64, ' ');
+    hdr.push_back('\n');
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(RSG_ERR_ARG, "cannot open %s for writing", path);
+    const unsigned char pre[10] = {0x93, 'N', 'U', 'M', 'P', 'Y', 1, 0, (unsigned char)(hdr.size() & 0xff),
+                                   (unsigned char)(hdr.size() >> 8)};
+    bool ok = std::fwrite(pre, 1, 10, f) == 10 && std::fwrite(hdr.data(), 1, hdr.size(), f) == hdr.size();
+    for (int64_t p = 0; ok && p < P; p++)
+        ok = std::fwrite(src + (size_t)p * ld * cb, cb, (size_t)S, f) == (size_t)S;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(RSG_ERR_ARG, "writing %s failed", path);
+    const std::string meta = std::string(path) + ".json";
+    FILE *m = std::fopen(meta.c_str(), "w");
+    if (!m) return fail(RSG_ERR_ARG, "cannot open %s for writing", meta.c_str());
+    std::fprintf(m,
+                 "{\"format\": \"rsg-states-1\", \"points\": %lld, \"states\": %lld, \"dtype\": \"%s\", "
+                 "\"step\": %lld, \"time\": %.17g, \"seed\": %llu}\n",
+                 (long long)P, (long long)S, H->dtype == RSG_C64 ? "complex64" : "complex128", (long long)step, time,
+                 (unsigned long long)seed);
+    if (std::fclose(m) != 0) return fail(RSG_ERR_ARG, "writing %s failed", meta.c_str());
+    return RSG_OK;
+}
+
+rsg_status rsg_states_load(rsg_ham H, const char *path, void *psi, int64_t S, int64_t ld, int psi_on_device,
+                           int64_t *step, double *time, uint64_t *seed) {
+    if (!H || !path || !psi) return fail(RSG_ERR_ARG, "NULL argument");
+    if (S < 1 || ld < S) return fail(RSG_ERR_ARG, "need 1 <= S <= ld");
+    const size_t cb = cbytes(H->dtype);
+    const int64_t P = H->m->P;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(RSG_ERR_ARG, "cannot open %s", path);
+    unsigned char pre[12];
+    std::string hdr;
+    bool ok = std::fread(pre, 1, 8, f) == 8 && std::memcmp(pre, "\x93NUMPY", 6) == 0 && (pre[6] == 1 || pre[6] == 2);
+    size_t hlen = 0;
+    if (ok && pre[6] == 1) {
+        ok = std::fread(pre + 8, 1, 2, f) == 2;
+        hlen = (size_t)pre[8] | ((size_t)pre[9] << 8);
+    } else if (ok) {
+        ok = std::fread(pre + 8, 1, 4, f) == 4;
+        hlen = (size_t)pre[8] | ((size_t)pre[9] << 8) | ((size_t)pre[10] << 16) | ((size_t)pre[11] << 24);
+    }
+    if (ok && hlen < (1u << 16)) {
+        hdr.resize(hlen);
+        ok = std::fread(&hdr[0], 1, hlen, f) == hlen;
+    } else {
+        ok = false;
+    }
+    char want[128];
+    std::snprintf(want, sizeof want, "(%lld, %lld)", (long long)P, (long long)S);
+    if (ok && (hdr.find("'descr': '" + npy_descr(H->dtype) + "'") == std::string::npos ||
+               hdr.find("'fortran_order': False") == std::string::npos ||
+               hdr.find(std::string("'shape': ") + want) == std::string::npos)) {
+        std::fclose(f);
+        return fail(RSG_ERR_ARG, "%s does not hold a C-ordered %s block of shape %s", path,
+                    npy_descr(H->dtype).c_str(), want);
+    }
+    std::vector<char> host((size_t)P * ld * cb, 0);
+    for (int64_t p = 0; ok && p < P; p++)
+        ok = std::fread(host.data() + (size_t)p * ld * cb, cb, (size_t)S, f) == (size_t)S;
+    std::fclose(f);
+    if (!ok) return fail(RSG_ERR_ARG, "%s is not a readable .npy state block", path);
+    if (step || time || seed) {
+        const std::string meta = std::string(path) + ".json";
+        FILE *m = std::fopen(meta.c_str(), "r");
+        if (!m) return fail(RSG_ERR_ARG, "metadata %s missing", meta.c_str());
+        char buf[1024] = {0};
+        const size_t n = std::fread(buf, 1, sizeof buf - 1, m);
+        std::fclose(m);
+        buf[n] = 0;
+        long long st = 0, pts = -1, sts = -1;
+        double t = 0.0;
+        unsigned long long sd = 0;
+        const char *q;
+        bool mok = (q = std::strstr(buf, "\"points\":")) && std::sscanf(q + 9, "%lld", &pts) == 1 &&
+                   (q = std::strstr(buf, "\"states\":")) && std::sscanf(q + 9, "%lld", &sts) == 1 &&
+                   (q = std::strstr(buf, "\"step\":")) && std::sscanf(q + 7, "%lld", &st) == 1 &&
+                   (q = std::strstr(buf, "\"time\":")) && std::sscanf(q + 7, "%lg", &t) == 1 &&
+                   (q = std::strstr(buf, "\"seed\":")) && std::sscanf(q + 7, "%llu", &sd) == 1;
+        if (!mok || pts != P || sts != S) return fail(RSG_ERR_ARG, "metadata %s does not match", meta.c_str());
+        if (step) *step = st;
+        if (time) *time = t;
+        if (seed) *seed = sd;
+    }
+    if (psi_on_device)
+        CK(cudaMemcpy(psi, host.data(), host.size(), cudaMemcpyHostToDevice));
+    else
+        std::memcpy(psi, host.data(), host.size());
+    return RSG_OK;
+}
+
 rsg_status rsg_state_norms(rsg_ham H, const void *psi, int64_t S, int64_t ld, double *norms2_out,
                            void *stream) {
     if (!H || !norms2_out) return fail(RSG_ERR_ARG, "NULL argument");

@@ -45,6 +45,8 @@ SIGNATURES = {
     "rsg_propagate_steps": [_vp, _vp, _i64, _i64, _i64, _dbl, _int, _int, _vp, _vp, _int, _vp, _vp],
     "rsg_orthonormalize": [_vp, _vp, _i64, _i64, _vp, _vp],
     "rsg_absorber_set": [_vp, _vp, _int],
+    "rsg_states_save": [_vp, C.c_char_p, _vp, _i64, _i64, _int, _i64, _dbl, C.c_uint64],
+    "rsg_states_load": [_vp, C.c_char_p, _vp, _i64, _i64, _int, _vp, _vp, _vp],
     "rsg_mesh_set_boundary": [_vp, _int],
     "rsg_projectors_set_raw": [_vp, _int, _vp, _vp, _vp, _vp, _vp],
     "rsg_complex_scaling_set": [_vp, _dbl, _vp, _int],
@@ -243,6 +245,40 @@ class Hamiltonian:
             a = v_theta.numpy() if isinstance(v_theta, torch.Tensor) else np.asarray(v_theta)
             v = np.ascontiguousarray(a.astype(np.complex128)).view(np.float64)
             _ck(load().rsg_complex_scaling_set(self._h, float(theta), _ptr(v), 0))
+
+    def save_states(self, path, psi, S=None, step: int = 0, time: float = 0.0, seed: int = 0):
+        """Write the S live columns of psi (cuda tensor or host array of
+        shape (P, ld)) to path (.npy) and its metadata to path.json."""
+        dev = isinstance(psi, torch.Tensor) and psi.is_cuda
+        if dev:
+            self._check(psi)
+            ptr, ld = C.c_void_p(psi.data_ptr()), psi.shape[1]
+        else:
+            a = psi.numpy() if isinstance(psi, torch.Tensor) else psi
+            a = np.ascontiguousarray(a, dtype=np.complex64 if self.dtype == torch.complex64 else np.complex128)
+            ptr, ld = _ptr(a), a.shape[1]
+        S = ld if S is None else S
+        _ck(load().rsg_states_save(self._h, os.fsencode(str(path)), ptr, S, ld, int(dev), int(step), float(time),
+                                   int(seed)))
+
+    def load_states(self, path, psi, S=None):
+        """Read path into psi (cuda tensor, or a writable C-contiguous host
+        array of shape (P, ld)); returns (step, time, seed)."""
+        dev = isinstance(psi, torch.Tensor) and psi.is_cuda
+        if dev:
+            self._check(psi)
+            ptr, ld = C.c_void_p(psi.data_ptr()), psi.shape[1]
+        else:
+            a = psi.numpy() if isinstance(psi, torch.Tensor) else psi
+            want = np.complex64 if self.dtype == torch.complex64 else np.complex128
+            if not (a.dtype == want and a.flags.c_contiguous and a.flags.writeable and a.ndim == 2):
+                raise ValueError("psi: writable C-contiguous (P, ld) array of the Hamiltonian's dtype")
+            ptr, ld = _ptr(a), a.shape[1]
+        S = ld if S is None else S
+        st, t, sd = C.c_int64(), C.c_double(), C.c_uint64()
+        _ck(load().rsg_states_load(self._h, os.fsencode(str(path)), ptr, S, ld, int(dev), C.byref(st), C.byref(t),
+                                   C.byref(sd)))
+        return int(st.value), float(t.value), int(sd.value)
 
     def set_option(self, key: str, value: int):
         _ck(load().rsg_ham_set_option(self._h, key.encode(), int(value)))
