@@ -456,6 +456,12 @@ rsg_status rsg_ham_kernel_stats(rsg_ham H, double *kernel_ms, int64_t *kernel_la
 rsg_status rsg_selftest_bounded_wait(rsg_ham H, int polls, void *stream);
 rsg_status rsg_debug_fail_allocations(int n);
 
+/* Diagnostics on stderr: 0 silent (default), 1 every error status with
+ * its message, 2 also the stencil-kernel fallbacks (small problems, block
+ * shapes a kernel does not take).  The environment variable RSG_LOG_LEVEL
+ * sets the initial level.  Errors: RSG_ERR_ARG for a level outside 0..2. */
+rsg_status rsg_set_log_level(int level);
+
 /* Thread-local description of the last error (empty if none). */
 const char *rsg_last_error(void);
 

@@ -16,6 +16,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -44,6 +45,31 @@ namespace {
 
 thread_local std::string g_err;
 
+// Diagnostics on stderr (rsg_set_log_level): 0 silent, 1 every error
+// status, 2 also stencil-kernel fallbacks.  RSG_LOG_LEVEL sets the initial
+// level.
+std::atomic<int> g_log_level{-1};
+
+int log_level() {
+    int l = g_log_level.load();
+    if (l < 0) {
+        const char *e = std::getenv("RSG_LOG_LEVEL");
+        l = e ? std::max(0, std::min(2, std::atoi(e))) : 0;
+        g_log_level.store(l);
+    }
+    return l;
+}
+
+void log_info(const char *fmt, ...) {
+    if (log_level() < 2) return;
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    std::fprintf(stderr, "rsg: %s\n", buf);
+}
+
 rsg_status fail(rsg_status s, const char *fmt, ...) {
     char buf[512];
     va_list ap;
@@ -51,6 +77,7 @@ rsg_status fail(rsg_status s, const char *fmt, ...) {
     vsnprintf(buf, sizeof(buf), fmt, ap);
     va_end(ap);
     g_err = buf;
+    if (log_level() >= 1) std::fprintf(stderr, "rsg: error %d: %s\n", (int)s, buf);
     return s;
 }
 
@@ -455,7 +482,11 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
             // kernel instead
             int cv, nxr, ty;
             stage_shape(cfg, SV, &cv, &nxr, &ty);
-            if ((int64_t)ntiles * ((SV + cv - 1) / cv) < 2 * 152) cfg.kernel = 1;
+            if ((int64_t)ntiles * ((SV + cv - 1) / cv) < 2 * 152) {
+                log_info("small problem (%d tiles): one-thread-per-value kernel instead of kernel %d", ntiles,
+                         cfg.kernel);
+                cfg.kernel = 1;
+            }
         }
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -517,6 +548,7 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         } else {
             TileCfg c0 = cfg;
             int n = ntiles;
+            if (c0.kernel >= 3) log_info("kernel %d not available for this block shape: kernel 0 runs", c0.kernel);
             if (c0.kernel >= 3) {
                 // same tiles for kernel 4 (the staged block shape)
                 const bool retile = c0.kernel != 4;
@@ -1424,6 +1456,12 @@ rsg_status rsg_selftest_bounded_wait(rsg_ham H, int polls, void *stream) {
     CK(launch_selftest_wait(polls, H->status.as<int>(), st));
     H->n_launch++;
     return read_status(H, st);
+}
+
+rsg_status rsg_set_log_level(int level) {
+    if (level < 0 || level > 2) return fail(RSG_ERR_ARG, "log level must be 0, 1 or 2");
+    g_log_level.store(level);
+    return RSG_OK;
 }
 
 rsg_status rsg_debug_fail_allocations(int n) {

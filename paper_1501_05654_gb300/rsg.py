@@ -70,6 +70,7 @@ SIGNATURES = {
     "rsg_ham_kernel_stats": [_vp, _vp, _vp, _vp, _vp],
     "rsg_selftest_bounded_wait": [_vp, _int, _vp],
     "rsg_debug_fail_allocations": [_int],
+    "rsg_set_log_level": [_int],
     "rsg_last_error": [],
 }
 

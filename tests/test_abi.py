@@ -231,3 +231,21 @@ def test_mesh_boundary_rule(lib):
     assert lib.rsg_mesh_set_boundary(None, 0) == -1
     assert lib.rsg_mesh_set_boundary(cube._h, rsg.BC_ODD) == 0
     assert lib.rsg_mesh_set_boundary(cube._h, rsg.BC_ZERO) == 0
+
+
+def test_log_level(lib):
+    """Errors go to stderr at level >= 1 (RSG_LOG_LEVEL or rsg_set_log_level);
+    the default level is silent."""
+    import subprocess
+    import sys
+    code = ("import paper_1501_05654_gb300 as rsg; L = rsg.load(); "
+            "L.rsg_mesh_set_boundary(None, 0)")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RSG_LOG_LEVEL="1", PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "rsg: error -1: NULL mesh" in r.stderr, r.stderr
+    env["RSG_LOG_LEVEL"] = "0"
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "rsg:" not in r.stderr, r.stderr
+    assert lib.rsg_set_log_level(3) == -1
+    assert lib.rsg_set_log_level(0) == 0
