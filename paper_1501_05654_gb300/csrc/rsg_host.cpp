@@ -1,13 +1,19 @@
 // Host side of the C ABI declared in include/rsg.h: handles, mesh and
 // projector tables, argument checks, workspace and the launch sequences of
 // the Hamiltonian application, the Taylor-4 propagator, the Cholesky-QR
-// re-orthonormalisation and the discrete adjoint of the control gradient.
+// re-orthonormalisation and the discrete adjoint of the control gradient;
+// the solvers built on the application (L-BFGS control loop, Chebyshev-
+// filtered eigensolver, COCG shifted solves); batches; checkpoint files;
+// the failure-path and diagnostic helpers.
 //
 // Method passages (arXiv:1501.05654): Sec. 1 (uniform grids, finite
 // differences), Sec. "Parallelization, optimizations and graphics processing units" (Hamiltonian application on groups of
 // states; linear arrays plus grid tables; re-orthonormalisation only rarely
 // needed in real time), Sec. "Magnetic response and gauge invariance in real-space grids" (non-local pseudopotential),
-// Sec. "Quantum optimal control" (Eq. (qoctgradient), costate propagation).
+// Sec. "Quantum optimal control" (Eq. (qoctgradient), costate propagation,
+// the parameters that shape the field), Sec. "The Sternheimer formulation of
+// linear-response" (shifted systems), Sec. "Photoemission" (mask split),
+// Sec. "Complex scaling and resonances" (H_theta).
 #include <atomic>
 #include <cuda_runtime.h>
 
