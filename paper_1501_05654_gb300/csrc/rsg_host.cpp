@@ -350,6 +350,10 @@ void block_shape(const TileCfg &c, int SV, int *TX, int *TY) {
         quad_shape(c, TX, TY);
         return;
     }
+    if (c.kernel == 7) {
+        wide_shape(c, TX, TY);
+        return;
+    }
     if (c.kernel == 3) {
         int cv, nxr, ty;
         tma_shape(c, SV, &cv, &nxr, &ty);
@@ -488,7 +492,8 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
             // kernel instead
             int cv, nxr, ty;
             stage_shape(cfg, SV, &cv, &nxr, &ty);
-            if ((int64_t)ntiles * ((SV + cv - 1) / cv) < 2 * 152) {
+            if (cfg.kernel == 7) cv = 8;   // 128-byte chunks: 8 vectors
+            if ((int64_t)ntiles * ((SV + cv - 1) / cv) < (cfg.kernel == 7 ? 152 : 2 * 152)) {
                 log_info("small problem (%d tiles): one-thread-per-value kernel instead of kernel %d", ntiles,
                          cfg.kernel);
                 cfg.kernel = 1;
@@ -547,8 +552,10 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         bool done = false;
         if (cfg.kernel == 3) CK(launch_apply_tma<R>(b, cfg, ntiles, st, &done));
         if (cfg.kernel == 4) CK(launch_apply_rowtma<R>(b, cfg, ntiles, st, &done));
-        if constexpr (std::is_same<R, float>::value)
+        if constexpr (std::is_same<R, float>::value) {
             if (cfg.kernel == 5) CK(launch_apply_quad(b, cfg, ntiles, st, &done));
+            if (cfg.kernel == 7) CK(launch_apply_wide(b, cfg, ntiles, st, &done));
+        }
         if (done) {
             H->last_kernel = cfg.kernel;
         } else {
@@ -937,6 +944,8 @@ rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value) {
     else if (k == "last_kernel") *value = H->last_kernel;
     else if (k == "rx") *value = H->cfg.rx;
     else if (k == "ty") *value = H->cfg.ty;
+    else if (k == "wide_ty") *value = H->cfg.wty;
+    else if (k == "producers") *value = H->cfg.npw;
     else if (k == "zseg") *value = H->cfg.zseg;
     else if (k == "cv") *value = H->cfg.cv;
     else if (k == "threads") *value = H->cfg.threads;
@@ -950,7 +959,7 @@ rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value) {
 rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     if (!H || !key) return fail(RSG_ERR_ARG, "NULL argument");
     std::string k(key);
-    if (k == "kernel" && (value >= 0 && value <= 5)) {
+    if (k == "kernel" && ((value >= 0 && value <= 5) || value == 7)) {
         H->cfg.kernel = (int)value;
         H->force_kernel = true;
     }
@@ -958,6 +967,8 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     else if (k == "ty" && (value == 1 || value == 2 || value == 4 || value == 8 || value == 16))
         H->cfg.ty = (int)value;
     else if (k == "zseg" && value >= 1 && value <= 256) H->cfg.zseg = (int)value;
+    else if (k == "wide_ty" && (value == 4 || value == 6 || value == 8)) H->cfg.wty = (int)value;
+    else if (k == "producers" && value >= 1 && value <= 4) H->cfg.npw = (int)value;
     else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
     else if (k == "adjoint_keep_powers" && value >= -1 && value <= 1) H->adj_keep = (int)value;
     else if (k == "threads" && (value == 160 || value == 192 || value == 256 || value == 512))

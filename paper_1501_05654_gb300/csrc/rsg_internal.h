@@ -28,9 +28,11 @@ struct Tile {
 // Kernel tile configuration.
 struct TileCfg {
     int kernel = 0;   // 0 shared-memory staged, 1 naive, 2 L1 z-march, 3 TMA gather, 4 row-TMA staged,
-                      // 5 register-blocked staged (complex64)
+                      // 5 register-blocked staged (complex64), 7 warp-specialised tensor-copy staged (complex64)
     int rx = 1;       // points per thread along x
     int ty = 16;      // rows per tile (blockDim.z)
+    int wty = 8;      // kernel 7: rows per tile, 8, 6 or 4
+    int npw = 1;      // kernel 7: producer warps, 1 to 4
     int zseg = 120;   // planes per z segment
     int cv = 2;       // staged kernel: 16-byte vectors per point in a chunk (1..8)
     int stages = 4;   // staged kernels: shared-memory pipeline depth (3 or 4; kernel 4: 4 or 5 with 256 threads)
@@ -103,6 +105,12 @@ cudaError_t launch_apply_tma(const ApplyArgs<R> &a, const TileCfg &cfg, int ntil
 // launcher; *launched = false when it does not apply.
 void quad_shape(const TileCfg &cfg, int *TX, int *TY);
 cudaError_t launch_apply_quad(const ApplyArgs<float> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
+                              bool *launched);
+// Warp-specialised stencil with tensor-copy staging (kernel 7, complex64,
+// rsg_wide.cu): tile shape and launcher; *launched = false when it does not
+// apply (unaligned blocks, complex scaling, shared memory too small).
+void wide_shape(const TileCfg &cfg, int *TX, int *TY);
+cudaError_t launch_apply_wide(const ApplyArgs<float> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
                               bool *launched);
 // Row-TMA staged stencil (kernel 4, the staged block shape); *launched =
 // false when it does not apply.

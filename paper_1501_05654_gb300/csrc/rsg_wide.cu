@@ -1,0 +1,561 @@
+// Warp-specialised stencil for complex64 blocks (kernel 7).
+//
+// The operator and epilogue are those of the other stencil kernels: the
+// 8th-order 25-point star Laplacian with zero values outside the mesh, and
+// the local potential and dipole field on the diagonal (arXiv:1501.05654
+// Sec. 1 and Sec. "Parallelization, optimizations and graphics processing
+// units"); projector terms are added afterwards by k_proj_scatter.
+//
+// A block owns a 16 x TY tile of (x, y) columns, marched along z, and one
+// 128-byte chunk of every point's state row (16 complex64 values, the
+// "record" of the point).
+//
+// One producer warp moves each plane into shared memory with 2-D tensor
+// copies.  The copies view the state block as (points, state floats), and a
+// mesh row is a run of consecutive point indices.  So each row of the plane's
+// cross-shaped window is one box of 24 (or 16) records, or a few boxes of 16,
+// 8, 4, 2 and 1 records where the mesh row covers only part of the window.
+// Window positions outside the mesh must read zero.  They are filled by
+// boxes placed wholly before point 0, which the copy engine fills with zeros.
+// A position is re-zeroed only if it held a mesh point the last time its slot
+// was used.  The base values of the plane's outputs (16-record boxes) and the
+// potential (4-byte cp.async) travel in the same slot.
+//
+// Synchronisation uses two mbarriers per slot. The "full" barrier completes
+// on the expected byte count plus the potential's cp.async arrivals. The
+// "empty" barrier takes one arrival from each compute warp after its last
+// read of the slot. No block-wide barrier runs inside the march.
+//
+// Compute warps (4 NYP of them): a thread owns one complex value of the chunk
+// at a 2 x 2 group of points and keeps four nine-deep z queues, as in the
+// register-blocked kernel 5.  A warp covers 4 x 2 columns.  Planes before the
+// first mesh point of its columns, and after its last output, are passed with
+// a wait and a release only.
+//
+// Every mbarrier wait is bounded.  A wait that gives up sets a block-wide
+// abort flag.  Later waits then return at once, the producer stops issuing,
+// and the block records status 2 (RSG_ERR_TIMEOUT) before it leaves.  The
+// producer first waits, again with a bound, for the copies it has issued.
+#include <cuda.h>
+
+#include <array>
+#include <mutex>
+#include <unordered_map>
+
+#include "rsg_async.cuh"
+#include "rsg_internal.h"
+#include "rsg_vec.cuh"
+
+namespace rsg {
+
+template <int NYP, int NPW = 1>
+struct WideGeom {
+    static constexpr int TX = 16, TY = 2 * NYP;
+    static constexpr int WX = TX + 8, WY = TY + 8;   // window (cross inside the rectangle)
+    static constexpr int NC = 16;                    // complex values per record
+    static constexpr int REC = NC * 8;               // bytes per record
+    static constexpr int NCW = 4 * NYP;              // compute warps
+    static constexpr int NT = 32 * (NCW + NPW);      // plus the producer warps
+    static constexpr int SLOT = WY * WX;             // records per plane
+    static constexpr int NPTS = TX * TY;             // interior points
+    static_assert(WY + TY <= 32 * NPW, "one producer lane per window row and per base row");
+    static_assert((TX * TY) % 32 == 0, "the potential's points in groups of 32");
+};
+
+// Tensor maps of one launch: boxes of 1, 2, 4, 8, 16 and 24 records over the
+// input block, and of 1 .. 16 records over the base block.
+struct WideMaps {
+    CUtensorMap u[6];
+    CUtensorMap b[5];
+};
+
+constexpr long kWideWaitLimit = 1L << 21;
+constexpr int kWideZeroPoint = -64;   // first point of a zero-fill box (every row out of range)
+
+__device__ __forceinline__ bool wide_wait(unsigned bar, unsigned parity, volatile int *abort_flag) {
+    for (long it = 0; it < kWideWaitLimit; ++it) {
+        unsigned ok;
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(ok)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (*abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void wide_box(unsigned dst, const CUtensorMap *tm, int c0, int p0, unsigned bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"(tm), "r"(c0), "r"(p0), "r"(bar)
+        : "memory");
+}
+
+// y = alpha * acc + beta * base; out = y; optional acc += gamma * y
+__device__ __forceinline__ void wide_finish(const ApplyArgs<float> &a, int o, float2 acc, float2 bv) {
+    float2 y = f2_fma(make_float2(-a.ai, a.ai), make_float2(acc.y, acc.x), f2_mul(make_float2(a.ar, a.ar), acc));
+    if (a.base != nullptr) {
+        y = f2_fma(make_float2(a.br, a.br), bv, y);
+        y = f2_fma(make_float2(-a.bi, a.bi), make_float2(bv.y, bv.x), y);
+    }
+    ((float2 *)a.out)[o] = y;
+    if (a.acc != nullptr) {
+        float2 s = a.acc_base != nullptr ? ((const float2 *)a.acc_base)[o] : ((float2 *)a.acc)[o];
+        s = f2_fma(make_float2(a.gr, a.gr), y, s);
+        s = f2_fma(make_float2(-a.gi, a.gi), make_float2(y.y, y.x), s);
+        ((float2 *)a.acc)[o] = s;
+    }
+}
+
+// EPI 1: Horner stage, out = (i ai) H u + base (ar = 0, beta = 1, no
+// accumulator); EPI 0: the general epilogue of wide_finish.
+template <int NYP, int NS, int NPW, int EPI>
+__global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
+    k_apply_wide(const ApplyArgs<float> a, int nchunks, const __grid_constant__ WideMaps maps) {
+    using G = WideGeom<NYP, NPW>;
+    constexpr int TX = G::TX, TY = G::TY, WX = G::WX, WY = G::WY, NC = G::NC, NCW = G::NCW;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    // 1024-byte aligned start: u ring, base ring, potential ring, row table,
+    // barriers, abort flag
+    const unsigned sraw = (unsigned)__cvta_generic_to_shared(smraw);
+    const unsigned s_u = (sraw + 1023u) & ~1023u;
+    unsigned char *gbase = smraw + (s_u - sraw);
+    const unsigned s_b = s_u + NS * G::SLOT * G::REC;
+    const unsigned s_v = s_b + NS * G::NPTS * G::REC;
+    const Tile tl = a.tiles[blockIdx.x / nchunks];
+    const int chunk = blockIdx.x % nchunks;
+    const int np = tl.zhi - tl.zlo + 8;
+    SRow *srows = (SRow *)(gbase + (s_v - s_u) + NS * G::NPTS * 4);
+    const unsigned s_rows = s_v + NS * G::NPTS * 4;
+    const unsigned bar0 = (s_rows + (unsigned)(WY * np * sizeof(SRow)) + 7u) & ~7u;
+    volatile int *abort_flag = (volatile int *)(gbase + (bar0 - s_u) + 16 * NS);
+
+    const int ny = a.ny, nz = a.nz, ld = 2 * a.SV;
+    const int tx0 = tl.tx * TX, ty0 = tl.ty * TY;
+    const int xb = tx0 - 4, ybase = ty0 - 4, zbase = tl.zlo - 4;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < WY * np; i += G::NT) {
+        const int zz = i / WY;
+        const int yy = ybase + (i - zz * WY);
+        const int zg = zbase + zz;
+        // start holds the point index of bbox column 0 of the row (start -
+        // xmin), so that point (x, row) is start + x
+        SRow r{0, 1, 0};
+        if (yy >= 0 && yy < ny && zg >= 0 && zg < nz) {
+            const Row g = a.rows[zg * ny + yy];
+            r.start = g.start - g.xmin;
+            r.xmin = (int16_t)g.xmin;
+            r.xmax = (int16_t)g.xmax;
+        }
+        srows[i] = r;
+    }
+    if (tid == 0) {
+        for (int k = 0; k < NS; k++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8 * k), "r"(33 * NPW)
+                         : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8 * (NS + k)), "r"(NCW)
+                         : "memory");
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int k0 = NC * chunk;        // first complex value of the chunk
+    const int c0 = 2 * k0;            // its float column in the tensor view
+
+    if (warp >= NCW) {
+        // ------------------------------------------------ producer warps
+        // Row tasks of a plane: the WY window rows of the state block, then
+        // the TY base rows of the outputs four planes back.  Lane l of
+        // producer warp pw takes row task pw + NPW l.  The potential's points
+        // are shared out in groups of 32.  Every lane first works out its
+        // boxes; the boxes are then issued from one call site per pass, so
+        // the issue loop runs once per box and not once per call site.
+        const int pw = warp - NCW;
+        const int r = pw + NPW * lane;
+        const bool rowlane = r < WY;
+        const bool baselane = a.base != nullptr && r >= WY && r < WY + TY;
+        const int br = r - WY;
+        const bool halo = r < 4 || r >= TY + 4;
+        const int clo = halo ? 4 : 0, chi = halo ? 20 : 24;
+        int pa[NS], pb[NS];   // window columns that held mesh points at the slot's last use
+#pragma unroll
+        for (int s = 0; s < NS; s++) {
+            pa[s] = clo;
+            pb[s] = chi;
+        }
+        int issued = 0;
+        for (int j0 = 0; j0 < np; j0 += NS) {
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+                const int j = j0 + s;
+                if (j >= np || *abort_flag) break;
+                const unsigned full = bar0 + 8 * s, empty = bar0 + 8 * (NS + s);
+                if (j >= NS && !wide_wait(empty, (unsigned)((j / NS - 1) & 1), abort_flag)) break;
+                // this lane's spans: records to copy (dst, first point, count)
+                // and records to zero (two runs)
+                unsigned vd = 0, zd = 0, zd2 = 0;
+                int vp = 0, vn = 0, zn = 0, zn2 = 0;
+                if (rowlane) {
+                    const SRow rw = srows[j * WY + r];
+                    int ua = max(clo, rw.xmin - xb), ub = min(chi, rw.xmax - xb + 1);
+                    if (ua >= ub) ua = ub = clo;
+                    const unsigned drow = s_u + (unsigned)((s * G::SLOT + r * WX) * G::REC);
+                    vd = drow + ua * G::REC;
+                    vp = rw.start + xb + ua;
+                    vn = ub - ua;
+                    // re-zero what held mesh points at the slot's last use
+                    const int z1a = pa[s], z1b = ua == ub ? pa[s] : min(pb[s], ua);
+                    const int z2a = ua == ub ? pa[s] : max(pa[s], ub), z2b = pb[s];
+                    zd = drow + z1a * G::REC;
+                    zn = max(0, z1b - z1a);
+                    zd2 = drow + z2a * G::REC;
+                    zn2 = max(0, z2b - z2a);
+                    pa[s] = ua;
+                    pb[s] = ub;
+                } else if (baselane && j >= 4) {
+                    const SRow rb = srows[(j - 4) * WY + 4 + br];
+                    int ba = max(0, rb.xmin - tx0), bb = min(TX, rb.xmax - tx0 + 1);
+                    if (ba >= bb) ba = bb = 0;
+                    vd = s_b + (unsigned)((s * G::NPTS + br * TX + ba) * G::REC);
+                    vp = rb.start + tx0 + ba;
+                    vn = bb - ba;
+                }
+                const unsigned bytes = __reduce_add_sync(0xffffffffu, (unsigned)(vn + zn + zn2) * G::REC);
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(bytes)
+                                 : "memory");
+                __syncwarp();
+                const CUtensorMap *vm = rowlane ? maps.u : maps.b;
+                // copies: widest box first (24 records for a whole window row)
+                while (__any_sync(0xffffffffu, vn > 0)) {
+                    if (vn > 0) {
+                        const int mi = (rowlane && vn == 24) ? 5 : 31 - __clz(vn);
+                        const int w = mi == 5 ? 24 : 1 << mi;
+                        wide_box(vd, vm + mi, c0, vp, full);
+                        vd += (unsigned)(w * G::REC);
+                        vp += w;
+                        vn -= w;
+                    }
+                }
+                // zero fills: boxes wholly before point 0
+                while (__any_sync(0xffffffffu, zn > 0 || zn2 > 0)) {
+                    if (zn == 0 && zn2 > 0) {
+                        zd = zd2;
+                        zn = zn2;
+                        zn2 = 0;
+                    }
+                    if (zn > 0) {
+                        const int mi = zn == 24 ? 5 : 31 - __clz(zn);
+                        const int w = mi == 5 ? 24 : 1 << mi;
+                        wide_box(zd, maps.u + mi, c0, kWideZeroPoint, full);
+                        zd += (unsigned)(w * G::REC);
+                        zn -= w;
+                    }
+                }
+                // potential of the interior points (zero outside the mesh)
+#pragma unroll
+                for (int i = pw; i < G::NPTS / 32; i += NPW) {
+                    const int pt = lane + 32 * i, py = pt / TX, px = pt - py * TX;
+                    const SRow rv = srows[j * WY + 4 + py];
+                    const int x = tx0 + px;
+                    const bool ok = x >= rv.xmin && x <= rv.xmax;
+                    cp_async_small<4>(s_v + (unsigned)((s * G::NPTS + pt) * 4), a.V + (ok ? rv.start + x : 0),
+                                      ok ? 4 : 0);
+                }
+                asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full) : "memory");
+                issued = j + 1;
+            }
+        }
+        cp_async_wait<0>();
+        // the copies issued for the last planes have landed before the block
+        // can leave (the compute warps wait for them too, unless aborted)
+        for (int j = max(0, issued - NS); j < issued; j++) {
+            const unsigned full = bar0 + 8 * (j % NS);
+            volatile int never = 0;
+            wide_wait(full, (unsigned)((j / NS) & 1), &never);
+        }
+        if (pw == 0 && lane == 0 && *abort_flag && a.err != nullptr) atomicExch(a.err, 2);
+        return;
+    }
+
+    // ---------------------------------------------------- compute warps
+    const int cc = lane & 15, xh = lane >> 4;
+    const int xl = 2 * (2 * (warp & 3) + xh);    // tile-local x of the thread's first column
+    const int yl = 2 * (warp >> 2);              // tile-local y of its first row
+    const int k = k0 + cc;
+    const bool vok = k < ld;
+    const int x0 = tx0 + xl, y0 = ty0 + yl;
+    // planes (0-based j) where any of the warp's columns holds a point
+    int jc0 = 1 << 30, jc1 = -1;
+    for (int jj = 0; jj < np; jj++) {
+        const SRow r0 = srows[jj * WY + 4 + yl], r1 = srows[jj * WY + 5 + yl];
+        const bool on = (x0 + 1 >= r0.xmin && x0 <= r0.xmax) || (x0 + 1 >= r1.xmin && x0 <= r1.xmax);
+        if (on) {
+            jc0 = min(jc0, jj);
+            jc1 = max(jc1, jj);
+        }
+    }
+    jc0 = __reduce_min_sync(0xffffffffu, jc0);
+    jc1 = __reduce_max_sync(0xffffffffu, jc1);
+    float fxy[4];
+#pragma unroll
+    for (int pt = 0; pt < 4; pt++) fxy[pt] = a.f0 + a.fx * (float)(x0 + (pt & 1)) + a.fy * (float)(y0 + (pt >> 1));
+    const float2 w1 = make_float2(a.w[1], a.w[1]), w2 = make_float2(a.w[2], a.w[2]);
+    const float2 w3 = make_float2(a.w[3], a.w[3]), w4 = make_float2(a.w[4], a.w[4]);
+    const float w0c = 3.0f * a.w[0];
+    constexpr int RW = WX * NC;   // float2 entries per slot row
+    const float2 *uwin = (const float2 *)gbase + ((4 + yl) * WX + xl) * NC + cc;
+    const float2 *bwin = (const float2 *)(gbase + (s_b - s_u)) + (yl * TX + xl) * NC + cc;
+    const float *vwin = (const float *)(gbase + (s_v - s_u)) + yl * TX + xl;
+    const int ox0 = x0 * ld + k;   // output offset of column x0 relative to its row's start
+    float2 *const out2 = (float2 *)a.out;
+
+    // q[pt][e]: partial sums of the outputs at planes j - 4 + e (e = 0..7)
+    // before plane j is added
+    float2 q[4][8];
+#pragma unroll
+    for (int pt = 0; pt < 4; pt++)
+#pragma unroll
+        for (int kk = 0; kk < 8; kk++) q[pt][kk] = make_float2(0.f, 0.f);
+
+    int sl = 0;
+    unsigned par = 0;
+    bool live = true;
+#pragma unroll 1
+    for (int j = 0; j < np; j++) {
+        const unsigned full = bar0 + 8 * sl, empty = bar0 + 8 * (NS + sl);
+        if (live) live = wide_wait(full, par, abort_flag);
+        if (j >= jc0 && j <= jc1 + 4 && live) {
+            float2 s[4], cen[4];
+            if (j <= jc1) {
+                const float2 *pw = uwin + sl * G::SLOT * NC;
+#define QW(r, kk) pw[(r) * RW + (kk) * NC]
+#pragma unroll
+                for (int r = 0; r < 2; r++) {
+                    float2 W[10];
+#pragma unroll
+                    for (int kk = 0; kk < 10; kk++) W[kk] = QW(r, kk);
+                    cen[2 * r] = W[4];
+                    cen[2 * r + 1] = W[5];
+                    float2 t = f2_mul(w1, f2_add(W[3], W[5]));
+                    t = f2_fma(w2, f2_add(W[2], W[6]), t);
+                    t = f2_fma(w3, f2_add(W[1], W[7]), t);
+                    s[2 * r] = f2_fma(w4, f2_add(W[0], W[8]), t);
+                    t = f2_mul(w1, f2_add(W[4], W[6]));
+                    t = f2_fma(w2, f2_add(W[3], W[7]), t);
+                    t = f2_fma(w3, f2_add(W[2], W[8]), t);
+                    s[2 * r + 1] = f2_fma(w4, f2_add(W[1], W[9]), t);
+                }
+#pragma unroll
+                for (int dx = 0; dx < 2; dx++) {
+                    const float2 m4 = QW(-4, 4 + dx), m3 = QW(-3, 4 + dx), m2 = QW(-2, 4 + dx), m1 = QW(-1, 4 + dx);
+                    const float2 p2 = QW(2, 4 + dx), p3 = QW(3, 4 + dx), p4 = QW(4, 4 + dx), p5 = QW(5, 4 + dx);
+                    float2 t = f2_fma(w1, f2_add(m1, cen[2 + dx]), s[dx]);
+                    t = f2_fma(w2, f2_add(m2, p2), t);
+                    t = f2_fma(w3, f2_add(m3, p3), t);
+                    s[dx] = f2_fma(w4, f2_add(m4, p4), t);
+                    t = f2_fma(w1, f2_add(cen[dx], p2), s[2 + dx]);
+                    t = f2_fma(w2, f2_add(m1, p3), t);
+                    t = f2_fma(w3, f2_add(m2, p4), t);
+                    s[2 + dx] = f2_fma(w4, f2_add(m3, p5), t);
+                }
+#undef QW
+                const float fz = a.fz * (float)(zbase + j) + w0c;
+                const float *vv = vwin + sl * G::NPTS;
+#pragma unroll
+                for (int pt = 0; pt < 4; pt++) {
+                    // diagonal: staged V (zero outside the mesh) plus the field
+                    const float d = vv[(pt >> 1) * TX + (pt & 1)] + fxy[pt] + fz;
+                    s[pt].x = fmaf(d, cen[pt].x, s[pt].x);
+                    s[pt].y = fmaf(d, cen[pt].y, s[pt].y);
+                }
+            } else {
+#pragma unroll
+                for (int pt = 0; pt < 4; pt++) s[pt] = cen[pt] = make_float2(0.f, 0.f);
+            }
+            // add plane j to the queues; the output of plane j - 4 completes
+            float2 done[4];
+#pragma unroll
+            for (int pt = 0; pt < 4; pt++) {
+                float2 *qq = q[pt];
+                const float2 cv = cen[pt];
+                done[pt] = f2_fma(w4, cv, qq[0]);
+                qq[0] = f2_fma(w3, cv, qq[1]);
+                qq[1] = f2_fma(w2, cv, qq[2]);
+                qq[2] = f2_fma(w1, cv, qq[3]);
+                qq[3] = f2_add(qq[4], s[pt]);
+                qq[4] = f2_fma(w1, cv, qq[5]);
+                qq[5] = f2_fma(w2, cv, qq[6]);
+                qq[6] = f2_fma(w3, cv, qq[7]);
+                qq[7] = f2_mul(w4, cv);
+            }
+            const int zo = zbase + j - 4;
+            if (zo >= tl.zlo && zo < tl.zhi && vok) {
+                const SRow *ro = srows + (j - 4) * WY + 4 + yl;
+                const float2 *bb = bwin + sl * G::NPTS * NC;
+#pragma unroll
+                for (int dy = 0; dy < 2; dy++) {
+                    const SRow rw = ro[dy];
+                    const int orow = rw.start * ld + ox0;
+#pragma unroll
+                    for (int dx = 0; dx < 2; dx++) {
+                        const int x = x0 + dx;
+                        if (x >= rw.xmin && x <= rw.xmax) {
+                            const int o = orow + dx * ld;
+                            const float2 acc = done[2 * dy + dx];
+                            if constexpr (EPI == 1) {
+                                const float2 bv = bb[(dy * TX + dx) * NC];
+                                float2 y;
+                                y.x = fmaf(-a.ai, acc.y, bv.x);
+                                y.y = fmaf(a.ai, acc.x, bv.y);
+                                out2[o] = y;
+                            } else {
+                                wide_finish(a, o, acc, bb[(dy * TX + dx) * NC]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(empty) : "memory");
+        if (++sl == NS) {
+            sl = 0;
+            par ^= 1u;
+        }
+    }
+}
+
+// ------------------------------------------------------------- host side
+typedef CUresult (*WideEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static WideEncodeFn wide_encode_fn() {
+    static WideEncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (WideEncodeFn)p;
+    });
+    return fn;
+}
+
+// Boxes of 1, 2, 4, 8, 16 and 24 records (16 complex64 values each) over the
+// (P, ld) complex64 block at p, as (points, 2 ld floats); out-of-range rows
+// read zero.  Encoded once per (pointer, ld, P) and kept.
+static bool wide_maps_for(const void *p, int64_t P, int ld, CUtensorMap out[6]) {
+    struct Key {
+        const void *p;
+        int64_t P;
+        int ld;
+        bool operator==(const Key &o) const { return p == o.p && P == o.P && ld == o.ld; }
+    };
+    struct KeyHash {
+        size_t operator()(const Key &k) const {
+            return std::hash<const void *>()(k.p) ^ (std::hash<int64_t>()(k.P) * 31u) ^ (size_t)k.ld * 1315423911u;
+        }
+    };
+    static std::mutex mu;
+    static std::unordered_map<Key, std::array<CUtensorMap, 6>, KeyHash> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    const Key key{p, P, ld};
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        WideEncodeFn fn = wide_encode_fn();
+        if (!fn) return false;
+        std::array<CUtensorMap, 6> m;
+        const int widths[6] = {1, 2, 4, 8, 16, 24};
+        for (int i = 0; i < 6; i++) {
+            cuuint64_t dims[2] = {(cuuint64_t)2 * ld, (cuuint64_t)P};
+            cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
+            cuuint32_t box[2] = {32, (cuuint32_t)widths[i]};
+            cuuint32_t es[2] = {1, 1};
+            if (fn(&m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(p), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return false;
+        }
+        if (cache.size() >= 256) cache.clear();
+        it = cache.emplace(key, m).first;
+    }
+    for (int i = 0; i < 6; i++) out[i] = it->second[i];
+    return true;
+}
+
+void wide_shape(const TileCfg &cfg, int *TX, int *TY) {
+    *TX = 16;
+    *TY = cfg.wty == 6 || cfg.wty == 4 ? cfg.wty : 8;
+}
+
+size_t wide_smem_bytes(int nyp, int ns, int zseg) {
+    const size_t tx = 16, ty = 2 * (size_t)nyp, wx = tx + 8, wy = ty + 8;
+    return 1024 + (size_t)ns * (wy * wx * 128 + tx * ty * 128 + tx * ty * 4) + wy * ((size_t)zseg + 8) * sizeof(SRow) +
+           8 + 16 * (size_t)ns + 16;
+}
+
+template <int NYP, int NS, int NPW>
+static cudaError_t launch_wide_t(const ApplyArgs<float> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
+                                 bool *launched) {
+    // the Horner stage out = (-i tau / k) H u + psi has its own epilogue
+    const bool horner = a.ar == 0.f && a.base != nullptr && a.br == 1.f && a.bi == 0.f && a.acc == nullptr;
+    using G = WideGeom<NYP, NPW>;
+    const size_t smem = wide_smem_bytes(NYP, NS, cfg.zseg);
+    if (smem > 227 * 1024) return cudaSuccess;
+    const int ld = 2 * a.SV;
+    WideMaps maps;
+    if (!wide_maps_for(a.in, a.P, ld, maps.u)) return cudaSuccess;
+    CUtensorMap bm[6];
+    if (!wide_maps_for(a.base != nullptr ? a.base : a.in, a.P, ld, bm)) return cudaSuccess;
+    for (int i = 0; i < 5; i++) maps.b[i] = bm[i];
+    auto kern = horner ? k_apply_wide<NYP, NS, NPW, 1> : k_apply_wide<NYP, NS, NPW, 0>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nchunks = (ld + G::NC - 1) / G::NC;
+    const long long nblk = (long long)ntiles * nchunks;
+    if (nblk > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    kern<<<(unsigned)nblk, G::NT, smem, st>>>(a, nchunks, maps);
+    *launched = true;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_wide(const ApplyArgs<float> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
+                              bool *launched) {
+    *launched = false;
+    // complex offsets are 32-bit; window coordinates are 16-bit
+    if (ntiles == 0 || (long long)a.P * 2 * a.SV >= 0x7fffffffLL || a.nx > 32000) return cudaSuccess;
+    // the tensor view needs 16-byte aligned blocks (ld is even for complex64)
+    if (((uintptr_t)a.in & 15) != 0 || (a.base != nullptr && ((uintptr_t)a.base & 15) != 0)) return cudaSuccess;
+    if (a.err == nullptr || a.Vc != nullptr) return cudaSuccess;
+    // NYP, NS and producer warps: 8-row tiles with 3 slots, 6-row tiles with 3
+    // slots (or 4 with short segments), 4-row tiles with 4 or 5 slots
+#define RSG_WIDE_NPW(NYP_, NS_)                                                        \
+    switch (cfg.npw) {                                                                 \
+    case 2: return launch_wide_t<NYP_, NS_, 2>(a, cfg, ntiles, st, launched);          \
+    case 3: return launch_wide_t<NYP_, NS_, 3>(a, cfg, ntiles, st, launched);          \
+    case 4: return launch_wide_t<NYP_, NS_, 4>(a, cfg, ntiles, st, launched);          \
+    default: return launch_wide_t<NYP_, NS_, 1>(a, cfg, ntiles, st, launched);         \
+    }
+    if (cfg.wty == 4) {
+        if (cfg.stages == 5) RSG_WIDE_NPW(2, 5)
+        RSG_WIDE_NPW(2, 4)
+    }
+    if (cfg.wty == 6) {
+        if (cfg.stages == 4) RSG_WIDE_NPW(3, 4)
+        RSG_WIDE_NPW(3, 3)
+    }
+    RSG_WIDE_NPW(4, 3)
+#undef RSG_WIDE_NPW
+}
+
+}  // namespace rsg

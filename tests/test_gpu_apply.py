@@ -131,6 +131,44 @@ def test_quad_kernel(opts, S):
     assert rel_err(p.states_from_gpu(y, S), want) < TOL[torch.complex64]
 
 
+@pytest.mark.parametrize("opts", [{"kernel": 7}, {"kernel": 7, "wide_ty": 6}, {"kernel": 7, "zseg": 7},
+                                  {"kernel": 7, "zseg": 1}, {"kernel": 7, "wide_ty": 6, "zseg": 3},
+                                  {"kernel": 7, "zseg": 200}])
+@pytest.mark.parametrize("S", [1, 2, 13, 16, 17, 40])
+def test_wide_kernel(opts, S):
+    """Warp-specialised tensor-copy stencil (complex64) on a sphere with
+    projectors and a field: rows that end inside the window (partial boxes and
+    zero-fill boxes), empty planes and columns, a partial last 16-value chunk
+    (S = 1, 2, 13, 17, 40) and a Horner stage (base rows by tensor copy)."""
+    p, g = wells_system("sphere", radius=4.6, h=0.25, dtype=torch.complex64, seed=10, natoms=3, lmax=2)
+    _check_apply(p, g, S, eps=0.02, dir=(0.0, 0.6, 0.8), opts=opts, expect_kernel=7)
+    psi = round_c64(white_noise_states(g, p.P, S))
+    want = p.O.taylor4(psi, 0.01, eps=0.02, dir=(0.0, 0.6, 0.8))
+    y = p.H.taylor(p.states_to_gpu(psi), 0.01, S=S)
+    torch.cuda.synchronize()
+    assert p.H.get_option("last_kernel") == 7
+    assert rel_err(p.states_from_gpu(y, S), want) < TOL[torch.complex64]
+
+
+def test_wide_kernel_cube_box_and_long_segments():
+    """Full rows (one 24-record box per window row), ragged tile tails in x, y
+    and z, extents below the stencil radius, and a 260-plane box in one
+    segment; the same block reused across launches with different inputs."""
+    for shape, n, zseg, wty in (("cube", 37, 150, 8), ("box", (23, 9, 14), 150, 8), ("box", (3, 2, 40), 150, 6),
+                                ("box", (12, 10, 260), 200, 8), ("box", (12, 10, 260), 256, 6),
+                                ("box", (40, 33, 5), 2, 8)):
+        p, g = wells_system(shape, n, h=0.3, dtype=torch.complex64, seed=4, natoms=2, lmax=1)
+        for S in (10, 64):
+            _check_apply(p, g, S, opts={"kernel": 7, "zseg": zseg, "wide_ty": wty}, expect_kernel=7)
+
+
+def test_wide_kernel_declines_oversized_segments():
+    """8-row tiles with 256-plane segments need more shared memory than a
+    block may have: the launcher declines and the staged kernel runs."""
+    p, g = wells_system("box", (12, 10, 260), h=0.3, dtype=torch.complex64, seed=4, natoms=1, lmax=0)
+    _check_apply(p, g, 6, opts={"kernel": 7, "zseg": 256, "wide_ty": 8}, expect_kernel=0)
+
+
 def test_quad_kernel_cube_box_and_complex128_fallback():
     for shape, n in (("cube", 37), ("box", (23, 9, 14)), ("box", (3, 2, 40))):
         p, g = wells_system(shape, n, h=0.3, dtype=torch.complex64, seed=4, natoms=2, lmax=1)
