@@ -62,23 +62,28 @@ struct WideGeom {
     static_assert((TX * TY) % 32 == 0, "the potential's points in groups of 32");
 };
 
-// Tensor maps of one launch: boxes of 1, 2, 4, 8, 16 and 24 records over the
-// input block, and of 1 .. 16 records over the base block.
+// Tensor maps of one launch, one per box width: u[w - 1] copies w = 1 .. 24
+// records of the input block, b[w - 1] w = 1 .. 16 records of the base block,
+// so that every run of consecutive records is a single copy.
 struct WideMaps {
-    CUtensorMap u[6];
-    CUtensorMap b[5];
+    CUtensorMap u[24];
+    CUtensorMap b[16];
 };
 
-constexpr long kWideWaitLimit = 1L << 21;
+// Each poll suspends the thread until the phase completes or about 2 us
+// pass; 2^20 polls bound a wait at about 2 s.
+constexpr long kWideWaitLimit = 1L << 20;
+constexpr unsigned kWideSuspendNs = 2000;
 constexpr int kWideZeroPoint = -64;   // first point of a zero-fill box (every row out of range)
 
 __device__ __forceinline__ bool wide_wait(unsigned bar, unsigned parity, volatile int *abort_flag) {
     for (long it = 0; it < kWideWaitLimit; ++it) {
         unsigned ok;
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                     : "=r"(ok)
-                     : "r"(bar), "r"(parity)
-                     : "memory");
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity), "r"(kWideSuspendNs)
+            : "memory");
         if (ok) return true;
         if (*abort_flag) return false;
     }
@@ -128,15 +133,18 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
     const Tile tl = a.tiles[blockIdx.x / nchunks];
     const int chunk = blockIdx.x % nchunks;
     const int np = tl.zhi - tl.zlo + 8;
+    // window rows (producers) and tile rows (all warps) of every plane
     SRow *srows = (SRow *)(gbase + (s_v - s_u) + NS * G::NPTS * 4);
+    int2 *orows = (int2 *)(srows + WY * np);
     const unsigned s_rows = s_v + NS * G::NPTS * 4;
-    const unsigned bar0 = (s_rows + (unsigned)(WY * np * sizeof(SRow)) + 7u) & ~7u;
+    const unsigned bar0 = (s_rows + (unsigned)(WY * np * sizeof(SRow) + TY * np * sizeof(int2)) + 7u) & ~7u;
     volatile int *abort_flag = (volatile int *)(gbase + (bar0 - s_u) + 16 * NS);
 
     const int ny = a.ny, nz = a.nz, ld = 2 * a.SV;
     const int tx0 = tl.tx * TX, ty0 = tl.ty * TY;
     const int xb = tx0 - 4, ybase = ty0 - 4, zbase = tl.zlo - 4;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+#pragma unroll 4
     for (int i = tid; i < WY * np; i += G::NT) {
         const int zz = i / WY;
         const int yy = ybase + (i - zz * WY);
@@ -151,6 +159,22 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
             r.xmax = (int16_t)g.xmax;
         }
         srows[i] = r;
+    }
+    // per plane and tile row: the point of bbox column 0 and a mask of the
+    // tile columns that are mesh points
+#pragma unroll 4
+    for (int i = tid; i < TY * np; i += G::NT) {
+        const int zz = i / TY;
+        const int yy = ty0 + (i - zz * TY);
+        const int zg = zbase + zz;
+        int2 e = make_int2(0, 0);
+        if (yy < ny && zg >= 0 && zg < nz) {
+            const Row g = a.rows[zg * ny + yy];
+            const int lo = max(g.xmin - tx0, 0), hi = min(g.xmax - tx0, TX - 1);
+            e.x = g.start - g.xmin;
+            e.y = lo <= hi ? (int)(((2u << hi) - 1u) & ~((1u << lo) - 1u)) : 0;
+        }
+        orows[i] = e;
     }
     if (tid == 0) {
         for (int k = 0; k < NS; k++) {
@@ -218,11 +242,11 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
                     pa[s] = ua;
                     pb[s] = ub;
                 } else if (baselane && j >= 4) {
-                    const SRow rb = srows[(j - 4) * WY + 4 + br];
-                    int ba = max(0, rb.xmin - tx0), bb = min(TX, rb.xmax - tx0 + 1);
-                    if (ba >= bb) ba = bb = 0;
+                    // mesh columns of tile row br at plane j - 4: one run
+                    const int2 e = orows[(j - 4) * TY + br];
+                    const int ba = e.y ? __ffs(e.y) - 1 : 0, bb = e.y ? 32 - __clz(e.y) : 0;
                     vd = s_b + (unsigned)((s * G::NPTS + br * TX + ba) * G::REC);
-                    vp = rb.start + tx0 + ba;
+                    vp = e.x + tx0 + ba;
                     vn = bb - ba;
                 }
                 const unsigned bytes = __reduce_add_sync(0xffffffffu, (unsigned)(vn + zn + zn2) * G::REC);
@@ -230,41 +254,17 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(bytes)
                                  : "memory");
                 __syncwarp();
-                const CUtensorMap *vm = rowlane ? maps.u : maps.b;
-                // copies: widest box first (24 records for a whole window row)
-                while (__any_sync(0xffffffffu, vn > 0)) {
-                    if (vn > 0) {
-                        const int mi = (rowlane && vn == 24) ? 5 : 31 - __clz(vn);
-                        const int w = mi == 5 ? 24 : 1 << mi;
-                        wide_box(vd, vm + mi, c0, vp, full);
-                        vd += (unsigned)(w * G::REC);
-                        vp += w;
-                        vn -= w;
-                    }
-                }
-                // zero fills: boxes wholly before point 0
-                while (__any_sync(0xffffffffu, zn > 0 || zn2 > 0)) {
-                    if (zn == 0 && zn2 > 0) {
-                        zd = zd2;
-                        zn = zn2;
-                        zn2 = 0;
-                    }
-                    if (zn > 0) {
-                        const int mi = zn == 24 ? 5 : 31 - __clz(zn);
-                        const int w = mi == 5 ? 24 : 1 << mi;
-                        wide_box(zd, maps.u + mi, c0, kWideZeroPoint, full);
-                        zd += (unsigned)(w * G::REC);
-                        zn -= w;
-                    }
-                }
+                // one copy per run: the records of the mesh points, then the two
+                // zero runs (boxes wholly before point 0)
+                if (vn > 0) wide_box(vd, (rowlane ? maps.u : maps.b) + (vn - 1), c0, vp, full);
+                if (zn > 0) wide_box(zd, maps.u + (zn - 1), c0, kWideZeroPoint, full);
+                if (zn2 > 0) wide_box(zd2, maps.u + (zn2 - 1), c0, kWideZeroPoint, full);
                 // potential of the interior points (zero outside the mesh)
-#pragma unroll
                 for (int i = pw; i < G::NPTS / 32; i += NPW) {
                     const int pt = lane + 32 * i, py = pt / TX, px = pt - py * TX;
-                    const SRow rv = srows[j * WY + 4 + py];
-                    const int x = tx0 + px;
-                    const bool ok = x >= rv.xmin && x <= rv.xmax;
-                    cp_async_small<4>(s_v + (unsigned)((s * G::NPTS + pt) * 4), a.V + (ok ? rv.start + x : 0),
+                    const int2 e = orows[j * TY + py];
+                    const bool ok = (e.y >> px) & 1;
+                    cp_async_small<4>(s_v + (unsigned)((s * G::NPTS + pt) * 4), a.V + (ok ? e.x + tx0 + px : 0),
                                       ok ? 4 : 0);
                 }
                 asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full) : "memory");
@@ -290,12 +290,13 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
     const int k = k0 + cc;
     const bool vok = k < ld;
     const int x0 = tx0 + xl, y0 = ty0 + yl;
-    // planes (0-based j) where any of the warp's columns holds a point
+    // planes (0-based j) where any of the warp's 4 x 2 columns holds a
+    // point; the lanes share out the planes
     int jc0 = 1 << 30, jc1 = -1;
-    for (int jj = 0; jj < np; jj++) {
-        const SRow r0 = srows[jj * WY + 4 + yl], r1 = srows[jj * WY + 5 + yl];
-        const bool on = (x0 + 1 >= r0.xmin && x0 <= r0.xmax) || (x0 + 1 >= r1.xmin && x0 <= r1.xmax);
-        if (on) {
+    const int xw = 4 * (warp & 3);
+    for (int jj = lane; jj < np; jj += 32) {
+        const int m = orows[jj * TY + yl].y | orows[jj * TY + yl + 1].y;
+        if ((m >> xw) & 15) {
             jc0 = min(jc0, jj);
             jc1 = max(jc1, jj);
         }
@@ -307,12 +308,11 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
     for (int pt = 0; pt < 4; pt++) fxy[pt] = a.f0 + a.fx * (float)(x0 + (pt & 1)) + a.fy * (float)(y0 + (pt >> 1));
     const float2 w1 = make_float2(a.w[1], a.w[1]), w2 = make_float2(a.w[2], a.w[2]);
     const float2 w3 = make_float2(a.w[3], a.w[3]), w4 = make_float2(a.w[4], a.w[4]);
-    const float w0c = 3.0f * a.w[0];
+    const float w0c = 3.0f * a.w[0], ai = a.ai;
     constexpr int RW = WX * NC;   // float2 entries per slot row
     const float2 *uwin = (const float2 *)gbase + ((4 + yl) * WX + xl) * NC + cc;
     const float2 *bwin = (const float2 *)(gbase + (s_b - s_u)) + (yl * TX + xl) * NC + cc;
     const float *vwin = (const float *)(gbase + (s_v - s_u)) + yl * TX + xl;
-    const int ox0 = x0 * ld + k;   // output offset of column x0 relative to its row's start
     float2 *const out2 = (float2 *)a.out;
 
     // q[pt][e]: partial sums of the outputs at planes j - 4 + e (e = 0..7)
@@ -325,12 +325,11 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
 
     int sl = 0;
     unsigned par = 0;
-    bool live = true;
 #pragma unroll 1
     for (int j = 0; j < np; j++) {
         const unsigned full = bar0 + 8 * sl, empty = bar0 + 8 * (NS + sl);
-        if (live) live = wide_wait(full, par, abort_flag);
-        if (j >= jc0 && j <= jc1 + 4 && live) {
+        if (!wide_wait(full, par, abort_flag)) break;
+        if (j >= jc0 && j <= jc1 + 4) {
             float2 s[4], cen[4];
             if (j <= jc1) {
                 const float2 *pw = uwin + sl * G::SLOT * NC;
@@ -396,27 +395,22 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
             }
             const int zo = zbase + j - 4;
             if (zo >= tl.zlo && zo < tl.zhi && vok) {
-                const SRow *ro = srows + (j - 4) * WY + 4 + yl;
+                const int2 *ro = orows + (j - 4) * TY + yl;
                 const float2 *bb = bwin + sl * G::NPTS * NC;
 #pragma unroll
                 for (int dy = 0; dy < 2; dy++) {
-                    const SRow rw = ro[dy];
-                    const int orow = rw.start * ld + ox0;
+                    const int2 e = ro[dy];
+                    const int orow = (e.x + x0) * ld + k;
+                    const int m = e.y >> xl;
 #pragma unroll
                     for (int dx = 0; dx < 2; dx++) {
-                        const int x = x0 + dx;
-                        if (x >= rw.xmin && x <= rw.xmax) {
-                            const int o = orow + dx * ld;
-                            const float2 acc = done[2 * dy + dx];
-                            if constexpr (EPI == 1) {
-                                const float2 bv = bb[(dy * TX + dx) * NC];
-                                float2 y;
-                                y.x = fmaf(-a.ai, acc.y, bv.x);
-                                y.y = fmaf(a.ai, acc.x, bv.y);
-                                out2[o] = y;
-                            } else {
-                                wide_finish(a, o, acc, bb[(dy * TX + dx) * NC]);
-                            }
+                        const float2 acc = done[2 * dy + dx];
+                        const float2 bv = bb[(dy * TX + dx) * NC];
+                        if constexpr (EPI == 1) {
+                            const float2 y = make_float2(fmaf(-ai, acc.y, bv.x), fmaf(ai, acc.x, bv.y));
+                            if ((m >> dx) & 1) out2[orow + dx * ld] = y;
+                        } else {
+                            if ((m >> dx) & 1) wide_finish(a, orow + dx * ld, acc, bv);
                         }
                     }
                 }
@@ -451,10 +445,10 @@ static WideEncodeFn wide_encode_fn() {
     return fn;
 }
 
-// Boxes of 1, 2, 4, 8, 16 and 24 records (16 complex64 values each) over the
-// (P, ld) complex64 block at p, as (points, 2 ld floats); out-of-range rows
-// read zero.  Encoded once per (pointer, ld, P) and kept.
-static bool wide_maps_for(const void *p, int64_t P, int ld, CUtensorMap out[6]) {
+// Boxes of 1 .. 24 records (16 complex64 values each) over the (P, ld)
+// complex64 block at p, as (points, 2 ld floats); out-of-range rows read
+// zero.  Encoded once per (pointer, ld, P) and kept.
+static bool wide_maps_for(const void *p, int64_t P, int ld, CUtensorMap out[24]) {
     struct Key {
         const void *p;
         int64_t P;
@@ -467,19 +461,18 @@ static bool wide_maps_for(const void *p, int64_t P, int ld, CUtensorMap out[6]) 
         }
     };
     static std::mutex mu;
-    static std::unordered_map<Key, std::array<CUtensorMap, 6>, KeyHash> cache;
+    static std::unordered_map<Key, std::array<CUtensorMap, 24>, KeyHash> cache;
     std::lock_guard<std::mutex> lock(mu);
     const Key key{p, P, ld};
     auto it = cache.find(key);
     if (it == cache.end()) {
         WideEncodeFn fn = wide_encode_fn();
         if (!fn) return false;
-        std::array<CUtensorMap, 6> m;
-        const int widths[6] = {1, 2, 4, 8, 16, 24};
-        for (int i = 0; i < 6; i++) {
+        std::array<CUtensorMap, 24> m;
+        for (int i = 0; i < 24; i++) {
             cuuint64_t dims[2] = {(cuuint64_t)2 * ld, (cuuint64_t)P};
             cuuint64_t strides[1] = {(cuuint64_t)ld * 8};
-            cuuint32_t box[2] = {32, (cuuint32_t)widths[i]};
+            cuuint32_t box[2] = {32, (cuuint32_t)(i + 1)};
             cuuint32_t es[2] = {1, 1};
             if (fn(&m[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(p), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -489,7 +482,7 @@ static bool wide_maps_for(const void *p, int64_t P, int ld, CUtensorMap out[6]) 
         if (cache.size() >= 256) cache.clear();
         it = cache.emplace(key, m).first;
     }
-    for (int i = 0; i < 6; i++) out[i] = it->second[i];
+    for (int i = 0; i < 24; i++) out[i] = it->second[i];
     return true;
 }
 
@@ -500,8 +493,8 @@ void wide_shape(const TileCfg &cfg, int *TX, int *TY) {
 
 size_t wide_smem_bytes(int nyp, int ns, int zseg) {
     const size_t tx = 16, ty = 2 * (size_t)nyp, wx = tx + 8, wy = ty + 8;
-    return 1024 + (size_t)ns * (wy * wx * 128 + tx * ty * 128 + tx * ty * 4) + wy * ((size_t)zseg + 8) * sizeof(SRow) +
-           8 + 16 * (size_t)ns + 16;
+    return 1024 + (size_t)ns * (wy * wx * 128 + tx * ty * 128 + tx * ty * 4) +
+           (wy * sizeof(SRow) + ty * 8) * ((size_t)zseg + 8) + 8 + 16 * (size_t)ns + 16;
 }
 
 template <int NYP, int NS, int NPW>
@@ -515,9 +508,9 @@ static cudaError_t launch_wide_t(const ApplyArgs<float> &a, const TileCfg &cfg, 
     const int ld = 2 * a.SV;
     WideMaps maps;
     if (!wide_maps_for(a.in, a.P, ld, maps.u)) return cudaSuccess;
-    CUtensorMap bm[6];
+    CUtensorMap bm[24];
     if (!wide_maps_for(a.base != nullptr ? a.base : a.in, a.P, ld, bm)) return cudaSuccess;
-    for (int i = 0; i < 5; i++) maps.b[i] = bm[i];
+    for (int i = 0; i < 16; i++) maps.b[i] = bm[i];
     auto kern = horner ? k_apply_wide<NYP, NS, NPW, 1> : k_apply_wide<NYP, NS, NPW, 0>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -537,23 +530,17 @@ cudaError_t launch_apply_wide(const ApplyArgs<float> &a, const TileCfg &cfg, int
     // the tensor view needs 16-byte aligned blocks (ld is even for complex64)
     if (((uintptr_t)a.in & 15) != 0 || (a.base != nullptr && ((uintptr_t)a.base & 15) != 0)) return cudaSuccess;
     if (a.err == nullptr || a.Vc != nullptr) return cudaSuccess;
-    // NYP, NS and producer warps: 8-row tiles with 3 slots, 6-row tiles with 3
-    // slots (or 4 with short segments), 4-row tiles with 4 or 5 slots
+    // tile rows and slots: 8-row and 6-row tiles with 3 slots, 4-row tiles
+    // with 4; 1 to 4 producer warps
 #define RSG_WIDE_NPW(NYP_, NS_)                                                        \
     switch (cfg.npw) {                                                                 \
+    case 1: return launch_wide_t<NYP_, NS_, 1>(a, cfg, ntiles, st, launched);          \
     case 2: return launch_wide_t<NYP_, NS_, 2>(a, cfg, ntiles, st, launched);          \
     case 3: return launch_wide_t<NYP_, NS_, 3>(a, cfg, ntiles, st, launched);          \
-    case 4: return launch_wide_t<NYP_, NS_, 4>(a, cfg, ntiles, st, launched);          \
-    default: return launch_wide_t<NYP_, NS_, 1>(a, cfg, ntiles, st, launched);         \
+    default: return launch_wide_t<NYP_, NS_, 4>(a, cfg, ntiles, st, launched);         \
     }
-    if (cfg.wty == 4) {
-        if (cfg.stages == 5) RSG_WIDE_NPW(2, 5)
-        RSG_WIDE_NPW(2, 4)
-    }
-    if (cfg.wty == 6) {
-        if (cfg.stages == 4) RSG_WIDE_NPW(3, 4)
-        RSG_WIDE_NPW(3, 3)
-    }
+    if (cfg.wty == 4) RSG_WIDE_NPW(2, 4)
+    if (cfg.wty == 6) RSG_WIDE_NPW(3, 3)
     RSG_WIDE_NPW(4, 3)
 #undef RSG_WIDE_NPW
 }

@@ -133,7 +133,9 @@ def test_quad_kernel(opts, S):
 
 @pytest.mark.parametrize("opts", [{"kernel": 7}, {"kernel": 7, "wide_ty": 6}, {"kernel": 7, "zseg": 7},
                                   {"kernel": 7, "zseg": 1}, {"kernel": 7, "wide_ty": 6, "zseg": 3},
-                                  {"kernel": 7, "zseg": 200}])
+                                  {"kernel": 7, "wide_ty": 6, "zseg": 200}, {"kernel": 7, "wide_ty": 6, "producers": 4},
+                                  {"kernel": 7, "wide_ty": 4, "stages": 4, "producers": 3},
+                                  {"kernel": 7, "wide_ty": 8, "producers": 2, "zseg": 64}])
 @pytest.mark.parametrize("S", [1, 2, 13, 16, 17, 40])
 def test_wide_kernel(opts, S):
     """Warp-specialised tensor-copy stencil (complex64) on a sphere with
@@ -155,18 +157,37 @@ def test_wide_kernel_cube_box_and_long_segments():
     and z, extents below the stencil radius, and a 260-plane box in one
     segment; the same block reused across launches with different inputs."""
     for shape, n, zseg, wty in (("cube", 37, 150, 8), ("box", (23, 9, 14), 150, 8), ("box", (3, 2, 40), 150, 6),
-                                ("box", (12, 10, 260), 200, 8), ("box", (12, 10, 260), 256, 6),
+                                ("box", (12, 10, 260), 150, 8), ("box", (12, 10, 260), 256, 6),
                                 ("box", (40, 33, 5), 2, 8)):
         p, g = wells_system(shape, n, h=0.3, dtype=torch.complex64, seed=4, natoms=2, lmax=1)
         for S in (10, 64):
             _check_apply(p, g, S, opts={"kernel": 7, "zseg": zseg, "wide_ty": wty}, expect_kernel=7)
 
 
+@pytest.mark.parametrize("opts", [{"kernel": 7, "wide_ty": 6, "producers": 4, "zseg": 190},
+                                  {"kernel": 7, "wide_ty": 8, "producers": 1, "zseg": 5}])
+def test_wide_kernel_taylor_in_place(opts):
+    """A Taylor exponential written over its input: the last Horner stage's
+    outputs (stored from shared memory by tensor copies) land on the base
+    block they were computed from."""
+    p, g = wells_system("sphere", radius=4.6, h=0.25, dtype=torch.complex64, seed=11, natoms=3, lmax=2)
+    for k, v in opts.items():
+        p.H.set_option(k, v)
+    psi = round_c64(white_noise_states(g, p.P, 16))
+    want = p.O.taylor4(psi, 0.01)
+    x = p.states_to_gpu(psi)
+    y = p.H.taylor(x, 0.01, out=x, S=16)
+    torch.cuda.synchronize()
+    assert y.data_ptr() == x.data_ptr()
+    assert p.H.get_option("last_kernel") == 7
+    assert rel_err(p.states_from_gpu(x, 16), want) < TOL[torch.complex64]
+
+
 def test_wide_kernel_declines_oversized_segments():
     """8-row tiles with 256-plane segments need more shared memory than a
     block may have: the launcher declines and the staged kernel runs."""
     p, g = wells_system("box", (12, 10, 260), h=0.3, dtype=torch.complex64, seed=4, natoms=1, lmax=0)
-    _check_apply(p, g, 6, opts={"kernel": 7, "zseg": 256, "wide_ty": 8}, expect_kernel=0)
+    _check_apply(p, g, 6, opts={"kernel": 7, "zseg": 256, "wide_ty": 8, "stages": 3}, expect_kernel=0)
 
 
 def test_quad_kernel_cube_box_and_complex128_fallback():
