@@ -81,11 +81,11 @@ def peaks():
 
 # stencil kernel of each "kernel" option value (rsg_ham_get_option "last_kernel")
 KERNEL_NAMES = {0: "k_apply_staged", 1: "k_apply_naive", 2: "k_apply_zmarch", 3: "k_apply_tma",
-                4: "k_apply_rowtma", 5: "k_apply_quad"}
-# the files the dominant stencil kernel (k_apply_quad) is compiled from; the
+                4: "k_apply_rowtma", 5: "k_apply_quad", 7: "k_apply_wide"}
+# the files the dominant stencil kernel (k_apply_wide) is compiled from; the
 # public header it also includes holds only C declarations the kernel does
 # not use
-KERNEL_SOURCES = ("rsg_quad.cu", "rsg_vec.cuh", "rsg_async.cuh", "rsg_batch.cuh", "rsg_internal.h")
+KERNEL_SOURCES = ("rsg_wide.cu", "rsg_vec.cuh", "rsg_async.cuh", "rsg_internal.h")
 
 
 def traffic_record(kernel_src_hash, kernel_name):
@@ -452,6 +452,8 @@ def main():
     ap.add_argument("--rx", type=int, default=None)
     ap.add_argument("--ty", type=int, default=None)
     ap.add_argument("--zseg", type=int, default=None)
+    ap.add_argument("--wide-ty", type=int, default=None, help="kernel 7: tile rows (4, 6 or 8)")
+    ap.add_argument("--producers", type=int, default=None, help="kernel 7: producer warps (1 to 4)")
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the complex128 / plain-kernel / control-gradient side measurements")
@@ -482,7 +484,7 @@ def main():
     H = rsg.Hamiltonian(mesh, dtype)
     H.set_potential(potential_wells(mesh.xyz, *wells))
     H.set_projectors(*proj)
-    for k in ("kernel", "threads", "rx", "ty", "zseg"):
+    for k in ("kernel", "threads", "rx", "ty", "zseg", "wide_ty", "producers"):
         if getattr(args, k) is not None:
             H.set_option(k, getattr(args, k))
     S = 64

@@ -480,6 +480,20 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     int ntiles = 0;
     a.tiles = nullptr;
     TileCfg cfg = H->cfg;
+    // kernel 7 moves 16-value chunks of each point row: blocks whose rows are
+    // narrow or end in a mostly empty chunk, and complex scaling (which it
+    // does not implement), take the register-blocked kernel in its default
+    // shape unless kernel 7 was chosen explicitly
+    if (cfg.kernel == 7) {
+        const int ldc = SV * (int)(16 / cbytes(H->dtype));
+        if (H->has_scaling || (!H->force_kernel && ldc % 16 != 0 && ldc < 40)) {
+            cfg.kernel = 5;
+            cfg.threads = 192;
+            cfg.zseg = 150;
+            cfg.stages = 3;
+            cfg.sync = 0;
+        }
+    }
     // kernels 2 and 3 keep a static row table of at most 120-plane segments
     if ((cfg.kernel == 2 || cfg.kernel == 3) && cfg.zseg > 120) cfg.zseg = 120;
     if (cfg.kernel != 1) {
@@ -805,15 +819,18 @@ rsg_status rsg_ham_create(rsg_mesh m, rsg_dtype dtype, rsg_ham *out) {
     H->m = m;
     H->dtype = dtype;
     // complex128 is bound by FP64 arithmetic: the one-thread-per-value kernel
-    // does the least of it; complex64 runs the register-blocked staged
-    // kernel (16 x 12 tiles, 150-plane segments: fastest on the sphere
-    // workloads measured)
+    // does the least of it.  complex64 runs the warp-specialised tensor-copy
+    // kernel (16 x 6 tiles, four producer warps, 190-plane segments: fastest
+    // on the sphere workloads measured); narrow blocks and complex scaling
+    // run the register-blocked kernel (apply_t)
     if (dtype == RSG_C128) {
         H->cfg.kernel = 1;
     } else {
-        H->cfg.kernel = 5;
+        H->cfg.kernel = 7;
+        H->cfg.wty = 6;
+        H->cfg.npw = 4;
         H->cfg.threads = 192;
-        H->cfg.zseg = 150;
+        H->cfg.zseg = 190;
         H->cfg.stages = 3;
     }
     *out = H;
@@ -889,6 +906,18 @@ rsg_status rsg_ham_autotune(rsg_ham H, const void *psi, void *work, int64_t S, i
             c.zseg = zs;
             cand.push_back(c);
         }
+    // the warp-specialised tensor-copy kernel (complex64): tile rows, producer
+    // warps and segment length
+    const int wshapes[][3] = {{6, 4, 190}, {6, 3, 190}, {6, 2, 190}, {8, 4, 150}, {8, 2, 150}, {4, 4, 190}};
+    for (const auto &sh : wshapes) {
+        TileCfg c;
+        c.kernel = 7;
+        c.wty = sh[0];
+        c.npw = sh[1];
+        c.zseg = sh[2];
+        c.stages = 3;
+        cand.push_back(c);
+    }
     // the row-TMA staged kernel: 256 threads with 4 or 5 slots, 512 with 6
     const int rshapes[][3] = {{256, 2, 4}, {256, 2, 5}, {512, 2, 4}};
     for (const auto &sh : rshapes)

@@ -289,7 +289,7 @@ class Hamiltonian:
         _ck(load().rsg_ham_get_option(self._h, key.encode(), C.byref(v)))
         return int(v.value)
 
-    TUNED_KEYS = ("kernel", "threads", "cv", "stages", "zseg", "blocks_per_sm")
+    TUNED_KEYS = ("kernel", "threads", "cv", "stages", "zseg", "blocks_per_sm", "wide_ty", "producers")
 
     def autotune(self, psi, S=None, cache_path=None, stream=None):
         """Choose the fastest stencil configuration for this mesh and block.

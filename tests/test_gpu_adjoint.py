@@ -52,7 +52,7 @@ def test_adjoint_c64_error_reported():
     assert err < 1e-3
 
 
-@pytest.mark.parametrize("kernel", [0, 5])
+@pytest.mark.parametrize("kernel", [0, 5, 7])
 def test_adjoint_c64_kernels_agree(kernel):
     """The adjoint's power sums run through the stencil epilogue's running
     sum (acc, acc_base): the register-blocked kernel against the oracle."""
