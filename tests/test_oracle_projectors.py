@@ -151,3 +151,55 @@ def test_raw_projectors_spectrum_from_small_problem():
     h3 = m.h ** 3
     small = np.sort(np.concatenate([np.linalg.eigvals(hh @ (h3 * v.T @ v)).real for hh, v in zip(hs, vals)]))
     assert np.abs(big - small).max() < 1e-10 * np.abs(small).max(), (big, small)
+
+
+def test_radial_factor_is_gaussian_in_two_beta_squared():
+    """The radial part of every projector is exp(-|r - R_a|^2 / (2 beta^2))
+    (reading C-6 of the projector passage in Sec. "Magnetic response and
+    gauge invariance in real-space grids").  The discrete normalisation is a
+    constant per projector, so ratios between sphere points fix the radial
+    factor independently of it: for the s-projector
+    p(q) / p(q') = exp(-(d_q^2 - d_q'^2) / (2 beta^2)), and for the p- and
+    d-projectors the same after dividing out the solid harmonic.  A radial
+    factor exp(-d^2 / beta^2), or one in |r| instead of |r - R_a|, fails."""
+    m = oracle.Mesh(oracle.CUBE, 18, h=0.25)
+    H = oracle.Hamiltonian(m, np.zeros(m.P))
+    c = np.array([0.17, -0.08, 0.11])
+    rc, beta = 1.9, 0.55
+    H.set_projectors([c], [rc], [2], [beta], [np.eye(9)])
+    pts, vals = H.atom(0)
+    r = m.xyz[pts] - c
+    d2 = np.sum(r * r, axis=1)
+    x, y, z = r[:, 0], r[:, 1], r[:, 2]
+    shapes = [np.ones_like(x), x, y, z, x * y, y * z, z * x, x * x - y * y, 3 * z * z - d2]
+    g = rng(91)
+    for i, sh in enumerate(shapes):
+        ok = np.nonzero(np.abs(sh) > 0.2 * np.abs(sh).max())[0]
+        radial = vals[i][ok] / sh[ok]
+        a, b = g.choice(len(ok), 40), g.choice(len(ok), 40)
+        want = np.exp(-(d2[ok][a] - d2[ok][b]) / (2.0 * beta * beta))
+        assert np.allclose(radial[a] / radial[b], want, rtol=1e-12, atol=0.0), i
+
+
+def test_workload_projector_width_decays_to_e_minus_8_at_cutoff():
+    """The workloads take beta = r_c / 4, so the radial factor at the cutoff
+    sphere is exp(-r_c^2 / (2 (r_c/4)^2)) = e^-8; checked on the oracle's
+    sampled s-projector against its value at the point nearest the centre."""
+    _, rcut, lmax, beta, _ = projector_atoms_for_test()
+    assert np.allclose(beta, rcut / 4.0)
+    m = oracle.Mesh(oracle.CUBE, 24, h=0.2)
+    H = oracle.Hamiltonian(m, np.zeros(m.P))
+    c = np.zeros(3) + 0.1   # no mesh point at the centre
+    H.set_projectors([c], [rcut[0]], [0], [beta[0]], [np.eye(1)])
+    pts, vals = H.atom(0)
+    d = np.linalg.norm(m.xyz[pts] - c, axis=1)
+    i0, i1 = np.argmin(d), np.argmax(d)
+    ratio = vals[0][i1] / vals[0][i0]
+    assert abs(ratio - np.exp(-8.0 * (d[i1] ** 2 - d[i0] ** 2) / rcut[0] ** 2)) < 1e-13
+    # the farthest sphere point lies within one spacing of r_c
+    assert rcut[0] - m.h < d[i1] <= rcut[0]
+
+
+def projector_atoms_for_test():
+    from workloads import projector_atoms
+    return projector_atoms(rng(3), 2, 2.5, 1, ball_radius=5.0)
