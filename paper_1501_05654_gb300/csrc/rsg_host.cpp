@@ -179,7 +179,7 @@ struct rsg_ham_s {
     // projectors
     ProjDev pj;
     DevBuf q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm, nl_ptr, nl_ent, u_pts, u_ptr, e_atom, e_p;
-    DevBuf D, partial;
+    DevBuf D, partial, pcnt;   // coefficients, their partial sums, per-atom completion counters
     // workspace
     DevBuf w0, w1, red, G, W, Wc, drift, status, dots, M, ov, grad, Xd, Xdir;
     DevBuf w2, cg;     // shifted solver: third work block, per-state scalars
@@ -431,8 +431,12 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         const size_t need = (size_t)H->pj.nchunks * H->pj.npmax * ldc * 2 * sizeof(double);
         CK(H->partial.ensure(need));
         CK(H->D.ensure((size_t)H->pj.natoms * H->pj.npmax * ldc * cbytes(H->dtype)));
-        CK(launch_proj_dot<R>(in, SV, H->pj, H->partial.as<double>(), st));
-        CK(launch_proj_reduce<R>(H->partial.as<double>(), SV, H->pj, h3, H->D.p, st));
+        const size_t ncnt = (size_t)H->pj.natoms * proj_slices(SV) * sizeof(unsigned);
+        if (ncnt > H->pcnt.n || !H->pcnt.p) {
+            CK(H->pcnt.ensure(ncnt));
+            CK(cudaMemsetAsync(H->pcnt.p, 0, H->pcnt.n, st));
+        }
+        CK(launch_proj_coeffs<R>(in, SV, H->pj, H->partial.as<double>(), H->pcnt.as<unsigned>(), h3, H->D.p, st));
     }
     ApplyArgs<R> a;
     a.in = in;

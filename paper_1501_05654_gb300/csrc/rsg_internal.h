@@ -125,6 +125,16 @@ cudaError_t launch_apply(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles,
 // a.nl_ptr and the field terms are ignored (rsg_scaled.cu).
 template <typename R>
 cudaError_t launch_apply_scaled(const ApplyArgs<R> &a, const R *vt, double theta, cudaStream_t st);
+// Coefficients D = h_a h^3 <p|u> in one launch: partial sums per chunk and
+// the last block of each atom reducing them (counter: natoms * proj_slices
+// zeroed words, left zeroed).
+inline int proj_slices(int SV) {
+    const int bv = SV < 32 ? SV : 32;   // vector slices of the coefficient kernels: bv vectors each
+    return (SV + bv - 1) / bv;
+}
+template <typename R>
+cudaError_t launch_proj_coeffs(const void *u, int SV, const ProjDev &pj, double *partial, unsigned *counter,
+                               double h3, void *D, cudaStream_t st);
 template <typename R>
 cudaError_t launch_proj_dot(const void *u, int SV, const ProjDev &pj, double *partial,
                             cudaStream_t st);

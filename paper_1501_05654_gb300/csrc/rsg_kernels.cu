@@ -672,13 +672,23 @@ cudaError_t launch_apply(const ApplyArgs<R> &a, const TileCfg &cfg, int ntiles, 
 // ---------------------------------------------------------- projectors ---
 // Block: (BV vectors) x (PL point lanes).  Chunk c covers entries [q0, q1)
 // of one atom.  partial[((c * npmax + i) * SV + v) * 2 * NC + comp] (FP64).
+//
+// With counter != nullptr the coefficients are finished in the same launch:
+// after writing its partial sums a block counts itself done for its atom
+// (per vector slice blockIdx.y), and the last block of an atom sums the
+// atom's chunks in chunk order, scales by h^3 and applies h_a, exactly as
+// k_proj_reduce does, then resets the counter for the next launch.
 template <typename R, int NP>
 __global__ void __launch_bounds__(256) k_proj_dot(const typename VT<R>::T *__restrict__ u, int SV,
                                                   const int32_t *__restrict__ q_pt,
                                                   const R *__restrict__ q_p,
                                                   const int32_t *__restrict__ chunk_q0,
                                                   const int32_t *__restrict__ chunk_q1,
-                                                  double *__restrict__ partial) {
+                                                  double *__restrict__ partial,
+                                                  unsigned *__restrict__ counter,
+                                                  const int32_t *__restrict__ chunk_atom,
+                                                  const int32_t *__restrict__ atom_chunk0,
+                                                  const double *__restrict__ hm, double h3, R *__restrict__ D) {
     using V = VT<R>;
     using T = typename V::T;
     constexpr int NCOMP = 2 * V::NC;
@@ -730,25 +740,79 @@ __global__ void __launch_bounds__(256) k_proj_dot(const typename VT<R>::T *__res
         }
         __syncthreads();
     }
+    if (counter == nullptr) return;
+    // the last block of this atom and vector slice finishes its coefficients
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    const int at = chunk_atom[c];
+    if (tid == 0) {
+        const unsigned n = (unsigned)(atom_chunk0[at + 1] - atom_chunk0[at]);
+        unsigned *cnt = counter + (size_t)at * gridDim.y + blockIdx.y;
+        last = atomicAdd(cnt, 1u) == n - 1;
+        if (last) *cnt = 0u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int ldc = SV * V::NC;
+    const int s0 = blockIdx.y * blockDim.x * V::NC;                 // first complex column of the slice
+    const int ns = min((int)blockDim.x * V::NC, ldc - s0);          // complex columns in the slice
+    __shared__ double cbuf[2 * NP * 32 * V::NC];                    // c[i][s] of the slice (re, im)
+    for (int t = tid; t < NP * ns; t += blockDim.x * blockDim.y) {
+        const int i = t / ns, sc = s0 + (t - i * ns);
+        double sr = 0.0, si = 0.0;
+        for (int cc = atom_chunk0[at]; cc < atom_chunk0[at + 1]; cc++) {
+            const double *pp = partial + (((int64_t)cc * NP + i) * ldc + sc) * 2;
+            sr += __ldcg(pp);
+            si += __ldcg(pp + 1);
+        }
+        cbuf[2 * t] = h3 * sr;
+        cbuf[2 * t + 1] = h3 * si;
+    }
+    __syncthreads();
+    for (int t = tid; t < NP * ns; t += blockDim.x * blockDim.y) {
+        const int i = t / ns, sl = t - i * ns;
+        double dr = 0.0, di = 0.0;
+        for (int j = 0; j < NP; j++) {
+            const double hij = hm[((int64_t)at * NP + i) * NP + j];
+            dr += hij * cbuf[2 * (j * ns + sl)];
+            di += hij * cbuf[2 * (j * ns + sl) + 1];
+        }
+        R *dst = D + (((int64_t)at * NP + i) * ldc + s0 + sl) * 2;
+        dst[0] = (R)dr;
+        dst[1] = (R)di;
+    }
 }
 
 template <typename R>
 cudaError_t launch_proj_dot(const void *u, int SV, const ProjDev &pj, double *partial,
                             cudaStream_t st) {
+    return launch_proj_coeffs<R>(u, SV, pj, partial, nullptr, 0.0, nullptr, st);
+}
+
+template <typename R>
+cudaError_t launch_proj_coeffs(const void *u, int SV, const ProjDev &pj, double *partial, unsigned *counter,
+                               double h3, void *D, cudaStream_t st) {
     if (pj.natoms == 0 || pj.nchunks == 0) return cudaSuccess;
     const int bv = SV < 32 ? SV : 32;
     const int pl = 256 / bv > 64 ? 64 : 256 / bv;
     dim3 block(bv, pl);
-    dim3 grid(pj.nchunks, (SV + bv - 1) / bv);
+    dim3 grid(pj.nchunks, proj_slices(SV));
     using T = typename VT<R>::T;
     const T *uu = (const T *)u;
     const R *qp = (const R *)pj.q_p;
+    R *DD = (R *)D;
+#define RSG_PROJ_DOT(NP_)                                                                                     \
+    k_proj_dot<R, NP_><<<grid, block, 0, st>>>(uu, SV, pj.q_pt, qp, pj.chunk_q0, pj.chunk_q1, partial, counter, \
+                                               pj.chunk_atom, pj.atom_chunk0, pj.hm, h3, DD)
     switch (pj.npmax) {
-    case 1: k_proj_dot<R, 1><<<grid, block, 0, st>>>(uu, SV, pj.q_pt, qp, pj.chunk_q0, pj.chunk_q1, partial); break;
-    case 4: k_proj_dot<R, 4><<<grid, block, 0, st>>>(uu, SV, pj.q_pt, qp, pj.chunk_q0, pj.chunk_q1, partial); break;
-    case 9: k_proj_dot<R, 9><<<grid, block, 0, st>>>(uu, SV, pj.q_pt, qp, pj.chunk_q0, pj.chunk_q1, partial); break;
+    case 1: RSG_PROJ_DOT(1); break;
+    case 4: RSG_PROJ_DOT(4); break;
+    case 9: RSG_PROJ_DOT(9); break;
     default: return cudaErrorInvalidValue;
     }
+#undef RSG_PROJ_DOT
     return cudaGetLastError();
 }
 
@@ -1715,6 +1779,8 @@ template cudaError_t launch_apply_tma<float>(const ApplyArgs<float> &, const Til
 template cudaError_t launch_apply<float>(const ApplyArgs<float> &, const TileCfg &, int, cudaStream_t);
 template cudaError_t launch_apply_naive_odd<float>(const ApplyArgs<float> &, cudaStream_t);
 template cudaError_t launch_proj_dot<float>(const void *, int, const ProjDev &, double *, cudaStream_t);
+template cudaError_t launch_proj_coeffs<float>(const void *, int, const ProjDev &, double *, unsigned *, double,
+                                               void *, cudaStream_t);
 template cudaError_t launch_proj_reduce<float>(const double *, int, const ProjDev &, double, void *, cudaStream_t);
 template cudaError_t launch_proj_scatter<float>(const ApplyArgs<float> &, const ProjDev &, cudaStream_t);
 #endif
@@ -1724,6 +1790,8 @@ template cudaError_t launch_apply_rowtma<double>(const ApplyArgs<double> &, cons
 template cudaError_t launch_apply<double>(const ApplyArgs<double> &, const TileCfg &, int, cudaStream_t);
 template cudaError_t launch_apply_naive_odd<double>(const ApplyArgs<double> &, cudaStream_t);
 template cudaError_t launch_proj_dot<double>(const void *, int, const ProjDev &, double *, cudaStream_t);
+template cudaError_t launch_proj_coeffs<double>(const void *, int, const ProjDev &, double *, unsigned *, double,
+                                                void *, cudaStream_t);
 template cudaError_t launch_proj_reduce<double>(const double *, int, const ProjDev &, double, void *, cudaStream_t);
 template cudaError_t launch_proj_scatter<double>(const ApplyArgs<double> &, const ProjDev &, cudaStream_t);
 #endif
