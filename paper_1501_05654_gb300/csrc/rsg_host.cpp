@@ -176,6 +176,7 @@ struct rsg_ham_s {
     bool force_kernel = false;   // set when the caller chose the kernel explicitly
     int last_kernel = -1;        // stencil kernel of the last application
     int adj_keep = -1;           // adjoint: keep segment powers (1), recompute (0), by memory (-1)
+    int adj_merge = -1;          // adjoint: costate and recompute sweeps share launches (1), not (0), auto (-1)
     // projectors
     ProjDev pj;
     DevBuf q_pt, q_atom, q_p, ch_atom, ch_q0, ch_q1, atom_ch0, hm, nl_ptr, nl_ent, u_pts, u_ptr, e_atom, e_p;
@@ -191,6 +192,7 @@ struct rsg_ham_s {
     double theta = 0.0;
     double xdir_cached[3] = {NAN, NAN, NAN};
     std::vector<DevBuf> pool;   // control-gradient vectors
+    std::vector<DevBuf> pool2;  // control-gradient two-column blocks (shared sweeps)
     // measurement
     bool prof = false;
     std::vector<cudaEvent_t> ev;   // pairs (start, stop) of stencil launches
@@ -409,6 +411,10 @@ struct Epi {
     const void *acc_base = nullptr;
     double ar = 1, ai = 0, br = 1, bi = 0, gr = 0, gi = 0;
     double shift = 0;   // applies H - shift (folded into the diagonal's constant term)
+    // two-column blocks (ld = 2): column 1 has field amplitude eps1 and alpha
+    // (ar1, ai1); column 0 the call's eps and (ar, ai)
+    bool twocol = false;
+    double eps1 = 0, ar1 = 1, ai1 = 0;
 };
 
 // A potential is set: the real V, or the complex v_theta of complex scaling.
@@ -462,6 +468,24 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     a.fx = (R)fd[0];
     a.fy = (R)fd[1];
     a.fz = (R)fd[2];
+    if (ep.twocol) {
+        if (SV * (int)(16 / cbytes(H->dtype)) != 2 || !dir)
+            return fail(RSG_ERR_ARG, "two-column applications need ld = 2 and a field direction");
+        a.twocol = 1;
+        const double ec[2] = {eps, ep.eps1};
+        for (int c = 0; c < 2; c++) {
+            double g0 = 0;
+            for (int d = 0; d < 3; d++) {
+                g0 += ec[c] * dir[d] * (m->origin[d] + h * m->lo[d]);
+                a.cf[c][1 + d] = (R)(ec[c] * dir[d] * h);
+            }
+            a.cf[c][0] = (R)(g0 - ep.shift);
+        }
+        a.ca[0][0] = (R)ep.ar;
+        a.ca[0][1] = (R)ep.ai;
+        a.ca[1][0] = (R)ep.ar1;
+        a.ca[1][1] = (R)ep.ai1;
+    }
     for (int k = 0; k < 5; k++) a.w[k] = (R)(-0.5 * kFD[k] / (h * h));
     a.ar = (R)ep.ar;
     a.ai = (R)ep.ai;
@@ -500,6 +524,8 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     }
     // kernels 2 and 3 keep a static row table of at most 120-plane segments
     if ((cfg.kernel == 2 || cfg.kernel == 3) && cfg.zseg > 120) cfg.zseg = 120;
+    // two-column applications run on the one-thread-per-value kernel
+    if (ep.twocol) cfg.kernel = 1;
     if (cfg.kernel != 1) {
         int TX, TY;
         block_shape(cfg, SV, &TX, &TY);
@@ -604,7 +630,7 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     if (H->pj.natoms > 0 && !split_nl)
         bytes += 4.0 * (P + 1) + (double)H->pj.nq * (8.0 + H->pj.npmax * sizeof(R)) +
                  (double)H->pj.natoms * H->pj.npmax * row;
-    H->n_stencil++;
+    H->n_stencil += ep.twocol ? 2 : 1;   // Hamiltonian applications (two per two-column launch)
     H->stencil_bytes += bytes;
     H->n_launch += H->pj.natoms > 0 ? 3 : 1;
     return RSG_OK;
@@ -1004,6 +1030,7 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     else if (k == "producers" && value >= 1 && value <= 4) H->cfg.npw = (int)value;
     else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
     else if (k == "adjoint_keep_powers" && value >= -1 && value <= 1) H->adj_keep = (int)value;
+    else if (k == "adjoint_merge" && value >= -1 && value <= 1) H->adj_merge = (int)value;
     else if (k == "threads" && (value == 160 || value == 192 || value == 256 || value == 512))
         H->cfg.threads = (int)value;
     else if (k == "sync" && value >= 0 && value <= 2) H->cfg.sync = (int)value;
@@ -2062,7 +2089,94 @@ rsg_status control_gradient_t(rsg_ham H, const void *psi0, const void *target, i
         return RSG_OK;
     };
 
-    for (int64_t c = nck - 1; c >= 0; c--) {
+    // Shared sweeps: with every power of a segment kept, the costate sweep of
+    // segment c (backward) and the recompute sweep of segment c - 1 (forward)
+    // have the same number of exponentials and are independent, so each of
+    // their Hamiltonian applications runs as one two-column launch: column 0
+    // the recompute (A = -i tau H(eps_r)), column 1 the costate
+    // (A^dagger = +i tau H(eps_c)).  Two banks of two-column blocks hold the
+    // powers of consecutive segments.
+    const size_t vb2 = (size_t)P * 2 * cb;
+    const int64_t nper = (int64_t)K * m * 4 + 1;     // per bank: 4 powers of every step, and the segment's end
+    const bool merged = keep_powers && (H->adj_merge == 1 ||
+                                        (H->adj_merge < 0 && (double)(2 * nper + 1) * vb2 < 0.5 * (double)free_b));
+    if (merged) {
+        if ((int64_t)H->pool2.size() < 2 * nper + 1) H->pool2.resize((size_t)(2 * nper + 1));
+        for (int64_t i = 0; i < 2 * nper + 1; i++) CK(H->pool2[(size_t)i].ensure(vb2));
+        auto arr = [&](int b, int64_t t, int j) { return H->pool2[(size_t)(b * nper + t * 4 + j)].p; };
+        void *scr = H->pool2[(size_t)(2 * nper)].p;
+        // column col of a two-column block <-> a single-state vector
+        auto to_col = [&](void *blk, int col, const void *v) {
+            return cudaMemcpy2DAsync((char *)blk + col * cb, 2 * cb, v, ld * cb, cb, (size_t)P,
+                                     cudaMemcpyDeviceToDevice, st);
+        };
+        auto from_col = [&](void *v, const void *blk, int col) {
+            return cudaMemcpy2DAsync(v, ld * cb, (const char *)blk + col * cb, 2 * cb, cb, (size_t)P,
+                                     cudaMemcpyDeviceToDevice, st);
+        };
+        const int SV2 = sv_of(H, 2);
+        static const double invf[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
+        // step t of bank b: the exponential from arr(b, t, 0) to arr(b, t + 1, 0)
+        auto step = [&](int b, int64_t t, bool rec, double eps_r, bool cost, double eps_c) -> rsg_status {
+            void *pw[5] = {arr(b, t, 0), arr(b, t, 1), arr(b, t, 2), arr(b, t, 3), scr};
+            for (int j = 0; j < 4; j++) {
+                Epi ep;
+                ep.ar = 0.0;
+                ep.acc = arr(b, t + 1, 0);
+                if (j == 0) ep.acc_base = pw[0];
+                ep.gr = invf[j + 1];
+                ep.gi = 0.0;
+                double e = eps_r;
+                if (rec && cost) {
+                    ep.twocol = true;
+                    ep.ai = -tau;
+                    ep.ar1 = 0.0;
+                    ep.ai1 = tau;
+                    ep.eps1 = eps_c;
+                } else if (rec) {
+                    ep.ai = -tau;
+                } else {
+                    ep.ai = tau;
+                    e = eps_c;
+                }
+                CKS(apply(H, pw[j], pw[j + 1], SV2, e, dir, ep, st));
+            }
+            return RSG_OK;
+        };
+        // the last segment's powers first (bank of its index parity)
+        {
+            const int64_t c = nck - 1, k0 = c * K, L = std::min<int64_t>(k0 + K, nsteps) - k0;
+            const int b = (int)(c % 2);
+            CK(to_col(arr(b, 0, 0), 0, vec(ck0 + c)));
+            for (int64_t t = 0; t < L * m; t++) CKS(step(b, t, true, eps[k0 + t / m], false, 0.0));
+        }
+        for (int64_t c = nck - 1; c >= 0; c--) {
+            const int64_t k0c = c * K, k1c = std::min<int64_t>(k0c + K, nsteps), Tc = (k1c - k0c) * m;
+            const int bc = (int)(c % 2), br = 1 - bc;
+            const int64_t k0r = (c - 1) * K, Tr = c >= 1 ? (int64_t)K * m : 0;
+            CK(to_col(arr(br, 0, 0), 1, chi));
+            if (c >= 1) CK(to_col(arr(br, 0, 0), 0, vec(ck0 + c - 1)));
+            const int64_t T = std::max(Tc, Tr);
+            for (int64_t t = 0; t < T; t++) {
+                const bool rec = t < Tr, cost = t < Tc;
+                const int64_t k = k1c - 1 - t / m;
+                const int l = m - 1 - (int)(t % m);
+                CKS(step(br, t, rec, rec ? eps[k0r + t / m] : 0.0, cost, cost ? eps[k] : 0.0));
+                if (cost) {
+                    const int64_t tc = (k - k0c) * m + l;   // the costate's exponential in its segment's bank
+                    const void *bb[4], *aa[4];
+                    for (int j = 0; j < 4; j++) {
+                        bb[j] = (const char *)arr(br, t, j) + cb;
+                        aa[j] = arr(bc, tc, j);
+                    }
+                    CK(launch_adjoint_grad<R>(bb, aa, P, 2, H->Xd.as<R>(), h3, tau, H->dots.as<double>(), nb,
+                                              counter, H->grad.as<double>() + k, st));
+                }
+            }
+            CK(from_col(chi, arr(br, Tc, 0), 1));
+        }
+    }
+    for (int64_t c = merged ? -1 : nck - 1; c >= 0; c--) {
         const int64_t k0 = c * K, k1 = std::min<int64_t>(k0 + K, nsteps);
         if (keep_powers) {
             // one recompute sweep over the segment keeps every power

@@ -72,6 +72,13 @@ struct ApplyArgs {
     // v_theta e^{2i theta} per point (interleaved); the caller folds the
     // kinetic rotation e^{-2i theta} into (ar, ai); nullptr otherwise
     const void *Vc = nullptr;
+    // two-column blocks (ld = 2, one-thread-per-value kernels only): column c
+    // has its own field terms cf[c] = (f0, fx, fy, fz) and alpha ca[c] =
+    // (ar, ai) in place of (f0, fx, fy, fz) and (ar, ai); base and gamma are
+    // shared
+    int twocol = 0;
+    R cf[2][4] = {};
+    R ca[2][2] = {};
 };
 
 // Projector tables on the device (entry-major, see rsg_host.cpp).

@@ -44,8 +44,25 @@ __device__ __forceinline__ void finish_point(const ApplyArgs<R> &a, int64_t idx,
     using V = VT<R>;
     using T = typename V::T;
     const int SV = a.SV;
-    R diag = a.V[idx] + a.f0 + a.fx * (R)x + a.fy * (R)y + a.fz * (R)z;
-    V::fma(acc, diag, center);
+    if (a.twocol) {
+        // two columns with their own field terms: column (v, component
+        // pair) of a complex64 vector, or vector v of complex128
+        auto diag_of = [&](int c) {
+            return a.V[idx] + a.cf[c][0] + a.cf[c][1] * (R)x + a.cf[c][2] * (R)y + a.cf[c][3] * (R)z;
+        };
+        if constexpr (sizeof(R) == 4) {
+            const R d0 = diag_of(0), d1 = diag_of(1);
+            acc.x = fmaf(d0, center.x, acc.x);
+            acc.y = fmaf(d0, center.y, acc.y);
+            acc.z = fmaf(d1, center.z, acc.z);
+            acc.w = fmaf(d1, center.w, acc.w);
+        } else {
+            V::fma(acc, diag_of(v), center);
+        }
+    } else {
+        const R diag = a.V[idx] + a.f0 + a.fx * (R)x + a.fy * (R)y + a.fz * (R)z;
+        V::fma(acc, diag, center);
+    }
     if (a.nl_ptr != nullptr) {
         const int e0 = a.nl_ptr[idx], e1 = a.nl_ptr[idx + 1];
         const T *D = (const T *)a.D;
@@ -58,7 +75,18 @@ __device__ __forceinline__ void finish_point(const ApplyArgs<R> &a, int64_t idx,
         }
     }
     const int64_t o = idx * SV + v;
-    T y0 = V::cmul(a.ar, a.ai, acc);
+    T y0;
+    if (a.twocol) {
+        if constexpr (sizeof(R) == 4) {
+            const R r0 = a.ca[0][0], i0 = a.ca[0][1], r1 = a.ca[1][0], i1 = a.ca[1][1];
+            y0 = make_float4(r0 * acc.x - i0 * acc.y, r0 * acc.y + i0 * acc.x, r1 * acc.z - i1 * acc.w,
+                             r1 * acc.w + i1 * acc.z);
+        } else {
+            y0 = V::cmul(a.ca[v][0], a.ca[v][1], acc);
+        }
+    } else {
+        y0 = V::cmul(a.ar, a.ai, acc);
+    }
     if (a.base != nullptr) V::cfma(y0, a.br, a.bi, ((const T *)a.base)[o]);
     ((T *)a.out)[o] = y0;
     if (a.acc != nullptr) {

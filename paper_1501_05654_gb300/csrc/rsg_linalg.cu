@@ -635,71 +635,69 @@ __global__ void __launch_bounds__(256) k_adjoint_grad(const R *b0, const R *b1, 
                                                       int64_t P, int ld, const R *__restrict__ X, double h3,
                                                       double tau, double *__restrict__ partial, int nblk,
                                                       unsigned *counter, double *grad_k) {
-    __shared__ double red[256];
+    // The gradient needs only sum_{i+j<=3} Im <b_j|X|a_i> / (i+j+1)!.  With
+    // c_i = sum_{j<=3-i} b_j / (i+j+1)! (real weights) it is
+    // sum_p X_p sum_i Im(conj(c_i) a_i): one FP64 accumulator per thread.
+    __shared__ double wsum[8];
     __shared__ bool last;
-    const R *bb[4] = {b0, b1, b2, b3};
-    const R *aa[4] = {a0, a1, a2, a3};
-    double acc[20];
-#pragma unroll
-    for (int i = 0; i < 20; i++) acc[i] = 0.0;
     const int64_t per = (P + nblk - 1) / nblk;
     const int64_t p0 = blockIdx.x * per;
     const int64_t p1 = p0 + per < P ? p0 + per : P;
+    constexpr double f2 = 0.5, f3 = 1.0 / 6.0, f4 = 1.0 / 24.0;
+    double acc = 0.0;
     for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        double br[4], bi[4], ar[4], ai[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            ld_c(bb[j] + p * ld * 2, br[j], bi[j]);
-            ld_c(aa[j] + p * ld * 2, ar[j], ai[j]);
-        }
-        const double x = (double)X[p];
-        int k = 0;
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int i = 0; i + j <= 3; i++) {
-                acc[2 * k] += x * (br[j] * ar[i] + bi[j] * ai[i]);
-                acc[2 * k + 1] += x * (br[j] * ai[i] - bi[j] * ar[i]);
-                k++;
-            }
+        const int64_t o = p * ld * 2;
+        double br0, bi0, br1, bi1, br2, bi2, br3, bi3, ar, ai;
+        ld_c(b0 + o, br0, bi0);
+        ld_c(b1 + o, br1, bi1);
+        ld_c(b2 + o, br2, bi2);
+        ld_c(b3 + o, br3, bi3);
+        // c_0 .. c_3
+        const double c0r = fma(f4, br3, fma(f3, br2, fma(f2, br1, br0)));
+        const double c0i = fma(f4, bi3, fma(f3, bi2, fma(f2, bi1, bi0)));
+        const double c1r = fma(f4, br2, fma(f3, br1, f2 * br0));
+        const double c1i = fma(f4, bi2, fma(f3, bi1, f2 * bi0));
+        const double c2r = fma(f4, br1, f3 * br0), c2i = fma(f4, bi1, f3 * bi0);
+        const double c3r = f4 * br0, c3i = f4 * bi0;
+        double t;
+        ld_c(a0 + o, ar, ai);
+        t = fma(c0r, ai, -c0i * ar);
+        ld_c(a1 + o, ar, ai);
+        t = fma(c1r, ai, fma(-c1i, ar, t));
+        ld_c(a2 + o, ar, ai);
+        t = fma(c2r, ai, fma(-c2i, ar, t));
+        ld_c(a3 + o, ar, ai);
+        t = fma(c3r, ai, fma(-c3i, ar, t));
+        acc = fma((double)X[p], t, acc);
     }
-    for (int k = 0; k < 20; k++) {
-        red[threadIdx.x] = acc[k];
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * 20 + k] = red[0];
-        __syncthreads();
-    }
+    // block sum: shuffles within each warp, then the warps in order
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += wsum[w];
+        partial[blockIdx.x] = s;
         __threadfence();
         last = atomicAdd(counter, 1u) == (unsigned)(nblk - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // the last block: ten threads each sum the imaginary part of one packed
-    // inner product over the blocks (fixed order), then thread 0 combines
-    __shared__ double Mi[10];
-    if (threadIdx.x < 10) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; b++) s += partial[(int64_t)b * 20 + 2 * threadIdx.x + 1];
-        Mi[threadIdx.x] = h3 * s;
-    }
+    // the last block sums the blocks' values: thread t takes blocks t,
+    // t + 256, ..., then the same fixed shuffle and warp order
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(partial + b);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x != 0) return;
-    // packed order: j = 0..3, i = 0..3-j; the term has order n = i + j + 1
-    const double invf[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
-    double si = 0.0;
-    int k = 0;
-    for (int j = 0; j < 4; j++)
-        for (int i = 0; i + j <= 3; i++) {
-            si += invf[i + j + 1] * Mi[k];
-            k++;
-        }
-    *grad_k += 2.0 * tau * si;
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += wsum[w];
+    *grad_k += 2.0 * tau * h3 * tot;
     *counter = 0u;
 }
 

@@ -30,11 +30,16 @@ def _setup(dtype, n=14, h=0.5, nsteps=12, seed=0):
     return p, a[:, 0], b[:, 0], psi0, phi, eps
 
 
-@pytest.mark.parametrize("keep", [-1, 0, 1])
+@pytest.mark.parametrize("keep,merge", [(-1, -1), (0, -1), (1, 0), (1, 1)])
 @pytest.mark.parametrize("scheme,nsub,K", [(1, 1, 5), (0, 2, 3), (1, 2, 12)])
-def test_adjoint_matches_oracle_c128(scheme, nsub, K, keep):
+def test_adjoint_matches_oracle_c128(scheme, nsub, K, keep, merge):
+    """keep 1, merge 1: the costate sweep of each checkpoint segment and the
+    recompute sweep of the segment before it share two-column launches, each
+    column with its own field and sign; with K = 5 the last segment is
+    shorter than its partner, with K = 12 there is one segment."""
     p, a, b, psi0, phi, eps = _setup(torch.complex128)
     p.H.set_option("adjoint_keep_powers", keep)
+    p.H.set_option("adjoint_merge", merge)
     Jw, gw = p.O.control_gradient(a, b, eps, 0.05, scheme=scheme, nsub=nsub, checkpoint_every=4)
     J, gr = p.H.control_gradient(psi0, phi, eps, 0.05, scheme=scheme, nsub=nsub,
                                  checkpoint_every=K)
@@ -52,15 +57,19 @@ def test_adjoint_c64_error_reported():
     assert err < 1e-3
 
 
-@pytest.mark.parametrize("kernel", [0, 5, 7])
-def test_adjoint_c64_kernels_agree(kernel):
+@pytest.mark.parametrize("kernel,merge", [(0, 0), (5, 0), (7, 0), (0, 1)])
+def test_adjoint_c64_kernels_agree(kernel, merge):
     """The adjoint's power sums run through the stencil epilogue's running
-    sum (acc, acc_base): the register-blocked kernel against the oracle."""
+    sum (acc, acc_base): the staged, register-blocked and tensor-copy kernels
+    against the oracle; with merge 1 the shared two-column sweeps (which run
+    on the one-thread-per-value kernel)."""
     p, a, b, psi0, phi, eps = _setup(torch.complex64, n=20, h=0.45)
     p.H.set_option("kernel", kernel)
+    p.H.set_option("adjoint_merge", merge)
     Jw, gw = p.O.control_gradient(a, b, eps, 0.05, checkpoint_every=4)
     J, gr = p.H.control_gradient(psi0, phi, eps, 0.05, checkpoint_every=4)
-    assert p.H.get_option("last_kernel") == kernel
+    if merge == 0:
+        assert p.H.get_option("last_kernel") == kernel
     assert abs(J - Jw) < 1e-5 * abs(Jw)
     assert np.abs(gr - gw).max() < 1e-3 * np.abs(gw).max()
 
