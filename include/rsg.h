@@ -91,8 +91,10 @@ rsg_status rsg_mesh_create(rsg_shape shape, const int32_t n[3], double radius,
  * one-thread-per-value kernels (1, or 6 with complex scaling); batches
  * refuse such meshes.  Set it before building Hamiltonians' work on the
  * mesh or between calls (not while a call on the mesh is in flight).
- * Errors: RSG_ERR_ARG for an unknown rule, RSG_ERR_UNSUPPORTED for RSG_BC_ODD
- * on a sphere. */
+ * A neighbour is reflected once, which reaches its image inside the mesh
+ * only with at least 4 points along every axis.
+ * Errors: RSG_ERR_ARG for an unknown rule or RSG_BC_ODD with an extent below
+ * 4, RSG_ERR_UNSUPPORTED for RSG_BC_ODD on a sphere. */
 rsg_status rsg_mesh_set_boundary(rsg_mesh m, int bc);
 /* Number of mesh points P. */
 rsg_status rsg_mesh_num_points(rsg_mesh m, int64_t *P);
@@ -276,7 +278,11 @@ rsg_status rsg_shifted_solve(rsg_ham H, const void *b, void *x, int64_t S, int64
  * and the caller's `seed`.  rsg_states_load reads such a file back into
  * psi, zeroing the columns S..ld-1, and returns the metadata through any
  * non-NULL output pointer (then the .json file must exist and match).
- * Both synchronise; neither needs a stream.  Errors: RSG_ERR_ARG for NULL,
+ * With a device block, both wait for all work on the device (every stream)
+ * before touching it, and load waits again after the copy, so they need no
+ * stream.  The files are written under temporary names and renamed into
+ * place: a failed save leaves an earlier checkpoint at `path` intact.
+ * Errors: RSG_ERR_ARG for NULL,
  * S outside 1..ld, an unreadable or unwritable file, or a file whose dtype,
  * shape or metadata do not match H and S. */
 rsg_status rsg_states_save(rsg_ham H, const char *path, const void *psi, int64_t S, int64_t ld,

@@ -117,6 +117,8 @@ class Mesh:
         self.h = float(h)
         self.shape = shape
         self._m = L.orc_mesh_new(int(shape), nn, float(radius), float(h), int(bc))
+        if not self._m:
+            raise ValueError("image walls need at least 4 points along every axis")
         self.P = int(L.orc_mesh_npoints(self._m))
         self.ijk = np.empty((self.P, 3), dtype=np.int32)
         L.orc_mesh_ijk(self._m, _p(self.ijk))

@@ -133,6 +133,12 @@ void *orc_mesh_new(int shape, const int32_t *n, double radius, double h, int bc)
         }
     }
     for (int d = 0; d < 3; d++) m->ext[d] = m->hi[d] - m->lo[d] + 1;
+    /* image walls: one reflection reaches every neighbour's image only with
+     * at least 4 points along each axis */
+    if (bc == ORC_ODD && (m->ext[0] < 4 || m->ext[1] < 4 || m->ext[2] < 4)) {
+        free(m);
+        return NULL;
+    }
     int64_t nbox = (int64_t)m->ext[0] * m->ext[1] * m->ext[2];
     m->lookup = (int64_t *)malloc(sizeof(int64_t) * nbox);
     int64_t P = 0;

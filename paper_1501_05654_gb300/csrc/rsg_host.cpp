@@ -24,6 +24,7 @@
 #include <complex>
 #include <cstdlib>
 #include <cstring>
+#include <unistd.h>
 #include <map>
 #include <memory>
 #include <string>
@@ -771,6 +772,11 @@ rsg_status rsg_mesh_set_boundary(rsg_mesh m, int bc) {
     if (bc != RSG_BC_ZERO && bc != RSG_BC_ODD) return fail(RSG_ERR_ARG, "unknown boundary rule %d", bc);
     if (bc == RSG_BC_ODD && m->shape == RSG_SHAPE_SPHERE)
         return fail(RSG_ERR_UNSUPPORTED, "image walls need a cube or a box");
+    // the kernels reflect a neighbour once; with at least 4 points per axis
+    // every neighbour up to 4 spacings away has its image inside the mesh
+    if (bc == RSG_BC_ODD && (m->nx < 4 || m->ny < 4 || m->nz < 4))
+        return fail(RSG_ERR_ARG, "image walls need at least 4 points along every axis (%d x %d x %d)", m->nx, m->ny,
+                    m->nz);
     m->bc = bc;
     return RSG_OK;
 }
@@ -1410,6 +1416,9 @@ rsg_status rsg_states_save(rsg_ham H, const char *path, const void *psi, int64_t
     std::vector<char> host;
     const char *src = (const char *)psi;
     if (psi_on_device) {
+        // the block may still be written by work on any stream, including
+        // non-blocking ones that the legacy stream does not wait for
+        CK(cudaDeviceSynchronize());
         host.resize((size_t)P * ld * cb);
         CK(cudaMemcpy(host.data(), psi, host.size(), cudaMemcpyDeviceToHost));
         src = host.data();
@@ -1421,24 +1430,39 @@ rsg_status rsg_states_save(rsg_ham H, const char *path, const void *psi, int64_t
     const size_t unpadded = 10 + hdr.size() + 1;
     hdr.append((64 - unpadded % 64) % 64, ' ');
     hdr.push_back('\n');
-    FILE *f = std::fopen(path, "wb");
-    if (!f) return fail(RSG_ERR_ARG, "cannot open %s for writing", path);
+    // both files are written under temporary names and renamed into place,
+    // so a failure part way leaves any earlier checkpoint intact
+    const std::string tmp = std::string(path) + ".tmp" + std::to_string((long long)getpid());
+    FILE *f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return fail(RSG_ERR_ARG, "cannot open %s for writing", tmp.c_str());
     const unsigned char pre[10] = {0x93, 'N', 'U', 'M', 'P', 'Y', 1, 0, (unsigned char)(hdr.size() & 0xff),
                                    (unsigned char)(hdr.size() >> 8)};
     bool ok = std::fwrite(pre, 1, 10, f) == 10 && std::fwrite(hdr.data(), 1, hdr.size(), f) == hdr.size();
     for (int64_t p = 0; ok && p < P; p++)
         ok = std::fwrite(src + (size_t)p * ld * cb, cb, (size_t)S, f) == (size_t)S;
     ok = (std::fclose(f) == 0) && ok;
-    if (!ok) return fail(RSG_ERR_ARG, "writing %s failed", path);
-    const std::string meta = std::string(path) + ".json";
-    FILE *m = std::fopen(meta.c_str(), "w");
-    if (!m) return fail(RSG_ERR_ARG, "cannot open %s for writing", meta.c_str());
+    if (!ok) {
+        std::remove(tmp.c_str());
+        return fail(RSG_ERR_ARG, "writing %s failed", tmp.c_str());
+    }
+    const std::string meta = std::string(path) + ".json", mtmp = meta + ".tmp" + std::to_string((long long)getpid());
+    FILE *m = std::fopen(mtmp.c_str(), "w");
+    if (!m) {
+        std::remove(tmp.c_str());
+        return fail(RSG_ERR_ARG, "cannot open %s for writing", mtmp.c_str());
+    }
     std::fprintf(m,
                  "{\"format\": \"rsg-states-1\", \"points\": %lld, \"states\": %lld, \"dtype\": \"%s\", "
                  "\"step\": %lld, \"time\": %.17g, \"seed\": %llu}\n",
                  (long long)P, (long long)S, H->dtype == RSG_C64 ? "complex64" : "complex128", (long long)step, time,
                  (unsigned long long)seed);
-    if (std::fclose(m) != 0) return fail(RSG_ERR_ARG, "writing %s failed", meta.c_str());
+    if (std::fclose(m) != 0) {
+        std::remove(tmp.c_str());
+        std::remove(mtmp.c_str());
+        return fail(RSG_ERR_ARG, "writing %s failed", mtmp.c_str());
+    }
+    if (std::rename(tmp.c_str(), path) != 0 || std::rename(mtmp.c_str(), meta.c_str()) != 0)
+        return fail(RSG_ERR_ARG, "cannot move the checkpoint into place at %s", path);
     return RSG_OK;
 }
 
@@ -1503,10 +1527,15 @@ rsg_status rsg_states_load(rsg_ham H, const char *path, void *psi, int64_t S, in
         if (time) *time = t;
         if (seed) *seed = sd;
     }
-    if (psi_on_device)
+    if (psi_on_device) {
+        // no stream may still use the block while it is overwritten, and the
+        // restored values have landed before any later launch on any stream
+        CK(cudaDeviceSynchronize());
         CK(cudaMemcpy(psi, host.data(), host.size(), cudaMemcpyHostToDevice));
-    else
+        CK(cudaDeviceSynchronize());
+    } else {
         std::memcpy(psi, host.data(), host.size());
+    }
     return RSG_OK;
 }
 

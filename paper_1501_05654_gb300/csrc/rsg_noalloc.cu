@@ -59,6 +59,8 @@ extern "C" rsg_status rsg_state_norms_noalloc(rsg_ham H, const void *psi, int64_
     double h;
     rsg::ham_info(H, &dt, &P, &h);
     if (S < 1 || ld < S) return rsg::set_error(RSG_ERR_ARG, "need 1 <= S <= ld");
+    // the kernels index with 32-bit ld and point offsets
+    if (ld > 0x7fffffffLL || P * ld > 0x7fffffffLL) return rsg::set_error(RSG_ERR_ARG, "ld too large");
     if (S > kMaxStates)
         return rsg::set_error(RSG_ERR_UNSUPPORTED,
                               "rsg_state_norms_noalloc handles at most 128 states (fixed workspace)");

@@ -249,3 +249,20 @@ def test_log_level(lib):
     assert r.returncode == 0 and "rsg:" not in r.stderr, r.stderr
     assert lib.rsg_set_log_level(3) == -1
     assert lib.rsg_set_log_level(0) == 0
+
+
+def test_image_walls_refused_on_short_axes():
+    """Image walls reflect a neighbour once, which reaches every neighbour's
+    image only with at least 4 points along each axis: shorter boxes are
+    refused by the library and by the oracle; 4 points are accepted."""
+    import oracle
+    lib = rsg.load()
+    for n in ((3, 8, 8), (8, 2, 8), (8, 8, 1)):
+        m = rsg.Mesh(rsg.BOX, n, spacing=0.3)
+        assert lib.rsg_mesh_set_boundary(m._h, rsg.BC_ODD) == -1
+        with pytest.raises(ValueError):
+            oracle.Mesh(oracle.BOX, n, h=0.3, bc=oracle.ODD)
+        assert lib.rsg_mesh_set_boundary(m._h, rsg.BC_ZERO) == 0
+    m = rsg.Mesh(rsg.BOX, (4, 4, 4), spacing=0.3)
+    assert lib.rsg_mesh_set_boundary(m._h, rsg.BC_ODD) == 0
+    assert oracle.Mesh(oracle.BOX, (4, 4, 4), h=0.3, bc=oracle.ODD).P == 64

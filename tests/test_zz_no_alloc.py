@@ -52,3 +52,40 @@ def test_noalloc_rejects_more_states_than_its_workspace():
                                      C.c_void_p(out.data_ptr()), None)
     assert st == -4
     assert b"128" in lib.rsg_last_error()
+
+
+def test_noalloc_large_block_while_library_allocations_fail():
+    """373,248 points (more than 128 reduction blocks of 2048 points, so the
+    block count is clamped to the array's 128 rows) and 128 states, on a
+    Hamiltonian that has never allocated: two calls in a row succeed while
+    every allocation the library attempts is made to fail, and their norms
+    equal those of the allocating rsg_state_norms (called afterwards) and the
+    FP64 oracle's."""
+    import oracle
+    rsg.build()
+    lib = binding.load()
+    mesh = rsg.Mesh(rsg.CUBE, 72, spacing=0.25)
+    assert mesh.P > 128 * 2048
+    H = rsg.Hamiltonian(mesh, torch.complex64)
+    S = 128
+    g = rng(56)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    out = torch.full((S,), -1.0, dtype=torch.float64, device="cuda")
+    for call in range(2):
+        host = white_noise_states(g, mesh.P, S, dtype=np.complex64) * (call + 1)
+        psi = torch.from_numpy(host).cuda()
+        torch.cuda.synchronize()
+        assert lib.rsg_debug_fail_allocations(1 << 20) == 0
+        try:
+            st = lib.rsg_state_norms_noalloc(H._h, C.c_void_p(psi.data_ptr()), S, S,
+                                             C.c_void_p(out.data_ptr()), stream)
+            torch.cuda.synchronize()
+        finally:
+            assert lib.rsg_debug_fail_allocations(0) == 0
+        assert st == 0, lib.rsg_last_error()
+        got = out.cpu().numpy()
+        want = H.norms(psi, S=S)                       # rsg_state_norms, allocating
+        assert np.allclose(got, want, rtol=1e-12, atol=0), call
+        om = oracle.Mesh(oracle.CUBE, 72, h=0.25)
+        ref = om.norms2(host.astype(np.complex128))    # same points, any order: a sum over all of them
+        assert np.allclose(got, ref, rtol=1e-9, atol=0), call
