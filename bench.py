@@ -167,26 +167,241 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(V_orc, proj, psi_seed, seconds=20.0):
-    """The FP64 oracle, as it stands, on the host cores: H applications to one
-    state on the full mesh, repeated for about `seconds`."""
+def lib_to_orc(lib_ijk, orc_ijk):
+    """idx with library point i = oracle point idx[i] (matched by lattice coordinates)."""
+    a = np.lexsort(np.asarray(lib_ijk).T[::-1])
+    b = np.lexsort(np.asarray(orc_ijk).T[::-1])
+    idx = np.empty(len(a), dtype=np.int64)
+    idx[a] = b
+    return idx
+
+
+def rel_err(got, want):
+    """Largest over states of max_p |got - want| / max_p |want|."""
+    got, want = np.asarray(got), np.asarray(want)
+    if got.ndim == 1:
+        got, want = got[:, None], want[:, None]
+    den = np.abs(want).max(axis=0)
+    den[den == 0] = 1.0
+    return float((np.abs(got - want).max(axis=0) / den).max())
+
+
+def oracle_leg(chk, wells, proj, seconds=20.0):
+    """The FP64 oracle, as it stands, on the host cores.
+
+    Times it (the headline workload with all threads and with one thread,
+    and bounded samples of the other workloads, extrapolated where stated)
+    and compares every result collected in chk with it.  Returns
+    (cpu_baseline, legs, errors)."""
     import oracle
-    from workloads import rng, white_noise_states
+    from workloads import (potential_double_well, potential_harmonic, potential_soft_coulomb_li,
+                           potential_wells, potential_wells_scaled, rng, white_noise_states)
+    errs, legs = {}, {}
+    nthr = oracle.num_threads()
     om = oracle.Mesh(oracle.SPHERE, radius=18.0, h=0.2)
-    O = oracle.Hamiltonian(om, V_orc(om.xyz))
+    O = oracle.Hamiltonian(om, potential_wells(om.xyz, *wells))
     O.set_projectors(*proj)
-    psi = white_noise_states(rng(2, psi_seed), om.P, 1)
-    n, t0 = 0, time.perf_counter()
-    while True:
-        O.apply(psi)
-        n += 1
-        dt = time.perf_counter() - t0
-        if dt > seconds or n >= 5000:
-            break
-    return {"value": om.P * n / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
+    # the headline timing: H applications to one state on the full mesh
+    x1 = white_noise_states(rng(2, 5), om.P, 1)
+
+    def timed_applies(secs, cap):
+        n, t0 = 0, time.perf_counter()
+        while True:
+            O.apply(x1)
+            n += 1
+            dt = time.perf_counter() - t0
+            if dt > secs or n >= cap:
+                return n, dt
+    n, dt = timed_applies(seconds, 5000)
+    base = {"value": om.P * n / dt / 1e9, "unit": UNIT, "cores": nthr, "kind": "oracle",
             "sample": f"{n} FP64 H applications to 1 state on the full 3,053,617-point sphere "
                       f"(wells + projectors), {dt:.1f} s"}
+    oracle.set_num_threads(1)
+    try:
+        n1, dt1 = timed_applies(seconds / 2, 5000)
+    finally:
+        oracle.set_num_threads(nthr)
+    legs["sphere_R18_1_thread"] = {"value": om.P * n1 / dt1 / 1e9, "unit": UNIT, "cores": 1,
+                                   "sample": f"{n1} H applications to 1 state, {dt1:.1f} s"}
+    hd = chk.get("headline")
+    if hd is not None:
+        idx = lib_to_orc(hd["lib_ijk"], om.ijk)
+        S = hd["psi"].shape[1]
+        psi = np.empty((om.P, S), dtype=np.complex128)
+        psi[idx] = hd["psi"]
+        samp = idx[hd["samp"]]
+        pidx, sidx = np.repeat(samp, S), np.tile(np.arange(S), len(samp))
+        t0 = time.perf_counter()
+        want = O.apply_sampled(psi, pidx, sidx).reshape(len(samp), S)
+        legs["sphere_R18_sampled_apply_s"] = time.perf_counter() - t0
+        errs["headline"] = {"h_apply_sampled": rel_err(hd["y"], want),
+                            "sample": f"{len(samp)} random points x {S} states, one application, "
+                                      f"kernel {hd['kernel']}"}
+        for name in ("c64_plain_kernel", "c128_default", "c128_staged_kernel"):
+            if name in chk:
+                errs[name] = {"h_apply_sampled": rel_err(chk[name]["y"], want),
+                              "sample": "the headline's sampled points and input"}
+        if "complex_scaling_c64" in chk:
+            c = chk["complex_scaling_c64"]
+            vt = potential_wells_scaled(om.xyz, *wells, c["theta"])
+            wz = om.apply_scaled_sampled(psi, c["theta"], vt, pidx, sidx).reshape(len(samp), S)
+            errs["complex_scaling_c64"] = {"h_apply_sampled": rel_err(c["y"], wz),
+                                           "sample": "the headline's sampled points and input"}
+        del psi
+    sm = chk.get("etrs_small")
+    if sm is not None:
+        o6 = oracle.Mesh(oracle.SPHERE, radius=sm["radius"], h=0.2)
+        O6 = oracle.Hamiltonian(o6, potential_wells(o6.xyz, *sm["wells"]))
+        O6.set_projectors(*sm["proj"])
+        idx = lib_to_orc(sm["lib_ijk"], o6.ijk)
+        psi = np.empty((o6.P, sm["psi"].shape[1]), dtype=np.complex128)
+        psi[idx] = sm["psi"]
+        t0 = time.perf_counter()
+        got, _ = O6.propagate(psi, 1, 0.01, scheme=oracle.ETRS)
+        legs["sphere_R6_etrs_step_s"] = time.perf_counter() - t0
+        errs["headline"]["etrs_step"] = rel_err(sm["out"], got[idx])
+        errs["headline"]["etrs_step_sample"] = (f"sphere R={sm['radius']:g} h=0.2 ({o6.P:,} points) with wells and "
+                                                f"projectors, {sm['psi'].shape[1]} states, one ETRS step, kernel "
+                                                f"{sm['kernel']}")
+    if "batch_256_systems" in chk:
+        e = []
+        for sy in chk["batch_256_systems"]["systems"]:
+            ob = oracle.Mesh(oracle.CUBE, sy["n"], h=0.25)
+            Ob = oracle.Hamiltonian(ob, potential_wells(ob.xyz, *sy["wells"]))
+            Ob.set_projectors(*sy["proj"])
+            idx = lib_to_orc(sy["lib_ijk"], ob.ijk)
+            psi = np.empty((ob.P, sy["psi"].shape[1]), dtype=np.complex128)
+            psi[idx] = sy["psi"]
+            got, _ = Ob.propagate(psi, 1, 0.02, scheme=oracle.ETRS)
+            e.append(rel_err(sy["out"], got[idx]))
+        errs["batch_256_systems"] = {"etrs_step": max(e), "sample": "the 3 smallest systems, one batched ETRS step"}
+    if "batch_sample" in chk:
+        bsm = chk["batch_sample"]
+        ps, tb = 0, 0.0
+        for n_, S_, (wl, pj) in zip(bsm["n"], bsm["S"], bsm["par"]):
+            ob = oracle.Mesh(oracle.CUBE, n_, h=0.25)
+            Ob = oracle.Hamiltonian(ob, potential_wells(ob.xyz, *wl))
+            Ob.set_projectors(*pj)
+            xb = white_noise_states(rng(9), ob.P, S_)
+            t0 = time.perf_counter()
+            Ob.apply(xb)
+            tb += time.perf_counter() - t0
+            ps += ob.P * S_
+        legs["batch_256_systems"] = {"value": ps / tb / 1e9, "unit": UNIT, "cores": nthr,
+                                     "step_s_extrapolated": N_APPLY_PER_STEP * bsm["point_states_all"] / (ps / tb),
+                                     "sample": f"one H application on each of the first 16 systems ({ps:,} "
+                                               f"point-states, {tb:.1f} s); the step time is extrapolated to all "
+                                               f"256 systems by point-states"}
+    if "large_cube_192" in chk:
+        c5 = chk["large_cube_192"]
+        o5 = oracle.Mesh(oracle.CUBE, 192, h=0.18)
+        O5 = oracle.Hamiltonian(o5, potential_wells(o5.xyz, *c5["wells"]))
+        O5.set_projectors(*c5["proj"])
+        idx = lib_to_orc(c5["lib_ijk"], o5.ijk)
+        psi = np.empty((o5.P, 8), dtype=np.complex128)
+        psi[idx] = c5["psi"]
+        t0 = time.perf_counter()
+        got, _ = O5.propagate(psi, 1, 0.01, scheme=oracle.ETRS, gs_every=1)
+        t5 = time.perf_counter() - t0
+        errs["large_cube_192"] = {"etrs_step_with_gram_schmidt": rel_err(c5["out"], got[idx]),
+                                  "sample": "states 0-7 of 128 (independent of 8-127 under index-order "
+                                            "orthonormalisation), one ETRS step then Gram-Schmidt"}
+        legs["large_cube_192"] = {"s_per_step_8_states": t5, "cores": nthr,
+                                  "s_1000_steps_128_states_extrapolated": t5 * 1000 * 16,
+                                  "sample": "states 0-7, one ETRS step with Gram-Schmidt; extrapolated to 128 "
+                                            "states and 1000 steps"}
+        del psi, got
+    for dt_name in ("c128", "c64"):
+        cg = chk.get(f"control_gradient_{dt_name}")
+        if cg is None:
+            continue
+        o4 = oracle.Mesh(oracle.CUBE, 64, h=0.3)
+        O4 = oracle.Hamiltonian(o4, potential_double_well(o4.xyz, 0.02, 2.0, 0.5))
+        idx = lib_to_orc(cg["lib_ijk"], o4.ijk)
+        a = np.empty(o4.P, dtype=np.complex128)
+        b = np.empty(o4.P, dtype=np.complex128)
+        a[idx], b[idx] = cg["psi0"], cg["target"]
+        t0 = time.perf_counter()
+        Jw, gw = O4.control_gradient(a, b, cg["eps"], 0.05, scheme=oracle.ETRS, nsub=4, checkpoint_every=50)
+        t4 = time.perf_counter() - t0
+        errs[f"control_gradient_{dt_name}"] = {
+            "J": abs(cg["J"] - Jw) / abs(Jw), "gradient": float(np.abs(cg["grad"] - gw).max() / np.abs(gw).max()),
+            "sample": "the first 5 intervals of the workload (its field, states and operator)"}
+        if dt_name == "c128":
+            nint = len(cg["eps"])
+            legs["control_gradient"] = {"s_forward_and_gradient_5_intervals": t4, "cores": nthr,
+                                        "s_2000_intervals_extrapolated": t4 * 2000 / nint,
+                                        "sample": "oracle forward + discrete adjoint, 5 intervals of 4 ETRS "
+                                                  "substeps, extrapolated to 2000"}
+    ss = chk.get("shifted_solve_c64")
+    if ss is not None and hd is not None:
+        idx = lib_to_orc(hd["lib_ijk"], om.ijk)
+        xs = np.empty_like(ss["x"])
+        bs = np.empty_like(ss["b"])
+        xs[idx], bs[idx] = ss["x"], ss["b"]
+        r = bs - (O.apply(xs) - ss["z"] * xs)
+        errs["shifted_solve_c64"] = {"true_relative_residual": float(
+            (np.linalg.norm(r, axis=0) / np.linalg.norm(bs, axis=0)).max()),
+            "sample": "all 8 right-hand sides, residual of the returned solutions under the oracle's operator"}
+    eg = chk.get("eigensolve_li_model")
+    if eg is not None:
+        ol = oracle.Mesh(oracle.CUBE, 61, h=0.4)
+        Ol = oracle.Hamiltonian(ol, potential_soft_coulomb_li(ol.xyz))
+        idx = lib_to_orc(eg["lib_ijk"], ol.ijk)
+        xe = np.empty_like(eg["x"])
+        xe[idx] = eg["x"]
+        r = Ol.apply(xe) - xe * eg["ev"][None, :]
+        rel = np.linalg.norm(r, axis=0) / (np.abs(eg["ev"]) * np.linalg.norm(xe, axis=0))
+        errs["eigensolve_li_model"] = {"relative_residual": float(rel.max()),
+                                       "sample": "the four wanted pairs under the oracle's operator"}
+    ho = chk.get("oscillator_32_c128")
+    if ho is not None:
+        o1 = oracle.Mesh(oracle.CUBE, 32, h=0.3)
+        O1 = oracle.Hamiltonian(o1, potential_harmonic(o1.xyz, 0.5))
+        idx = lib_to_orc(ho["lib_ijk"], o1.ijk)
+        psi = np.empty_like(ho["psi"])
+        psi[idx] = ho["psi"]
+        t0 = time.perf_counter()
+        got, _ = O1.propagate(psi, 100, 0.01, scheme=oracle.EXPMID)
+        t1 = time.perf_counter() - t0
+        errs["oscillator_32_c128"] = {"propagation_100_steps": rel_err(ho["out"], got[idx]),
+                                      "sample": "the whole run: 4 states, 100 steps"}
+        legs["oscillator_32_c128"] = {"s_100_steps": t1, "cores": nthr, "sample": "the whole run"}
+    return base, legs, errs
+
+
+def collect_headline_checks(H, mesh, psi_h, kname):
+    """One application of the headline Hamiltonian to the headline input at
+    4096 seeded points, and one ETRS step of a small sphere built the same
+    way with the same stencil kernel (kept on the host for the oracle leg)."""
+    import torch
+    import paper_1501_05654_gb300 as rsg
+    from workloads import gaussian_wells, potential_wells, projector_atoms, rng, white_noise_states
+    chk = {}
+    x = psi_h.to("cuda")
+    y = H.apply(x)
+    samp = rng(11).choice(mesh.P, 4096, replace=False)
+    torch.cuda.synchronize()
+    chk["headline"] = {"lib_ijk": mesh.ijk, "psi": psi_h.numpy(), "samp": samp, "kernel": kname,
+                       "y": y[torch.from_numpy(samp).cuda()].cpu().numpy().astype(np.complex128)}
+    del x, y
+    g6 = rng(12)
+    m6 = rsg.Mesh(rsg.SPHERE, radius=6.0, spacing=0.2)
+    w6 = gaussian_wells(g6, 8, 3.5)
+    p6 = projector_atoms(g6, 4, 2.5, 1, ball_radius=3.5)
+    H6 = rsg.Hamiltonian(m6, torch.complex64)
+    H6.set_potential(potential_wells(m6.xyz, *w6))
+    H6.set_projectors(*p6)
+    for k in ("kernel", "wide_ty", "producers", "zseg", "stages", "threads"):
+        H6.set_option(k, H.get_option(k))
+    x6 = white_noise_states(g6, m6.P, 64, dtype=np.complex64)
+    t6 = torch.from_numpy(x6).cuda()
+    H6.propagate(t6, 1, 0.01, scheme=rsg.ETRS, want_drift=False)
+    torch.cuda.synchronize()
+    chk["etrs_small"] = {"radius": 6.0, "wells": w6, "proj": p6, "lib_ijk": m6.ijk, "psi": x6.astype(np.complex128),
+                         "out": t6.cpu().numpy().astype(np.complex128),
+                         "kernel": KERNEL_NAMES.get(H6.get_option("last_kernel"), "unknown")}
+    return chk
 
 
 def time_steps(H, psi, steps, fn):
@@ -203,17 +418,32 @@ def time_steps(H, psi, steps, fn):
     return e0.elapsed_time(e1) / steps
 
 
-def extras(mesh, wells, proj, g):
+def extras(mesh, wells, proj, g, chk):
     """Side measurements on the same GPU: the FP64 (complex128) path with the
     default and the plain one-thread-per-value stencil, the FP32 plain
     stencil, and the optimal-control adjoint gradient against a forward
     propagation of the control workload (64^3 double well, dipole field,
-    2000 intervals of dt = 0.05 au, 4 ETRS substeps, checkpoints every 50)."""
+    2000 intervals of dt = 0.05 au, 4 ETRS substeps, checkpoints every 50).
+
+    chk (a dict, or None) collects host copies of inputs and results that the
+    oracle leg compares against the FP64 oracle: for every workload a small
+    sample (sampled points of one application, a short prefix of a
+    propagation or of a gradient)."""
     import torch
     import paper_1501_05654_gb300 as rsg
     from workloads import (control_field, potential_double_well, potential_wells, projector_atoms,
                            rng, white_noise_states)
     out = {}
+    hd = chk.get("headline") if chk is not None else None
+
+    def sampled_apply(Hx, dtype_):
+        """One application of Hx to the headline input, at the headline's sampled points."""
+        x = torch.from_numpy(hd["psi"]).to(dtype_).cuda()
+        y = Hx.apply(x)
+        torch.cuda.synchronize()
+        ys = y[torch.from_numpy(hd["samp"]).cuda()].cpu().numpy().astype(np.complex128)
+        del x, y
+        return ys
     peak, _ = peaks()
     P, S = mesh.P, 64
     for name, dtype, kernel in (("c64_plain_kernel", torch.complex64, 1),
@@ -229,7 +459,10 @@ def extras(mesh, wells, proj, g):
         ms = time_steps(H, psi, 2, lambda x: H.propagate(x, 1, 0.01, scheme=rsg.ETRS, want_drift=False))
         out[name] = {"ms_per_step": ms, "value": P * S * N_APPLY_PER_STEP / (ms * 1e-3) / 1e9,
                      "unit": UNIT}
-        del psi, H
+        del psi
+        if hd is not None:
+            chk[name] = {"kind": "sampled_apply", "y": sampled_apply(H, dtype)}
+        del H
         torch.cuda.empty_cache()
     # complex scaling on the headline mesh: the same wells at r e^{0.3 i}, no
     # projectors (refused while scaling is set), 64 complex64 states, ETRS
@@ -242,6 +475,11 @@ def extras(mesh, wells, proj, g):
     kms, kn, kbytes, _ = Hz.kernel_stats()
     Hz.profile(False)
     zk = Hz.get_option("last_kernel")
+    if hd is not None:
+        del psi
+        chk["complex_scaling_c64"] = {"kind": "sampled_apply_scaled", "theta": 0.3,
+                                      "y": sampled_apply(Hz, torch.complex64)}
+        psi = None
     out["complex_scaling_c64"] = {"ms_per_step": ms, "value": P * S * N_APPLY_PER_STEP / (ms * 1e-3) / 1e9,
                                   "unit": UNIT,
                                   "kernel": "k_apply_quad (complex diagonal)" if zk == 5 else "k_apply_scaled",
@@ -254,20 +492,36 @@ def extras(mesh, wells, proj, g):
     from workloads import batch_systems, gaussian_wells
     gb = rng(3)
     ns, Ss, nas = batch_systems(gb, 256)
-    hams, psis, pst = [], [], 0
+    hams, psis, pst, bpar = [], [], 0, []
     for n, S_, na in zip(ns, Ss, nas):
         m = rsg.Mesh(rsg.CUBE, int(n), spacing=0.25)
         half = 0.5 * (n - 1) * 0.25
         c, d, w = gaussian_wells(gb, int(na), 0.0, cube_half=0.6 * half)
         Hb = rsg.Hamiltonian(m, torch.complex64)
         Hb.set_potential(potential_wells(m.xyz, c, d, w))
-        Hb.set_projectors(*projector_atoms(gb, int(na), 2.5, 1, cube_half=0.6 * half))
+        pj = projector_atoms(gb, int(na), 2.5, 1, cube_half=0.6 * half)
+        Hb.set_projectors(*pj)
+        bpar.append(((c, d, w), pj))
         hams.append(Hb)
         psis.append(torch.randn((m.P, rsg.padded_ld(int(S_), torch.complex64)), dtype=torch.complex64,
                                 device="cuda") * 1e-3)
         pst += m.P * int(S_)
     batch = rsg.Batch(hams, [int(x) for x in Ss])
     ms = time_steps(None, psis, 10, lambda xs: batch.propagate(xs, 1, 0.02, scheme=rsg.ETRS))
+    if chk is not None:
+        # one more batched step; the three smallest systems are checked
+        small = [int(i) for i in np.argsort(ns)[:3]]
+        ins = [psis[i][:, :int(Ss[i])].cpu().numpy().astype(np.complex128) for i in small]
+        batch.propagate(psis, 1, 0.02, scheme=rsg.ETRS)
+        torch.cuda.synchronize()
+        chk["batch_256_systems"] = {
+            "kind": "batch", "systems": [
+                {"n": int(ns[i]), "wells": bpar[i][0], "proj": bpar[i][1], "lib_ijk": hams[i].mesh.ijk,
+                 "psi": x_in, "out": psis[i][:, :int(Ss[i])].cpu().numpy().astype(np.complex128)}
+                for i, x_in in zip(small, ins)]}
+        # the oracle leg times single applications on the first 16 systems
+        chk["batch_sample"] = {"n": [int(v) for v in ns[:16]], "S": [int(v) for v in Ss[:16]],
+                               "par": bpar[:16], "point_states_all": pst}
     # algorithmic stencil bytes of one step (read u, read psi, write, V per
     # Horner stage) over the whole step time: a lower bound on the batched
     # stencil's own fraction, since the step also holds the projector kernels
@@ -311,14 +565,30 @@ def extras(mesh, wells, proj, g):
     g0 = time.perf_counter()
     H5.orthonormalize(x5)
     gs_s = time.perf_counter() - g0
-    drift = H5.propagate(x5, 50, 0.01, scheme=rsg.ETRS, gs_every=50)
+    if chk is not None:
+        # one step with Gram-Schmidt after it; states 0-7 go to the oracle
+        # (index-order orthonormalisation makes them independent of 8-127)
+        x_in = x5[:, :8].cpu().numpy().astype(np.complex128)
+        H5.propagate(x5, 1, 0.01, scheme=rsg.ETRS, gs_every=1, want_drift=False)
+        torch.cuda.synchronize()
+        chk["large_cube_192"] = {"kind": "propagate", "wells": (c5, d5, w5), "proj": (cen, rc, lm, beta, hm),
+                                 "lib_ijk": cm5.ijk, "psi": x_in,
+                                 "out": x5[:, :8].cpu().numpy().astype(np.complex128)}
+    # the workload's full length: 1000 ETRS steps, Cholesky-QR every 50;
+    # per state, the largest |<psi|psi> - 1| seen before a re-orthonormalisation
+    t5 = time.perf_counter()
+    drift = H5.propagate(x5, 1000, 0.01, scheme=rsg.ETRS, gs_every=50)
+    torch.cuda.synchronize()
+    t5 = time.perf_counter() - t5
     k5_gbs = k5_bytes / (k5_ms * 1e-3) / 1e9 if k5_ms > 0 else None
     out["large_cube_192"] = {"ms_per_step": ms5, "value": cm5.P * S5 * N_APPLY_PER_STEP / (ms5 * 1e-3) / 1e9,
                              "unit": UNIT, "kernel": k5_name, "kernel_GBps": k5_gbs,
                              "kernel_frac_of_measured_hbm": k5_gbs / peak if k5_gbs else None,
-                             "gram_schmidt_s": gs_s, "norm_drift_max_50_steps": float(np.max(drift)),
+                             "gram_schmidt_s": gs_s, "run_1000_steps_s": t5,
+                             "norm_drift_max_1000_steps": float(np.max(drift)),
+                             "norm_drift_per_state": [float("%.3g" % v) for v in drift],
                              "workload": "192^3 h=0.18, 128 smooth states, 64 atoms x 9 projectors r_c=3, "
-                                         "ETRS dt=0.01, Cholesky-QR every 50 steps"}
+                                         "ETRS dt=0.01, Cholesky-QR every 50 steps, 1000 steps"}
     del H5, x5, xyz
     torch.cuda.empty_cache()
     # control gradient vs forward (the optimal-control workload)
@@ -345,6 +615,13 @@ def extras(mesh, wells, proj, g):
         J, grad = H.control_gradient(x, tgt, eps, 0.05, scheme=rsg.ETRS, nsub=4, checkpoint_every=50)
         tg = time.perf_counter() - t0
         ng = H.kernel_stats()[1]          # ... of the gradient (forward, recompute, costate)
+        if chk is not None:
+            # the first 5 intervals of the same problem, for the oracle
+            J5, g5 = H.control_gradient(x, tgt, eps[:5], 0.05, scheme=rsg.ETRS, nsub=4, checkpoint_every=50)
+            chk[f"control_gradient_{'c128' if dtype == torch.complex128 else 'c64'}"] = {
+                "kind": "gradient", "lib_ijk": cm.ijk, "psi0": x.cpu().numpy().astype(np.complex128),
+                "target": tgt.cpu().numpy().astype(np.complex128), "eps": np.array(eps[:5]), "J": J5,
+                "grad": np.array(g5)}
         out[f"control_gradient_{'c128' if dtype == torch.complex128 else 'c64'}"] = {
             "forward_s": tf, "gradient_s": tg, "ratio": tg / tf,
             "h_applications_forward": nf, "h_applications_gradient": ng, "h_application_ratio": ng / nf,
@@ -381,6 +658,10 @@ def extras(mesh, wells, proj, g):
     sres, sit = Hs.shifted_solve(bs, xs, -0.5 + 0.1j, max_iter=5000, tol=1e-4)
     torch.cuda.synchronize()
     tsv = time.perf_counter() - t0
+    if chk is not None:
+        chk["shifted_solve_c64"] = {"kind": "shifted", "z": -0.5 + 0.1j,
+                                    "b": bs.cpu().numpy().astype(np.complex128),
+                                    "x": xs.cpu().numpy().astype(np.complex128)}
     out["shifted_solve_c64"] = {"s": tsv, "iterations": sit, "ms_per_iteration": 1e3 * tsv / max(sit, 1),
                                 "max_relative_residual": float(np.max(sres)),
                                 "workload": "sphere R=18 h=0.2, wells + projectors, 8 right-hand sides, "
@@ -399,11 +680,40 @@ def extras(mesh, wells, proj, g):
     ev, res, it = Hl.eigensolve(x, nwant=4, max_iter=300, degree=16, tol=1e-8)
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
+    if chk is not None:
+        chk["eigensolve_li_model"] = {"kind": "eigen", "lib_ijk": lm.ijk,
+                                      "x": x[:, :4].cpu().numpy().astype(np.complex128),
+                                      "ev": np.array([float(v) for v in ev[:4]])}
     out["eigensolve_li_model"] = {
         "s": te, "iterations": it, "h_applications": (it * 16 + it + 1) * 8,
         "levels": [float(v) for v in ev[:4]], "max_residual": float(np.max(res[:4])),
         "paper_table": [-4.721, -4.211, -4.211, -4.086],
         "workload": "61^3 h=0.4 soft-Coulomb Li model, c128, 8 states (4 wanted), degree 16, tol 1e-8"}
+    del Hl, x
+    # the plain-method workload: 32^3, h = 0.3, oscillator w = 0.5, 4 smooth
+    # states, complex128, 100 exponential-midpoint steps of 0.01 au
+    from workloads import potential_harmonic, wavepacket_params, wavepacket_states
+    m1 = rsg.Mesh(rsg.CUBE, 32, spacing=0.3)
+    H1 = rsg.Hamiltonian(m1, torch.complex128)
+    H1.set_potential(potential_harmonic(m1.xyz, 0.5))
+    x1 = torch.from_numpy(wavepacket_states(m1.xyz, wavepacket_params(rng(1), 4, 1.5))).cuda()
+    H1.orthonormalize(x1)
+    x1_in = x1.cpu().numpy()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    d1 = H1.propagate(x1, 100, 0.01, scheme=rsg.EXPMID)
+    e1.record()
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    out["oscillator_32_c128"] = {"ms_per_step": ms1 / 100, "s_100_steps": ms1 * 1e-3,
+                                 "value": m1.P * 4 * 4 / (ms1 / 100 * 1e-3) / 1e9, "unit": UNIT,
+                                 "norm_drift_max": float(np.max(d1)),
+                                 "workload": "32^3 h=0.3 oscillator w=0.5, 4 smooth states, c128, 100 exponential "
+                                             "midpoint steps dt=0.01"}
+    if chk is not None:
+        chk["oscillator_32_c128"] = {"kind": "propagate_ho", "lib_ijk": m1.ijk, "psi": x1_in,
+                                     "out": x1.cpu().numpy()}
     return out
 
 
@@ -625,13 +935,24 @@ def main():
         "e2e": e2e,
     }
     line["clocks"] = clk.summary()
+    # host copies of results that the oracle leg checks against the FP64
+    # oracle (only with the oracle leg, on the headline workload)
+    chk = None
+    if not args.no_cpu_baseline and ws == 1 and args.radius == 18.0 and dtype == torch.complex64:
+        chk = collect_headline_checks(H, mesh, psi_h, kname)
     if not args.no_extras and ws == 1:
-        line["extras"] = extras(mesh, wells, proj, g)
+        line["extras"] = extras(mesh, wells, proj, g, chk)
     if not args.no_cpu_baseline and ws == 1:
         try:
-            line["cpu_baseline"] = cpu_baseline(lambda xyz: potential_wells(xyz, *wells), proj, 5)
+            base, legs, errs = oracle_leg(chk or {}, wells, proj)
+            line["cpu_baseline"] = base
+            line["cpu_baseline"]["legs"] = legs
+            line["error_vs_oracle"] = errs.get("headline")
+            for name, e in errs.items():
+                if name != "headline" and name in line.get("extras", {}):
+                    line["extras"][name]["error_vs_oracle"] = e
         except Exception as ex:     # reported, never fatal
-            line["cpu_baseline"] = {"error": str(ex)}
+            line["cpu_baseline"] = {"error": repr(ex)}
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
