@@ -79,6 +79,8 @@ def _load():
         L.orc_apply_sampled.argtypes = [vp, dbl, vp, vp, i64, i64, vp, vp, vp]
         L.orc_taylor4.argtypes = [vp, dbl, vp, dbl, vp, vp, i64]
         L.orc_norms2.argtypes = [vp, vp, i64, vp]
+        L.orc_taylor4_scaled.argtypes = [vp, dbl, vp, dbl, vp, vp, i64]
+        L.orc_propagate_scaled.argtypes = [vp, dbl, vp, vp, i64, i64, dbl, C.c_int]
         L.orc_mgs.argtypes = [vp, vp, i64]
         L.orc_propagate.argtypes = [vp, vp, i64, i64, dbl, C.c_int, C.c_int, vp, vp,
                                     C.c_int, vp]
@@ -156,6 +158,22 @@ class Mesh:
         _load().orc_apply_scaled_sampled(self._m, float(theta), _p(vt), _p(psi), psi.shape[1], pidx.shape[0],
                                          _p(pidx), _p(sidx), _p(out))
         return out
+
+    def taylor4_scaled(self, psi, theta: float, vtheta, tau: float):
+        """sum_{n<=4} (-i tau H_theta)^n psi / n! by explicit terms."""
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        vt = np.ascontiguousarray(vtheta, dtype=np.complex128)
+        out = np.empty_like(psi)
+        _load().orc_taylor4_scaled(self._m, float(theta), _p(vt), float(tau), _p(psi), _p(out), psi.shape[1])
+        return out
+
+    def propagate_scaled(self, psi, theta: float, vtheta, nsteps: int, dt: float, scheme: int = 0):
+        """nsteps steps of dt with H_theta (exponential midpoint, or ETRS)."""
+        psi = np.array(psi, dtype=np.complex128, order="C", copy=True)
+        vt = np.ascontiguousarray(vtheta, dtype=np.complex128)
+        _load().orc_propagate_scaled(self._m, float(theta), _p(vt), _p(psi), psi.shape[1], int(nsteps),
+                                     float(dt), int(scheme))
+        return psi
 
     def mgs(self, psi):
         psi = np.array(psi, dtype=np.complex128, order="C", copy=True)
@@ -253,6 +271,16 @@ class Hamiltonian:
         _load().orc_propagate(self._h, _p(psi), S, int(nsteps), float(dt), int(scheme),
                               int(nsub), _p(e), _p(d), int(gs_every), _p(drift))
         return psi, drift
+
+    def propagate_masked(self, psi, nsteps: int, dt: float, mask, scheme: int = EXPMID):
+        """nsteps steps, each followed by the pointwise product with the mask
+        M(r): the bounded part M psi of the mask split (Sec. "Photoemission",
+        Eq. (mask_split)) is kept after every step."""
+        mask = np.asarray(mask, dtype=np.float64)
+        for _ in range(int(nsteps)):
+            psi, _ = self.propagate(psi, 1, dt, scheme=scheme)
+            psi = psi * mask[:, None]
+        return psi
 
     def objective(self, psi0, target, eps, dt: float, scheme: int = ETRS, nsub: int = 1,
                   dir=(1.0, 0.0, 0.0)):

@@ -493,6 +493,49 @@ void orc_apply_scaled_sampled(void *mv, double theta, const cplx *vtheta, const 
     for (int64_t t = 0; t < nsamp; t++) out[t] = scaled_point(m, rot, vtheta, psi, S, pidx[t], sidx[t]);
 }
 
+/* Taylor-4 exponential of the complex-scaled operator, by explicit terms
+ * (as orc_taylor4): out = sum_{n=0..4} (-i tau H_theta)^n psi / n!. */
+void orc_taylor4_scaled(void *mv, double theta, const cplx *vtheta, double tau, const cplx *psi, cplx *out,
+                        int64_t S)
+{
+    const orc_mesh *m = (const orc_mesh *)mv;
+    int64_t N = m->P * S;
+    cplx *term = (cplx *)malloc(sizeof(cplx) * (N ? N : 1));
+    cplx *next = (cplx *)malloc(sizeof(cplx) * (N ? N : 1));
+    memcpy(term, psi, sizeof(cplx) * N);
+    memcpy(out, psi, sizeof(cplx) * N);
+    for (int n = 1; n <= 4; n++) {
+        orc_apply_scaled(mv, theta, vtheta, term, next, S);
+        cplx f = -I * tau / (double)n;
+        for (int64_t t = 0; t < N; t++) {
+            term[t] = f * next[t];
+            out[t] += term[t];
+        }
+    }
+    free(term);
+    free(next);
+}
+
+/* nsteps time steps of dt with the (time-independent) complex-scaled
+ * operator: exponential midpoint T(dt), or ETRS T(dt/2) T(dt/2). */
+void orc_propagate_scaled(void *mv, double theta, const cplx *vtheta, cplx *psi, int64_t S, int64_t nsteps,
+                          double dt, int scheme)
+{
+    const orc_mesh *m = (const orc_mesh *)mv;
+    int64_t N = m->P * S;
+    cplx *tmp = (cplx *)malloc(sizeof(cplx) * (N ? N : 1));
+    for (int64_t k = 0; k < nsteps; k++) {
+        if (scheme == 0) {
+            orc_taylor4_scaled(mv, theta, vtheta, dt, psi, tmp, S);
+            memcpy(psi, tmp, sizeof(cplx) * N);
+        } else {
+            orc_taylor4_scaled(mv, theta, vtheta, 0.5 * dt, psi, tmp, S);
+            orc_taylor4_scaled(mv, theta, vtheta, 0.5 * dt, tmp, psi, S);
+        }
+    }
+    free(tmp);
+}
+
 /* (H psi) at nsamp chosen (point, state) pairs only; for full-size checks. */
 void orc_apply_sampled(void *hv, double eps, const double *dir, const cplx *psi,
                        int64_t S, int64_t nsamp, const int64_t *pidx,

@@ -74,33 +74,20 @@ def test_apply_matches_oracle(dtype, shape, n, radius, S):
         assert torch.count_nonzero(y[:, S:]) == 0
 
 
-def _series(apply, psi, tau, order=4):
-    """sum_{n=0..order} (-i tau H)^n / n! psi, the terms by repeated application."""
-    out = psi.copy()
-    term = psi.copy()
-    for k in range(1, order + 1):
-        term = (-1j * tau / k) * apply(term)
-        out = out + term
-    return out
-
-
 def test_taylor_stage_and_etrs_steps():
     theta, tau = 0.3, 0.02
     p, vt = _scaled_pair("sphere", radius=2.4, theta=theta)
     psi = _states(p, 4, seed=7)
-    app = lambda u: p.om.apply_scaled(u, theta, vt)  # noqa: E731
     x = p.states_to_gpu(psi)
     out = torch.zeros_like(x)
     p.H.taylor(x, tau, out=out, S=4)
-    want = _series(app, psi, tau)
+    want = p.om.taylor4_scaled(psi, theta, vt, tau)
     got = p.states_from_gpu(out, 4)
     assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
     # ETRS without a field: two half stages per step, the same operator
     nsteps, dt = 5, 0.04
     p.H.propagate(x, nsteps, dt, scheme=rsg.ETRS, S=4)
-    want = psi
-    for _ in range(2 * nsteps):
-        want = _series(app, want, dt / 2)
+    want = p.om.propagate_scaled(psi, theta, vt, nsteps, dt, scheme=oracle.ETRS)
     got = p.states_from_gpu(x, 4)
     assert np.abs(got - want).max() < 1e-11 * np.abs(want).max()
 
@@ -210,8 +197,7 @@ def test_register_blocked_scaled_kernel(shape, n, radius, S):
     out = torch.zeros_like(x)
     p.H.taylor(x, 0.01, out=out, S=S)
     assert p.H.get_option("last_kernel") == 5
-    app = lambda u: p.om.apply_scaled(u, theta, vt)  # noqa: E731
-    tw = _series(app, psi, 0.01)
+    tw = p.om.taylor4_scaled(psi, theta, vt, 0.01)
     assert np.abs(p.states_from_gpu(out, S) - tw).max() < 2e-6 * np.abs(tw).max()
     # the same results as the one-thread-per-value kernel
     p.H.set_option("kernel", 1)

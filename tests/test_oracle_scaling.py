@@ -15,10 +15,19 @@ resonances": H_theta = -1/2 e^{-2 i theta} lap + V(r e^{i theta})):
   first non-real eigenvalue that stays put between theta = 0.4 and 0.5 has
   0 < Re < 1 and -1e-4 < Im < -1e-6 (this discretisation converges in h
   to 0.35448 - 4.70e-5 i).
+
+The scaled Taylor-4 exponential and propagation are pinned by the same
+closed-form modes through the scalar polynomial R(-i tau lambda), and by
+the plain exponential at theta = 0; the mask-absorber propagation (Sec.
+"Photoemission", Eq. (mask_split)) by its reductions to the plain
+propagation.
 """
+import math
+
 import numpy as np
 
 import oracle
+from workloads import rng, white_noise_states
 
 C = [-205 / 72, 8 / 5, -1 / 5, 8 / 315, -1 / 560]
 
@@ -111,3 +120,62 @@ def test_rotated_wells_generator():
     want = v + 1j * t * rgrad
     got = potential_wells_scaled(xyz, c, d, w, t)
     assert np.abs(got - want).max() < 1e-7 * max(1.0, np.abs(v).max())
+
+
+def _R4(z):
+    return sum(z ** n / math.factorial(n) for n in range(5))
+
+
+def test_scaled_taylor_and_propagation_on_closed_form_modes():
+    """The scaled Taylor-4 exponential and propagation against the closed
+    form: a product of sines between image walls is an eigenvector of H_theta
+    with lambda = e^{-2i theta} E + v0 (E from the stencil's symbol), so one
+    exponential multiplies it by R(-i tau lambda), R(z) = sum_{n<=4} z^n/n!,
+    a scalar polynomial (a route other than repeated applications); an ETRS
+    step by R(-i dt lambda / 2)^2 and an exponential-midpoint step by
+    R(-i dt lambda)."""
+    n, h, v0, theta, tau = 9, 0.35, 0.7 - 0.05j, 0.3, 0.04
+    m = oracle.Mesh(oracle.CUBE, n, h=h, bc=oracle.ODD)
+    vt = np.full(m.P, v0)
+    for modes in ((1, 1, 1), (2, 3, 1)):
+        f = np.ones(m.P, dtype=np.complex128)
+        for d, md in enumerate(modes):
+            f = f * np.sin(np.pi * md * (m.ijk[:, d] + 1) / (n + 1))
+        E = sum(_sigma(np.pi * md / (n + 1)) for md in modes) / (2 * h * h)
+        lam = np.exp(-2j * theta) * E + v0
+        got = m.taylor4_scaled(f.reshape(-1, 1), theta, vt, tau)[:, 0]
+        assert np.abs(got - _R4(-1j * tau * lam) * f).max() < 1e-12 * np.abs(f).max()
+        et = m.propagate_scaled(f.reshape(-1, 1), theta, vt, 3, 2 * tau, scheme=oracle.ETRS)[:, 0]
+        assert np.abs(et - _R4(-1j * tau * lam) ** 6 * f).max() < 1e-12 * np.abs(f).max()
+        mid = m.propagate_scaled(f.reshape(-1, 1), theta, vt, 2, tau, scheme=oracle.EXPMID)[:, 0]
+        assert np.abs(mid - _R4(-1j * tau * lam) ** 2 * f).max() < 1e-12 * np.abs(f).max()
+
+
+def test_scaled_taylor_at_zero_angle_is_the_plain_exponential():
+    """theta = 0 with a real v_theta: the plain operator's Taylor-4 exponential."""
+    m = oracle.Mesh(oracle.SPHERE, radius=2.0, h=0.3)
+    g = rng(31)
+    V = g.uniform(-1.0, 1.0, m.P)
+    psi = white_noise_states(g, m.P, 3)
+    O = oracle.Hamiltonian(m, V)
+    want = O.taylor4(psi, 0.03)
+    got = m.taylor4_scaled(psi, 0.0, V.astype(np.complex128), 0.03)
+    assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
+
+
+def test_masked_propagation_reduces_to_plain_and_scales():
+    """A mask of ones is the plain propagation; a constant mask c multiplies
+    n steps by c^n (every step is linear); a mask vanishing outside a ball
+    leaves zero there after the first step."""
+    m = oracle.Mesh(oracle.CUBE, 12, h=0.35)
+    g = rng(32)
+    O = oracle.Hamiltonian(m, 0.5 * np.sum(m.xyz ** 2, axis=1))
+    psi = white_noise_states(g, m.P, 2)
+    plain, _ = O.propagate(psi, 4, 0.02, scheme=oracle.ETRS)
+    ones = O.propagate_masked(psi, 4, 0.02, np.ones(m.P), scheme=oracle.ETRS)
+    assert np.array_equal(ones, plain)
+    half = O.propagate_masked(psi, 4, 0.02, np.full(m.P, 0.5), scheme=oracle.ETRS)
+    assert np.abs(half - 0.0625 * plain).max() < 1e-15 * np.abs(plain).max() + 1e-300
+    ball = (np.linalg.norm(m.xyz, axis=1) < 1.2).astype(np.float64)
+    inside = O.propagate_masked(psi, 2, 0.02, ball, scheme=oracle.ETRS)
+    assert not inside[ball == 0].any()
