@@ -418,6 +418,63 @@ def time_steps(H, psi, steps, fn):
     return e0.elapsed_time(e1) / steps
 
 
+def batch_extra(chk, peak, steps=10):
+    """The batch of 256 uneven systems: ms per ETRS step through the batched
+    launch, and (with chk) the host copies the oracle leg checks."""
+    import torch
+    import paper_1501_05654_gb300 as rsg
+    from workloads import potential_wells, projector_atoms, rng
+    out = {}
+    # batch of 256 uneven systems (cubes 24^3..96^3 at h = 0.25, 1..16 states,
+    # 1..8 atoms x 4 projectors): one launch per Horner stage for all systems
+    from workloads import batch_systems, gaussian_wells
+    gb = rng(3)
+    ns, Ss, nas = batch_systems(gb, 256)
+    hams, psis, pst, bpar = [], [], 0, []
+    for n, S_, na in zip(ns, Ss, nas):
+        m = rsg.Mesh(rsg.CUBE, int(n), spacing=0.25)
+        half = 0.5 * (n - 1) * 0.25
+        c, d, w = gaussian_wells(gb, int(na), 0.0, cube_half=0.6 * half)
+        Hb = rsg.Hamiltonian(m, torch.complex64)
+        Hb.set_potential(potential_wells(m.xyz, c, d, w))
+        pj = projector_atoms(gb, int(na), 2.5, 1, cube_half=0.6 * half)
+        Hb.set_projectors(*pj)
+        bpar.append(((c, d, w), pj))
+        hams.append(Hb)
+        psis.append(torch.randn((m.P, rsg.padded_ld(int(S_), torch.complex64)), dtype=torch.complex64,
+                                device="cuda") * 1e-3)
+        pst += m.P * int(S_)
+    batch = rsg.Batch(hams, [int(x) for x in Ss])
+    ms = time_steps(None, psis, steps, lambda xs: batch.propagate(xs, 1, 0.02, scheme=rsg.ETRS))
+    if chk is not None:
+        # one more batched step; the three smallest systems are checked
+        small = [int(i) for i in np.argsort(ns)[:3]]
+        ins = [psis[i][:, :int(Ss[i])].cpu().numpy().astype(np.complex128) for i in small]
+        batch.propagate(psis, 1, 0.02, scheme=rsg.ETRS)
+        torch.cuda.synchronize()
+        chk["batch_256_systems"] = {
+            "kind": "batch", "systems": [
+                {"n": int(ns[i]), "wells": bpar[i][0], "proj": bpar[i][1], "lib_ijk": hams[i].mesh.ijk,
+                 "psi": x_in, "out": psis[i][:, :int(Ss[i])].cpu().numpy().astype(np.complex128)}
+                for i, x_in in zip(small, ins)]}
+        # the oracle leg times single applications on the first 16 systems
+        chk["batch_sample"] = {"n": [int(v) for v in ns[:16]], "S": [int(v) for v in Ss[:16]],
+                               "par": bpar[:16], "point_states_all": pst}
+    # algorithmic stencil bytes of one step (read u, read psi, write, V per
+    # Horner stage) over the whole step time: a lower bound on the batched
+    # stencil's own fraction, since the step also holds the projector kernels
+    sbytes = N_APPLY_PER_STEP * sum(h.mesh.P * (3 * x.shape[1] * 8 + 4) for h, x in zip(hams, psis))
+    out["batch_256_systems"] = {"ms_per_step": ms, "point_states": pst,
+                                "value": pst * N_APPLY_PER_STEP / (ms * 1e-3) / 1e9, "unit": UNIT,
+                                "step_stencil_GBps": sbytes / (ms * 1e-3) / 1e9,
+                                "step_frac_of_measured_hbm": sbytes / (ms * 1e-3) / 1e9 / peak,
+                                "workload": "256 cubes n~U{24..96} h=0.25, S~U{1..16}, 1..8 atoms x 4 "
+                                            "projectors, ETRS dt=0.02, one captured graph per step"}
+    del batch, hams, psis
+    torch.cuda.empty_cache()
+    return out
+
+
 def extras(mesh, wells, proj, g, chk):
     """Side measurements on the same GPU: the FP64 (complex128) path with the
     default and the plain one-thread-per-value stencil, the FP32 plain
@@ -431,8 +488,8 @@ def extras(mesh, wells, proj, g, chk):
     propagation or of a gradient)."""
     import torch
     import paper_1501_05654_gb300 as rsg
-    from workloads import (control_field, potential_double_well, potential_wells, projector_atoms,
-                           rng, white_noise_states)
+    from workloads import (control_field, gaussian_wells, potential_double_well, potential_wells,
+                           projector_atoms, rng, white_noise_states)
     out = {}
     hd = chk.get("headline") if chk is not None else None
 
@@ -487,53 +544,7 @@ def extras(mesh, wells, proj, g, chk):
                                   "workload": "sphere R=18 h=0.2, 32 wells at r e^{0.3i}, 64 states, ETRS dt=0.01"}
     del psi, Hz
     torch.cuda.empty_cache()
-    # batch of 256 uneven systems (cubes 24^3..96^3 at h = 0.25, 1..16 states,
-    # 1..8 atoms x 4 projectors): one launch per Horner stage for all systems
-    from workloads import batch_systems, gaussian_wells
-    gb = rng(3)
-    ns, Ss, nas = batch_systems(gb, 256)
-    hams, psis, pst, bpar = [], [], 0, []
-    for n, S_, na in zip(ns, Ss, nas):
-        m = rsg.Mesh(rsg.CUBE, int(n), spacing=0.25)
-        half = 0.5 * (n - 1) * 0.25
-        c, d, w = gaussian_wells(gb, int(na), 0.0, cube_half=0.6 * half)
-        Hb = rsg.Hamiltonian(m, torch.complex64)
-        Hb.set_potential(potential_wells(m.xyz, c, d, w))
-        pj = projector_atoms(gb, int(na), 2.5, 1, cube_half=0.6 * half)
-        Hb.set_projectors(*pj)
-        bpar.append(((c, d, w), pj))
-        hams.append(Hb)
-        psis.append(torch.randn((m.P, rsg.padded_ld(int(S_), torch.complex64)), dtype=torch.complex64,
-                                device="cuda") * 1e-3)
-        pst += m.P * int(S_)
-    batch = rsg.Batch(hams, [int(x) for x in Ss])
-    ms = time_steps(None, psis, 10, lambda xs: batch.propagate(xs, 1, 0.02, scheme=rsg.ETRS))
-    if chk is not None:
-        # one more batched step; the three smallest systems are checked
-        small = [int(i) for i in np.argsort(ns)[:3]]
-        ins = [psis[i][:, :int(Ss[i])].cpu().numpy().astype(np.complex128) for i in small]
-        batch.propagate(psis, 1, 0.02, scheme=rsg.ETRS)
-        torch.cuda.synchronize()
-        chk["batch_256_systems"] = {
-            "kind": "batch", "systems": [
-                {"n": int(ns[i]), "wells": bpar[i][0], "proj": bpar[i][1], "lib_ijk": hams[i].mesh.ijk,
-                 "psi": x_in, "out": psis[i][:, :int(Ss[i])].cpu().numpy().astype(np.complex128)}
-                for i, x_in in zip(small, ins)]}
-        # the oracle leg times single applications on the first 16 systems
-        chk["batch_sample"] = {"n": [int(v) for v in ns[:16]], "S": [int(v) for v in Ss[:16]],
-                               "par": bpar[:16], "point_states_all": pst}
-    # algorithmic stencil bytes of one step (read u, read psi, write, V per
-    # Horner stage) over the whole step time: a lower bound on the batched
-    # stencil's own fraction, since the step also holds the projector kernels
-    sbytes = N_APPLY_PER_STEP * sum(h.mesh.P * (3 * x.shape[1] * 8 + 4) for h, x in zip(hams, psis))
-    out["batch_256_systems"] = {"ms_per_step": ms, "point_states": pst,
-                                "value": pst * N_APPLY_PER_STEP / (ms * 1e-3) / 1e9, "unit": UNIT,
-                                "step_stencil_GBps": sbytes / (ms * 1e-3) / 1e9,
-                                "step_frac_of_measured_hbm": sbytes / (ms * 1e-3) / 1e9 / peak,
-                                "workload": "256 cubes n~U{24..96} h=0.25, S~U{1..16}, 1..8 atoms x 4 "
-                                            "projectors, ETRS dt=0.02, one captured graph per step"}
-    del batch, hams, psis
-    torch.cuda.empty_cache()
+    out.update(batch_extra(chk, peak))
     # large cube: 192^3 at h = 0.18, 128 smooth complex64 states, 64 atoms x 9
     # projectors (s, p, d) on 3-bohr spheres, ETRS dt = 0.01, FP64-checked
     # Cholesky-QR every 50 steps; drift = max |<psi|psi> - 1| before it
@@ -767,6 +778,8 @@ def main():
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the complex128 / plain-kernel / control-gradient side measurements")
+    ap.add_argument("--only", default=None, choices=["batch"],
+                    help="run one side measurement alone and print it (for profiler captures)")
     ap.add_argument("--radius", type=float, default=18.0,
                     help="sphere radius (bohr); 18 is the benchmark workload, smaller radii "
                          "are for profiler captures only")
@@ -787,6 +800,10 @@ def main():
     if ws > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     rsg.build()
+    if args.only == "batch":
+        if rank == 0:
+            print(json.dumps(batch_extra(None, peaks()[0], steps=args.steps)), flush=True)
+        return
 
     g, wells, proj = build_inputs()
     mesh = rsg.Mesh(rsg.SPHERE, radius=args.radius, spacing=0.2)

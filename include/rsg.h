@@ -373,22 +373,43 @@ rsg_status rsg_fourier_basis(int64_t nsteps, int64_t nparam, double *basis_out);
 
 /* -------------------------------------------------------------- batches ---
  * Many independent systems (Sec. "Parallelization, optimizations and graphics processing units": groups of states as the
- * unit of work) propagated together: one launch per Taylor stage covers the
- * tiles of every system.  hams: nsys Hamiltonians (all complex64), S[i]
- * states per system.  The handles must outlive the batch. */
+ * unit of work) propagated together.  hams: nsys Hamiltonians (all
+ * complex64, zero ghosts, no mask or complex scaling; otherwise
+ * RSG_ERR_UNSUPPORTED), S[i] >= 1 states per system.  The handles must
+ * outlive the batch.  RSG_ERR_UNSUPPORTED also when a system has P * ld_i
+ * >= 2^31 or more than 32000 points along x. */
 rsg_status rsg_batch_create(const rsg_ham *hams, const int64_t *S, int nsys,
                             rsg_batch *out);
-/* psis[i]: device (P_i, ld_i) block with ld_i = S[i] rounded up to even.
- * Same step rule as rsg_propagate_steps with no field and nsub = 1.  When
- * every system has S <= 16 and all projector sets have the same size, each
- * Horner stage of every system is one launch of each kernel (projector
- * coefficients, their reduction, stencil, projector scatter) and one time
- * step is a captured CUDA graph replayed nsteps times on an internal stream
- * ordered after `stream`; otherwise the systems are propagated one by one.
- * gs_every > 0 re-orthonormalises every system every gs_every steps. */
+/* psis[i]: device (P_i, ld_i) block, 16-byte aligned, with ld_i = S[i]
+ * rounded up to even (RSG_ERR_ARG otherwise).  Same step rule as
+ * rsg_propagate_steps with no field and nsub = 1.  One time step is a
+ * captured CUDA graph, replayed nsteps times on an internal stream ordered
+ * after `stream`: by default one persistent launch (k_batch_step) that runs
+ * every Horner stage of every system from a queue of work items (projector
+ * coefficients per atom, stencil tile segments, projector terms), each item
+ * waiting, with a bound, for the items of its own system it depends on.
+ * gs_every > 0 re-orthonormalises every system every gs_every steps.  The
+ * call returns after the steps complete; RSG_ERR_TIMEOUT if a bounded wait
+ * of the step gave up (the states are then undefined, the context stays
+ * usable). */
 rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps,
                                double dt, rsg_scheme scheme, int gs_every,
                                void *stream);
+/* Batch knobs; unknown keys or values give RSG_ERR_ARG.
+ *   "persistent": 1 (default) the persistent step kernel; 0 one launch per
+ *       Horner stage and kernel (projector coefficients, their reduction,
+ *       stencil, projector terms), which propagates the systems one by one
+ *       when any has S > 16 or the projector sets differ in size.
+ *   "zseg": planes per tile segment of the persistent step (8..128, default
+ *       96; RSG_ERR_UNSUPPORTED if the segment does not fit in shared memory).
+ *   "wait_limit": polls of one dependency wait before it gives up (each
+ *       about 0.5 us; default 2^22).
+ *   "debug_stall": 1 makes system 0 wait for a stencil item that never comes,
+ *       so that the step's bounded waits run out (a test of that path).
+ * rsg_batch_get_option also reads "batched", "launches_per_step",
+ * "items_per_stage" and "blocks" (persistent blocks per launch). */
+rsg_status rsg_batch_set_option(rsg_batch b, const char *name, int64_t value);
+rsg_status rsg_batch_get_option(rsg_batch b, const char *name, int64_t *value);
 rsg_status rsg_batch_destroy(rsg_batch b);
 
 /* Tuning knobs (kernel tile shapes); unknown keys give RSG_ERR_ARG.

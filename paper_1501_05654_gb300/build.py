@@ -21,7 +21,7 @@ LIB = os.path.join(OUT, "librsg.so")
 # the complex64 row-TMA kernels separately (parallel compiles)
 SOURCES = [("rsg_kernels.cu", ["-DRSG_ONLY_FLOAT"]), ("rsg_kernels.cu", ["-DRSG_ONLY_FLOAT", "-DRSG_ROWTMA_TU"]),
            ("rsg_kernels.cu", ["-DRSG_ONLY_DOUBLE"]),
-           ("rsg_quad.cu", []), ("rsg_wide.cu", []), ("rsg_scaled.cu", []), ("rsg_selftest.cu", []), ("rsg_linalg.cu", []), ("rsg_noalloc.cu", []), ("rsg_host.cpp", [])]
+           ("rsg_quad.cu", []), ("rsg_wide.cu", []), ("rsg_bstep.cu", []), ("rsg_scaled.cu", []), ("rsg_selftest.cu", []), ("rsg_linalg.cu", []), ("rsg_noalloc.cu", []), ("rsg_host.cpp", [])]
 HEADERS = ["rsg_internal.h", "rsg_vec.cuh", "rsg_async.cuh", "rsg_batch.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -221,6 +221,15 @@ struct rsg_batch_s {
     int step_scheme = -1;
     std::vector<void *> step_psis;
     int64_t n_launch_step = 0;
+    // persistent step (mode 1, the default): one k_batch_step launch per
+    // time step; mode 0: one launch per Horner stage and kernel
+    int mode = 1;
+    int zseg = 96;                 // planes per tile segment (mode 1)
+    long wait_limit = 1L << 22;    // polls of a dependency wait
+    int stall = 0;                 // > 0: system 0 waits for a stencil item that never comes
+    std::vector<BItem> stage_items;   // the items of one stage, stage bits 0
+    int np_cap = 0, nblocks = 0, step_nst = 0;
+    DevBuf d_items, d_cnt, d_ctl, d_status, d_zero;
     ~rsg_batch_s() {
         if (step) cudaGraphExecDestroy(step);
         if (ev_in) cudaEventDestroy(ev_in);
@@ -2495,7 +2504,7 @@ rsg_status batch_exponential(rsg_batch b, double tau, cudaStream_t st) {
     return RSG_OK;
 }
 
-rsg_status batch_build(rsg_batch b) {
+rsg_status batch_build_stages(rsg_batch b) {
     const int n = (int)b->hams.size();
     b->args.assign((size_t)n, SysArgs{});
     b->w0.resize((size_t)n);
@@ -2602,6 +2611,193 @@ rsg_status batch_build(rsg_batch b) {
     return RSG_OK;
 }
 
+// Work items of one stage of the persistent step: the projector
+// coefficients of every atom, the stencil items (tile segments times 16-value
+// chunks, longest first across systems) and the scatter items of every
+// system, in that order.
+rsg_status batch_build_step(rsg_batch b) {
+    const int n = (int)b->hams.size();
+    b->batched = false;
+    for (int i = 0; i < n; i++)
+        if (b->ld[(size_t)i] > kBMaxLd) return RSG_OK;   // propagated one by one
+    b->args.assign((size_t)n, SysArgs{});
+    b->w0.resize((size_t)n);
+    b->w1.resize((size_t)n);
+    b->D.resize((size_t)n);
+    b->partial.resize((size_t)n);
+    std::vector<BItem> dots, sten, scat;
+    std::vector<int> sten_len;
+    int np_cap = 8;
+    for (int i = 0; i < n; i++) {
+        rsg_ham H = b->hams[(size_t)i];
+        rsg_mesh m = H->m;
+        if (!H->has_V) return fail(RSG_ERR_STATE, "system %d has no potential", i);
+        const int64_t ld = b->ld[(size_t)i];
+        if ((int64_t)m->P * ld >= 0x7fffffffLL || m->nx > 32000)
+            return fail(RSG_ERR_UNSUPPORTED, "system %d: P * ld above 2^31 or nx above 32000", i);
+        CKS(ensure_rows(m));
+        const size_t bytes = (size_t)m->P * ld * 8;
+        CK(b->w0[(size_t)i].ensure(bytes));
+        CK(b->w1[(size_t)i].ensure(bytes));
+        int TX = 16, TY = 6;
+        batch_step_tile((int)ld, &TX, &TY);
+        const Tile *tiles = nullptr;
+        int ntiles = 0;
+        CKS(get_tiles(m, TX, TY, b->zseg, &tiles, &ntiles));
+        const std::vector<Tile> &ht = m->tiles_host[std::make_tuple(TX, TY, b->zseg)];
+        SysArgs &A = b->args[(size_t)i];
+        A.vec[0] = nullptr;
+        A.vec[1] = b->w0[(size_t)i].p;
+        A.vec[2] = b->w1[(size_t)i].p;
+        A.rows = m->d_rows.as<Row>();
+        A.tiles = tiles;
+        A.nx = m->nx;
+        A.ny = m->ny;
+        A.nz = m->nz;
+        A.SV = (int)(ld / 2);
+        A.ld = (int)ld;
+        A.P = (int)m->P;
+        A.V = H->V.as<float>();
+        for (int k = 0; k < 5; k++) A.w[k] = (float)(-0.5 * kFD[k] / (m->h * m->h));
+        A.h3 = m->h * m->h * m->h;
+        const int nch = ld > 16 ? (int)((ld + 15) / 16) : 1;
+        for (int t = 0; t < ntiles; t++) {
+            const int len = ht[(size_t)t].zhi - ht[(size_t)t].zlo;
+            np_cap = std::max(np_cap, len + 8);
+            for (int c = 0; c < nch; c++) {
+                sten.push_back(BItem{1, i, t, c});
+                sten_len.push_back(len);
+            }
+        }
+        A.nsten = ntiles * nch;
+        A.stall = (i == 0 && b->stall > 0) ? 1 : 0;
+        const ProjDev &pj = H->pj;
+        A.natoms = pj.natoms;
+        A.npmax = pj.npmax;
+        A.nu = pj.nu;
+        A.ndot = 0;
+        A.nsca = 0;
+        if (pj.natoms > 0) {
+            if (pj.npmax != 1 && pj.npmax != 4 && pj.npmax != 9)
+                return fail(RSG_ERR_UNSUPPORTED, "system %d: %d projectors per atom", i, pj.npmax);
+            A.q_pt = pj.q_pt;
+            A.q_atom = pj.q_atom;
+            A.nl_ent = pj.nl_ent;
+            A.chunk_q0 = pj.chunk_q0;
+            A.chunk_q1 = pj.chunk_q1;
+            A.atom_chunk0 = pj.atom_chunk0;
+            A.u_pts = pj.u_pts;
+            A.u_ptr = pj.u_ptr;
+            A.e_atom = pj.e_atom;
+            A.e_p = (const float *)pj.e_p;
+            A.q_p = (const float *)pj.q_p;
+            A.hm = pj.hm;
+            CK(b->D[(size_t)i].ensure((size_t)pj.natoms * pj.npmax * ld * 8));
+            A.D = b->D[(size_t)i].as<float>();
+            for (int at = 0; at < pj.natoms; at++) dots.push_back(BItem{0, i, at, 0});
+            for (int u = 0; u < pj.nu; u += kBScatterPts) scat.push_back(BItem{2, i, u, std::min(kBScatterPts, pj.nu - u)});
+            A.ndot = pj.natoms;
+            A.nsca = (pj.nu + kBScatterPts - 1) / kBScatterPts;
+        }
+    }
+    if (batch_step_smem(np_cap) > 227 * 1024)
+        return fail(RSG_ERR_UNSUPPORTED, "tile segments of %d planes do not fit in shared memory", np_cap - 8);
+    {
+        std::vector<size_t> idx(sten.size());
+        for (size_t k = 0; k < idx.size(); k++) idx[k] = k;
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) { return sten_len[x] > sten_len[y]; });
+        std::vector<BItem> sorted(sten.size());
+        for (size_t k = 0; k < idx.size(); k++) sorted[k] = sten[idx[k]];
+        sten.swap(sorted);
+    }
+    b->stage_items.clear();
+    b->stage_items.insert(b->stage_items.end(), dots.begin(), dots.end());
+    b->stage_items.insert(b->stage_items.end(), sten.begin(), sten.end());
+    b->stage_items.insert(b->stage_items.end(), scat.begin(), scat.end());
+    b->np_cap = np_cap;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    b->nblocks = std::max(1, std::min(sms, (int)b->stage_items.size()));
+    CK(b->d_status.ensure(sizeof(int)));
+    CK(cudaMemset(b->d_status.p, 0, sizeof(int)));
+    CK(b->d_ctl.ensure(sizeof(BCtl)));
+    CK(b->d_zero.ensure(kBZeroBytes));
+    CK(cudaMemset(b->d_zero.p, 0, kBZeroBytes));
+    b->step_nst = 0;   // items and counters follow the scheme at capture
+    b->batched = true;
+    b->n_launch_step = 1;
+    return RSG_OK;
+}
+
+rsg_status batch_build(rsg_batch b) {
+    if (b->cs) CK(cudaStreamSynchronize(b->cs));
+    if (b->step) {
+        CK(cudaGraphExecDestroy(b->step));
+        b->step = nullptr;
+    }
+    return b->mode == 1 ? batch_build_step(b) : batch_build_stages(b);
+}
+
+// Stages of one step of the persistent kernel: each exponential T(tau) is
+// four Horner stages k = 4..1, out = psi + (-i tau / k) H u, with the same
+// buffer rotation as taylor() (0 = psi, 1 = w0, 2 = w1).
+int batch_stages(rsg_scheme scheme, double dt, BStage *st) {
+    const int nexp = scheme == RSG_ETRS ? 2 : 1;
+    const double tau = scheme == RSG_ETRS ? 0.5 * dt : dt;
+    int t = 0;
+    for (int e = 0; e < nexp; e++) {
+        int src = 0;
+        for (int k = 4; k >= 1; k--) {
+            const int dst = (k == 1) ? 0 : ((k & 1) ? 2 : 1);
+            st[t++] = BStage{src, dst, (float)(-tau / k)};
+            src = dst;
+        }
+    }
+    return t;
+}
+
+// The queue of one step (every stage's items, stage bits set) and its
+// counters, uploaded before the step is captured.
+rsg_status batch_prepare_step(rsg_batch b, rsg_scheme scheme) {
+    if (b->mode != 1) return RSG_OK;
+    BStage st[8];
+    const int nst = batch_stages(scheme, 1.0, st);
+    if (b->step_nst == nst) return RSG_OK;
+    std::vector<BItem> items;
+    items.reserve(b->stage_items.size() * (size_t)nst);
+    for (int t = 0; t < nst; t++)
+        for (const BItem &w : b->stage_items) items.push_back(BItem{w.kind | (t << 2), w.sys, w.a, w.b});
+    CK(b->d_items.upload(items));
+    CK(b->d_cnt.ensure(b->hams.size() * (size_t)nst * 3 * sizeof(unsigned)));
+    b->step_nst = nst;
+    return RSG_OK;
+}
+
+rsg_status batch_capture_step(rsg_batch b, double dt, rsg_scheme scheme, cudaStream_t cs) {
+    if (b->mode == 1) {
+        BStepArgs a{};
+        a.nst = batch_stages(scheme, dt, a.st);
+        if (b->step_nst != a.nst) return fail(RSG_ERR_STATE, "batch queue not prepared");
+        a.sys = b->d_args.as<SysArgs>();
+        a.items = b->d_items.as<BItem>();
+        a.nitems = (int)(b->stage_items.size() * (size_t)a.nst);
+        a.cnt = b->d_cnt.as<unsigned>();
+        a.ctl = b->d_ctl.as<BCtl>();
+        a.status = b->d_status.as<int>();
+        a.zeros = b->d_zero.p;
+        a.wait_limit = b->wait_limit;
+        a.np_cap = b->np_cap;
+        CK(cudaMemsetAsync(b->d_cnt.p, 0, b->hams.size() * (size_t)a.nst * 3 * sizeof(unsigned), cs));
+        CK(cudaMemsetAsync(b->d_ctl.p, 0, sizeof(BCtl), cs));
+        CK(launch_batch_step(a, b->nblocks, cs));
+        return RSG_OK;
+    }
+    if (scheme == RSG_EXPMID) return batch_exponential(b, dt, cs);
+    CKS(batch_exponential(b, 0.5 * dt, cs));
+    return batch_exponential(b, 0.5 * dt, cs);
+}
+
 }  // namespace
 
 extern "C" {
@@ -2644,6 +2840,8 @@ rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps, d
     bool same = b->step && b->step_dt == dt && b->step_scheme == (int)scheme && b->step_psis.size() == n;
     for (size_t i = 0; same && i < n; i++) same = b->step_psis[i] == psis[i];
     if (!same) {
+        // the previous step graph may still read the tables being replaced
+        if (b->cs) CK(cudaStreamSynchronize(b->cs));
         for (size_t i = 0; i < n; i++) b->args[i].vec[0] = psis[i];
         CK(b->d_args.upload(b->args));
         if (!b->cs) {
@@ -2655,15 +2853,10 @@ rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps, d
             CK(cudaGraphExecDestroy(b->step));
             b->step = nullptr;
         }
+        CKS(batch_prepare_step(b, scheme));
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
-        rsg_status s = RSG_OK;
-        if (scheme == RSG_EXPMID) {
-            s = batch_exponential(b, dt, b->cs);
-        } else {
-            s = batch_exponential(b, 0.5 * dt, b->cs);
-            if (s == RSG_OK) s = batch_exponential(b, 0.5 * dt, b->cs);
-        }
+        rsg_status s = batch_capture_step(b, dt, scheme, b->cs);
         cudaError_t ee = cudaStreamEndCapture(b->cs, &g);
         if (s != RSG_OK) {
             if (g) cudaGraphDestroy(g);
@@ -2689,6 +2882,52 @@ rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps, d
     CK(cudaStreamWaitEvent(st, b->ev_out, 0));
     if (gs_every > 0)
         for (size_t i = 0; i < n; i++) CKS(read_status(b->hams[i], st));
+    if (b->mode == 1 && b->d_status.p) {
+        int s = 0;
+        CK(cudaMemcpyAsync(&s, b->d_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (s != 0) {
+            CK(cudaMemset(b->d_status.p, 0, sizeof(int)));
+            return fail(RSG_ERR_TIMEOUT, "a bounded wait of the batched step gave up");
+        }
+    }
+    return RSG_OK;
+}
+
+rsg_status rsg_batch_set_option(rsg_batch b, const char *name, int64_t value) {
+    if (!b || !name) return fail(RSG_ERR_ARG, "NULL argument");
+    const std::string k(name);
+    if (k == "persistent" && (value == 0 || value == 1)) {
+        b->mode = (int)value;
+    } else if (k == "zseg" && value >= 8 && value <= 128) {
+        b->zseg = (int)value;
+    } else if (k == "wait_limit" && value >= 1) {
+        b->wait_limit = (long)value;
+        if (b->step) {
+            CK(cudaGraphExecDestroy(b->step));
+            b->step = nullptr;
+        }
+        return RSG_OK;
+    } else if (k == "debug_stall" && (value == 0 || value == 1)) {
+        b->stall = (int)value;
+    } else {
+        return fail(RSG_ERR_ARG, "unknown batch option %s = %lld", name, (long long)value);
+    }
+    return batch_build(b);
+}
+
+rsg_status rsg_batch_get_option(rsg_batch b, const char *name, int64_t *value) {
+    if (!b || !name || !value) return fail(RSG_ERR_ARG, "NULL argument");
+    const std::string k(name);
+    if (k == "persistent") *value = b->mode;
+    else if (k == "zseg") *value = b->zseg;
+    else if (k == "wait_limit") *value = b->wait_limit;
+    else if (k == "debug_stall") *value = b->stall;
+    else if (k == "batched") *value = b->batched ? 1 : 0;
+    else if (k == "launches_per_step") *value = b->mode == 1 ? 1 : b->n_launch_step * 8;
+    else if (k == "items_per_stage") *value = (int64_t)b->stage_items.size();
+    else if (k == "blocks") *value = b->nblocks;
+    else return fail(RSG_ERR_ARG, "unknown batch option %s", name);
     return RSG_OK;
 }
 

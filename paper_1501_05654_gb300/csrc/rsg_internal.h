@@ -248,6 +248,11 @@ struct SysArgs {
     float *D;
     double *partial;
     double h3;
+    // persistent step (k_batch_step): complex values per point, and per
+    // stage the number of dot (one per atom), stencil and scatter items;
+    // stall > 0 makes the stencil count unreachable (a test of the bounded
+    // waits)
+    int ld, ndot, nsten, nsca, stall;
 };
 // Work item: stencil (sys, tile, chunk); projector dot (sys, chunk);
 // projector reduce (sys, atom); scatter (sys, first union point).
@@ -263,6 +268,43 @@ cudaError_t launch_batch_proj(const SysArgs *sys, const BWork *dot_work, int ndo
                               int nred, int in_c, int npmax, cudaStream_t st);
 cudaError_t launch_batch_scatter(const SysArgs *sys, const BWork *work, int nwork, int out_c, float ar,
                                  float ai, cudaStream_t st);
+
+// ---- persistent batched time step (rsg_bstep.cu) ----
+// Stage t of a step: out = vec[dst] = psi + i ai H vec[src] (ai = -tau / k).
+struct BStage {
+    int src, dst;
+    float ai;
+};
+// Work item: kind = 4 * stage + {0 dot (a = atom), 1 stencil (a = tile, b =
+// 16-value chunk), 2 scatter (a = first union point, b = count)}.
+struct BItem {
+    int32_t kind, sys, a, b;
+};
+struct BCtl {
+    unsigned head;   // next queue position
+    int abort;       // set by a wait that gave up
+};
+constexpr int kBWinRowsMax = 32, kBTileRowsMax = 24;   // window and tile rows of any batch tile
+constexpr int kBZeroBytes = 4096;                      // zero page read by the window fills
+constexpr int kBScatterPts = 1024;                     // union points per scatter item
+constexpr int kBMaxLd = 128;                           // complex values per point in the persistent step
+struct BStepArgs {
+    const SysArgs *sys;
+    const BItem *items;
+    int nitems, nst;
+    BStage st[8];
+    unsigned *cnt;       // (system, stage, kind): items finished
+    BCtl *ctl;
+    int *status;         // 2 when a bounded wait gave up
+    const void *zeros;   // kBZeroBytes of zeros, 16-byte aligned
+    long wait_limit;     // polls of a dependency wait (about 0.5 us each)
+    int np_cap;          // planes of the longest tile segment plus 8
+};
+// Tile of a system with ld complex values per point (ld > 16: 16-value chunks).
+void batch_step_tile(int ld, int *TX, int *TY);
+size_t batch_step_smem(int np_cap);
+int batch_step_threads();
+cudaError_t launch_batch_step(const BStepArgs &a, int nblocks, cudaStream_t st);
 
 // Host-side accessors for code outside rsg_host.cpp: the Hamiltonian's
 // compute type, point count and spacing, and the thread-local error message.

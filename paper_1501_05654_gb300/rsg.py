@@ -63,6 +63,8 @@ SIGNATURES = {
     "rsg_batch_create": [_vp, _vp, _int, _vp],
     "rsg_batch_propagate": [_vp, _vp, _i64, _dbl, _int, _int, _vp],
     "rsg_batch_destroy": [_vp],
+    "rsg_batch_set_option": [_vp, C.c_char_p, _i64],
+    "rsg_batch_get_option": [_vp, C.c_char_p, _vp],
     "rsg_ham_set_option": [_vp, C.c_char_p, _i64],
     "rsg_ham_get_option": [_vp, C.c_char_p, _vp],
     "rsg_ham_autotune": [_vp, _vp, _vp, _i64, _i64, _vp, _vp],
@@ -543,3 +545,11 @@ class Batch:
         ptrs = (C.c_void_p * len(psis))(*[p.data_ptr() for p in psis])
         _ck(load().rsg_batch_propagate(self._h, ptrs, int(nsteps), float(dt), int(scheme),
                                        int(gs_every), _stream(stream)))
+
+    def set_option(self, key: str, value: int):
+        _ck(load().rsg_batch_set_option(self._h, key.encode(), int(value)))
+
+    def get_option(self, key: str) -> int:
+        v = C.c_int64()
+        _ck(load().rsg_batch_get_option(self._h, key.encode(), C.byref(v)))
+        return int(v.value)
