@@ -404,12 +404,25 @@ rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps,
  *       96; RSG_ERR_UNSUPPORTED if the segment does not fit in shared memory).
  *   "wait_limit": polls of one dependency wait before it gives up (each
  *       about 0.5 us; default 2^22).
+ *   "tile_variants": bit (ls / 2 - 1) set selects tile variant 1 for the
+ *       systems whose staged records hold ls = min(ld, 16) values (ls = 6,
+ *       8, 10, 12, 14 have two variants: 0 one thread per value on wide
+ *       tiles, 1 power-of-two value lanes on narrower tiles); default 0.
  *   "debug_stall": 1 makes system 0 wait for a stencil item that never comes,
  *       so that the step's bounded waits run out (a test of that path).
  * rsg_batch_get_option also reads "batched", "launches_per_step",
  * "items_per_stage" and "blocks" (persistent blocks per launch). */
 rsg_status rsg_batch_set_option(rsg_batch b, const char *name, int64_t value);
 rsg_status rsg_batch_get_option(rsg_batch b, const char *name, int64_t *value);
+/* Batch autotuner: times steps of the given scheme and dt on device copies
+ * of psis (psis are read, not changed; the copies are freed before return)
+ * for the per-stage launches and the persistent step, and for the persistent
+ * step its segment length ("zseg" 48, 64, 96, 128) and, per record length
+ * with two tile variants (largest share of bytes first), the variant; keeps
+ * the fastest and returns its time per step in *best_ms (may be NULL).
+ * Synchronises.  Errors as rsg_batch_propagate. */
+rsg_status rsg_batch_autotune(rsg_batch b, void *const *psis, double dt, rsg_scheme scheme, void *stream,
+                              double *best_ms);
 rsg_status rsg_batch_destroy(rsg_batch b);
 
 /* Tuning knobs (kernel tile shapes); unknown keys give RSG_ERR_ARG.

@@ -51,55 +51,60 @@ constexpr int kBNS = 3;                      // pipeline slots
 constexpr unsigned kBSuspendNs = 2000;
 constexpr long kBSlotWaitLimit = 1L << 20;   // about 2 s per slot wait
 
-// Tile (TX x TY) by value lanes R (the record width rounded up to 2, 4, 8, 16)
-template <int R>
-struct BGeom;
-template <>
-struct BGeom<16> {
-    static constexpr int TX = 16, TY = 6;
-};
-template <>
-struct BGeom<8> {
-    static constexpr int TX = 16, TY = 12;
-};
-template <>
-struct BGeom<4> {
-    static constexpr int TX = 32, TY = 12;
-};
-template <>
-struct BGeom<2> {
-    static constexpr int TX = 32, TY = 24;
-};
+// Tile (TX x TY) of a system whose staged record holds LS complex values,
+// two variants per LS that the autotuner chooses between.  Variant 0: one
+// compute thread per value (LANES = LS) at a 2 x 2 group of points, wide
+// rows where the record is short (fewer, longer copies).  Variant 1: LANES =
+// LS rounded up to a power of two (idle lanes, but warps aligned to groups
+// and records) on narrower tiles.
+template <int LS, int VAR>
+struct BTile;
+template <> struct BTile<2, 0> { static constexpr int TX = 32, TY = 24, LANES = 2; };
+template <> struct BTile<4, 0> { static constexpr int TX = 32, TY = 12, LANES = 4; };
+template <> struct BTile<6, 0> { static constexpr int TX = 32, TY = 8, LANES = 6; };
+template <> struct BTile<8, 0> { static constexpr int TX = 32, TY = 6, LANES = 8; };
+template <> struct BTile<10, 0> { static constexpr int TX = 18, TY = 8, LANES = 10; };
+template <> struct BTile<12, 0> { static constexpr int TX = 16, TY = 8, LANES = 12; };
+template <> struct BTile<14, 0> { static constexpr int TX = 18, TY = 6, LANES = 14; };
+template <> struct BTile<16, 0> { static constexpr int TX = 16, TY = 6, LANES = 16; };
+template <> struct BTile<6, 1> { static constexpr int TX = 16, TY = 12, LANES = 8; };
+template <> struct BTile<8, 1> { static constexpr int TX = 16, TY = 12, LANES = 8; };
+template <> struct BTile<10, 1> { static constexpr int TX = 16, TY = 6, LANES = 16; };
+template <> struct BTile<12, 1> { static constexpr int TX = 16, TY = 6, LANES = 16; };
+template <> struct BTile<14, 1> { static constexpr int TX = 16, TY = 6, LANES = 16; };
+// record lengths with two distinct variants
+__host__ __device__ constexpr bool bhas_var1(int ls) { return ls == 6 || ls == 8 || ls == 10 || ls == 12 || ls == 14; }
 
 // Staging geometry of records of LS complex values
-template <int LS>
+template <int LS, int VAR>
 struct BShape {
-    static constexpr int R = LS <= 2 ? 2 : LS <= 4 ? 4 : LS <= 8 ? 8 : 16;
-    static constexpr int TX = BGeom<R>::TX, TY = BGeom<R>::TY;
+    static constexpr int TX = BTile<LS, VAR>::TX, TY = BTile<LS, VAR>::TY, LANES = BTile<LS, VAR>::LANES;
     static constexpr int WX = TX + 8, WY = TY + 8;
     static constexpr int REC = LS * 8;             // bytes per staged record
     static constexpr int UB = WX * WY * REC;       // input window of one plane
     static constexpr int BB = TX * TY * REC;       // base values of one plane
     static constexpr int VB = TX * TY * 4;         // potential of one plane
     static constexpr int GX = TX / 2;              // 2 x 2 groups per tile row
-    static_assert(R * GX * (TY / 2) == 32 * kBNCW, "one compute thread per value and point group");
+    static constexpr int NG = GX * (TY / 2);       // groups per tile
+    static_assert(TX % 2 == 0 && TY % 2 == 0 && LANES >= LS, "2 x 2 groups, a lane per value");
+    static_assert(LANES * NG <= 32 * kBNCW, "one compute thread per value lane and point group");
     static_assert(WY + TY <= 32 * kBNPW, "one producer lane per window row and per base row");
-    static_assert((TX * TY) % 32 == 0, "the potential's points in groups of 32");
     static_assert(TX <= 32 && WY <= kBWinRowsMax && TY <= kBTileRowsMax, "table sizes");
+    static_assert(WX * REC <= kBZeroBytes, "the zero page covers a window row");
 };
 
 constexpr int bslot_need(int ub, int bb, int vb) { return ub + bb + vb; }
 static_assert(kBMaxLd % 2 == 0, "complex64 rows are whole float4");
 constexpr int bmax(int a, int b) { return a > b ? a : b; }
+template <int LS, int VAR>
+constexpr int bslot_ls() { return bslot_need(BShape<LS, VAR>::UB, BShape<LS, VAR>::BB, BShape<LS, VAR>::VB); }
 constexpr int kBSlot =
-    (bmax(bmax(bslot_need(BShape<16>::UB, BShape<16>::BB, BShape<16>::VB),
-               bslot_need(BShape<8>::UB, BShape<8>::BB, BShape<8>::VB)),
-          bmax(bslot_need(BShape<4>::UB, BShape<4>::BB, BShape<4>::VB),
-               bslot_need(BShape<2>::UB, BShape<2>::BB, BShape<2>::VB))) +
+    (bmax(bmax(bmax(bmax(bslot_ls<2, 0>(), bslot_ls<4, 0>()), bmax(bslot_ls<6, 0>(), bslot_ls<8, 0>())),
+               bmax(bmax(bslot_ls<10, 0>(), bslot_ls<12, 0>()), bmax(bslot_ls<14, 0>(), bslot_ls<16, 0>()))),
+          bmax(bmax(bslot_ls<6, 1>(), bslot_ls<8, 1>()),
+               bmax(bslot_ls<10, 1>(), bmax(bslot_ls<12, 1>(), bslot_ls<14, 1>())))) +
      1023) & ~1023;
 static_assert(9 * 4 * (kBNT + kBMaxLd / 2) * 8 <= kBNS * kBSlot, "the dot reduction fits in the ring");
-static_assert(kBZeroBytes >= BShape<16>::WX * BShape<16>::REC && kBZeroBytes >= BShape<2>::WX * BShape<2>::REC,
-              "the zero page covers a window row");
 
 // shared memory: ring of slots, window-row and tile-row tables, barriers,
 // flags (block abort, current item)
@@ -158,12 +163,18 @@ __device__ bool bs_dep_wait(const unsigned *p, unsigned need, long limit, const 
 // The z-march over one tile column segment of one system (see the file
 // comment).  J counts the planes the block staged before this item: slot and
 // mbarrier phase of plane j are (J + j) mod NS and (J + j) / NS.
-template <int LS>
-__device__ void bs_stencil(const BStepArgs &A, const SysArgs &S, const BItem &w, const BStage &bs,
-                           unsigned s_ring, unsigned char *gring, SRow *srows, int2 *orows, unsigned bar0,
-                           volatile int *babort, unsigned J) {
-    using G = BShape<LS>;
-    constexpr int TX = G::TX, TY = G::TY, WX = G::WX, WY = G::WY, R = G::R, REC = G::REC;
+template <int LS, int VAR>
+__device__ void bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned char *gring, unsigned J) {
+    const BLayout L = blayout(A.np_cap);
+    SRow *srows = (SRow *)(gring + L.off_srows);
+    int2 *orows = (int2 *)(gring + L.off_orows);
+    const unsigned bar0 = s_ring + (unsigned)L.off_bar;
+    volatile int *babort = (volatile int *)(gring + L.off_flag);
+    const BItem w = A.items[it];
+    const SysArgs &S = A.sys[w.sys];
+    const BStage bs = A.st[w.kind >> 2];
+    using G = BShape<LS, VAR>;
+    constexpr int TX = G::TX, TY = G::TY, WX = G::WX, WY = G::WY, REC = G::REC, LANES = G::LANES;
     static_assert(G::UB + G::BB + G::VB <= kBSlot, "a plane fits in its slot");
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const Tile tl = S.tiles[w.a];
@@ -172,6 +183,7 @@ __device__ void bs_stencil(const BStepArgs &A, const SysArgs &S, const BItem &w,
     const int k0 = 16 * w.b;   // first complex value of the chunk (ld > 16)
     const int tx0 = tl.tx * TX, ty0 = tl.ty * TY;
     const int xb = tx0 - 4, ybase = ty0 - 4, zbase = tl.zlo - 4;
+#pragma unroll 4
     for (int i = tid; i < WY * np; i += kBNT) {
         const int zz = i / WY;
         const int yy = ybase + (i - zz * WY);
@@ -185,6 +197,7 @@ __device__ void bs_stencil(const BStepArgs &A, const SysArgs &S, const BItem &w,
         }
         srows[i] = r;
     }
+#pragma unroll 4
     for (int i = tid; i < TY * np; i += kBNT) {
         const int zz = i / TY;
         const int yy = ty0 + (i - zz * TY);
@@ -283,12 +296,14 @@ __device__ void bs_stencil(const BStepArgs &A, const SysArgs &S, const BItem &w,
             if (zn > 0) bs_copy(zd, A.zeros, (unsigned)(zn * REC), full);
             if (zn2 > 0) bs_copy(zd2, A.zeros, (unsigned)(zn2 * REC), full);
             // potential of the interior points (zero outside the mesh)
-            for (int i = pw; i < TX * TY / 32; i += kBNPW) {
+            for (int i = pw; i < (TX * TY + 31) / 32; i += kBNPW) {
                 const int pt = lane + 32 * i, py = pt / TX, px = pt - py * TX;
-                const int2 e = orows[j * TY + py];
-                const bool ok = (e.y >> px) & 1;
-                cp_async_small<4>(slot + (unsigned)(G::UB + G::BB + pt * 4), S.V + (ok ? e.x + tx0 + px : 0),
-                                  ok ? 4 : 0);
+                if (pt < TX * TY) {
+                    const int2 e = orows[j * TY + py];
+                    const bool ok = (e.y >> px) & 1;
+                    cp_async_small<4>(slot + (unsigned)(G::UB + G::BB + pt * 4), S.V + (ok ? e.x + tx0 + px : 0),
+                                      ok ? 4 : 0);
+                }
             }
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full) : "memory");
             issued = j + 1;
@@ -307,25 +322,32 @@ __device__ void bs_stencil(const BStepArgs &A, const SysArgs &S, const BItem &w,
     }
 
     // ---------------------------------------------------- compute warps
-    const int c = tid % R, g = tid / R;
+    const int c = tid % LANES, g0 = tid / LANES;
+    // threads past the tile's groups compute for the last group, lanes past
+    // the record for its last value; neither stores
+    const bool gok = g0 < G::NG;
+    const int g = gok ? g0 : G::NG - 1;
     const int xl = 2 * (g % G::GX), yl = 2 * (g / G::GX);
     const int cc = c < LS ? c : LS - 1;
     const int k = k0 + c;
-    const bool vok = c < LS && k < ld;
+    const bool vok = gok && c < LS && k < ld;
     const int x0 = tx0 + xl;
-    // planes where any of the warp's columns holds a point
-    int jc0 = 1 << 30, jc1 = -1;
+    // planes where any of the thread's four points is a mesh point (first
+    // and last, scanning from both ends), united over the warp
+    int jc0 = np, jc1 = -1;
     {
-        constexpr int NCOL = 64 / R;   // columns covered by a warp
-        const int gx0 = ((warp * 32 / R) % G::GX);
-        const unsigned cmask = NCOL >= 32 ? 0xffffffffu : ((1u << NCOL) - 1u);
-        for (int jj = lane; jj < np; jj += 32) {
-            const unsigned m = (unsigned)(orows[jj * TY + yl].y | orows[jj * TY + yl + 1].y);
-            if ((m >> (2 * gx0)) & cmask) {
-                jc0 = min(jc0, jj);
-                jc1 = max(jc1, jj);
+        const unsigned need = 3u << xl;
+        for (int jj = 0; jj < np; jj++)
+            if ((unsigned)(orows[jj * TY + yl].y | orows[jj * TY + yl + 1].y) & need) {
+                jc0 = jj;
+                break;
             }
-        }
+        for (int jj = np - 1; jj >= jc0; jj--)
+            if ((unsigned)(orows[jj * TY + yl].y | orows[jj * TY + yl + 1].y) & need) {
+                jc1 = jj;
+                break;
+            }
+        if (jc1 < 0) jc0 = 1 << 30;
     }
     jc0 = __reduce_min_sync(0xffffffffu, jc0);
     jc1 = __reduce_max_sync(0xffffffffu, jc1);
@@ -441,37 +463,51 @@ __device__ void bs_stencil(const BStepArgs &A, const SysArgs &S, const BItem &w,
 // c_i = h^3 sum_q p_i(q) u(q) over the sphere entries of one atom, then
 // D_i = sum_j h_a[i][j] c_j.  Thread (y, v): float4 v of the point row and
 // entry lane y of ny = NT / SV; each lane sums its entries (every ny-th) in
-// FP32, the lanes are summed in FP64 in lane order.  red: NP * 4 * NT
-// doubles of shared memory.
+// FP32, the lanes are summed in FP64 in lane order.  Shared memory (sm):
+// the lane values (NP * 4 * NT doubles), the c values, and the atom's entry
+// points when they fit.
 template <int NP>
-__device__ void bs_dot(const SysArgs &S, int atom, int src, double *red) {
+__device__ void bs_dot(const SysArgs &S, int atom, int src, unsigned char *sm) {
     using V = VT<float>;
+    constexpr int UNR = NP > 4 ? 4 : 8;   // entries per lane and pass, loads in flight together
     const int tid = threadIdx.x, SV = S.SV;
     const int ny = kBNT / SV, y = tid / SV, v = tid - y * SV;
+    double *red = (double *)sm;
+    double *cv = red + NP * 4 * kBNT;
+    int *qs = (int *)(cv + NP * 4 * kBMaxLd / 2);
+    const int q0 = __ldg(S.chunk_q0 + __ldg(S.atom_chunk0 + atom));
+    const int q1 = __ldg(S.chunk_q1 + __ldg(S.atom_chunk0 + atom + 1) - 1);
+    const int nq = q1 - q0;
+    const bool staged = (size_t)((unsigned char *)(qs + nq) - sm) <= (size_t)kBNS * kBSlot;
+    if (staged) {
+#pragma unroll 4
+        for (int i = tid; i < nq; i += kBNT) qs[i] = __ldg(S.q_pt + q0 + i);
+        __syncthreads();
+    }
     const float4 *u = (const float4 *)S.vec[src];
+    const float *qp = S.q_p + (size_t)q0 * NP;
     float4 acc[NP];
 #pragma unroll
     for (int i = 0; i < NP; i++) acc[i] = V::zero();
     if (y < ny) {
-        const int q0 = S.chunk_q0[S.atom_chunk0[atom]], q1 = S.chunk_q1[S.atom_chunk0[atom + 1] - 1];
-        int q = q0 + y;
-        // four entries per pass: their loads are in flight together
-        for (; q + 3 * ny < q1; q += 4 * ny) {
-            int pt[4];
+        int q = y;
+        for (; q + (UNR - 1) * ny < nq; q += UNR * ny) {
+            int pt[UNR];
 #pragma unroll
-            for (int k = 0; k < 4; k++) pt[k] = S.q_pt[q + k * ny];
-            float4 val[4];
+            for (int k = 0; k < UNR; k++) pt[k] = staged ? qs[q + k * ny] : __ldg(S.q_pt + q0 + q + k * ny);
+            float4 val[UNR];
 #pragma unroll
-            for (int k = 0; k < 4; k++) val[k] = __ldcg(u + (size_t)pt[k] * SV + v);
+            for (int k = 0; k < UNR; k++) val[k] = __ldcg(u + (size_t)pt[k] * SV + v);
 #pragma unroll
-            for (int k = 0; k < 4; k++)
+            for (int k = 0; k < UNR; k++)
 #pragma unroll
-                for (int i = 0; i < NP; i++) V::fma(acc[i], S.q_p[(size_t)(q + k * ny) * NP + i], val[k]);
+                for (int i = 0; i < NP; i++) V::fma(acc[i], __ldg(qp + (size_t)(q + k * ny) * NP + i), val[k]);
         }
-        for (; q < q1; q += ny) {
-            const float4 val = __ldcg(u + (size_t)S.q_pt[q] * SV + v);
+        for (; q < nq; q += ny) {
+            const int pt = staged ? qs[q] : __ldg(S.q_pt + q0 + q);
+            const float4 val = __ldcg(u + (size_t)pt * SV + v);
 #pragma unroll
-            for (int i = 0; i < NP; i++) V::fma(acc[i], S.q_p[(size_t)q * NP + i], val);
+            for (int i = 0; i < NP; i++) V::fma(acc[i], __ldg(qp + (size_t)q * NP + i), val);
         }
     }
 #pragma unroll
@@ -483,9 +519,8 @@ __device__ void bs_dot(const SysArgs &S, int atom, int src, double *red) {
     }
     __syncthreads();
     // (i, comp, v): the sum over the entry lanes in lane order, times h^3,
-    // stored after the lane values at cv[(i * 4 + comp) * SV + v]
+    // at cv[(i * 4 + comp) * SV + v]
     const int nval = NP * 4 * SV;
-    double *cv = red + NP * 4 * kBNT;
     for (int idx = tid; idx < nval; idx += kBNT) {
         const int ic = idx / SV, vv = idx - ic * SV;
         const double *r = red + (size_t)ic * kBNT + vv;
@@ -498,57 +533,77 @@ __device__ void bs_dot(const SysArgs &S, int atom, int src, double *red) {
     for (int idx = tid; idx < nval; idx += kBNT) {
         const int ic = idx / SV, vv = idx - ic * SV, i = ic >> 2, cmp = ic & 3;
         double dsum = 0.0;
-        for (int jj = 0; jj < NP; jj++) dsum += S.hm[((size_t)atom * NP + i) * NP + jj] * cv[(jj * 4 + cmp) * SV + vv];
+        for (int jj = 0; jj < NP; jj++)
+            dsum += __ldg(S.hm + ((size_t)atom * NP + i) * NP + jj) * cv[(jj * 4 + cmp) * SV + vv];
         D[(((size_t)atom * NP + i) * SV + vv) * 4 + cmp] = (float)dsum;
     }
 }
 
 // ------------------------------------------------------------ scatter item
 // out += (-i tau/k) sum_a sum_i p_ai D_ai at cnt union points from u0.
-// D of the system is copied to shared memory (dsm, dcap float4) when it
-// fits.  Thread (point lane, v) with NT / SV point lanes; four points per
-// lane and pass, their loads in flight together.
-__device__ void bs_scatter(const SysArgs &S, int u0, int cnt, int dst, float ai, float4 *dsm, int dcap) {
+// The item's point list, its entries (atom and projector values) and the
+// system's D are first copied to shared memory with coalesced loads, when
+// they fit; then thread (point lane, v), with NT / SV point lanes, takes
+// four points per pass with their state loads in flight together.
+constexpr int kBScD = 32768;     // bytes of D staged
+constexpr int kBScEnt = 2048;    // entries staged
+__device__ void bs_scatter(const SysArgs &S, int u0, int cnt, int dst, float ai, unsigned char *sm) {
     using V = VT<float>;
     const int tid = threadIdx.x, SV = S.SV, npmax = S.npmax;
     const int nD = S.natoms * npmax * SV;
-    const float4 *D = (const float4 *)S.D;
-    if (nD <= dcap) {
-        for (int i = tid; i < nD; i += kBNT) dsm[i] = __ldcg(D + i);
-        __syncthreads();
-        D = dsm;
+    const int ea = __ldg(S.u_ptr + u0), ne = __ldg(S.u_ptr + u0 + cnt) - ea;
+    float4 *dsm = (float4 *)sm;
+    int *ipt = (int *)(sm + kBScD);
+    int *iptr = ipt + kBScatterPts;
+    int *iat = iptr + kBScatterPts + 1;
+    float *ipv = (float *)(iat + kBScEnt);
+    const bool dfit = nD * 16 <= kBScD, efit = ne <= kBScEnt;
+    const float4 *Dg = (const float4 *)S.D;
+    if (dfit)
+#pragma unroll 4
+        for (int i = tid; i < nD; i += kBNT) dsm[i] = __ldcg(Dg + i);
+#pragma unroll 2
+    for (int i = tid; i < cnt; i += kBNT) ipt[i] = __ldg(S.u_pts + u0 + i);
+#pragma unroll 2
+    for (int i = tid; i <= cnt; i += kBNT) iptr[i] = __ldg(S.u_ptr + u0 + i) - ea;
+    if (efit) {
+#pragma unroll 4
+        for (int i = tid; i < ne; i += kBNT) iat[i] = __ldg(S.e_atom + ea + i);
+#pragma unroll 4
+        for (int i = tid; i < ne * npmax; i += kBNT) ipv[i] = __ldg(S.e_p + (size_t)ea * npmax + i);
     }
+    __syncthreads();
+    const float4 *D = dfit ? dsm : Dg;
     float4 *out = (float4 *)S.vec[dst];
     const int npt = kBNT / SV, pl = tid / SV, v = tid - pl * SV;
     if (pl >= npt) return;
-    const int end = u0 + cnt;
-    for (int b0 = u0 + pl; b0 < end; b0 += 4 * npt) {
-        int p[4], e0[4], e1[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const int uu = b0 + k * npt;
-            const bool ok = uu < end;
-            p[k] = ok ? S.u_pts[uu] : 0;
-            e0[k] = ok ? S.u_ptr[uu] : 0;
-            e1[k] = ok ? S.u_ptr[uu + 1] : 0;
-        }
+    for (int b0 = pl; b0 < cnt; b0 += 4 * npt) {
+        int pp[4];
         float4 o[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) o[k] = e1[k] > e0[k] ? __ldcg(out + (size_t)p[k] * SV + v) : V::zero();
+        for (int k = 0; k < 4; k++) {
+            const int i = b0 + k * npt;
+            pp[k] = i < cnt ? ipt[i] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) o[k] = pp[k] >= 0 ? __ldcg(out + (size_t)pp[k] * SV + v) : V::zero();
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            if (e1[k] <= e0[k]) continue;
+            if (pp[k] < 0) continue;
+            const int i = b0 + k * npt;
             float4 sum = V::zero();
-            for (int e = e0[k]; e < e1[k]; e++) {
-                const int at = S.e_atom[e];
-                const float *pv = S.e_p + (size_t)e * npmax;
+            for (int e = iptr[i]; e < iptr[i + 1]; e++) {
+                const int at = efit ? iat[e] : __ldg(S.e_atom + ea + e);
+                const float *pv = efit ? ipv + (size_t)e * npmax : S.e_p + (size_t)(ea + e) * npmax;
                 const float4 *Da = D + (size_t)at * npmax * SV + v;
-                for (int i = 0; i < npmax; i++) V::fma(sum, pv[i], Da[(size_t)i * SV]);
+                for (int j = 0; j < npmax; j++) V::fma(sum, pv[j], Da[(size_t)j * SV]);
             }
-            out[(size_t)p[k] * SV + v] = V::add(o[k], V::cmul(0.f, ai, sum));
+            out[(size_t)pp[k] * SV + v] = V::add(o[k], V::cmul(0.f, ai, sum));
         }
     }
 }
+static_assert(kBScD + (2 * kBScatterPts + 1 + kBScEnt) * 4 + kBScEnt * 9 * 4 <= kBNS * kBSlot,
+              "the scatter item's tables fit in the ring");
 
 __global__ void __launch_bounds__(kBNT, 1) k_batch_step(const __grid_constant__ BStepArgs A) {
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -556,8 +611,6 @@ __global__ void __launch_bounds__(kBNT, 1) k_batch_step(const __grid_constant__ 
     const unsigned s_ring = (sraw + 1023u) & ~1023u;
     unsigned char *gring = smraw + (s_ring - sraw);
     const BLayout L = blayout(A.np_cap);
-    SRow *srows = (SRow *)(gring + L.off_srows);
-    int2 *orows = (int2 *)(gring + L.off_orows);
     const unsigned bar0 = s_ring + (unsigned)L.off_bar;
     volatile int *flags = (volatile int *)(gring + L.off_flag);   // [0] block abort, [1] item
     const int tid = threadIdx.x;
@@ -608,34 +661,40 @@ __global__ void __launch_bounds__(kBNT, 1) k_batch_step(const __grid_constant__ 
         __syncthreads();
         const int it = flags[1];
         if (it < 0) break;
-        const BItem w = A.items[it];
-        const int stage = w.kind >> 2, kind = w.kind & 3;
-        const SysArgs &S = A.sys[w.sys];
-        const BStage bs = A.st[stage];
-        if (kind == 1) {
-            const int ls = S.ld > 16 ? 16 : S.ld;
-            switch (ls) {
-            case 2: bs_stencil<2>(A, S, w, bs, s_ring, gring, srows, orows, bar0, flags, J); break;
-            case 4: bs_stencil<4>(A, S, w, bs, s_ring, gring, srows, orows, bar0, flags, J); break;
-            case 6: bs_stencil<6>(A, S, w, bs, s_ring, gring, srows, orows, bar0, flags, J); break;
-            case 8: bs_stencil<8>(A, S, w, bs, s_ring, gring, srows, orows, bar0, flags, J); break;
-            case 10: bs_stencil<10>(A, S, w, bs, s_ring, gring, srows, orows, bar0, flags, J); break;
-            case 12: bs_stencil<12>(A, S, w, bs, s_ring, gring, srows, orows, bar0, flags, J); break;
-            case 14: bs_stencil<14>(A, S, w, bs, s_ring, gring, srows, orows, bar0, flags, J); break;
-            default: bs_stencil<16>(A, S, w, bs, s_ring, gring, srows, orows, bar0, flags, J); break;
+        const int kind0 = A.items[it].kind & 3;
+        if (kind0 == 1) {
+            const SysArgs &S0 = A.sys[A.items[it].sys];
+            const int ls = S0.ld > 16 ? 16 : S0.ld;
+            const int var = S0.var != 0 && bhas_var1(ls) ? 1 : 0;
+#define RSG_BS(L_, V_) bs_stencil<L_, V_>(A, it, s_ring, gring, J)
+            switch (ls * 2 + var) {
+            case 4: RSG_BS(2, 0); break;
+            case 8: RSG_BS(4, 0); break;
+            case 12: RSG_BS(6, 0); break;
+            case 13: RSG_BS(6, 1); break;
+            case 16: RSG_BS(8, 0); break;
+            case 17: RSG_BS(8, 1); break;
+            case 20: RSG_BS(10, 0); break;
+            case 21: RSG_BS(10, 1); break;
+            case 24: RSG_BS(12, 0); break;
+            case 25: RSG_BS(12, 1); break;
+            case 28: RSG_BS(14, 0); break;
+            case 29: RSG_BS(14, 1); break;
+            default: RSG_BS(16, 0); break;
             }
-            const Tile tl = S.tiles[w.a];
-            J += (unsigned)(tl.zhi - tl.zlo + 8);
+#undef RSG_BS
         } else {
-            if (kind == 0) {
-                double *red = (double *)gring;
+            const BItem w = A.items[it];
+            const SysArgs &S = A.sys[w.sys];
+            const BStage bs = A.st[w.kind >> 2];
+            if (kind0 == 0) {
                 switch (S.npmax) {
-                case 1: bs_dot<1>(S, w.a, bs.src, red); break;
-                case 4: bs_dot<4>(S, w.a, bs.src, red); break;
-                default: bs_dot<9>(S, w.a, bs.src, red); break;
+                case 1: bs_dot<1>(S, w.a, bs.src, gring); break;
+                case 4: bs_dot<4>(S, w.a, bs.src, gring); break;
+                default: bs_dot<9>(S, w.a, bs.src, gring); break;
                 }
             } else {
-                bs_scatter(S, w.a, w.b, bs.dst, bs.ai, (float4 *)gring, kBNS * kBSlot / 16);
+                bs_scatter(S, w.a, w.b, bs.dst, bs.ai, gring);
             }
             // the ring is written by bulk copies again in later items
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -643,14 +702,19 @@ __global__ void __launch_bounds__(kBNT, 1) k_batch_step(const __grid_constant__ 
         // this item's stores are read by later items, some through bulk copies
         asm volatile("fence.proxy.async.global;" ::: "memory");
         __syncthreads();
+        const BItem w = A.items[it];
         if (tid == 0) {
             if (flags[0]) {
                 atomicExch(&A.ctl->abort, 1);
                 atomicExch(A.status, 2);
             } else {
                 __threadfence();
-                atomicAdd(A.cnt + ((size_t)w.sys * A.nst + stage) * 3 + kind, 1u);
+                atomicAdd(A.cnt + ((size_t)w.sys * A.nst + (w.kind >> 2)) * 3 + (w.kind & 3), 1u);
             }
+        }
+        if ((w.kind & 3) == 1) {
+            const Tile tl = A.sys[w.sys].tiles[w.a];
+            J += (unsigned)(tl.zhi - tl.zlo + 8);
         }
         if (flags[0]) break;
     }
@@ -660,11 +724,32 @@ __global__ void __launch_bounds__(kBNT, 1) k_batch_step(const __grid_constant__ 
 
 size_t batch_step_smem(int np_cap) { return 1024 + (size_t)blayout(np_cap).bytes; }
 
-void batch_step_tile(int ld, int *TX, int *TY) {
+void batch_step_tile(int ld, int var, int *TX, int *TY) {
     const int ls = ld > 16 ? 16 : ld;
-    const int r = ls <= 2 ? 2 : ls <= 4 ? 4 : ls <= 8 ? 8 : 16;
-    *TX = r == 16 ? BGeom<16>::TX : r == 8 ? BGeom<8>::TX : r == 4 ? BGeom<4>::TX : BGeom<2>::TX;
-    *TY = r == 16 ? BGeom<16>::TY : r == 8 ? BGeom<8>::TY : r == 4 ? BGeom<4>::TY : BGeom<2>::TY;
+#define RSG_BT(L, V)              \
+    *TX = BTile<L, V>::TX;        \
+    *TY = BTile<L, V>::TY;        \
+    return;
+    if (var != 0 && bhas_var1(ls)) {
+        switch (ls) {
+        case 6: RSG_BT(6, 1)
+        case 8: RSG_BT(8, 1)
+        case 10: RSG_BT(10, 1)
+        case 12: RSG_BT(12, 1)
+        default: RSG_BT(14, 1)
+        }
+    }
+    switch (ls) {
+    case 2: RSG_BT(2, 0)
+    case 4: RSG_BT(4, 0)
+    case 6: RSG_BT(6, 0)
+    case 8: RSG_BT(8, 0)
+    case 10: RSG_BT(10, 0)
+    case 12: RSG_BT(12, 0)
+    case 14: RSG_BT(14, 0)
+    default: RSG_BT(16, 0)
+    }
+#undef RSG_BT
 }
 
 int batch_step_threads() { return kBNT; }

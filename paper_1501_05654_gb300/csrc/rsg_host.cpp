@@ -227,6 +227,7 @@ struct rsg_batch_s {
     int zseg = 96;                 // planes per tile segment (mode 1)
     long wait_limit = 1L << 22;    // polls of a dependency wait
     int stall = 0;                 // > 0: system 0 waits for a stencil item that never comes
+    int tile_var_mask = 0;         // bit ls / 2 - 1: tile variant 1 for records of ls values
     std::vector<BItem> stage_items;   // the items of one stage, stage bits 0
     int np_cap = 0, nblocks = 0, step_nst = 0;
     DevBuf d_items, d_cnt, d_ctl, d_status, d_zero;
@@ -2640,7 +2641,9 @@ rsg_status batch_build_step(rsg_batch b) {
         CK(b->w0[(size_t)i].ensure(bytes));
         CK(b->w1[(size_t)i].ensure(bytes));
         int TX = 16, TY = 6;
-        batch_step_tile((int)ld, &TX, &TY);
+        const int ls = ld > 16 ? 16 : (int)ld;
+        const int var = (b->tile_var_mask >> (ls / 2 - 1)) & 1;
+        batch_step_tile((int)ld, var, &TX, &TY);
         const Tile *tiles = nullptr;
         int ntiles = 0;
         CKS(get_tiles(m, TX, TY, b->zseg, &tiles, &ntiles));
@@ -2671,6 +2674,7 @@ rsg_status batch_build_step(rsg_batch b) {
         }
         A.nsten = ntiles * nch;
         A.stall = (i == 0 && b->stall > 0) ? 1 : 0;
+        A.var = var;
         const ProjDev &pj = H->pj;
         A.natoms = pj.natoms;
         A.npmax = pj.npmax;
@@ -2910,6 +2914,8 @@ rsg_status rsg_batch_set_option(rsg_batch b, const char *name, int64_t value) {
         return RSG_OK;
     } else if (k == "debug_stall" && (value == 0 || value == 1)) {
         b->stall = (int)value;
+    } else if (k == "tile_variants" && value >= 0 && value <= 255) {
+        b->tile_var_mask = (int)value;
     } else {
         return fail(RSG_ERR_ARG, "unknown batch option %s = %lld", name, (long long)value);
     }
@@ -2923,11 +2929,96 @@ rsg_status rsg_batch_get_option(rsg_batch b, const char *name, int64_t *value) {
     else if (k == "zseg") *value = b->zseg;
     else if (k == "wait_limit") *value = b->wait_limit;
     else if (k == "debug_stall") *value = b->stall;
+    else if (k == "tile_variants") *value = b->tile_var_mask;
     else if (k == "batched") *value = b->batched ? 1 : 0;
     else if (k == "launches_per_step") *value = b->mode == 1 ? 1 : b->n_launch_step * 8;
     else if (k == "items_per_stage") *value = (int64_t)b->stage_items.size();
     else if (k == "blocks") *value = b->nblocks;
     else return fail(RSG_ERR_ARG, "unknown batch option %s", name);
+    return RSG_OK;
+}
+
+rsg_status rsg_batch_autotune(rsg_batch b, void *const *psis, double dt, rsg_scheme scheme, void *stream,
+                              double *best_ms) {
+    if (!b || !psis) return fail(RSG_ERR_ARG, "NULL argument");
+    if (!std::isfinite(dt) || (scheme != RSG_EXPMID && scheme != RSG_ETRS)) return fail(RSG_ERR_ARG, "bad dt/scheme");
+    const size_t n = b->hams.size();
+    for (size_t i = 0; i < n; i++)
+        if (!psis[i] || ((uintptr_t)psis[i]) % 16) return fail(RSG_ERR_ARG, "psis[%zu] NULL or misaligned", i);
+    cudaStream_t st = (cudaStream_t)stream;
+    // trial steps run on copies of the states
+    std::vector<DevBuf> sc(n);
+    std::vector<void *> ptrs(n);
+    for (size_t i = 0; i < n; i++) {
+        const size_t bytes = (size_t)b->hams[i]->m->P * b->ld[i] * 8;
+        CK(sc[i].ensure(bytes));
+        CK(cudaMemcpyAsync(sc[i].p, psis[i], bytes, cudaMemcpyDeviceToDevice, st));
+        ptrs[i] = sc[i].p;
+    }
+    CK(cudaStreamSynchronize(st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto trial = [&](int mode, int zseg, int mask, double *ms) -> rsg_status {
+        b->mode = mode;
+        b->zseg = zseg;
+        b->tile_var_mask = mask;
+        CKS(batch_build(b));
+        CKS(rsg_batch_propagate(b, ptrs.data(), 1, dt, scheme, 0, stream));
+        CK(cudaEventRecord(e0, st));
+        CKS(rsg_batch_propagate(b, ptrs.data(), 2, dt, scheme, 0, stream));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        *ms = 0.5 * t;
+        return RSG_OK;
+    };
+    int bmode = b->mode, bz = b->zseg, bm = b->tile_var_mask;
+    double best = 1e30, t = 0.0;
+    rsg_status s = RSG_OK;
+    // the per-stage launches, then the persistent step's segment length and,
+    // per record length with two tile variants (largest share of bytes
+    // first), the tile variant
+    for (int mode : {0, 1}) {
+        if (s == RSG_OK) s = trial(mode, bz, bm, &t);
+        if (s == RSG_OK && t < best) {
+            best = t;
+            bmode = mode;
+        }
+    }
+    if (s == RSG_OK && bmode == 1) {
+        for (int z : {48, 64, 96, 128}) {
+            if (z == bz) continue;
+            if (trial(1, z, bm, &t) == RSG_OK && t < best) {
+                best = t;
+                bz = z;
+            }
+        }
+        std::vector<std::pair<double, int>> cls;   // (bytes, ls)
+        for (int ls = 6; ls <= 14; ls += 2) {
+            double bytes = 0.0;
+            for (size_t i = 0; i < n; i++)
+                if (std::min<int64_t>(b->ld[i], 16) == ls) bytes += (double)b->hams[i]->m->P * b->ld[i];
+            if (bytes > 0) cls.push_back({bytes, ls});
+        }
+        std::sort(cls.rbegin(), cls.rend());
+        for (auto &c : cls) {
+            const int m2 = bm ^ (1 << (c.second / 2 - 1));
+            if (trial(1, bz, m2, &t) == RSG_OK && t < best) {
+                best = t;
+                bm = m2;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->mode = bmode;
+    b->zseg = bz;
+    b->tile_var_mask = bm;
+    CKS(batch_build(b));
+    if (s != RSG_OK) return s;
+    if (best_ms) *best_ms = best;
     return RSG_OK;
 }
 

@@ -253,6 +253,7 @@ struct SysArgs {
     // stall > 0 makes the stencil count unreachable (a test of the bounded
     // waits)
     int ld, ndot, nsten, nsca, stall;
+    int var;   // tile variant of the system's record length (0 or 1)
 };
 // Work item: stencil (sys, tile, chunk); projector dot (sys, chunk);
 // projector reduce (sys, atom); scatter (sys, first union point).
@@ -300,8 +301,10 @@ struct BStepArgs {
     long wait_limit;     // polls of a dependency wait (about 0.5 us each)
     int np_cap;          // planes of the longest tile segment plus 8
 };
-// Tile of a system with ld complex values per point (ld > 16: 16-value chunks).
-void batch_step_tile(int ld, int *TX, int *TY);
+// Tile of a system with ld complex values per point (ld > 16: 16-value
+// chunks) in tile variant var (0 or 1; the same tile where a record length
+// has one variant).
+void batch_step_tile(int ld, int var, int *TX, int *TY);
 size_t batch_step_smem(int np_cap);
 int batch_step_threads();
 cudaError_t launch_batch_step(const BStepArgs &a, int nblocks, cudaStream_t st);

@@ -65,6 +65,7 @@ SIGNATURES = {
     "rsg_batch_destroy": [_vp],
     "rsg_batch_set_option": [_vp, C.c_char_p, _i64],
     "rsg_batch_get_option": [_vp, C.c_char_p, _vp],
+    "rsg_batch_autotune": [_vp, _vp, _dbl, _int, _vp, _vp],
     "rsg_ham_set_option": [_vp, C.c_char_p, _i64],
     "rsg_ham_get_option": [_vp, C.c_char_p, _vp],
     "rsg_ham_autotune": [_vp, _vp, _vp, _i64, _i64, _vp, _vp],
@@ -553,3 +554,11 @@ class Batch:
         v = C.c_int64()
         _ck(load().rsg_batch_get_option(self._h, key.encode(), C.byref(v)))
         return int(v.value)
+
+    def autotune(self, psis, dt: float, scheme: int = ETRS, stream=None) -> float:
+        """Choose launch mode, segment length and tile variants by timing
+        steps on copies of psis; returns the best time per step in ms."""
+        ptrs = (C.c_void_p * len(psis))(*[p.data_ptr() for p in psis])
+        ms = C.c_double()
+        _ck(load().rsg_batch_autotune(self._h, ptrs, float(dt), int(scheme), _stream(stream), C.byref(ms)))
+        return float(ms.value)

@@ -180,3 +180,27 @@ def test_persistent_batch_falls_back_above_128_states():
     for (p, psi, S), x in zip(systems, xs):
         want, _ = p.O.propagate(psi, 1, 0.02, scheme=oracle.ETRS)
         assert rel_err(p.states_from_gpu(x, S), want) < 2e-5
+
+
+def test_batch_tile_variants_and_autotune():
+    """Both tile variants of every record length give the same step (the
+    arithmetic per point does not depend on the tile), and the autotuner
+    leaves the states it times untouched and keeps a valid configuration."""
+    specs = [(12, 5, 1), (16, 7, 1), (10, 9, 1), (14, 11, 2), (9, 13, 1), (18, 3, 1)]
+    systems = _systems(seed=9, specs=specs, atoms=False)
+    _, xs = _run_batch(systems, 2, 0.02, rsg.ETRS, tile_variants=0)
+    _, ys = _run_batch(systems, 2, 0.02, rsg.ETRS, tile_variants=255)
+    for (p, psi, S), x, y in zip(systems, xs, ys):
+        assert torch.equal(x, y), (p.P, S)
+    systems = _systems(seed=10, specs=specs)
+    batch = rsg.Batch([p.H for p, _, _ in systems], [S for _, _, S in systems])
+    xs = [p.states_to_gpu(psi) for p, psi, _ in systems]
+    before = [x.clone() for x in xs]
+    ms = batch.autotune(xs, 0.02)
+    assert ms > 0
+    assert all(torch.equal(a, b) for a, b in zip(xs, before))
+    batch.propagate(xs, 2, 0.02, scheme=rsg.ETRS)
+    torch.cuda.synchronize()
+    for (p, psi, S), x in zip(systems, xs):
+        want, _ = p.O.propagate(psi, 2, 0.02, scheme=oracle.ETRS)
+        assert rel_err(p.states_from_gpu(x, S), want) < 2e-5
