@@ -161,10 +161,15 @@ __device__ bool bs_dep_wait(const unsigned *p, unsigned need, long limit, const 
 
 // ------------------------------------------------------------ stencil item
 // The z-march over one tile column segment of one system (see the file
-// comment).  J counts the planes the block staged before this item: slot and
-// mbarrier phase of plane j are (J + j) mod NS and (J + j) / NS.
+// comment).  Only planes [j0, j1] are staged: from the first plane with a
+// point in the tile's own columns to four planes past the last one (jl);
+// planes outside hold no value that reaches an output of the segment.  The
+// last four carry only the base values of the outputs they complete.  J
+// counts the planes the block staged before this item: slot and mbarrier
+// phase of plane j are (J + j - j0) mod NS and (J + j - j0) / NS.  Returns
+// the number of planes staged.
 template <int LS, int VAR>
-__device__ void bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned char *gring, unsigned J) {
+__device__ int bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned char *gring, unsigned J) {
     const BLayout L = blayout(A.np_cap);
     SRow *srows = (SRow *)(gring + L.off_srows);
     int2 *orows = (int2 *)(gring + L.off_orows);
@@ -212,6 +217,22 @@ __device__ void bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned
         orows[i] = e;
     }
     __syncthreads();
+    // planes with a point in the tile's own columns (every warp computes the
+    // same range)
+    int jf = np, jl = -1;
+    for (int jj = lane; jj < np; jj += 32) {
+        int m = 0;
+#pragma unroll
+        for (int rr = 0; rr < TY; rr++) m |= orows[jj * TY + rr].y;
+        if (m) {
+            jf = min(jf, jj);
+            jl = max(jl, jj);
+        }
+    }
+    jf = __reduce_min_sync(0xffffffffu, jf);
+    jl = __reduce_max_sync(0xffffffffu, jl);
+    if (jl < 0) return 0;
+    const int j0 = jf, j1 = min(np - 1, jl + 4);
 
     if (warp >= kBNCW) {
         // ------------------------------------------------ producer warps
@@ -236,9 +257,9 @@ __device__ void bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned
             pb[s] = chi;
         }
         int issued = 0;
-        for (int j = 0; j < np; j++) {
+        for (int j = j0; j <= j1; j++) {
             if (*babort) break;
-            const unsigned jg = J + (unsigned)j;
+            const unsigned jg = J + (unsigned)(j - j0);
             const int s = (int)(jg % kBNS);
             const unsigned full = bar0 + 8 * s, empty = bar0 + 8 * (kBNS + s);
             if (jg >= (unsigned)kBNS && !bs_wait(empty, (jg / kBNS - 1u) & 1u, babort)) break;
@@ -246,7 +267,7 @@ __device__ void bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned
             unsigned vd = 0, zd = 0, zd2 = 0;
             int vp = 0, vn = 0, zn = 0, zn2 = 0;
             int ps = s;
-            if (rowlane) {
+            if (rowlane && j <= jl) {
                 const SRow rw = srows[j * WY + r];
                 int ua = max(clo, rw.xmin - xb), ub = min(chi, rw.xmax - xb + 1);
                 if (ua >= ub) ua = ub = clo;
@@ -296,7 +317,7 @@ __device__ void bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned
             if (zn > 0) bs_copy(zd, A.zeros, (unsigned)(zn * REC), full);
             if (zn2 > 0) bs_copy(zd2, A.zeros, (unsigned)(zn2 * REC), full);
             // potential of the interior points (zero outside the mesh)
-            for (int i = pw; i < (TX * TY + 31) / 32; i += kBNPW) {
+            for (int i = pw; i < (TX * TY + 31) / 32 && j <= jl; i += kBNPW) {
                 const int pt = lane + 32 * i, py = pt / TX, px = pt - py * TX;
                 if (pt < TX * TY) {
                     const int2 e = orows[j * TY + py];
@@ -306,19 +327,19 @@ __device__ void bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned
                 }
             }
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full) : "memory");
-            issued = j + 1;
+            issued = j - j0 + 1;
         }
         cp_async_wait<0>();
         if (*babort) {
             // the copies issued for the last planes land before the block
             // moves on (the compute warps may have stopped waiting for them)
-            for (int j = max(0, issued - kBNS); j < issued; j++) {
-                const unsigned jg = J + (unsigned)j;
+            for (int q = max(0, issued - kBNS); q < issued; q++) {
+                const unsigned jg = J + (unsigned)q;
                 volatile int never = 0;
                 bs_wait(bar0 + 8 * (jg % kBNS), (jg / kBNS) & 1u, &never);
             }
         }
-        return;
+        return j1 - j0 + 1;
     }
 
     // ---------------------------------------------------- compute warps
@@ -367,8 +388,8 @@ __device__ void bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned
         for (int kk = 0; kk < 8; kk++) q[pt][kk] = make_float2(0.f, 0.f);
 
 #pragma unroll 1
-    for (int j = 0; j < np; j++) {
-        const unsigned jg = J + (unsigned)j;
+    for (int j = j0; j <= j1; j++) {
+        const unsigned jg = J + (unsigned)(j - j0);
         const int sl = (int)(jg % kBNS);
         const unsigned full = bar0 + 8 * sl, empty = bar0 + 8 * (kBNS + sl);
         if (!bs_wait(full, (jg / kBNS) & 1u, babort)) break;
@@ -457,6 +478,7 @@ __device__ void bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(empty) : "memory");
     }
+    return j1 - j0 + 1;
 }
 
 // ---------------------------------------------------------------- dot item
@@ -625,30 +647,34 @@ __global__ void __launch_bounds__(kBNT, 1) k_batch_step(const __grid_constant__ 
     }
     __syncthreads();
     unsigned J = 0;   // planes staged by this block so far
+    // thread 0 takes the next queue position while the block works on the
+    // current item (a taken item is always worked on next, unless the batch
+    // aborts)
+    unsigned nxt = 0;
+    if (tid == 0) nxt = atomicAdd(&A.ctl->head, 1u);
     for (;;) {
         if (tid == 0) {
             int it = -1;
-            if (!*(volatile int *)&A.ctl->abort) {
-                const unsigned h = atomicAdd(&A.ctl->head, 1u);
-                if (h < (unsigned)A.nitems) it = (int)h;
-            }
+            if (!*(volatile int *)&A.ctl->abort && nxt < (unsigned)A.nitems) it = (int)nxt;
             if (it >= 0) {
+                nxt = atomicAdd(&A.ctl->head, 1u);
                 const BItem w = A.items[it];
                 const int stage = w.kind >> 2, kind = w.kind & 3;
                 const SysArgs &S = A.sys[w.sys];
                 const unsigned *cn = A.cnt + (size_t)w.sys * A.nst * 3;
+                // (counter, count needed) pairs: stage t - 1 complete for dots and
+                // stencil items, this stage's dots and stencil items for scatters
+                const unsigned *cp = cn + (kind != 2 ? max(stage - 1, 0) : stage) * 3;
+                const int nd = kind != 2 ? (stage > 0 ? 3 : 0) : 2;
+                const unsigned need[3] = {(unsigned)S.ndot, (unsigned)(S.nsten + S.stall), (unsigned)S.nsca};
                 bool ok = true;
-                if (kind != 2) {
-                    if (stage > 0) {
-                        const unsigned *cp = cn + (stage - 1) * 3;
-                        ok = bs_dep_wait(cp + 0, (unsigned)S.ndot, A.wait_limit, &A.ctl->abort) &&
-                             bs_dep_wait(cp + 1, (unsigned)(S.nsten + S.stall), A.wait_limit, &A.ctl->abort) &&
-                             bs_dep_wait(cp + 2, (unsigned)S.nsca, A.wait_limit, &A.ctl->abort);
-                    }
-                } else {
-                    const unsigned *cp = cn + stage * 3;
-                    ok = bs_dep_wait(cp + 0, (unsigned)S.ndot, A.wait_limit, &A.ctl->abort) &&
-                         bs_dep_wait(cp + 1, (unsigned)(S.nsten + S.stall), A.wait_limit, &A.ctl->abort);
+                if (nd > 0) {
+                    // all counters read at once; the bounded waits only when one is short
+                    unsigned have[3];
+#pragma unroll
+                    for (int q = 0; q < 3; q++) have[q] = q < nd ? ld_acquire(cp + q) : 0u;
+                    for (int q = 0; q < nd && ok; q++)
+                        if (have[q] < need[q]) ok = bs_dep_wait(cp + q, need[q], A.wait_limit, &A.ctl->abort);
                 }
                 if (!ok) {
                     atomicExch(&A.ctl->abort, 1);
@@ -662,11 +688,12 @@ __global__ void __launch_bounds__(kBNT, 1) k_batch_step(const __grid_constant__ 
         const int it = flags[1];
         if (it < 0) break;
         const int kind0 = A.items[it].kind & 3;
+        int staged = 0;
         if (kind0 == 1) {
             const SysArgs &S0 = A.sys[A.items[it].sys];
             const int ls = S0.ld > 16 ? 16 : S0.ld;
             const int var = S0.var != 0 && bhas_var1(ls) ? 1 : 0;
-#define RSG_BS(L_, V_) bs_stencil<L_, V_>(A, it, s_ring, gring, J)
+#define RSG_BS(L_, V_) staged = bs_stencil<L_, V_>(A, it, s_ring, gring, J)
             switch (ls * 2 + var) {
             case 4: RSG_BS(2, 0); break;
             case 8: RSG_BS(4, 0); break;
@@ -712,10 +739,7 @@ __global__ void __launch_bounds__(kBNT, 1) k_batch_step(const __grid_constant__ 
                 atomicAdd(A.cnt + ((size_t)w.sys * A.nst + (w.kind >> 2)) * 3 + (w.kind & 3), 1u);
             }
         }
-        if ((w.kind & 3) == 1) {
-            const Tile tl = A.sys[w.sys].tiles[w.a];
-            J += (unsigned)(tl.zhi - tl.zlo + 8);
-        }
+        J += (unsigned)staged;
         if (flags[0]) break;
     }
 }
