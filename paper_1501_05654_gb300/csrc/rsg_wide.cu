@@ -176,6 +176,26 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
         }
         orows[i] = e;
     }
+    __syncthreads();
+    // Only planes [j0, j1] are staged: from the first plane with a point in
+    // the tile's own columns to four planes past the last one (jl).  Planes
+    // outside hold no value that reaches an output of the segment; the last
+    // four carry only the base values of the outputs they complete.  Every
+    // warp computes the same range.
+    int jf = np, jl = -1;
+    for (int jj = lane; jj < np; jj += 32) {
+        int m = 0;
+#pragma unroll
+        for (int rr = 0; rr < TY; rr++) m |= orows[jj * TY + rr].y;
+        if (m) {
+            jf = min(jf, jj);
+            jl = max(jl, jj);
+        }
+    }
+    jf = __reduce_min_sync(0xffffffffu, jf);
+    jl = __reduce_max_sync(0xffffffffu, jl);
+    if (jl < 0) return;
+    const int j0 = jf, j1 = min(np - 1, jl + 4);
     if (tid == 0) {
         for (int k = 0; k < NS; k++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0 + 8 * k), "r"(33 * NPW)
@@ -213,18 +233,18 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
             pb[s] = chi;
         }
         int issued = 0;
-        for (int j0 = 0; j0 < np; j0 += NS) {
+        for (int q0 = 0; q0 <= j1 - j0; q0 += NS) {
 #pragma unroll
             for (int s = 0; s < NS; s++) {
-                const int j = j0 + s;
-                if (j >= np || *abort_flag) break;
+                const int q = q0 + s, j = j0 + q;   // q: staged plane count, slot q mod NS
+                if (j > j1 || *abort_flag) break;
                 const unsigned full = bar0 + 8 * s, empty = bar0 + 8 * (NS + s);
-                if (j >= NS && !wide_wait(empty, (unsigned)((j / NS - 1) & 1), abort_flag)) break;
+                if (q >= NS && !wide_wait(empty, (unsigned)((q / NS - 1) & 1), abort_flag)) break;
                 // this lane's spans: records to copy (dst, first point, count)
                 // and records to zero (two runs)
                 unsigned vd = 0, zd = 0, zd2 = 0;
                 int vp = 0, vn = 0, zn = 0, zn2 = 0;
-                if (rowlane) {
+                if (rowlane && j <= jl) {
                     const SRow rw = srows[j * WY + r];
                     int ua = max(clo, rw.xmin - xb), ub = min(chi, rw.xmax - xb + 1);
                     if (ua >= ub) ua = ub = clo;
@@ -260,7 +280,7 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
                 if (zn > 0) wide_box(zd, maps.u + (zn - 1), c0, kWideZeroPoint, full);
                 if (zn2 > 0) wide_box(zd2, maps.u + (zn2 - 1), c0, kWideZeroPoint, full);
                 // potential of the interior points (zero outside the mesh)
-                for (int i = pw; i < G::NPTS / 32; i += NPW) {
+                for (int i = pw; i < G::NPTS / 32 && j <= jl; i += NPW) {
                     const int pt = lane + 32 * i, py = pt / TX, px = pt - py * TX;
                     const int2 e = orows[j * TY + py];
                     const bool ok = (e.y >> px) & 1;
@@ -268,16 +288,16 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
                                       ok ? 4 : 0);
                 }
                 asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full) : "memory");
-                issued = j + 1;
+                issued = q + 1;
             }
         }
         cp_async_wait<0>();
         // the copies issued for the last planes have landed before the block
         // can leave (the compute warps wait for them too, unless aborted)
-        for (int j = max(0, issued - NS); j < issued; j++) {
-            const unsigned full = bar0 + 8 * (j % NS);
+        for (int q = max(0, issued - NS); q < issued; q++) {
+            const unsigned full = bar0 + 8 * (q % NS);
             volatile int never = 0;
-            wide_wait(full, (unsigned)((j / NS) & 1), &never);
+            wide_wait(full, (unsigned)((q / NS) & 1), &never);
         }
         if (pw == 0 && lane == 0 && *abort_flag && a.err != nullptr) atomicExch(a.err, 2);
         return;
@@ -326,7 +346,7 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
     int sl = 0;
     unsigned par = 0;
 #pragma unroll 1
-    for (int j = 0; j < np; j++) {
+    for (int j = j0; j <= j1; j++) {
         const unsigned full = bar0 + 8 * sl, empty = bar0 + 8 * (NS + sl);
         if (!wide_wait(full, par, abort_flag)) break;
         if (j >= jc0 && j <= jc1 + 4) {
