@@ -567,8 +567,8 @@ __device__ void bs_dot(const SysArgs &S, int atom, int src, unsigned char *sm) {
 // system's D are first copied to shared memory with coalesced loads, when
 // they fit; then thread (point lane, v), with NT / SV point lanes, takes
 // four points per pass with their state loads in flight together.
-constexpr int kBScD = 32768;     // bytes of D staged
-constexpr int kBScEnt = 2048;    // entries staged
+constexpr int kBScD = 16384;     // bytes of D staged
+constexpr int kBScEnt = 3072;    // entries staged
 __device__ void bs_scatter(const SysArgs &S, int u0, int cnt, int dst, float ai, unsigned char *sm) {
     using V = VT<float>;
     const int tid = threadIdx.x, SV = S.SV, npmax = S.npmax;

@@ -287,7 +287,7 @@ struct BCtl {
 };
 constexpr int kBWinRowsMax = 32, kBTileRowsMax = 24;   // window and tile rows of any batch tile
 constexpr int kBZeroBytes = 4096;                      // zero page read by the window fills
-constexpr int kBScatterPts = 1024;                     // union points per scatter item
+constexpr int kBScatterPts = 2048;                     // union points per scatter item
 constexpr int kBMaxLd = 128;                           // complex values per point in the persistent step
 struct BStepArgs {
     const SysArgs *sys;
