@@ -418,7 +418,7 @@ def time_steps(H, psi, steps, fn):
     return e0.elapsed_time(e1) / steps
 
 
-def batch_extra(chk, peak, steps=10, nsys=256):
+def batch_extra(chk, peak, steps=10, nsys=256, tune=True):
     """The batch of 256 uneven systems: ms per ETRS step through the batched
     launch, and (with chk) the host copies the oracle leg checks.  nsys < 256
     keeps the first nsys systems (profiler captures)."""
@@ -446,7 +446,7 @@ def batch_extra(chk, peak, steps=10, nsys=256):
                                 device="cuda") * 1e-3)
         pst += m.P * int(S_)
     batch = rsg.Batch(hams, [int(x) for x in Ss[:nsys]])
-    tune_ms = batch.autotune(psis, 0.02, scheme=rsg.ETRS)
+    tune_ms = batch.autotune(psis, 0.02, scheme=rsg.ETRS) if tune else None
     tuned = {k: batch.get_option(k) for k in ("persistent", "zseg", "tile_variants", "launches_per_step",
                                               "items_per_stage", "blocks")}
     ms = time_steps(None, psis, steps, lambda xs: batch.propagate(xs, 1, 0.02, scheme=rsg.ETRS))
@@ -478,6 +478,54 @@ def batch_extra(chk, peak, steps=10, nsys=256):
                                             "(persistent: one launch per step)"}
     del batch, hams, psis
     torch.cuda.empty_cache()
+    return out
+
+
+def control_extra(chk, nint=2000, dtypes=None):
+    """The optimal-control workload: time of one control gradient (discrete
+    adjoint with checkpoints) against one forward propagation, 64^3 double
+    well, nint intervals of 0.05 au, 4 ETRS substeps, checkpoints every 50."""
+    import torch
+    import paper_1501_05654_gb300 as rsg
+    from workloads import control_field, potential_double_well, rng, white_noise_states
+    if dtypes is None:
+        dtypes = (torch.complex128, torch.complex64)
+    out = {}
+    cm = rsg.Mesh(rsg.CUBE, 64, spacing=0.3)
+    gg = rng(4)
+    eps = control_field(gg, nint, 0.05)
+    for dtype in dtypes:
+        H = rsg.Hamiltonian(cm, dtype)
+        H.set_potential(potential_double_well(cm.xyz, 0.02, 2.0, 0.5))
+        x = torch.from_numpy(white_noise_states(gg, cm.P, 1)[:, 0]).to(dtype).cuda()
+        x /= torch.linalg.vector_norm(x) * cm.h ** 1.5
+        tgt = torch.roll(x, 1).contiguous()
+        ld = rsg.padded_ld(1, dtype)
+        blk = torch.zeros((cm.P, ld), dtype=dtype, device="cuda")
+        blk[:, 0] = x
+        torch.cuda.synchronize()
+        H.kernel_stats()                  # reset the library's counters
+        t0 = time.perf_counter()
+        H.propagate(blk, nint, 0.05, scheme=rsg.ETRS, nsub=4, eps=eps, want_drift=False, S=1)
+        torch.cuda.synchronize()
+        tf = time.perf_counter() - t0
+        nf = H.kernel_stats()[1]          # Hamiltonian applications of the forward propagation
+        t0 = time.perf_counter()
+        J, grad = H.control_gradient(x, tgt, eps, 0.05, scheme=rsg.ETRS, nsub=4, checkpoint_every=50)
+        tg = time.perf_counter() - t0
+        ng = H.kernel_stats()[1]          # ... of the gradient (forward, recompute, costate)
+        if chk is not None:
+            # the first 5 intervals of the same problem, for the oracle
+            J5, g5 = H.control_gradient(x, tgt, eps[:5], 0.05, scheme=rsg.ETRS, nsub=4, checkpoint_every=50)
+            chk[f"control_gradient_{'c128' if dtype == torch.complex128 else 'c64'}"] = {
+                "kind": "gradient", "lib_ijk": cm.ijk, "psi0": x.cpu().numpy().astype(np.complex128),
+                "target": tgt.cpu().numpy().astype(np.complex128), "eps": np.array(eps[:5]), "J": J5,
+                "grad": np.array(g5)}
+        out[f"control_gradient_{'c128' if dtype == torch.complex128 else 'c64'}"] = {
+            "forward_s": tf, "gradient_s": tg, "ratio": tg / tf,
+            "h_applications_forward": nf, "h_applications_gradient": ng, "h_application_ratio": ng / nf,
+            "workload": f"64^3 h=0.3 double well, {nint} intervals dt=0.05, ETRS nsub=4, K=50"}
+        del H, blk
     return out
 
 
@@ -608,42 +656,8 @@ def extras(mesh, wells, proj, g, chk):
                                          "ETRS dt=0.01, Cholesky-QR every 50 steps, 1000 steps"}
     del H5, x5, xyz
     torch.cuda.empty_cache()
-    # control gradient vs forward (the optimal-control workload)
+    out.update(control_extra(chk))
     cm = rsg.Mesh(rsg.CUBE, 64, spacing=0.3)
-    gg = rng(4)
-    eps = control_field(gg, 2000, 0.05)
-    for dtype in (torch.complex128, torch.complex64):
-        H = rsg.Hamiltonian(cm, dtype)
-        H.set_potential(potential_double_well(cm.xyz, 0.02, 2.0, 0.5))
-        x = torch.from_numpy(white_noise_states(gg, cm.P, 1)[:, 0]).to(dtype).cuda()
-        x /= torch.linalg.vector_norm(x) * cm.h ** 1.5
-        tgt = torch.roll(x, 1).contiguous()
-        ld = rsg.padded_ld(1, dtype)
-        blk = torch.zeros((cm.P, ld), dtype=dtype, device="cuda")
-        blk[:, 0] = x
-        torch.cuda.synchronize()
-        H.kernel_stats()                  # reset the library's counters
-        t0 = time.perf_counter()
-        H.propagate(blk, 2000, 0.05, scheme=rsg.ETRS, nsub=4, eps=eps, want_drift=False, S=1)
-        torch.cuda.synchronize()
-        tf = time.perf_counter() - t0
-        nf = H.kernel_stats()[1]          # Hamiltonian applications of the forward propagation
-        t0 = time.perf_counter()
-        J, grad = H.control_gradient(x, tgt, eps, 0.05, scheme=rsg.ETRS, nsub=4, checkpoint_every=50)
-        tg = time.perf_counter() - t0
-        ng = H.kernel_stats()[1]          # ... of the gradient (forward, recompute, costate)
-        if chk is not None:
-            # the first 5 intervals of the same problem, for the oracle
-            J5, g5 = H.control_gradient(x, tgt, eps[:5], 0.05, scheme=rsg.ETRS, nsub=4, checkpoint_every=50)
-            chk[f"control_gradient_{'c128' if dtype == torch.complex128 else 'c64'}"] = {
-                "kind": "gradient", "lib_ijk": cm.ijk, "psi0": x.cpu().numpy().astype(np.complex128),
-                "target": tgt.cpu().numpy().astype(np.complex128), "eps": np.array(eps[:5]), "J": J5,
-                "grad": np.array(g5)}
-        out[f"control_gradient_{'c128' if dtype == torch.complex128 else 'c64'}"] = {
-            "forward_s": tf, "gradient_s": tg, "ratio": tg / tf,
-            "h_applications_forward": nf, "h_applications_gradient": ng, "h_application_ratio": ng / nf,
-            "workload": "64^3 h=0.3 double well, 2000 intervals dt=0.05, ETRS nsub=4, K=50"}
-        del H, blk
     # optimal control loop on the control workload's operator (64^3 double
     # well, 200 intervals of 0.05 au, 4 ETRS substeps): from the ground to the
     # first excited state of H_0 (both from the eigensolver), 8 L-BFGS steps
@@ -784,8 +798,12 @@ def main():
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the complex128 / plain-kernel / control-gradient side measurements")
-    ap.add_argument("--only", default=None, choices=["batch"],
+    ap.add_argument("--only", default=None, choices=["batch", "adjoint"],
                     help="run one side measurement alone and print it (for profiler captures)")
+    ap.add_argument("--batch-no-tune", action="store_true",
+                    help="with --only batch: default batch options, no autotuning (profiler captures)")
+    ap.add_argument("--adjoint-intervals", type=int, default=2000,
+                    help="with --only adjoint: control intervals (2000 is the workload)")
     ap.add_argument("--batch-systems", type=int, default=256,
                     help="with --only batch: the first N systems of the batch (profiler captures)")
     ap.add_argument("--radius", type=float, default=18.0,
@@ -810,7 +828,13 @@ def main():
     rsg.build()
     if args.only == "batch":
         if rank == 0:
-            print(json.dumps(batch_extra(None, peaks()[0], steps=args.steps, nsys=args.batch_systems)), flush=True)
+            print(json.dumps(batch_extra(None, peaks()[0], steps=args.steps, nsys=args.batch_systems,
+                                         tune=not args.batch_no_tune)), flush=True)
+        return
+    if args.only == "adjoint":
+        if rank == 0:
+            dt_ = torch.complex64 if args.dtype == "c64" else torch.complex128
+            print(json.dumps(control_extra(None, nint=args.adjoint_intervals, dtypes=(dt_,))), flush=True)
         return
 
     g, wells, proj = build_inputs()
