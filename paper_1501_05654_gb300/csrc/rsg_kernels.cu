@@ -728,19 +728,20 @@ __global__ void __launch_bounds__(256) k_proj_dot(const typename VT<R>::T *__res
 #pragma unroll
     for (int i = 0; i < NP; i++) acc[i] = V::zero();
     if (v < SV) {
-        // four entries per iteration: their point indices, then their values,
+        // UNR entries per iteration: their point indices, then their values,
         // are independent loads in flight together
+        constexpr int UNR = 4;
         const int by = blockDim.y;
         int q = q0 + threadIdx.y;
-        for (; q + 3 * by < q1; q += 4 * by) {
-            int pt[4];
+        for (; q + (UNR - 1) * by < q1; q += UNR * by) {
+            int pt[UNR];
 #pragma unroll
-            for (int k = 0; k < 4; k++) pt[k] = q_pt[q + k * by];
-            T val[4];
+            for (int k = 0; k < UNR; k++) pt[k] = q_pt[q + k * by];
+            T val[UNR];
 #pragma unroll
-            for (int k = 0; k < 4; k++) val[k] = V::ldg(u + (int64_t)pt[k] * SV + v);
+            for (int k = 0; k < UNR; k++) val[k] = V::ldg(u + (int64_t)pt[k] * SV + v);
 #pragma unroll
-            for (int k = 0; k < 4; k++)
+            for (int k = 0; k < UNR; k++)
 #pragma unroll
                 for (int i = 0; i < NP; i++) V::fma(acc[i], q_p[(int64_t)(q + k * by) * NP + i], val[k]);
         }
@@ -885,6 +886,10 @@ __global__ void k_proj_reduce(const double *__restrict__ partial, int SV, int na
 //     acc[p, v] += gamma * alpha * (same)            (when acc is used)
 // one thread per (union point, vector); the union points and their entry
 // lists come from the point-centric CSR, so there are no atomics.
+// Each block row (threadIdx.y) takes kScatPts union points, blockDim.y rows
+// apart; their index, state and first-entry loads are issued before any of
+// them is used, so that several points' loads are in flight per warp.
+constexpr int kScatPts = 4;
 template <typename R>
 __global__ void __launch_bounds__(256) k_proj_scatter(const ApplyArgs<R> a, const int32_t *__restrict__ upts,
                                                       const int32_t *__restrict__ uptr,
@@ -892,27 +897,42 @@ __global__ void __launch_bounds__(256) k_proj_scatter(const ApplyArgs<R> a, cons
                                                       const R *__restrict__ e_p, int nu) {
     using V = VT<R>;
     using T = typename V::T;
-    const int u = blockIdx.x * blockDim.y + threadIdx.y;
-    if (u >= nu) return;
-    const int p = upts[u];
-    const int e0 = uptr[u], e1 = uptr[u + 1];
+    const int ub = blockIdx.x * blockDim.y * kScatPts + threadIdx.y;
     const T *D = (const T *)a.D;
+    T *out = (T *)a.out;
+    int p[kScatPts], e0[kScatPts], e1[kScatPts], at0[kScatPts];
+#pragma unroll
+    for (int k = 0; k < kScatPts; k++) {
+        const int u = ub + k * (int)blockDim.y;
+        const bool ok = u < nu;
+        p[k] = ok ? upts[u] : -1;
+        e0[k] = ok ? uptr[u] : 0;
+        e1[k] = ok ? uptr[u + 1] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kScatPts; k++) at0[k] = e1[k] > e0[k] ? e_atom[e0[k]] : 0;
     for (int v = threadIdx.x; v < a.SV; v += blockDim.x) {
-        T sum = V::zero();
-        for (int e = e0; e < e1; e++) {
-            const int at = e_atom[e];
-            const R *pv = e_p + e * a.npmax;
-            const T *Da = D + at * a.npmax * a.SV + v;
-            for (int i = 0; i < a.npmax; i++) V::fma(sum, pv[i], Da[i * a.SV]);
-        }
-        const int o = p * a.SV + v;
-        const T y = V::cmul(a.ar, a.ai, sum);
-        T *out = (T *)a.out;
-        out[o] = V::add(out[o], y);
-        if (a.acc != nullptr) {
-            T s = ((T *)a.acc)[o];
-            V::cfma(s, a.gr, a.gi, y);
-            ((T *)a.acc)[o] = s;
+        T o[kScatPts];
+#pragma unroll
+        for (int k = 0; k < kScatPts; k++) o[k] = p[k] >= 0 ? out[(int64_t)p[k] * a.SV + v] : V::zero();
+#pragma unroll
+        for (int k = 0; k < kScatPts; k++) {
+            if (p[k] < 0) continue;
+            T sum = V::zero();
+            for (int e = e0[k]; e < e1[k]; e++) {
+                const int at = e == e0[k] ? at0[k] : e_atom[e];
+                const R *pv = e_p + (int64_t)e * a.npmax;
+                const T *Da = D + (int64_t)at * a.npmax * a.SV + v;
+                for (int i = 0; i < a.npmax; i++) V::fma(sum, pv[i], Da[(int64_t)i * a.SV]);
+            }
+            const int64_t oi = (int64_t)p[k] * a.SV + v;
+            const T y = V::cmul(a.ar, a.ai, sum);
+            out[oi] = V::add(o[k], y);
+            if (a.acc != nullptr) {
+                T sacc = ((T *)a.acc)[oi];
+                V::cfma(sacc, a.gr, a.gi, y);
+                ((T *)a.acc)[oi] = sacc;
+            }
         }
     }
 }
@@ -923,8 +943,9 @@ cudaError_t launch_proj_scatter(const ApplyArgs<R> &a, const ProjDev &pj, cudaSt
     if (nu == 0) return cudaSuccess;
     const int bx = a.SV < 32 ? a.SV : 32;
     const int by = 256 / bx;
-    k_proj_scatter<R><<<(nu + by - 1) / by, dim3(bx, by), 0, st>>>(a, pj.u_pts, pj.u_ptr, pj.e_atom,
-                                                                   (const R *)pj.e_p, nu);
+    const int per = by * kScatPts;
+    k_proj_scatter<R><<<(nu + per - 1) / per, dim3(bx, by), 0, st>>>(a, pj.u_pts, pj.u_ptr, pj.e_atom,
+                                                                    (const R *)pj.e_p, nu);
     return cudaGetLastError();
 }
 
