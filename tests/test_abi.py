@@ -266,3 +266,27 @@ def test_image_walls_refused_on_short_axes():
     m = rsg.Mesh(rsg.BOX, (4, 4, 4), spacing=0.3)
     assert lib.rsg_mesh_set_boundary(m._h, rsg.BC_ODD) == 0
     assert oracle.Mesh(oracle.BOX, (4, 4, 4), h=0.3, bc=oracle.ODD).P == 64
+
+
+def test_batch_entry_points_argument_errors(lib):
+    """Host-side checks of the batch calls, before any device work (no GPU
+    needed): NULL handles and arguments, and batches of unsupported systems."""
+    v = C.c_int64()
+    ms = C.c_double()
+    assert lib.rsg_batch_set_option(None, b"zseg", 64) == -1
+    assert lib.rsg_batch_get_option(None, b"zseg", C.byref(v)) == -1
+    assert lib.rsg_batch_autotune(None, None, 0.02, 1, None, C.byref(ms)) == -1
+    assert lib.rsg_batch_propagate(None, None, 1, 0.02, 1, 0, None) == -1
+    assert lib.rsg_batch_create(None, None, 0, None) == -1
+    m = rsg.Mesh(rsg.CUBE, 6, spacing=0.3)
+    H = rsg.Hamiltonian(m, torch.complex128)
+    arr = (C.c_void_p * 1)(H._h.value)
+    S = np.ones(1, dtype=np.int64)
+    b = C.c_void_p()
+    # complex128 systems are refused before any allocation
+    assert lib.rsg_batch_create(arr, S.ctypes.data_as(C.c_void_p), 1, C.byref(b)) == -4
+    assert b"complex64" in lib.rsg_last_error()
+    H2 = rsg.Hamiltonian(m)
+    arr2 = (C.c_void_p * 1)(H2._h.value)
+    S0 = np.zeros(1, dtype=np.int64)
+    assert lib.rsg_batch_create(arr2, S0.ctypes.data_as(C.c_void_p), 1, C.byref(b)) == -1
