@@ -593,8 +593,10 @@ def extras(mesh, wells, proj, g, chk):
         psi = None
     out["complex_scaling_c64"] = {"ms_per_step": ms, "value": P * S * N_APPLY_PER_STEP / (ms * 1e-3) / 1e9,
                                   "unit": UNIT,
-                                  "kernel": "k_apply_quad (complex diagonal)" if zk == 5 else "k_apply_scaled",
+                                  "kernel": {5: "k_apply_quad (complex diagonal)",
+                                             7: "k_apply_wide (complex diagonal)"}.get(zk, "k_apply_scaled"),
                                   "kernel_GBps": kbytes / (kms * 1e-3) / 1e9 if kms > 0 else None,
+                                  "kernel_frac_of_measured_hbm": kbytes / (kms * 1e-3) / 1e9 / peak if kms > 0 else None,
                                   "workload": "sphere R=18 h=0.2, 32 wells at r e^{0.3i}, 64 states, ETRS dt=0.01"}
     del psi, Hz
     torch.cuda.empty_cache()

@@ -520,12 +520,13 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     a.tiles = nullptr;
     TileCfg cfg = H->cfg;
     // kernel 7 moves 16-value chunks of each point row: blocks whose rows are
-    // narrow or end in a mostly empty chunk, and complex scaling (which it
-    // does not implement), take the register-blocked kernel in its default
-    // shape unless kernel 7 was chosen explicitly
+    // narrow or end in a mostly empty chunk take the register-blocked kernel
+    // in its default shape unless kernel 7 was chosen explicitly; complex
+    // scaling runs on kernel 7 in its default shape only
     if (cfg.kernel == 7) {
         const int ldc = SV * (int)(16 / cbytes(H->dtype));
-        if (H->has_scaling || (!H->force_kernel && ldc % 16 != 0 && ldc < 40)) {
+        if ((H->has_scaling && (cfg.wty != 6 || cfg.npw != 4)) ||
+            (!H->force_kernel && ldc % 16 != 0 && ldc < 40)) {
             cfg.kernel = 5;
             cfg.threads = 192;
             cfg.zseg = 150;
@@ -586,15 +587,20 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         if constexpr (std::is_same<R, float>::value) {
             // register-blocked kernel: alpha (lap + v_theta e^{2i theta} u) with
             // alpha rotated by e^{-2i theta}, without a diagonal constant
-            if (cfg.kernel == 5 && a.f0 == 0.f && a.fx == 0.f && a.fy == 0.f && a.fz == 0.f) {
+            if ((cfg.kernel == 5 || cfg.kernel == 7) && a.f0 == 0.f && a.fx == 0.f && a.fy == 0.f && a.fz == 0.f) {
                 ApplyArgs<R> b = a;
                 b.Vc = H->vtheta_rot.p;
                 b.nl_ptr = nullptr;
                 const double kr = std::cos(2.0 * H->theta), ki = -std::sin(2.0 * H->theta);
                 b.ar = (R)(ep.ar * kr - ep.ai * ki);
                 b.ai = (R)(ep.ar * ki + ep.ai * kr);
-                CK(launch_apply_quad(b, cfg, ntiles, st, &done));
-                if (done) H->last_kernel = 5;
+                if (cfg.kernel == 7) {
+                    CK(launch_apply_wide(b, cfg, ntiles, st, &done));
+                    if (done) H->last_kernel = 7;
+                } else {
+                    CK(launch_apply_quad(b, cfg, ntiles, st, &done));
+                    if (done) H->last_kernel = 5;
+                }
             }
         }
         if (!done) {

@@ -116,8 +116,12 @@ __device__ __forceinline__ void wide_finish(const ApplyArgs<float> &a, int o, fl
 }
 
 // EPI 1: Horner stage, out = (i ai) H u + base (ar = 0, beta = 1, no
-// accumulator); EPI 0: the general epilogue of wide_finish.
-template <int NYP, int NS, int NPW, int EPI>
+// accumulator); EPI 2: the same with a complex alpha (complex scaling's
+// rotated Horner stage); EPI 0: the general epilogue of wide_finish.  CS 1: complex
+// scaling, the diagonal is the complex a.Vc per point (v_theta e^{2i theta},
+// interleaved) plus the stencil's real centre weight; the caller folds the
+// kinetic rotation e^{-2i theta} into alpha and sets no field.
+template <int NYP, int NS, int NPW, int EPI, int CS = 0>
 __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
     k_apply_wide(const ApplyArgs<float> a, int nchunks, const __grid_constant__ WideMaps maps) {
     using G = WideGeom<NYP, NPW>;
@@ -130,13 +134,14 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
     unsigned char *gbase = smraw + (s_u - sraw);
     const unsigned s_b = s_u + NS * G::SLOT * G::REC;
     const unsigned s_v = s_b + NS * G::NPTS * G::REC;
+    constexpr int VBY = CS ? 8 : 4;   // bytes of the staged diagonal per point
     const Tile tl = a.tiles[blockIdx.x / nchunks];
     const int chunk = blockIdx.x % nchunks;
     const int np = tl.zhi - tl.zlo + 8;
     // window rows (producers) and tile rows (all warps) of every plane
-    SRow *srows = (SRow *)(gbase + (s_v - s_u) + NS * G::NPTS * 4);
+    SRow *srows = (SRow *)(gbase + (s_v - s_u) + NS * G::NPTS * VBY);
     int2 *orows = (int2 *)(srows + WY * np);
-    const unsigned s_rows = s_v + NS * G::NPTS * 4;
+    const unsigned s_rows = s_v + NS * G::NPTS * VBY;
     const unsigned bar0 = (s_rows + (unsigned)(WY * np * sizeof(SRow) + TY * np * sizeof(int2)) + 7u) & ~7u;
     volatile int *abort_flag = (volatile int *)(gbase + (bar0 - s_u) + 16 * NS);
 
@@ -284,8 +289,12 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
                     const int pt = lane + 32 * i, py = pt / TX, px = pt - py * TX;
                     const int2 e = orows[j * TY + py];
                     const bool ok = (e.y >> px) & 1;
-                    cp_async_small<4>(s_v + (unsigned)((s * G::NPTS + pt) * 4), a.V + (ok ? e.x + tx0 + px : 0),
-                                      ok ? 4 : 0);
+                    if constexpr (CS)
+                        cp_async_small<8>(s_v + (unsigned)((s * G::NPTS + pt) * 8),
+                                          (const float2 *)a.Vc + (ok ? e.x + tx0 + px : 0), ok ? 8 : 0);
+                    else
+                        cp_async_small<4>(s_v + (unsigned)((s * G::NPTS + pt) * 4), a.V + (ok ? e.x + tx0 + px : 0),
+                                          ok ? 4 : 0);
                 }
                 asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(full) : "memory");
                 issued = q + 1;
@@ -328,11 +337,12 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
     for (int pt = 0; pt < 4; pt++) fxy[pt] = a.f0 + a.fx * (float)(x0 + (pt & 1)) + a.fy * (float)(y0 + (pt >> 1));
     const float2 w1 = make_float2(a.w[1], a.w[1]), w2 = make_float2(a.w[2], a.w[2]);
     const float2 w3 = make_float2(a.w[3], a.w[3]), w4 = make_float2(a.w[4], a.w[4]);
-    const float w0c = 3.0f * a.w[0], ai = a.ai;
+    const float w0c = 3.0f * a.w[0], ai = a.ai, ar = a.ar;
     constexpr int RW = WX * NC;   // float2 entries per slot row
     const float2 *uwin = (const float2 *)gbase + ((4 + yl) * WX + xl) * NC + cc;
     const float2 *bwin = (const float2 *)(gbase + (s_b - s_u)) + (yl * TX + xl) * NC + cc;
-    const float *vwin = (const float *)(gbase + (s_v - s_u)) + yl * TX + xl;
+    // staged diagonal of the thread's first point (float, or float2 with CS)
+    const float *vwin = (const float *)(gbase + (s_v - s_u)) + (yl * TX + xl) * (VBY / 4);
     float2 *const out2 = (float2 *)a.out;
 
     // q[pt][e]: partial sums of the outputs at planes j - 4 + e (e = 0..7)
@@ -385,13 +395,25 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
                 }
 #undef QW
                 const float fz = a.fz * (float)(zbase + j) + w0c;
-                const float *vv = vwin + sl * G::NPTS;
+                if constexpr (CS) {
+                    // complex diagonal: staged v_theta e^{2i theta} plus the centre weight
+                    const float2 *vc = (const float2 *)vwin + sl * G::NPTS;
 #pragma unroll
-                for (int pt = 0; pt < 4; pt++) {
-                    // diagonal: staged V (zero outside the mesh) plus the field
-                    const float d = vv[(pt >> 1) * TX + (pt & 1)] + fxy[pt] + fz;
-                    s[pt].x = fmaf(d, cen[pt].x, s[pt].x);
-                    s[pt].y = fmaf(d, cen[pt].y, s[pt].y);
+                    for (int pt = 0; pt < 4; pt++) {
+                        const float2 dv = vc[(pt >> 1) * TX + (pt & 1)];
+                        const float dr = dv.x + fxy[pt] + fz;
+                        s[pt].x = fmaf(-dv.y, cen[pt].y, fmaf(dr, cen[pt].x, s[pt].x));
+                        s[pt].y = fmaf(dv.y, cen[pt].x, fmaf(dr, cen[pt].y, s[pt].y));
+                    }
+                } else {
+                    const float *vv = vwin + sl * G::NPTS;
+#pragma unroll
+                    for (int pt = 0; pt < 4; pt++) {
+                        // diagonal: staged V (zero outside the mesh) plus the field
+                        const float d = vv[(pt >> 1) * TX + (pt & 1)] + fxy[pt] + fz;
+                        s[pt].x = fmaf(d, cen[pt].x, s[pt].x);
+                        s[pt].y = fmaf(d, cen[pt].y, s[pt].y);
+                    }
                 }
             } else {
 #pragma unroll
@@ -428,6 +450,10 @@ __global__ void __launch_bounds__(WideGeom<NYP, NPW>::NT, 1)
                         const float2 bv = bb[(dy * TX + dx) * NC];
                         if constexpr (EPI == 1) {
                             const float2 y = make_float2(fmaf(-ai, acc.y, bv.x), fmaf(ai, acc.x, bv.y));
+                            if ((m >> dx) & 1) out2[orow + dx * ld] = y;
+                        } else if constexpr (EPI == 2) {
+                            const float2 y = make_float2(fmaf(-ai, acc.y, fmaf(ar, acc.x, bv.x)),
+                                                         fmaf(ai, acc.x, fmaf(ar, acc.y, bv.y)));
                             if ((m >> dx) & 1) out2[orow + dx * ld] = y;
                         } else {
                             if ((m >> dx) & 1) wide_finish(a, orow + dx * ld, acc, bv);
@@ -511,19 +537,19 @@ void wide_shape(const TileCfg &cfg, int *TX, int *TY) {
     *TY = cfg.wty == 6 || cfg.wty == 4 ? cfg.wty : 8;
 }
 
-size_t wide_smem_bytes(int nyp, int ns, int zseg) {
+size_t wide_smem_bytes(int nyp, int ns, int zseg, int cs) {
     const size_t tx = 16, ty = 2 * (size_t)nyp, wx = tx + 8, wy = ty + 8;
-    return 1024 + (size_t)ns * (wy * wx * 128 + tx * ty * 128 + tx * ty * 4) +
+    return 1024 + (size_t)ns * (wy * wx * 128 + tx * ty * 128 + tx * ty * (cs ? 8 : 4)) +
            (wy * sizeof(SRow) + ty * 8) * ((size_t)zseg + 8) + 8 + 16 * (size_t)ns + 16;
 }
 
-template <int NYP, int NS, int NPW>
+template <int NYP, int NS, int NPW, int CS = 0>
 static cudaError_t launch_wide_t(const ApplyArgs<float> &a, const TileCfg &cfg, int ntiles, cudaStream_t st,
                                  bool *launched) {
     // the Horner stage out = (-i tau / k) H u + psi has its own epilogue
     const bool horner = a.ar == 0.f && a.base != nullptr && a.br == 1.f && a.bi == 0.f && a.acc == nullptr;
     using G = WideGeom<NYP, NPW>;
-    const size_t smem = wide_smem_bytes(NYP, NS, cfg.zseg);
+    const size_t smem = wide_smem_bytes(NYP, NS, cfg.zseg, CS);
     if (smem > 227 * 1024) return cudaSuccess;
     const int ld = 2 * a.SV;
     WideMaps maps;
@@ -531,7 +557,14 @@ static cudaError_t launch_wide_t(const ApplyArgs<float> &a, const TileCfg &cfg, 
     CUtensorMap bm[24];
     if (!wide_maps_for(a.base != nullptr ? a.base : a.in, a.P, ld, bm)) return cudaSuccess;
     for (int i = 0; i < 16; i++) maps.b[i] = bm[i];
-    auto kern = horner ? k_apply_wide<NYP, NS, NPW, 1> : k_apply_wide<NYP, NS, NPW, 0>;
+    // complex scaling: alpha carries the rotation, so its Horner stage has a
+    // complex alpha
+    auto kern = k_apply_wide<NYP, NS, NPW, 0, CS>;
+    if constexpr (CS == 0) {
+        if (horner) kern = k_apply_wide<NYP, NS, NPW, 1, 0>;
+    } else {
+        if (a.base != nullptr && a.br == 1.f && a.bi == 0.f && a.acc == nullptr) kern = k_apply_wide<NYP, NS, NPW, 2, CS>;
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nchunks = (ld + G::NC - 1) / G::NC;
@@ -549,7 +582,15 @@ cudaError_t launch_apply_wide(const ApplyArgs<float> &a, const TileCfg &cfg, int
     if (ntiles == 0 || (long long)a.P * 2 * a.SV >= 0x7fffffffLL || a.nx > 32000) return cudaSuccess;
     // the tensor view needs 16-byte aligned blocks (ld is even for complex64)
     if (((uintptr_t)a.in & 15) != 0 || (a.base != nullptr && ((uintptr_t)a.base & 15) != 0)) return cudaSuccess;
-    if (a.err == nullptr || a.Vc != nullptr) return cudaSuccess;
+    if (a.err == nullptr) return cudaSuccess;
+    // complex scaling: the default shape only (6-row tiles, 4 producer
+    // warps), no field
+    if (a.Vc != nullptr) {
+        if (cfg.wty != 6 || cfg.npw != 4 || ((uintptr_t)a.Vc & 7) != 0 || a.f0 != 0.f || a.fx != 0.f ||
+            a.fy != 0.f || a.fz != 0.f)
+            return cudaSuccess;
+        return launch_wide_t<3, 3, 4, 1>(a, cfg, ntiles, st, launched);
+    }
     // tile rows and slots: 8-row and 6-row tiles with 3 slots, 4-row tiles
     // with 4; 1 to 4 producer warps
 #define RSG_WIDE_NPW(NYP_, NS_)                                                        \

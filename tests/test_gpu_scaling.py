@@ -177,26 +177,27 @@ def test_refusals_and_removal():
     _ = oracle
 
 
+@pytest.mark.parametrize("kernel", [5, 7])
 @pytest.mark.parametrize("shape,n,radius,S", [("sphere", 0, 3.3, 4), ("box", (37, 23, 29), 0.0, 6),
                                               ("sphere", 0, 3.0, 64), ("sphere", 0, 2.7, 1),
                                               ("box", (21, 30, 17), 0.0, 13)])
-def test_register_blocked_scaled_kernel(shape, n, radius, S):
-    """complex64 with the register-blocked kernel forced: the complex
-    diagonal v_theta e^{2i theta} in shared memory and e^{-2i theta} folded
-    into alpha; apply, a Taylor stage (alpha, base) and a shifted solve."""
+def test_register_blocked_scaled_kernel(shape, n, radius, S, kernel):
+    """complex64 with the register-blocked (5) or tensor-copy (7) kernel
+    forced: the complex diagonal v_theta e^{2i theta} in shared memory and
+    e^{-2i theta} folded into alpha; apply and a Taylor stage (alpha, base)."""
     theta = 0.35
     p, vt = _scaled_pair(shape, n, radius, dtype=torch.complex64, theta=theta)
-    p.H.set_option("kernel", 5)
+    p.H.set_option("kernel", kernel)
     psi = _states(p, S, seed=S + 3)
     x = p.states_to_gpu(psi)
     y = p.H.apply(x, S=S)
-    assert p.H.get_option("last_kernel") == 5
+    assert p.H.get_option("last_kernel") == kernel
     want = p.om.apply_scaled(psi, theta, vt)
     got = p.states_from_gpu(y, S)
     assert np.abs(got - want).max() < 2e-6 * np.abs(want).max()
     out = torch.zeros_like(x)
     p.H.taylor(x, 0.01, out=out, S=S)
-    assert p.H.get_option("last_kernel") == 5
+    assert p.H.get_option("last_kernel") == kernel
     tw = p.om.taylor4_scaled(psi, theta, vt, 0.01)
     assert np.abs(p.states_from_gpu(out, S) - tw).max() < 2e-6 * np.abs(tw).max()
     # the same results as the one-thread-per-value kernel
@@ -206,16 +207,17 @@ def test_register_blocked_scaled_kernel(shape, n, radius, S):
     assert np.abs(p.states_from_gpu(y1, S) - got).max() < 2e-6 * np.abs(want).max()
 
 
-def test_register_blocked_scaled_shifted_solve():
+@pytest.mark.parametrize("kernel", [5, 7])
+def test_register_blocked_scaled_shifted_solve(kernel):
     theta, z = 0.3, 0.4 + 0.15j
     p, vt = _scaled_pair("cube", 12, h=0.35, dtype=torch.complex64, theta=theta)
-    p.H.set_option("kernel", 5)
+    p.H.set_option("kernel", kernel)
     A = p.om.apply_scaled(np.eye(p.P, dtype=np.complex128), theta, vt) - z * np.eye(p.P)
     b = _states(p, 3, seed=12)
     want = np.linalg.solve(A, b)
     x = torch.zeros_like(p.states_to_gpu(b))
     res, it = p.H.shifted_solve(p.states_to_gpu(b), x, z, max_iter=3000, tol=1e-4, S=3)
-    assert p.H.get_option("last_kernel") == 5
+    assert p.H.get_option("last_kernel") == kernel
     assert np.all(res <= 1e-4), (res, it)
     assert np.abs(p.states_from_gpu(x, 3) - want).max() < 1e-3 * np.abs(want).max()
 
@@ -223,8 +225,8 @@ def test_register_blocked_scaled_shifted_solve():
 def test_full_size_sphere_sampled_register_blocked():
     """The benchmark's complex-scaled configuration: R = 18 bohr, h = 0.2
     (3,053,617 points), 64 complex64 states, 32 wells at r e^{0.3i}, the
-    default register-blocked kernel; every state of 4096 sampled points
-    against the oracle."""
+    default kernel (tensor-copy staging with a complex diagonal); every state
+    of 4096 sampled points against the oracle."""
     from workloads import gaussian_wells, potential_wells_scaled
     g = rng(2)
     theta = 0.3
@@ -236,7 +238,7 @@ def test_full_size_sphere_sampled_register_blocked():
     psi = white_noise_states(g, p.P, S, dtype=np.complex64).astype(np.complex128)
     y = p.H.apply(p.states_to_gpu(psi))
     torch.cuda.synchronize()
-    assert p.H.get_option("last_kernel") == 5
+    assert p.H.get_option("last_kernel") == 7
     samp = g.choice(p.P, 4096, replace=False)
     pidx = np.repeat(samp, S)
     sidx = np.tile(np.arange(S), len(samp))
