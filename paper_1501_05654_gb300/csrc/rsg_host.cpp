@@ -200,8 +200,15 @@ struct rsg_ham_s {
     size_t ev_used = 0;
     int64_t n_launch = 0, n_stencil = 0;
     double stencil_bytes = 0.0;
+    // projector coefficients on a side stream, concurrent with the stencil
+    // they do not feed (the scatter after the stencil waits for them)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~rsg_ham_s() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
     }
 };
 
@@ -453,7 +460,6 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
             CK(H->pcnt.ensure(ncnt));
             CK(cudaMemsetAsync(H->pcnt.p, 0, H->pcnt.n, st));
         }
-        CK(launch_proj_coeffs<R>(in, SV, H->pj, H->partial.as<double>(), H->pcnt.as<unsigned>(), h3, H->D.p, st));
     }
     ApplyArgs<R> a;
     a.in = in;
@@ -556,6 +562,28 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
             }
         }
     }
+    const bool odd = m->bc == RSG_BC_ODD;
+    const bool split_nl = !odd && !H->has_scaling && cfg.kernel != 1 && cfg.kernel != 2 && H->pj.natoms > 0;
+    // projector coefficients D = h_a h^3 <p|in>: read by the stencil itself
+    // when it adds the projector terms (kernels 1, 2), else only by the
+    // scatter after it, so they run on a side stream next to the stencil
+    bool joined = true;
+    if (H->pj.natoms > 0) {
+        cudaStream_t cs = st;
+        if (split_nl) {
+            if (!H->side) {
+                CK(cudaStreamCreateWithFlags(&H->side, cudaStreamNonBlocking));
+                CK(cudaEventCreateWithFlags(&H->ev_fork, cudaEventDisableTiming));
+                CK(cudaEventCreateWithFlags(&H->ev_join, cudaEventDisableTiming));
+            }
+            CK(cudaEventRecord(H->ev_fork, st));
+            CK(cudaStreamWaitEvent(H->side, H->ev_fork, 0));
+            cs = H->side;
+            joined = false;
+        }
+        CK(launch_proj_coeffs<R>(in, SV, H->pj, H->partial.as<double>(), H->pcnt.as<unsigned>(), h3, H->D.p, cs));
+        if (split_nl) CK(cudaEventRecord(H->ev_join, H->side));
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (H->prof) {
         if (H->ev_used + 2 > H->ev.size()) {
@@ -570,8 +598,6 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         H->ev_used += 2;
         CK(cudaEventRecord(e0, st));
     }
-    const bool odd = m->bc == RSG_BC_ODD;
-    const bool split_nl = !odd && !H->has_scaling && cfg.kernel != 1 && cfg.kernel != 2 && H->pj.natoms > 0;
     if (odd) {
         // image walls: the one-thread-per-value kernels, neighbours through the image rule
         if (H->has_scaling) {
@@ -634,6 +660,7 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
         }
     }
     if (H->prof) CK(cudaEventRecord(e1, st));
+    if (!joined) CK(cudaStreamWaitEvent(st, H->ev_join, 0));
     if (split_nl) {
         CK(launch_proj_scatter<R>(a, H->pj, st));
         H->n_launch++;
