@@ -450,7 +450,14 @@ rsg_status rsg_batch_destroy(rsg_batch b);
  * "blocks_per_sm" (staged kernel with 256 threads: register budget for 2 or
  * 3 resident blocks per SM), "adjoint_keep_powers" (rsg_control_gradient: 1 keeps the Taylor powers of
  * a whole checkpoint segment, 0 recomputes them per interval, -1 = choose by
- * free device memory, the default).
+ * free device memory, the default), "adjoint_merge" (rsg_control_gradient
+ * with kept powers: 1 runs the costate sweep of a segment and the recompute
+ * sweep of the segment before it as two-column launches, 0 one after the
+ * other, -1 = 1 when the two banks of two-column blocks fit in half the free
+ * memory, the default), "proj_overlap" (1: the projector
+ * coefficients of each application run on an internal side stream next to
+ * the stencil, which does not read them, and the projector terms after the
+ * stencil wait for them; 0, the default: all on the caller's stream).
  * A shape whose shared memory does not fit the SM fails with RSG_ERR_CUDA. */
 rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value);
 

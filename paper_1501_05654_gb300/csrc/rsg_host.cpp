@@ -200,8 +200,10 @@ struct rsg_ham_s {
     size_t ev_used = 0;
     int64_t n_launch = 0, n_stencil = 0;
     double stencil_bytes = 0.0;
-    // projector coefficients on a side stream, concurrent with the stencil
-    // they do not feed (the scatter after the stencil waits for them)
+    // option "proj_overlap": projector coefficients on a side stream,
+    // concurrent with the stencil they do not feed (the scatter after the
+    // stencil waits for them)
+    int proj_overlap = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~rsg_ham_s() {
@@ -566,11 +568,12 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
     const bool split_nl = !odd && !H->has_scaling && cfg.kernel != 1 && cfg.kernel != 2 && H->pj.natoms > 0;
     // projector coefficients D = h_a h^3 <p|in>: read by the stencil itself
     // when it adds the projector terms (kernels 1, 2), else only by the
-    // scatter after it, so they run on a side stream next to the stencil
+    // scatter after it; with "proj_overlap" they then run on a side stream
+    // next to the stencil
     bool joined = true;
     if (H->pj.natoms > 0) {
         cudaStream_t cs = st;
-        if (split_nl) {
+        if (split_nl && H->proj_overlap) {
             if (!H->side) {
                 CK(cudaStreamCreateWithFlags(&H->side, cudaStreamNonBlocking));
                 CK(cudaEventCreateWithFlags(&H->ev_fork, cudaEventDisableTiming));
@@ -582,7 +585,7 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
             joined = false;
         }
         CK(launch_proj_coeffs<R>(in, SV, H->pj, H->partial.as<double>(), H->pcnt.as<unsigned>(), h3, H->D.p, cs));
-        if (split_nl) CK(cudaEventRecord(H->ev_join, H->side));
+        if (!joined) CK(cudaEventRecord(H->ev_join, H->side));
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (H->prof) {
@@ -1060,6 +1063,7 @@ rsg_status rsg_ham_get_option(rsg_ham H, const char *key, int64_t *value) {
     else if (k == "sync") *value = H->cfg.sync;
     else if (k == "stages") *value = H->cfg.stages;
     else if (k == "blocks_per_sm") *value = H->cfg.blocks_per_sm;
+    else if (k == "proj_overlap") *value = H->proj_overlap;
     else return fail(RSG_ERR_ARG, "unknown option: %s", key);
     return RSG_OK;
 }
@@ -1080,6 +1084,7 @@ rsg_status rsg_ham_set_option(rsg_ham H, const char *key, int64_t value) {
     else if (k == "cv" && (value == 1 || value == 2 || value == 4 || value == 8)) H->cfg.cv = (int)value;
     else if (k == "adjoint_keep_powers" && value >= -1 && value <= 1) H->adj_keep = (int)value;
     else if (k == "adjoint_merge" && value >= -1 && value <= 1) H->adj_merge = (int)value;
+    else if (k == "proj_overlap" && (value == 0 || value == 1)) H->proj_overlap = (int)value;
     else if (k == "threads" && (value == 160 || value == 192 || value == 256 || value == 512))
         H->cfg.threads = (int)value;
     else if (k == "sync" && value >= 0 && value <= 2) H->cfg.sync = (int)value;

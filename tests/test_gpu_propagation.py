@@ -120,3 +120,26 @@ def test_norms_against_numpy():
     n2 = p.H.norms(x, S=9)
     want = p.h ** 3 * np.sum(np.abs(psi) ** 2, axis=0)
     assert np.abs(n2 - want).max() < 1e-12 * want.max()
+
+
+def test_projector_coefficients_on_a_side_stream_give_the_same_step():
+    """Option proj_overlap: the coefficients run on an internal side stream
+    next to the stencil; the step is bit-for-bit the one on one stream."""
+    import paper_1501_05654_gb300 as rsg_
+    from tests._systems import wells_system
+    from tests._parity import round_c64
+    from workloads import white_noise_states
+    p, g = wells_system("sphere", 0, radius=4.0, h=0.2, dtype=torch.complex64, seed=2, natoms=3, lmax=1)
+    psi = round_c64(white_noise_states(g, p.P, 16))
+    p.H.set_option("kernel", 7)      # the stencil that leaves the projector terms to the scatter
+    x = p.states_to_gpu(psi)
+    y = x.clone()
+    p.H.propagate(x, 3, 0.01, scheme=rsg_.ETRS, S=16)
+    assert p.H.get_option("last_kernel") == 7
+    p.H.set_option("proj_overlap", 1)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p.H.propagate(y, 3, 0.01, scheme=rsg_.ETRS, S=16)
+    s.synchronize()
+    assert p.H.get_option("proj_overlap") == 1
+    assert torch.equal(x, y)
