@@ -405,9 +405,14 @@ rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps,
  *   "wait_limit": polls of one dependency wait before it gives up (each
  *       about 0.5 us; default 2^22).
  *   "tile_variants": bit (ls / 2 - 1) set selects tile variant 1 for the
- *       systems whose staged records hold ls = min(ld, 16) values (ls = 6,
- *       8, 10, 12, 14 have two variants: 0 one thread per value on wide
- *       tiles, 1 power-of-two value lanes on narrower tiles); default 0.
+ *       systems whose staged records hold ls = min(ld, 16) values; only
+ *       ls = 14 has one (16 value lanes on a 16 x 6 tile instead of one
+ *       lane per value on 18 x 6), other bits are accepted and ignored;
+ *       default 0.
+ *   "split_pairs": bit (ls / 2 - 1) set, for ls = 2, 4, 6, 8, gives the
+ *       thread's two x points of variant 0's tile TX / 2 apart instead of
+ *       adjacent (conflict-free shared-memory loads, more loads per output);
+ *       it overrides "tile_variants" for those lengths; default 0.
  *   "debug_stall": 1 makes system 0 wait for a stencil item that never comes,
  *       so that the step's bounded waits run out (a test of that path).
  * rsg_batch_get_option also reads "batched", "launches_per_step",
@@ -418,7 +423,7 @@ rsg_status rsg_batch_get_option(rsg_batch b, const char *name, int64_t *value);
  * of psis (psis are read, not changed; the copies are freed before return)
  * for the per-stage launches and the persistent step, and for the persistent
  * step its segment length ("zseg" 48, 64, 96, 128) and, per record length
- * with two tile variants (largest share of bytes first), the variant; keeps
+ * (largest share of bytes first), the tile variant and the split pairs; keeps
  * the fastest and returns its time per step in *best_ms (may be NULL).
  * Synchronises.  Errors as rsg_batch_propagate. */
 rsg_status rsg_batch_autotune(rsg_batch b, void *const *psis, double dt, rsg_scheme scheme, void *stream,

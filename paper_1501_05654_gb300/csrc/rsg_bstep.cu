@@ -52,11 +52,10 @@ constexpr unsigned kBSuspendNs = 2000;
 constexpr long kBSlotWaitLimit = 1L << 20;   // about 2 s per slot wait
 
 // Tile (TX x TY) of a system whose staged record holds LS complex values,
-// two variants per LS that the autotuner chooses between.  Variant 0: one
-// compute thread per value (LANES = LS) at a 2 x 2 group of points, wide
-// rows where the record is short (fewer, longer copies).  Variant 1: LANES =
-// LS rounded up to a power of two (idle lanes, but warps aligned to groups
-// and records) on narrower tiles.
+// with variants that the autotuner chooses between.  Variant 0: one compute
+// thread per value (LANES = LS) at a 2 x 2 group of points, wide rows where
+// the record is short (fewer, longer copies).  Variant 1 (LS = 14): 16 value
+// lanes (two idle, warps aligned to groups and records) on a narrower tile.
 template <int LS, int VAR>
 struct BTile;
 template <> struct BTile<2, 0> { static constexpr int TX = 32, TY = 24, LANES = 2; };
@@ -67,13 +66,18 @@ template <> struct BTile<10, 0> { static constexpr int TX = 18, TY = 8, LANES = 
 template <> struct BTile<12, 0> { static constexpr int TX = 16, TY = 8, LANES = 12; };
 template <> struct BTile<14, 0> { static constexpr int TX = 18, TY = 6, LANES = 14; };
 template <> struct BTile<16, 0> { static constexpr int TX = 16, TY = 6, LANES = 16; };
-template <> struct BTile<6, 1> { static constexpr int TX = 16, TY = 12, LANES = 8; };
-template <> struct BTile<8, 1> { static constexpr int TX = 16, TY = 12, LANES = 8; };
-template <> struct BTile<10, 1> { static constexpr int TX = 16, TY = 6, LANES = 16; };
-template <> struct BTile<12, 1> { static constexpr int TX = 16, TY = 6, LANES = 16; };
 template <> struct BTile<14, 1> { static constexpr int TX = 16, TY = 6, LANES = 16; };
-// record lengths with two distinct variants
-__host__ __device__ constexpr bool bhas_var1(int ls) { return ls == 6 || ls == 8 || ls == 10 || ls == 12 || ls == 14; }
+// Variant 2 (records of 2-8 values): variant 0's tile, with the two x points
+// of a thread TX / 2 apart instead of adjacent, so that the lanes of a warp
+// read consecutive records (no shared-memory bank conflicts) at the cost of
+// more loads per output (the two points' x windows no longer overlap).
+template <> struct BTile<2, 2> : BTile<2, 0> {};
+template <> struct BTile<4, 2> : BTile<4, 0> {};
+template <> struct BTile<6, 2> : BTile<6, 0> {};
+template <> struct BTile<8, 2> : BTile<8, 0> {};
+// record lengths with variant 1, and with the split-pair variant
+__host__ __device__ constexpr bool bhas_var1(int ls) { return ls == 14; }
+__host__ __device__ constexpr bool bhas_var2(int ls) { return ls <= 8; }
 
 // Staging geometry of records of LS complex values
 template <int LS, int VAR>
@@ -101,8 +105,7 @@ constexpr int bslot_ls() { return bslot_need(BShape<LS, VAR>::UB, BShape<LS, VAR
 constexpr int kBSlot =
     (bmax(bmax(bmax(bmax(bslot_ls<2, 0>(), bslot_ls<4, 0>()), bmax(bslot_ls<6, 0>(), bslot_ls<8, 0>())),
                bmax(bmax(bslot_ls<10, 0>(), bslot_ls<12, 0>()), bmax(bslot_ls<14, 0>(), bslot_ls<16, 0>()))),
-          bmax(bmax(bslot_ls<6, 1>(), bslot_ls<8, 1>()),
-               bmax(bslot_ls<10, 1>(), bmax(bslot_ls<12, 1>(), bslot_ls<14, 1>())))) +
+          bslot_ls<14, 1>()) +
      1023) & ~1023;
 static_assert(9 * 4 * (kBNT + kBMaxLd / 2) * 8 <= kBNS * kBSlot, "the dot reduction fits in the ring");
 
@@ -348,7 +351,10 @@ __device__ int bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned 
     // the record for its last value; neither stores
     const bool gok = g0 < G::NG;
     const int g = gok ? g0 : G::NG - 1;
-    const int xl = 2 * (g % G::GX), yl = 2 * (g / G::GX);
+    // the thread's points: columns xl and xl + XS, rows yl and yl + 1
+    constexpr bool SPLIT = VAR == 2;
+    constexpr int XS = SPLIT ? G::GX : 1;
+    const int xl = SPLIT ? g % G::GX : 2 * (g % G::GX), yl = 2 * (g / G::GX);
     const int cc = c < LS ? c : LS - 1;
     const int k = k0 + c;
     const bool vok = gok && c < LS && k < ld;
@@ -357,7 +363,7 @@ __device__ int bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned 
     // and last, scanning from both ends), united over the warp
     int jc0 = np, jc1 = -1;
     {
-        const unsigned need = 3u << xl;
+        const unsigned need = (1u << xl) | (1u << (xl + XS));
         for (int jj = 0; jj < np; jj++)
             if ((unsigned)(orows[jj * TY + yl].y | orows[jj * TY + yl + 1].y) & need) {
                 jc0 = jj;
@@ -399,6 +405,23 @@ __device__ int bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned 
             if (j <= jc1) {
                 const float2 *pw = (const float2 *)slotp + uoff;
 #define QW(r, kk) pw[(r) * RW + (kk) * LS]
+                if constexpr (SPLIT) {
+                    // two 9-point x windows per row, TX / 2 apart
+#pragma unroll
+                    for (int r = 0; r < 2; r++) {
+#pragma unroll
+                        for (int dx = 0; dx < 2; dx++) {
+                            float2 W[9];
+#pragma unroll
+                            for (int kk = 0; kk < 9; kk++) W[kk] = QW(r, kk + dx * XS);
+                            cen[2 * r + dx] = W[4];
+                            float2 t = f2_mul(w1, f2_add(W[3], W[5]));
+                            t = f2_fma(w2, f2_add(W[2], W[6]), t);
+                            t = f2_fma(w3, f2_add(W[1], W[7]), t);
+                            s[2 * r + dx] = f2_fma(w4, f2_add(W[0], W[8]), t);
+                        }
+                    }
+                } else {
 #pragma unroll
                 for (int r = 0; r < 2; r++) {
                     float2 W[10];
@@ -415,10 +438,12 @@ __device__ int bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned 
                     t = f2_fma(w3, f2_add(W[2], W[8]), t);
                     s[2 * r + 1] = f2_fma(w4, f2_add(W[1], W[9]), t);
                 }
+                }
 #pragma unroll
                 for (int dx = 0; dx < 2; dx++) {
-                    const float2 m4 = QW(-4, 4 + dx), m3 = QW(-3, 4 + dx), m2 = QW(-2, 4 + dx), m1 = QW(-1, 4 + dx);
-                    const float2 p2 = QW(2, 4 + dx), p3 = QW(3, 4 + dx), p4 = QW(4, 4 + dx), p5 = QW(5, 4 + dx);
+                    const int cx = 4 + dx * XS;   // window column of the thread's point dx
+                    const float2 m4 = QW(-4, cx), m3 = QW(-3, cx), m2 = QW(-2, cx), m1 = QW(-1, cx);
+                    const float2 p2 = QW(2, cx), p3 = QW(3, cx), p4 = QW(4, cx), p5 = QW(5, cx);
                     float2 t = f2_fma(w1, f2_add(m1, cen[2 + dx]), s[dx]);
                     t = f2_fma(w2, f2_add(m2, p2), t);
                     t = f2_fma(w3, f2_add(m3, p3), t);
@@ -433,7 +458,7 @@ __device__ int bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned 
 #pragma unroll
                 for (int pt = 0; pt < 4; pt++) {
                     // diagonal: staged V (zero outside the mesh); no field
-                    const float d = vv[(pt >> 1) * TX + (pt & 1)] + w0c;
+                    const float d = vv[(pt >> 1) * TX + (pt & 1) * XS] + w0c;
                     s[pt].x = fmaf(d, cen[pt].x, s[pt].x);
                     s[pt].y = fmaf(d, cen[pt].y, s[pt].y);
                 }
@@ -468,9 +493,9 @@ __device__ int bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned 
 #pragma unroll
                     for (int dx = 0; dx < 2; dx++) {
                         const float2 acc = done[2 * dy + dx];
-                        const float2 bv = bb[(dy * TX + dx) * LS];
+                        const float2 bv = bb[(dy * TX + dx * XS) * LS];
                         const float2 y = make_float2(fmaf(-ai, acc.y, bv.x), fmaf(ai, acc.x, bv.y));
-                        if ((m >> dx) & 1) out2[orow + dx * ld] = y;
+                        if ((m >> (dx * XS)) & 1) out2[orow + dx * XS * ld] = y;
                     }
                 }
             }
@@ -692,21 +717,21 @@ __global__ void __launch_bounds__(kBNT, 1) k_batch_step(const __grid_constant__ 
         if (kind0 == 1) {
             const SysArgs &S0 = A.sys[A.items[it].sys];
             const int ls = S0.ld > 16 ? 16 : S0.ld;
-            const int var = S0.var != 0 && bhas_var1(ls) ? 1 : 0;
+            const int var = S0.var == 2 && bhas_var2(ls) ? 2 : (S0.var == 1 && bhas_var1(ls) ? 1 : 0);
 #define RSG_BS(L_, V_) staged = bs_stencil<L_, V_>(A, it, s_ring, gring, J)
-            switch (ls * 2 + var) {
-            case 4: RSG_BS(2, 0); break;
-            case 8: RSG_BS(4, 0); break;
-            case 12: RSG_BS(6, 0); break;
-            case 13: RSG_BS(6, 1); break;
-            case 16: RSG_BS(8, 0); break;
-            case 17: RSG_BS(8, 1); break;
-            case 20: RSG_BS(10, 0); break;
-            case 21: RSG_BS(10, 1); break;
-            case 24: RSG_BS(12, 0); break;
-            case 25: RSG_BS(12, 1); break;
-            case 28: RSG_BS(14, 0); break;
-            case 29: RSG_BS(14, 1); break;
+            switch (ls * 4 + var) {
+            case 8: RSG_BS(2, 0); break;
+            case 10: RSG_BS(2, 2); break;
+            case 16: RSG_BS(4, 0); break;
+            case 18: RSG_BS(4, 2); break;
+            case 24: RSG_BS(6, 0); break;
+            case 26: RSG_BS(6, 2); break;
+            case 32: RSG_BS(8, 0); break;
+            case 34: RSG_BS(8, 2); break;
+            case 40: RSG_BS(10, 0); break;
+            case 48: RSG_BS(12, 0); break;
+            case 56: RSG_BS(14, 0); break;
+            case 57: RSG_BS(14, 1); break;
             default: RSG_BS(16, 0); break;
             }
 #undef RSG_BS
@@ -754,14 +779,9 @@ void batch_step_tile(int ld, int var, int *TX, int *TY) {
     *TX = BTile<L, V>::TX;        \
     *TY = BTile<L, V>::TY;        \
     return;
-    if (var != 0 && bhas_var1(ls)) {
-        switch (ls) {
-        case 6: RSG_BT(6, 1)
-        case 8: RSG_BT(8, 1)
-        case 10: RSG_BT(10, 1)
-        case 12: RSG_BT(12, 1)
-        default: RSG_BT(14, 1)
-        }
+    // variant 2 keeps variant 0's tile
+    if (var == 1 && bhas_var1(ls)) {
+        RSG_BT(14, 1)
     }
     switch (ls) {
     case 2: RSG_BT(2, 0)
