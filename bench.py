@@ -447,7 +447,7 @@ def batch_extra(chk, peak, steps=10, nsys=256, tune=True):
         pst += m.P * int(S_)
     batch = rsg.Batch(hams, [int(x) for x in Ss[:nsys]])
     tune_ms = batch.autotune(psis, 0.02, scheme=rsg.ETRS) if tune else None
-    tuned = {k: batch.get_option(k) for k in ("persistent", "zseg", "tile_variants", "split_pairs", "launches_per_step",
+    tuned = {k: batch.get_option(k) for k in ("persistent", "zseg", "tile_variants", "launches_per_step",
                                               "items_per_stage", "blocks")}
     ms = time_steps(None, psis, steps, lambda xs: batch.propagate(xs, 1, 0.02, scheme=rsg.ETRS))
     if chk is not None:

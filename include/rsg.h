@@ -409,10 +409,6 @@ rsg_status rsg_batch_propagate(rsg_batch b, void *const *psis, int64_t nsteps,
  *       ls = 14 has one (16 value lanes on a 16 x 6 tile instead of one
  *       lane per value on 18 x 6), other bits are accepted and ignored;
  *       default 0.
- *   "split_pairs": bit (ls / 2 - 1) set, for ls = 2, 4, 6, 8, gives the
- *       thread's two x points of variant 0's tile TX / 2 apart instead of
- *       adjacent (conflict-free shared-memory loads, more loads per output);
- *       it overrides "tile_variants" for those lengths; default 0.
  *   "debug_stall": 1 makes system 0 wait for a stencil item that never comes,
  *       so that the step's bounded waits run out (a test of that path).
  * rsg_batch_get_option also reads "batched", "launches_per_step",
@@ -422,8 +418,8 @@ rsg_status rsg_batch_get_option(rsg_batch b, const char *name, int64_t *value);
 /* Batch autotuner: times steps of the given scheme and dt on device copies
  * of psis (psis are read, not changed; the copies are freed before return)
  * for the per-stage launches and the persistent step, and for the persistent
- * step its segment length ("zseg" 48, 64, 96, 128) and, per record length
- * (largest share of bytes first), the tile variant and the split pairs; keeps
+ * step its segment length ("zseg" 48, 64, 96, 128) and the tile variant of
+ * the systems with 14 values per point; keeps
  * the fastest and returns its time per step in *best_ms (may be NULL).
  * Synchronises.  Errors as rsg_batch_propagate. */
 rsg_status rsg_batch_autotune(rsg_batch b, void *const *psis, double dt, rsg_scheme scheme, void *stream,

@@ -51,11 +51,15 @@ constexpr int kBNS = 3;                      // pipeline slots
 constexpr unsigned kBSuspendNs = 2000;
 constexpr long kBSlotWaitLimit = 1L << 20;   // about 2 s per slot wait
 
-// Tile (TX x TY) of a system whose staged record holds LS complex values,
-// with variants that the autotuner chooses between.  Variant 0: one compute
-// thread per value (LANES = LS) at a 2 x 2 group of points, wide rows where
-// the record is short (fewer, longer copies).  Variant 1 (LS = 14): 16 value
-// lanes (two idle, warps aligned to groups and records) on a narrower tile.
+// Tile (TX x TY) of a system whose staged record holds LS complex values.
+// Variant 0: one compute thread per value (LANES = LS) at two columns and two
+// rows of the tile, wide rows where the record is short (fewer, longer
+// copies).  Below 16 values the thread's two columns are x and x + TX / 2
+// (not x and x + 1), so that the lanes of a warp read consecutive records:
+// adjacent pairs would put the lanes two records apart and, with records
+// shorter than 128 bytes, on the same shared-memory banks.  Variant 1
+// (LS = 14), which the autotuner may choose: 16 value lanes (two idle) and
+// adjacent columns on a 16 x 6 tile.
 template <int LS, int VAR>
 struct BTile;
 template <> struct BTile<2, 0> { static constexpr int TX = 32, TY = 24, LANES = 2; };
@@ -67,17 +71,8 @@ template <> struct BTile<12, 0> { static constexpr int TX = 16, TY = 8, LANES = 
 template <> struct BTile<14, 0> { static constexpr int TX = 18, TY = 6, LANES = 14; };
 template <> struct BTile<16, 0> { static constexpr int TX = 16, TY = 6, LANES = 16; };
 template <> struct BTile<14, 1> { static constexpr int TX = 16, TY = 6, LANES = 16; };
-// Variant 2 (records of 2-8 values): variant 0's tile, with the two x points
-// of a thread TX / 2 apart instead of adjacent, so that the lanes of a warp
-// read consecutive records (no shared-memory bank conflicts) at the cost of
-// more loads per output (the two points' x windows no longer overlap).
-template <> struct BTile<2, 2> : BTile<2, 0> {};
-template <> struct BTile<4, 2> : BTile<4, 0> {};
-template <> struct BTile<6, 2> : BTile<6, 0> {};
-template <> struct BTile<8, 2> : BTile<8, 0> {};
-// record lengths with variant 1, and with the split-pair variant
+// record lengths with variant 1
 __host__ __device__ constexpr bool bhas_var1(int ls) { return ls == 14; }
-__host__ __device__ constexpr bool bhas_var2(int ls) { return ls <= 8; }
 
 // Staging geometry of records of LS complex values
 template <int LS, int VAR>
@@ -352,7 +347,7 @@ __device__ int bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned 
     const bool gok = g0 < G::NG;
     const int g = gok ? g0 : G::NG - 1;
     // the thread's points: columns xl and xl + XS, rows yl and yl + 1
-    constexpr bool SPLIT = VAR == 2;
+    constexpr bool SPLIT = LANES == LS && LS < 16;
     constexpr int XS = SPLIT ? G::GX : 1;
     const int xl = SPLIT ? g % G::GX : 2 * (g % G::GX), yl = 2 * (g / G::GX);
     const int cc = c < LS ? c : LS - 1;
@@ -717,17 +712,13 @@ __global__ void __launch_bounds__(kBNT, 1) k_batch_step(const __grid_constant__ 
         if (kind0 == 1) {
             const SysArgs &S0 = A.sys[A.items[it].sys];
             const int ls = S0.ld > 16 ? 16 : S0.ld;
-            const int var = S0.var == 2 && bhas_var2(ls) ? 2 : (S0.var == 1 && bhas_var1(ls) ? 1 : 0);
+            const int var = S0.var == 1 && bhas_var1(ls) ? 1 : 0;
 #define RSG_BS(L_, V_) staged = bs_stencil<L_, V_>(A, it, s_ring, gring, J)
             switch (ls * 4 + var) {
             case 8: RSG_BS(2, 0); break;
-            case 10: RSG_BS(2, 2); break;
             case 16: RSG_BS(4, 0); break;
-            case 18: RSG_BS(4, 2); break;
             case 24: RSG_BS(6, 0); break;
-            case 26: RSG_BS(6, 2); break;
             case 32: RSG_BS(8, 0); break;
-            case 34: RSG_BS(8, 2); break;
             case 40: RSG_BS(10, 0); break;
             case 48: RSG_BS(12, 0); break;
             case 56: RSG_BS(14, 0); break;
@@ -779,7 +770,6 @@ void batch_step_tile(int ld, int var, int *TX, int *TY) {
     *TX = BTile<L, V>::TX;        \
     *TY = BTile<L, V>::TY;        \
     return;
-    // variant 2 keeps variant 0's tile
     if (var == 1 && bhas_var1(ls)) {
         RSG_BT(14, 1)
     }

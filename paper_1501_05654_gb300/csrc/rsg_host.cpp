@@ -237,7 +237,6 @@ struct rsg_batch_s {
     long wait_limit = 1L << 22;    // polls of a dependency wait
     int stall = 0;                 // > 0: system 0 waits for a stencil item that never comes
     int tile_var_mask = 0;         // bit ls / 2 - 1: tile variant 1 for records of ls values (ls = 14)
-    int split_mask = 0;            // bit ls / 2 - 1 (ls <= 8): split-pair variant 2, before tile_var_mask
     std::vector<BItem> stage_items;   // the items of one stage, stage bits 0
     int np_cap = 0, nblocks = 0, step_nst = 0;
     DevBuf d_items, d_cnt, d_ctl, d_status, d_zero;
@@ -2681,8 +2680,7 @@ rsg_status batch_build_step(rsg_batch b) {
         CK(b->w1[(size_t)i].ensure(bytes));
         int TX = 16, TY = 6;
         const int ls = ld > 16 ? 16 : (int)ld;
-        const int var = (ls <= 8 && ((b->split_mask >> (ls / 2 - 1)) & 1)) ? 2
-                                                                           : (b->tile_var_mask >> (ls / 2 - 1)) & 1;
+        const int var = (b->tile_var_mask >> (ls / 2 - 1)) & 1;
         batch_step_tile((int)ld, var, &TX, &TY);
         const Tile *tiles = nullptr;
         int ntiles = 0;
@@ -2956,8 +2954,7 @@ rsg_status rsg_batch_set_option(rsg_batch b, const char *name, int64_t value) {
         b->stall = (int)value;
     } else if (k == "tile_variants" && value >= 0 && value <= 255) {
         b->tile_var_mask = (int)value;
-    } else if (k == "split_pairs" && value >= 0 && value <= 15) {
-        b->split_mask = (int)value;
+
     } else {
         return fail(RSG_ERR_ARG, "unknown batch option %s = %lld", name, (long long)value);
     }
@@ -2972,7 +2969,6 @@ rsg_status rsg_batch_get_option(rsg_batch b, const char *name, int64_t *value) {
     else if (k == "wait_limit") *value = b->wait_limit;
     else if (k == "debug_stall") *value = b->stall;
     else if (k == "tile_variants") *value = b->tile_var_mask;
-    else if (k == "split_pairs") *value = b->split_mask;
     else if (k == "batched") *value = b->batched ? 1 : 0;
     else if (k == "launches_per_step") *value = b->mode == 1 ? 1 : b->n_launch_step * 8;
     else if (k == "items_per_stage") *value = (int64_t)b->stage_items.size();
@@ -3002,11 +2998,10 @@ rsg_status rsg_batch_autotune(rsg_batch b, void *const *psis, double dt, rsg_sch
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    auto trial = [&](int mode, int zseg, int mask, int split, double *ms) -> rsg_status {
+    auto trial = [&](int mode, int zseg, int mask, double *ms) -> rsg_status {
         b->mode = mode;
         b->zseg = zseg;
         b->tile_var_mask = mask;
-        b->split_mask = split;
         CKS(batch_build(b));
         CKS(rsg_batch_propagate(b, ptrs.data(), 1, dt, scheme, 0, stream));
         CK(cudaEventRecord(e0, st));
@@ -3018,14 +3013,13 @@ rsg_status rsg_batch_autotune(rsg_batch b, void *const *psis, double dt, rsg_sch
         *ms = 0.5 * t;
         return RSG_OK;
     };
-    int bmode = b->mode, bz = b->zseg, bm = b->tile_var_mask, bsp = b->split_mask;
+    int bmode = b->mode, bz = b->zseg, bm = b->tile_var_mask;
     double best = 1e30, t = 0.0;
     rsg_status s = RSG_OK;
-    // the per-stage launches, then the persistent step's segment length and,
-    // per record length with two tile variants (largest share of bytes
-    // first), the tile variant
+    // the per-stage launches, then the persistent step's segment length and
+    // the tile variant of the record length that has two
     for (int mode : {0, 1}) {
-        if (s == RSG_OK) s = trial(mode, bz, bm, bsp, &t);
+        if (s == RSG_OK) s = trial(mode, bz, bm, &t);
         if (s == RSG_OK && t < best) {
             best = t;
             bmode = mode;
@@ -3034,36 +3028,19 @@ rsg_status rsg_batch_autotune(rsg_batch b, void *const *psis, double dt, rsg_sch
     if (s == RSG_OK && bmode == 1) {
         for (int z : {48, 64, 96, 128}) {
             if (z == bz) continue;
-            if (trial(1, z, bm, bsp, &t) == RSG_OK && t < best) {
+            if (trial(1, z, bm, &t) == RSG_OK && t < best) {
                 best = t;
                 bz = z;
             }
         }
-        std::vector<std::pair<double, int>> cls;   // (bytes, ls)
-        for (int ls = 2; ls <= 14; ls += 2) {
-            double bytes = 0.0;
-            for (size_t i = 0; i < n; i++)
-                if (std::min<int64_t>(b->ld[i], 16) == ls) bytes += (double)b->hams[i]->m->P * b->ld[i];
-            if (bytes > 0) cls.push_back({bytes, ls});
-        }
-        std::sort(cls.rbegin(), cls.rend());
-        for (auto &c : cls) {
-            const int bit = 1 << (c.second / 2 - 1);
-            // variant 1 (record length 14), then the split-pair variant
-            // (record lengths 2-8)
-            if (c.second == 14) {
-                const int m2 = bm ^ bit;
-                if (trial(1, bz, m2, bsp, &t) == RSG_OK && t < best) {
-                    best = t;
-                    bm = m2;
-                }
-            }
-            if (c.second <= 8) {
-                const int s2 = bsp ^ bit;
-                if (trial(1, bz, bm, s2, &t) == RSG_OK && t < best) {
-                    best = t;
-                    bsp = s2;
-                }
+        // the record length with two tile variants (14 values), if present
+        bool has14 = false;
+        for (size_t i = 0; i < n; i++) has14 = has14 || std::min<int64_t>(b->ld[i], 16) == 14;
+        if (has14) {
+            const int m2 = bm ^ (1 << 6);
+            if (trial(1, bz, m2, &t) == RSG_OK && t < best) {
+                best = t;
+                bm = m2;
             }
         }
     }
@@ -3072,7 +3049,6 @@ rsg_status rsg_batch_autotune(rsg_batch b, void *const *psis, double dt, rsg_sch
     b->mode = bmode;
     b->zseg = bz;
     b->tile_var_mask = bm;
-    b->split_mask = bsp;
     CKS(batch_build(b));
     if (s != RSG_OK) return s;
     if (best_ms) *best_ms = best;

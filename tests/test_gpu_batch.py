@@ -192,13 +192,6 @@ def test_batch_tile_variants_and_autotune():
     _, ys = _run_batch(systems, 2, 0.02, rsg.ETRS, tile_variants=255)
     for (p, psi, S), x, y in zip(systems, xs, ys):
         assert torch.equal(x, y), (p.P, S)
-    # split pairs for the record lengths 2, 4, 6, 8 (S = 1..8 here)
-    specs2 = [(12, 1, 0), (16, 3, 0), (10, 5, 0), (14, 7, 0), (9, 2, 0), (18, 8, 0)]
-    systems2 = _systems(seed=11, specs=specs2, atoms=False)
-    _, xs = _run_batch(systems2, 2, 0.02, rsg.ETRS)
-    _, ys = _run_batch(systems2, 2, 0.02, rsg.ETRS, split_pairs=15)
-    for (p, psi, S), x, y in zip(systems2, xs, ys):
-        assert torch.equal(x, y), (p.P, S)
     systems = _systems(seed=10, specs=specs)
     batch = rsg.Batch([p.H for p, _, _ in systems], [S for _, _, S in systems])
     xs = [p.states_to_gpu(psi) for p, psi, _ in systems]
