@@ -505,7 +505,8 @@ __device__ int bs_stencil(const BStepArgs &A, int it, unsigned s_ring, unsigned 
 // c_i = h^3 sum_q p_i(q) u(q) over the sphere entries of one atom, then
 // D_i = sum_j h_a[i][j] c_j.  Thread (y, v): float4 v of the point row and
 // entry lane y of ny = NT / SV; each lane sums its entries (every ny-th) in
-// FP32, the lanes are summed in FP64 in lane order.  Shared memory (sm):
+// FP32, the lanes are summed in FP64: by warp shuffles and then over the
+// warps when SV divides 32, else in lane order.  Shared memory (sm):
 // the lane values (NP * 4 * NT doubles), the c values, and the atom's entry
 // points when they fit.
 template <int NP>
@@ -552,23 +553,47 @@ __device__ void bs_dot(const SysArgs &S, int atom, int src, unsigned char *sm) {
             for (int i = 0; i < NP; i++) V::fma(acc[i], __ldg(qp + (size_t)q * NP + i), val);
         }
     }
-#pragma unroll
-    for (int i = 0; i < NP; i++) {
-        red[(i * 4 + 0) * kBNT + tid] = acc[i].x;
-        red[(i * 4 + 1) * kBNT + tid] = acc[i].y;
-        red[(i * 4 + 2) * kBNT + tid] = acc[i].z;
-        red[(i * 4 + 3) * kBNT + tid] = acc[i].w;
-    }
-    __syncthreads();
-    // (i, comp, v): the sum over the entry lanes in lane order, times h^3,
-    // at cv[(i * 4 + comp) * SV + v]
     const int nval = NP * 4 * SV;
-    for (int idx = tid; idx < nval; idx += kBNT) {
-        const int ic = idx / SV, vv = idx - ic * SV;
-        const double *r = red + (size_t)ic * kBNT + vv;
-        double sum = 0.0;
-        for (int l = 0; l < ny; l++) sum += r[l * SV];
-        cv[idx] = S.h3 * sum;
+    if ((SV & (SV - 1)) == 0 && SV <= 32) {
+        // SV divides 32: the lanes of a warp with the same v are SV apart;
+        // warp shuffles sum them (a fixed tree), then the 16 warp sums of
+        // each (i, comp, v) are added in warp order
+        const int warp = tid >> 5, lane = tid & 31;
+        constexpr int NW = kBNT / 32;
+#pragma unroll
+        for (int i = 0; i < NP; i++) {
+            double d[4] = {acc[i].x, acc[i].y, acc[i].z, acc[i].w};
+#pragma unroll
+            for (int cmp = 0; cmp < 4; cmp++) {
+                for (int off = SV; off < 32; off <<= 1) d[cmp] += __shfl_xor_sync(0xffffffffu, d[cmp], off);
+                if (lane < SV) red[((i * 4 + cmp) * NW + warp) * SV + lane] = d[cmp];
+            }
+        }
+        __syncthreads();
+        for (int idx = tid; idx < nval; idx += kBNT) {
+            const int ic = idx / SV, vv = idx - ic * SV;
+            double sum = 0.0;
+            for (int wq = 0; wq < NW; wq++) sum += red[(ic * NW + wq) * SV + vv];
+            cv[idx] = S.h3 * sum;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; i++) {
+            red[(i * 4 + 0) * kBNT + tid] = acc[i].x;
+            red[(i * 4 + 1) * kBNT + tid] = acc[i].y;
+            red[(i * 4 + 2) * kBNT + tid] = acc[i].z;
+            red[(i * 4 + 3) * kBNT + tid] = acc[i].w;
+        }
+        __syncthreads();
+        // (i, comp, v): the sum over the entry lanes in lane order, times
+        // h^3, at cv[(i * 4 + comp) * SV + v]
+        for (int idx = tid; idx < nval; idx += kBNT) {
+            const int ic = idx / SV, vv = idx - ic * SV;
+            const double *r = red + (size_t)ic * kBNT + vv;
+            double sum = 0.0;
+            for (int l = 0; l < ny; l++) sum += r[l * SV];
+            cv[idx] = S.h3 * sum;
+        }
     }
     __syncthreads();
     float *D = (float *)S.D;
