@@ -679,7 +679,7 @@ rsg_status apply_t(rsg_ham H, const void *in, void *out, int SV, double eps, con
                  (double)H->pj.natoms * H->pj.npmax * row;
     H->n_stencil += ep.twocol ? 2 : 1;   // Hamiltonian applications (two per two-column launch)
     H->stencil_bytes += bytes;
-    H->n_launch += H->pj.natoms > 0 ? 3 : 1;
+    H->n_launch += H->pj.natoms > 0 ? 2 : 1;   // the stencil and the coefficient kernel (the scatter counts above)
     return RSG_OK;
 }
 
