@@ -2945,6 +2945,7 @@ rsg_status rsg_batch_set_option(rsg_batch b, const char *name, int64_t value) {
         b->zseg = (int)value;
     } else if (k == "wait_limit" && value >= 1) {
         b->wait_limit = (long)value;
+        if (b->cs) CK(cudaStreamSynchronize(b->cs));
         if (b->step) {
             CK(cudaGraphExecDestroy(b->step));
             b->step = nullptr;
@@ -3056,6 +3057,8 @@ rsg_status rsg_batch_autotune(rsg_batch b, void *const *psis, double dt, rsg_sch
 }
 
 rsg_status rsg_batch_destroy(rsg_batch b) {
+    // the last step graph may still run on the internal stream
+    if (b && b->cs) cudaStreamSynchronize(b->cs);
     delete b;
     return RSG_OK;
 }
