@@ -33,9 +33,9 @@
 // then one contiguous piece of the state block and moves as one bulk copy;
 // window positions outside the mesh are filled by bulk copies from a zero
 // page.  The tile shape follows the record width, so that every block has
-// the same 384 compute threads: one thread per complex value at a 2 x 2 group
-// of points.  Systems with more than 16 values per point take 16-value
-// chunks, one bulk copy per record.
+// the same 384 compute threads: one thread per complex value at two columns
+// and two rows of the tile.  Systems with more than 16 values per point take
+// 16-value chunks, one bulk copy per record.
 #include "rsg_async.cuh"
 #include "rsg_internal.h"
 #include "rsg_vec.cuh"
